@@ -1,0 +1,512 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused Gaussian-polynomial bilateral filter on one GB300.
+
+Workload (one step): a 2048 x 2048 float32 image of 64-pixel blocks with
+uniform levels in [0,255] plus N(0, 10^2) noise (seeded, synthetic), Gaussian
+spatial kernel sigma_s = 3 (W = 9), sigma_r = 30, N = 40 (the order from the
+accuracy bound for delta = 1, eq. eps + eq. LambW).  One step is the whole
+hot path: order selection (host), the fused forward (out and Q'), and the
+fused backward (image gradient and sigma_r gradient).  The headline value is
+forward+backward Mpixel/s; forward-only Mpixel/s, the direct eq. BF filter
+(forward and forward+backward) on the same image, the achieved HBM GB/s and
+the FP32-pipe roofline of the dominant kernel are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank filters its own image (weak scaling, no
+data-path collective); the barrier and the max over ranks of the timed
+region are the only collectives.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s fwd & fwd+bwd vs direct GPU BF at stated max error; HBM GB/s"
+UNIT = "Mpixel/s"
+WORKLOAD = ("2048x2048 blocks(64)+N(0,10^2) image; Gaussian spatial sigma_s=3 (W=9), "
+            "sigma_r=30, N=40 (bound for delta=1); step = fused forward + fused backward "
+            "(image and sigma_r gradients)")
+L2_NOTE = "L2 flushed between timed steps (512 MB write, outside the per-step events)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048, help="image side (profiling runs only)")
+    ap.add_argument("--kind", default="gauss", choices=["gauss", "box"])
+    ap.add_argument("--radius", type=int, default=9)
+    ap.add_argument("--sigma-s", type=float, default=3.0)
+    ap.add_argument("--sigma-r", type=float, default=30.0)
+    ap.add_argument("--order", type=int, default=0, help="N (0 = from delta = 1)")
+    ap.add_argument("--only", default="all", choices=["all", "fwd", "bwd"],
+                    help="restrict the timed step (profiling runs only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_ops(sm_count: int, mhz: float) -> float:
+    """FP32 pipe peak in lane-ops/s: SMs x 128 FP32 lanes x clock (one FMA = one op)."""
+    return sm_count * 128.0 * mhz * 1e6
+
+
+def fwd_ops_per_pixel(kind: int, R: int, N: int) -> float:
+    """Algorithmic FP32 lane-ops per output pixel of the fused forward:
+    per channel (N+1 of them) 2 (advance a_n) + filter + 3 (recombine), the
+    filter being 2(2R+1) FMAs for the separable Gaussian and 4 adds for the
+    box running sums; plus ~12 per pixel (centre, exp, ratio)."""
+    filt = 2 * (2 * R + 1) if kind == 1 else 4
+    return (N + 1) * (2 + filt + 3) + 12
+
+
+def bwd_ops_per_pixel(kind: int, R: int, N: int) -> float:
+    """Backward: per channel 2 (advance) + 3 (adjoint seed) + two filters +
+    8 (gather); plus ~20 per pixel."""
+    filt = 2 * (2 * R + 1) if kind == 1 else 4
+    return (N + 1) * (2 + 3 + 2 * filt + 8) + 20
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- CPU leg
+def cpu_baseline(img, kind, R, ss, sr, N, target_s=12.0, gpu_out=None):
+    """Time the FP64 checker (Algorithm 2 at sampled pixels + exact gradient
+    on a crop) on the host cores; report Mpixel/s of fwd+bwd work.  When
+    gpu_out is given, also return the GPU output's max error at the samples."""
+    import numpy as np
+
+    import oracle
+    w = oracle.spatial_kernel(kind, R, ss)
+    H, W = img.shape
+    rng = np.random.default_rng(11)
+    # forward: Algorithm 2 at sampled pixels; size the sample to ~target/2 seconds
+    n = 64
+    while True:
+        ys = rng.integers(0, H, n)
+        xs = rng.integers(0, W, n)
+        t0 = time.perf_counter()
+        ref = oracle.gpa_alg2_at(img, w, sr, N, (ys, xs))
+        dt_f = time.perf_counter() - t0
+        if dt_f > 0.25 * target_s or n >= 1 << 20:
+            break
+        n = int(n * min(8.0, max(2.0, 0.3 * target_s / max(dt_f, 1e-3))))
+    fwd_px_s = n / dt_f
+    err = None
+    if gpu_out is not None:
+        err = float(np.abs(gpu_out[ys, xs].astype(np.float64) - ref).max())
+    # backward: the exact gradient on a square crop sized to ~target/2 seconds
+    side = 32
+    while True:
+        crop = img[:side, :side]
+        g = np.ones_like(crop, dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.gpa_grad(crop, w, sr, N, g)
+        dt_b = time.perf_counter() - t0
+        if dt_b > 0.25 * target_s or side >= min(H, W):
+            break
+        side = min(min(H, W), int(side * min(3.0, max(1.4, math.sqrt(0.3 * target_s / max(dt_b, 1e-3))))))
+    bwd_px_s = side * side / dt_b
+    fb = 1.0 / (1.0 / fwd_px_s + 1.0 / bwd_px_s) / 1e6
+    sample = ("Algorithm 2 at %d sampled pixels (%.1f s) + exact gradient on a %dx%d crop "
+              "(%.1f s), FP64, OpenMP" % (n, dt_f, side, side, dt_b))
+    return {"value": fb, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+            "fwd_mpx_s": fwd_px_s / 1e6, "bwd_mpx_s": bwd_px_s / 1e6}, err
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1603_08109_gb300 import synth
+    kind = 1 if args.kind == "gauss" else 0
+    R, ss, sr = args.radius, args.sigma_s, args.sigma_r
+    from oracle import order
+    N = args.order or order.order_from_delta(kind, R, ss, sr, 1.0)
+    img = synth.blocks_image(args.size, args.size, 64, 10.0, seed=1000)
+    w = oracle.spatial_kernel(kind, R, ss)
+    # bounded sample per step: Algorithm 2 at 2048 pixels + exact gradient on a 48x48 crop
+    rng = np.random.default_rng(0)
+    crop = img[:48, :48]
+    g = np.ones_like(crop, dtype=np.float64)
+
+    def step():
+        ys = rng.integers(0, args.size, 2048)
+        xs = rng.integers(0, args.size, 2048)
+        t0 = time.perf_counter()
+        oracle.gpa_alg2_at(img, w, sr, N, (ys, xs))
+        t1 = time.perf_counter()
+        oracle.gpa_grad(crop, w, sr, N, g)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1
+
+    for _ in range(args.warmup):
+        step()
+    tf = tb = 0.0
+    for _ in range(args.steps):
+        a, b = step()
+        tf += a
+        tb += b
+    fwd = 2048 * args.steps / tf
+    bwd = 48 * 48 * args.steps / tb
+    value = 1.0 / (1.0 / fwd + 1.0 / bwd) / 1e6
+    sample = ("per step: Algorithm 2 at 2048 sampled pixels + exact gradient on a 48x48 crop "
+              "of the workload image, FP64 checker, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (tf + tb) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1603_08109_gb300 as bf
+    from paper_1603_08109_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    kind = bf.GAUSS if args.kind == "gauss" else bf.BOX
+    R, ss, sr = args.radius, args.sigma_s, args.sigma_r
+    S = args.size
+    t0 = time.perf_counter()
+    N = args.order or bf.order_from_delta(kind, R, ss, sr, 1.0)  # A0, host
+    order_ms = 1e3 * (time.perf_counter() - t0)
+    img_np = synth.blocks_image(S, S, 64, 10.0, seed=1000 + rank)
+    g_np = synth.random_like((S, S), seed=77 + rank)
+    x = torch.from_numpy(img_np).to(dev)
+    gout = torch.from_numpy(g_np).to(dev)
+    out = torch.empty_like(x)
+    q = torch.empty_like(x)
+    gin = torch.empty_like(x)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    p = bf._lib.make_params(kind, R, ss, sr, N)
+    import ctypes
+    lib = bf._lib.lib()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    nws = ctypes.c_size_t()
+    bf._lib.check(lib.bf_fast_backward_workspace(S, S, ctypes.byref(p), ctypes.byref(nws)), "ws")
+    ws = torch.empty(max(nws.value, 1), dtype=torch.uint8, device=dev)
+    gs = torch.zeros(1, dtype=torch.float64, device=dev)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+
+    def fwd():
+        bf._lib.check(lib.bf_fast_forward(P(x), P(out), P(q), S, S, S, ctypes.byref(p), sp), "fwd")
+
+    def bwd():
+        bf._lib.check(lib.bf_fast_backward(P(x), P(out), P(q), P(gout), P(gin), P(gs), S, S, S,
+                                           ctypes.byref(p), P(ws), nws, sp), "bwd")
+
+    launches_per = {"all": 3, "fwd": 1, "bwd": 2}[args.only]
+
+    def step(ev):
+        if args.only in ("all", "fwd"):
+            ev[0].record(stream)
+            fwd()
+            ev[1].record(stream)
+        if args.only in ("all", "bwd"):
+            if args.only == "bwd" and not hasattr(step, "primed"):
+                fwd()
+                step.primed = True
+            ev[2].record(stream)
+            bwd()
+            ev[3].record(stream)
+
+    def new_events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    for _ in range(args.warmup):
+        step(new_events())
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    if rank == 0:
+        sampler.start()
+    evs = [new_events() for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between steps (not inside the step's events)
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if rank == 0 else None
+
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs] if args.only in ("all", "fwd") else [0.0]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs] if args.only in ("all", "bwd") else [0.0]
+    step_ms = statistics.mean(fwd_ms) + statistics.mean(bwd_ms)
+    t_total = step_ms * args.steps
+    if dist:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    px = float(S) * S
+    value = px * world * args.steps / (t_total * 1e-3) / 1e6
+    fwd_mpx = px / (statistics.mean(fwd_ms) * 1e-3) / 1e6 if args.only != "bwd" else None
+
+    # ---- e2e through the public API with host buffers (pinned), copies inside the region
+    e2e = None
+    if args.only == "all":
+        hx = torch.from_numpy(img_np).pin_memory()
+        hg = torch.from_numpy(g_np).pin_memory()
+        hgin = torch.empty((S, S), dtype=torch.float32).pin_memory()
+        hgs = torch.empty(1, dtype=torch.float64).pin_memory()
+        sig = torch.tensor(sr, device=dev, requires_grad=True)
+
+        def e2e_step():
+            xd = hx.to(dev, non_blocking=True).requires_grad_(True)
+            gd = hg.to(dev, non_blocking=True)
+            o = bf.gpa_bilateral(xd, sig, kind=kind, N=N, radius=R, sigma_s=ss)
+            o.backward(gd)
+            hgin.copy_(xd.grad, non_blocking=True)
+            hgs.copy_(sig.grad.double().reshape(1), non_blocking=True)
+            sig.grad = None
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        ne = max(10, min(args.steps, 100))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ne):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1) / ne
+        e2e = {"value": px / (ems * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.numel() * 4 + hg.numel() * 4),
+               "d2h_bytes_per_step": int(hgin.numel() * 4 + 8),
+               "ms_per_step": ems, "api": "paper_1603_08109_gb300.gpa_bilateral + backward"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- direct filter on the same image (same-GPU comparison)
+    direct = None
+    if not args.no_direct and args.only == "all":
+        pd = bf._lib.make_params(kind, R, ss, sr, 1)
+        dws_n = ctypes.c_size_t()
+        bf._lib.check(lib.bf_direct_backward_workspace(S, S, ctypes.byref(pd), ctypes.byref(dws_n)),
+                      "dws")
+        dws = torch.empty(dws_n.value, dtype=torch.uint8, device=dev)
+        dout = torch.empty_like(x)
+        dgin = torch.empty_like(x)
+        dgs = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def dfwd():
+            bf._lib.check(lib.bf_direct(P(x), P(dout), S, S, S, ctypes.byref(pd), sp), "direct")
+
+        def dbwd():
+            bf._lib.check(lib.bf_direct_backward(P(x), P(gout), P(dgin), P(dgs), S, S, S,
+                                                 ctypes.byref(pd), P(dws), dws_n, sp), "dbwd")
+        for _ in range(2):
+            dfwd()
+            dbwd()
+        nd = 10
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nd)]
+        for k in range(nd):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            dfwd()
+            ev[k][1].record(stream)
+            dbwd()
+            ev[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+        dfm = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+        dbm = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+        fwd()
+        torch.cuda.synchronize(dev)
+        diff = (out.double() - dout.double())
+        direct = {"fwd_mpx_s": px / (dfm * 1e-3) / 1e6, "fwd_bwd_mpx_s": px / ((dfm + dbm) * 1e-3) / 1e6,
+                  "fwd_ms": dfm, "bwd_ms": dbm,
+                  "fast_vs_direct_max_abs": float(diff.abs().max()),
+                  "fast_vs_direct_mse_db": float(10 * math.log10(max(float((diff ** 2).mean()), 1e-300)))}
+
+    # ---- roofline of the dominant kernel (FP32 pipe), live CUDA-event timing
+    pk, pk_src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fpeak = fp32_peak_ops(props.multi_processor_count, sm_max)
+    fo = fwd_ops_per_pixel(kind, R, N) * px
+    bo = bwd_ops_per_pixel(kind, R, N) * px
+    mf = statistics.mean(fwd_ms) if args.only != "bwd" else None
+    mb = statistics.mean(bwd_ms) if args.only != "fwd" else None
+    cand = []
+    if mf:
+        cand.append(("gpa_fwd_kernel", mf, fo))
+    if mb:
+        cand.append(("gpa_bwd_kernel", mb, bo))
+    name, ms, ops = max(cand, key=lambda c: c[1])
+    achieved = ops / (ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        ent = tj.get(name)
+        if ent and ent.get("size") == S and ent.get("N") == N and ent.get("radius") == R:
+            traffic = ent.get("bytes")
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": fpeak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved * 1e12 / fpeak, "traffic": traffic,
+                "peak_src": "FP32 pipe: %d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz); one FMA = "
+                            "one op" % (props.multi_processor_count, sm_max, pk_src),
+                "ops_per_launch": ops}
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    fwd_bytes = px * 12.0  # read f, write out and Q'
+    hbm = None
+    if mf:
+        gbs = fwd_bytes / (mf * 1e-3) / 1e9
+        hbm = {"fwd_algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
+               "peak_gbs": hbm_peak, "peak_src": pk_src}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1 and args.only == "all":
+        fwd()
+        torch.cuda.synchronize(dev)
+        cpu, err = cpu_baseline(img_np, kind, R, ss, sr, N, gpu_out=out.cpu().numpy())
+        cpu["gpu_max_abs_err_at_samples"] = err
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "image": "%dx%d" % (S, S),
+                       "kind": "gaussian" if kind == 1 else "box", "radius": R, "sigma_s": ss,
+                       "sigma_r": sr, "N": N, "only": args.only, "l2": L2_NOTE,
+                       "parallelism": "dp%d (one image per rank)" % world},
+            "fwd_mpx_s": fwd_mpx, "fwd_ms": mf, "bwd_ms": mb, "order_selection_ms": order_ms,
+            "direct": direct, "hbm": hbm, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": launches_per * args.steps, "roofline": roofline,
+            "cpu_baseline": cpu, "wall_s_timed_region": wall}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

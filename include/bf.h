@@ -1,0 +1,250 @@
+/*
+ * bf.h -- C ABI of the GB300 (sm_103a) Gaussian-polynomial bilateral filter.
+ *
+ * Method: K. N. Chaudhury and S. D. Dabhade, "Fast and Provably Accurate
+ * Bilateral Filtering", arXiv 1603.08109.  The bilateral filter (eq. BF) with
+ * a Gaussian range kernel (eq. range_kernel) and a box (eq. spatial_kernel2)
+ * or Gaussian (eq. spatial_kernel1) spatial kernel on Omega = [-W, W]^2 is
+ * approximated by replacing each translated range kernel with the
+ * Gaussian-polynomial phi_N of eq. GaussPolynomial (eq. GPA).  With centred
+ * intensities h = f - t_c (eq. shift) and H = h / sigma_r the result is
+ *      f_GPA = t_c + sigma_r * P' / Q',
+ *      Q' = sum_{n<N} a_n (w * a_n),   P' = sum_{n<N} sqrt(n+1) a_n (w * a_{n+1}),
+ *      a_n = exp(-H^2/2) H^n / sqrt(n!),
+ * which is eqs. PbyQ, P, Q of Sec. III-A (Algorithm 2) with every auxiliary
+ * image divided by sqrt(n!) and the common factor exp(-H^2/2) of P and Q
+ * cancelled (an exact rescaling; it keeps every intermediate in [-1, 1]).
+ *
+ * Conventions shared by every entry point:
+ *  - Images are single-channel float32, row-major, `height` rows of `width`
+ *    pixels, consecutive rows `pitch` elements apart (pitch >= width).
+ *    Intensities are expected in [0, 2 t_c] (8-bit data: t_c = 128).
+ *  - The image domain is finite (Sec. I): every spatial sum runs over the
+ *    neighbours that lie inside the image only, without renormalisation
+ *    (w cancels in the ratio).  This is the same as zero-extending the
+ *    power images before filtering.
+ *  - `d_*` pointers are device pointers; the caller owns all device memory.
+ *    The library never allocates device memory and never synchronises the
+ *    stream: every GPU entry point only enqueues work on `stream` (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream).
+ *  - float arrays must be 4-byte aligned; inputs and outputs may not alias.
+ *  - Errors are returned, never raised: nothing traps or aborts.  A CUDA
+ *    launch error is reported as BF_ERR_CUDA (the CUDA error string is
+ *    available from bf_last_cuda_error()).
+ */
+#ifndef BF_GB300_H
+#define BF_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,  /* a size, pointer or parameter is out of range  */
+    BF_ERR_CUDA = 2,         /* a CUDA runtime call or launch failed          */
+    BF_ERR_UNSUPPORTED = 3,  /* valid, but beyond this build's limits         */
+    BF_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up            */
+    BF_ERR_WORKSPACE = 5,    /* workspace missing or smaller than required    */
+    BF_ERR_NONFINITE = 6     /* reserved: non-finite result reported by a check */
+} bf_status;
+
+typedef enum {
+    BF_SPATIAL_BOX = 0,      /* eq. spatial_kernel2: w = 1/|Omega|            */
+    BF_SPATIAL_GAUSS = 1     /* eq. spatial_kernel1: w = exp(-|j|^2 / 2 s^2)  */
+} bf_spatial_kind;
+
+/* Filter parameters (Sec. I, Sec. III).
+ *  kind     bf_spatial_kind.
+ *  radius   W, the half-width of Omega = [-W, W]^2 (support 2W+1 per axis).
+ *           For the Gaussian, radius <= 0 selects W = ceil(3 sigma_s) (Sec. I).
+ *  sigma_s  Gaussian spatial standard deviation (ignored for the box).
+ *  sigma_r  range standard deviation, > 0.  Because the rescaled power images
+ *           start from exp(-H^2/2) in float32, |f - t_c| / sigma_r must stay
+ *           below 13 (sigma_r >= 9.85 for 8-bit data); smaller sigma_r is
+ *           rejected with BF_ERR_UNSUPPORTED.
+ *  order_N  N, the number of Taylor terms of eq. approx (1 <= N <= BF_MAX_ORDER);
+ *           the method performs N + 1 spatial filterings (Algorithm 2).
+ *  t_c      centre of the intensity range (eq. shift); 128 for 8-bit data.   */
+typedef struct {
+    int kind;
+    int radius;
+    float sigma_s;
+    float sigma_r;
+    int order_N;
+    float t_c;
+} bf_params;
+
+#define BF_MAX_ORDER 1024
+#define BF_MAX_RADIUS 96
+
+/* ------------------------------------------------------------------ misc */
+const char *bf_status_string(int status);
+/* Message of the last CUDA error seen by this library in this thread. */
+const char *bf_last_cuda_error(void);
+/* Library version, as major * 10000 + minor * 100 + patch. */
+int bf_version(void);
+
+/* --------------------------------------------------- order selection (host)
+ * Centre weight w(0) of the normalised spatial kernel (eq. normal):
+ * 1/(2W+1)^2 for the box, 1/(sum_k exp(-k^2/2 sigma_s^2))^2 for the
+ * Gaussian on [-W, W]^2.  Host only; no GPU work. */
+bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out);
+
+/* Order N for a filter accuracy delta (Sec. III-C): eps from eq. eps,
+ * eps = w(0) delta / (2T + delta), then N = ceil(theta) where theta is the
+ * root above lambda = T^2/sigma_r^2 of nu(x) = x log x - p x - q
+ * (App. A; p = 1 + log lambda, q = -lambda - log eps), i.e. eq. LambW.
+ * The root is bracketed and refined by safeguarded Newton steps
+ * (eq. Newton_method).  T is the half dynamic range (128 for 8-bit data).
+ * BF_ERR_INVALID_ARG if delta <= 0, T <= 0, sigma_r <= 0 or radius < 0;
+ * BF_ERR_UNSUPPORTED if the order exceeds BF_MAX_ORDER.  Host only. */
+bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r,
+                              float delta, float T, int *N_out);
+
+/* ---------------------------------------------------------- fast forward
+ * f_GPA of eq. GPA via Algorithm 2 (eqs. intImg, spatialFiltering, PbyQ,
+ * P, Q), fused: each output tile reads its input tile plus a W-pixel halo
+ * once, generates the N+1 power images a_0..a_N in on-chip memory, filters
+ * them and accumulates P', Q' in registers.
+ *  d_in    input image (height x width, pitch elements per row).
+ *  d_out   output image, same layout as d_in.
+ *  d_qaux  optional (NULL allowed): receives Q' at every pixel, normalised
+ *          as sum_j w(j) phi_N(h(i-j), h(i)) with sum_Omega w = 1 (this is
+ *          Q_2 of App. C).  Needed by bf_fast_backward.
+ * BF_ERR_INVALID_ARG for null in/out, height or width < 1, pitch < width,
+ * or invalid params. */
+bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
+                          int height, int width, int pitch,
+                          const bf_params *p, void *stream);
+
+/* Same as bf_fast_forward, and also stores the N+1 filtered power images
+ * w * a_n (normalised kernel) to d_abar: plane n at d_abar + n * plane_stride,
+ * each plane height x width with row pitch `pitch`; plane_stride >=
+ * height * pitch.  For the stored-power-image backward. */
+bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux,
+                                 float *d_abar, size_t plane_stride,
+                                 int height, int width, int pitch,
+                                 const bf_params *p, void *stream);
+
+/* --------------------------------------------------------- fast backward
+ * Gradient of a loss L through f_GPA with respect to the input image and
+ * sigma_r (N and W held fixed), given gout = dL/d f_GPA.  The paper has no
+ * backward pass; this is the exact adjoint of the rescaled P'/Q' ratio:
+ *   pbar = gout sigma_r / Q',  qbar = -gout (out - t_c) / Q',
+ *   abar_n = qbar (w*a_n) [n<N] + pbar sqrt(n+1) (w*a_{n+1}) [n<N]
+ *            + w * (qbar a_n [n<N] + pbar sqrt(n) a_{n-1} [n>=1]),
+ *   Hbar = sum_n abar_n (sqrt(n) a_{n-1} - H a_n),  gin = Hbar / sigma_r,
+ *   gsigma = sum_i gout (out - t_c) / sigma_r - sum_i Hbar H / sigma_r.
+ * The power images are recomputed (not stored).
+ *  d_in, d_out, d_qaux  the forward's input, output and Q' (from the same params).
+ *  d_gout               dL/d out.           d_gin: dL/d in (written).
+ *  d_gsigma             optional: one double on the device, written (not added).
+ *  d_workspace          >= bf_fast_backward_workspace() bytes (may be NULL
+ *                       only if d_gsigma is NULL).  The sigma_r sum is reduced
+ *                       deterministically in a fixed order.
+ * BF_ERR_WORKSPACE if the workspace is missing or too small. */
+bf_status bf_fast_backward_workspace(int height, int width, const bf_params *p,
+                                     size_t *bytes);
+bf_status bf_fast_backward(const float *d_in, const float *d_out, const float *d_qaux,
+                           const float *d_gout, float *d_gin, double *d_gsigma,
+                           int height, int width, int pitch, const bf_params *p,
+                           void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Same gradient, reading the N+1 filtered power images written by
+ * bf_fast_forward_stored instead of recomputing them (only the adjoint
+ * channels are filtered).  Same workspace rule. */
+bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const float *d_qaux,
+                                  const float *d_abar, size_t plane_stride,
+                                  const float *d_gout, float *d_gin, double *d_gsigma,
+                                  int height, int width, int pitch, const bf_params *p,
+                                  void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------ direct filter
+ * eq. BF computed directly, O((2W+1)^2) exponentials per pixel (Sec. I-A),
+ * float32 accumulation; order_N is ignored.  The same-GPU comparison. */
+bf_status bf_direct(const float *d_in, float *d_out, int height, int width, int pitch,
+                    const bf_params *p, void *stream);
+
+/* Gradient of eq. BF with respect to the image and sigma_r (the paper has
+ * none; exact chain rule on the ratio, gather form).  Workspace: >=
+ * bf_direct_backward_workspace() bytes, always required (per-pixel
+ * denominators and partial sums). */
+bf_status bf_direct_backward_workspace(int height, int width, const bf_params *p,
+                                       size_t *bytes);
+bf_status bf_direct_backward(const float *d_in, const float *d_gout, float *d_gin,
+                             double *d_gsigma, int height, int width, int pitch,
+                             const bf_params *p, void *d_workspace,
+                             size_t workspace_bytes, void *stream);
+
+/* --------------------------------------------------- batched forward
+ * Many images of uneven sizes, each with its own spatial kind, W, sigma_s,
+ * sigma_r and N, filtered by ONE persistent launch: CTAs take output tiles
+ * from a device work queue (longest work first) until it is empty.
+ * Usage: bf_batch_plan_create (host: validates, picks tile shapes, orders
+ * the work) -> bf_batch_workspace -> bf_batch_upload (enqueue the plan's
+ * tables into the workspace; the plan must stay alive until that copy has
+ * completed) -> bf_batch_forward, any number of times (graph-capturable: a
+ * memset node and one kernel node; no allocation, no host synchronisation)
+ * -> bf_batch_plan_destroy. */
+typedef struct {
+    const float *d_in;   /* device input image                    */
+    float *d_out;        /* device output image                   */
+    float *d_qaux;       /* optional Q' output (NULL = none)       */
+    int height, width, pitch;
+    bf_params params;
+} bf_image_desc;
+
+typedef struct bf_batch_plan bf_batch_plan;
+
+bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_plan **plan);
+bf_status bf_batch_workspace(const bf_batch_plan *plan, size_t *bytes);
+/* Number of work items (tiles) and CTAs the plan launches. */
+bf_status bf_batch_info(const bf_batch_plan *plan, int *items, int *ctas);
+bf_status bf_batch_upload(const bf_batch_plan *plan, void *d_workspace,
+                          size_t workspace_bytes, void *stream);
+/* d_status (optional, device int): set to BF_ERR_INVALID_ARG by the kernel
+ * if a work item names a descriptor outside the plan; left unchanged
+ * otherwise.  CTAs never wait on one another (work is taken with one atomic
+ * add per item), so the launch has no device-side wait to time out. */
+bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_workspace,
+                           size_t workspace_bytes, int *d_status, void *stream);
+void bf_batch_plan_destroy(bf_batch_plan *plan);
+
+/* Capture bf_batch_forward into a CUDA graph on `stream` and instantiate
+ * it; bf_graph_launch replays it; bf_graph_destroy frees it. */
+bf_status bf_batch_graph_create(const bf_batch_plan *plan, void *d_workspace,
+                                size_t workspace_bytes, int *d_status, void *stream,
+                                void **graph_exec_out);
+bf_status bf_graph_launch(void *graph_exec, void *stream);
+void bf_graph_destroy(void *graph_exec);
+
+/* ---------------------------------------------------- tile autotuning
+ * The fused kernels come in several tile shapes (variants).  The library
+ * keeps a table variant[kind][radius bucket][order bucket]; the defaults
+ * are compiled in, bf_autotune times every variant on caller-provided
+ * device buffers (it synchronises `stream`) and records the fastest.
+ *  bf_variant_count        number of variants for a kind (>= 1).
+ *  bf_fast_forward_variant forward with an explicit variant (-1 = table).
+ *  bf_autotune             time all variants for (kind, W, N) at this size;
+ *                          writes the winner to *best and into the table.
+ *  bf_tuning_get/set       read / write one table entry (for a JSON cache). */
+int bf_variant_count(int kind);
+bf_status bf_fast_forward_variant(const float *d_in, float *d_out, float *d_qaux,
+                                  int height, int width, int pitch, const bf_params *p,
+                                  int variant, void *stream);
+bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, int pitch,
+                      const bf_params *p, int reps, void *stream, int *best,
+                      float *best_ms);
+int bf_tuning_radius_bucket(int radius);
+int bf_tuning_order_bucket(int order_N);
+bf_status bf_tuning_get(int kind, int radius_bucket, int order_bucket, int *variant);
+bf_status bf_tuning_set(int kind, int radius_bucket, int order_bucket, int variant);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_GB300_H */

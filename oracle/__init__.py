@@ -60,7 +60,8 @@ def _load():
                                               ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                               ctypes.c_double, dp, ip, ip, ctypes.c_long, dp, dp]
         lib.orc_gpa_alg2.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
-                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp]
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp,
+                                     dp]
         lib.orc_gpa_alg2_at.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_double, ip, ip,
                                         ctypes.c_long, dp, dp, dp]
@@ -142,18 +143,23 @@ def gpa_definition(img, w, sigma_r, N, T=128.0, samples=None, return_parts=False
     return (out, num, den) if return_parts else out
 
 
-def gpa_alg2(img, w, sigma_r, N, T=128.0, return_parts=False):
-    """Algorithm 2 over the whole image; parts are eq. P and eq. Q."""
+def gpa_alg2(img, w, sigma_r, N, T=128.0, return_parts=False, return_planes=False):
+    """Algorithm 2 over the whole image; parts are eq. P and eq. Q; planes
+    are the N + 1 filtered images Fbar_n = F_n * w of eq. spatialFiltering."""
     f = _f64(img)
     H, W = f.shape
     r = (w.shape[0] - 1) // 2
     out = np.empty((H, W))
     P = np.empty((H, W))
     Q = np.empty((H, W))
+    planes = np.empty((N + 1, H, W)) if return_planes else None
     rc = _load().orc_gpa_alg2(_dp(f), H, W, _dp(np.ascontiguousarray(w)), r, float(sigma_r),
-                              int(N), float(T), _dp(out), _dp(P), _dp(Q))
+                              int(N), float(T), _dp(out), _dp(P), _dp(Q), _dp(planes))
     _check(rc, "gpa_alg2")
-    return (out, P, Q) if return_parts else out
+    res = (out, P, Q) if return_parts else (out,)
+    if return_planes:
+        res = res + (planes,)
+    return res if len(res) > 1 else res[0]
 
 
 def gpa_alg2_at(img, w, sigma_r, N, samples, T=128.0, return_parts=False):

@@ -301,9 +301,10 @@ static void filter2d(const double *F, int H, int W, const double *w, int r, doub
 
 /* Algorithm 2 over the whole image. P and Q (may be NULL) receive the
  * algorithm's P and Q images (P includes the factor sigma_r of the final
- * step, i.e. out = P / Q + T). */
+ * step, i.e. out = P / Q + T).  Fbar_planes (may be NULL) receives the N + 1
+ * filtered images Fbar_n = F_n * w, n = 0..N, as consecutive H x W planes. */
 int orc_gpa_alg2(const double *f, int H, int W, const double *w, int r, double sr, int N,
-                 double T, double *out, double *Pout, double *Qout)
+                 double T, double *out, double *Pout, double *Qout, double *Fbar_planes)
 {
     if (!f || !w || !out || H < 1 || W < 1 || r < 0 || !(sr > 0.0) || N < 1) return ORC_BAD_ARG;
     long npix = (long)H * W;
@@ -324,12 +325,14 @@ int orc_gpa_alg2(const double *f, int H, int W, const double *w, int r, double s
         Hs[i] = h / sr;
     }
     filter2d(F, H, W, w, r, Fbar);
+    if (Fbar_planes) memcpy(Fbar_planes, Fbar, bytes);
     for (int n = 1; n <= N; ++n) {
         for (long i = 0; i < npix; ++i) {
             Q[i] = Q[i] + G[i] * Fbar[i];
             F[i] = Hs[i] * F[i];
         }
         filter2d(F, H, W, w, r, Fbar);
+        if (Fbar_planes) memcpy(Fbar_planes + (long)n * npix, Fbar, bytes);
         for (long i = 0; i < npix; ++i) {
             P[i] = P[i] + G[i] * Fbar[i];
             G[i] = Hs[i] * G[i] / (double)n;

@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) Gaussian-polynomial bilateral filter.
+
+Chaudhury & Dabhade, "Fast and Provably Accurate Bilateral Filtering"
+(arXiv 1603.08109): the bilateral filter with a Gaussian range kernel and a
+box or Gaussian spatial kernel, approximated to order N by N + 1 spatial
+filterings of power images (Algorithm 2), as hand-written CUDA kernels
+behind the C ABI in include/bf.h.  This package is the thin Python layer:
+``api`` (PyTorch tensors in, library calls out), ``_lib`` (ctypes
+signatures), ``build`` (nvcc), ``synth`` (seeded synthetic inputs).
+"""
+from .api import (BOX, GAUSS, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
+                  centre_weight, direct, direct_backward, direct_bilateral, gpa_backward,
+                  gpa_bilateral, gpa_forward, gpa_forward_stored, order_bucket, order_from_delta,
+                  radius_bucket, resolve_radius, tuning_get, tuning_set, variant_count)
+
+__version__ = "1.0.0"

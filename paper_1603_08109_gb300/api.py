@@ -1,0 +1,383 @@
+"""PyTorch-facing wrappers of the C ABI (include/bf.h).
+
+PyTorch supplies device memory and the current CUDA stream; every filter
+step runs inside libbf_gb300.so.  Inputs may be CUDA tensors (no copies) or
+CPU tensors (copied to the GPU and back around the library call).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Optional
+
+import torch
+
+from . import _lib
+from ._lib import BOX, GAUSS, check, lib, make_params
+
+__all__ = [
+    "BOX", "GAUSS", "resolve_radius", "centre_weight", "order_from_delta", "gpa_forward",
+    "gpa_forward_stored", "gpa_backward", "direct", "direct_backward", "GPABilateral",
+    "DirectBilateral", "gpa_bilateral", "direct_bilateral", "BatchPlan", "autotune",
+    "variant_count", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
+]
+
+
+def resolve_radius(kind: int, radius: int, sigma_s: float) -> int:
+    """W = ceil(3 sigma_s) for the Gaussian when radius <= 0 (Sec. I)."""
+    if kind == GAUSS and radius <= 0:
+        return int(math.ceil(3.0 * float(sigma_s) - 1e-9))
+    return int(radius)
+
+
+def centre_weight(kind: int, radius: int, sigma_s: float = 0.0) -> float:
+    out = ctypes.c_double()
+    check(lib().bf_centre_weight(int(kind), int(radius), float(sigma_s), ctypes.byref(out)),
+          "bf_centre_weight")
+    return out.value
+
+
+def order_from_delta(kind: int, radius: int, sigma_s: float, sigma_r: float, delta: float = 1.0,
+                     T: float = 128.0) -> int:
+    """Order N for filter accuracy delta (eq. eps + eq. LambW), host only."""
+    n = ctypes.c_int()
+    check(lib().bf_order_from_delta(int(kind), int(radius), float(sigma_s), float(sigma_r),
+                                    float(delta), float(T), ctypes.byref(n)), "bf_order_from_delta")
+    return n.value
+
+
+def _stream(dev: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[ctypes.c_void_p]:
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _as_device_image(img: torch.Tensor):
+    """Return (device tensor with unit column stride, was_on_cpu)."""
+    if not isinstance(img, torch.Tensor) or img.dim() != 2:
+        raise ValueError("expected a 2-D tensor (height x width)")
+    if img.dtype != torch.float32:
+        raise ValueError("expected float32 input")
+    on_cpu = img.device.type == "cpu"
+    if on_cpu:
+        src = img if img.is_pinned() or not torch.cuda.is_available() else img
+        img = src.to("cuda", non_blocking=src.is_pinned())
+    if img.device.type != "cuda":
+        raise ValueError("expected a CUDA or CPU tensor")
+    if img.stride(1) != 1 or img.stride(0) < img.shape[1] or img.storage_offset() % 1:
+        img = img.contiguous()
+    return img, on_cpu
+
+
+def _image_like(img: torch.Tensor, out: Optional[torch.Tensor]) -> torch.Tensor:
+    """Output with the input's row pitch (the ABI takes one pitch for both)."""
+    if out is None:
+        return torch.empty_strided(img.shape, img.stride(), dtype=img.dtype, device=img.device)
+    if out.shape != img.shape or out.dtype != torch.float32 or out.device != img.device \
+            or out.stride() != img.stride():
+        raise ValueError("out must match the input's shape, dtype, device and strides")
+    return out
+
+
+def _like(x: torch.Tensor) -> torch.Tensor:
+    return torch.empty_strided(x.shape, x.stride(), dtype=x.dtype, device=x.device)
+
+
+def _params(kind, radius, sigma_s, sigma_r, N, t_c):
+    return make_params(kind, radius, sigma_s, float(sigma_r), N, t_c)
+
+
+def gpa_forward(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
+                sigma_s: float = 0.0, t_c: float = 128.0, return_q: bool = False,
+                out: Optional[torch.Tensor] = None, variant: int = -1):
+    """f_GPA of eq. GPA (Algorithm 2, fused).  Returns out, or (out, Q')."""
+    x, on_cpu = _as_device_image(img)
+    o = _image_like(x, out if not on_cpu else None)
+    q = _like(x) if return_q else None
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    H, W = x.shape
+    st = lib().bf_fast_forward_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                       ctypes.byref(p), int(variant), _stream(x.device))
+    check(st, "bf_fast_forward")
+    if on_cpu:
+        o = o.cpu()
+        q = q.cpu() if q is not None else None
+    return (o, q) if return_q else o
+
+
+def gpa_forward_stored(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
+                       sigma_s: float = 0.0, t_c: float = 128.0):
+    """Forward that also keeps the N+1 filtered power images: (out, Q', Abar)."""
+    x, _ = _as_device_image(img)
+    o = _like(x)
+    q = _like(x)
+    H, W = x.shape
+    abar = torch.empty((N + 1, H, x.stride(0)), dtype=torch.float32, device=x.device)
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    st = lib().bf_fast_forward_stored(_ptr(x), _ptr(o), _ptr(q), _ptr(abar),
+                                      ctypes.c_size_t(H * x.stride(0)), H, W, x.stride(0),
+                                      ctypes.byref(p), _stream(x.device))
+    check(st, "bf_fast_forward_stored")
+    return o, q, abar[:, :, :W]
+
+
+def _workspace(fn_name, H, W, p, dev):
+    n = ctypes.c_size_t()
+    check(getattr(lib(), fn_name)(H, W, ctypes.byref(p), ctypes.byref(n)), fn_name)
+    return torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=dev), int(n.value)
+
+
+def gpa_backward(img, out, q, gout, kind: int, sigma_r: float, N: int, radius: int = 0,
+                 sigma_s: float = 0.0, t_c: float = 128.0, need_sigma: bool = True,
+                 abar: Optional[torch.Tensor] = None):
+    """(dL/d img, dL/d sigma_r or None) of the fast filter, given gout."""
+    x, _ = _as_device_image(img)
+    H, W = x.shape
+    tensors = []
+    for t in (out, q, gout):
+        if t.shape != x.shape or t.device != x.device or t.dtype != torch.float32:
+            raise ValueError("out, q, gout must match the image")
+        tensors.append(t)
+    if abar is None and any(t.stride() != x.stride() for t in tensors):
+        x = x.contiguous()
+        tensors = [t.contiguous() for t in tensors]
+    elif abar is not None and any(t.stride() != x.stride() for t in tensors):
+        raise ValueError("with stored planes, out, q and gout must share the image's layout")
+    pitch = x.stride(0)
+    o, qq, g = tensors
+    gin = _like(x)
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    gs = torch.zeros(1, dtype=torch.float64, device=x.device) if need_sigma else None
+    ws, nbytes = _workspace("bf_fast_backward_workspace", H, W, p, x.device)
+    if abar is None:
+        st = lib().bf_fast_backward(_ptr(x), _ptr(o), _ptr(qq), _ptr(g), _ptr(gin), _ptr(gs),
+                                    H, W, pitch, ctypes.byref(p), _ptr(ws), ctypes.c_size_t(nbytes),
+                                    _stream(x.device))
+        check(st, "bf_fast_backward")
+    else:
+        if abar.dim() != 3 or abar.shape[0] != N + 1 or abar.stride(2) != 1 \
+                or abar.stride(1) != pitch:
+            raise ValueError("abar must come from gpa_forward_stored on this image")
+        st = lib().bf_fast_backward_stored(_ptr(x), _ptr(o), _ptr(qq), _ptr(abar),
+                                           ctypes.c_size_t(abar.stride(0)), _ptr(g), _ptr(gin),
+                                           _ptr(gs), H, W, pitch, ctypes.byref(p), _ptr(ws),
+                                           ctypes.c_size_t(nbytes), _stream(x.device))
+        check(st, "bf_fast_backward_stored")
+    return gin, gs
+
+
+def direct(img: torch.Tensor, kind: int, sigma_r: float, radius: int = 0, sigma_s: float = 0.0,
+           t_c: float = 128.0, out: Optional[torch.Tensor] = None):
+    """eq. BF computed directly (the O(W^2) comparison filter)."""
+    x, on_cpu = _as_device_image(img)
+    o = _image_like(x, out if not on_cpu else None)
+    p = _params(kind, radius, sigma_s, sigma_r, 1, t_c)
+    H, W = x.shape
+    check(lib().bf_direct(_ptr(x), _ptr(o), H, W, x.stride(0), ctypes.byref(p), _stream(x.device)),
+          "bf_direct")
+    return o.cpu() if on_cpu else o
+
+
+def direct_backward(img, gout, kind: int, sigma_r: float, radius: int = 0, sigma_s: float = 0.0,
+                    t_c: float = 128.0, need_sigma: bool = True):
+    x, _ = _as_device_image(img)
+    H, W = x.shape
+    g = gout
+    if g.stride() != x.stride():
+        x, g = x.contiguous(), g.contiguous()
+    gin = _like(x)
+    p = _params(kind, radius, sigma_s, sigma_r, 1, t_c)
+    gs = torch.zeros(1, dtype=torch.float64, device=x.device) if need_sigma else None
+    ws, nbytes = _workspace("bf_direct_backward_workspace", H, W, p, x.device)
+    st = lib().bf_direct_backward(_ptr(x), _ptr(g), _ptr(gin), _ptr(gs), H, W, x.stride(0),
+                                  ctypes.byref(p), _ptr(ws), ctypes.c_size_t(nbytes),
+                                  _stream(x.device))
+    check(st, "bf_direct_backward")
+    return gin, gs
+
+
+# ------------------------------------------------------------------ autograd
+def _sigma_value(sigma_r) -> float:
+    return float(sigma_r.detach().item()) if isinstance(sigma_r, torch.Tensor) else float(sigma_r)
+
+
+class GPABilateral(torch.autograd.Function):
+    """Autograd wrapper: forward = bf_fast_forward, backward = bf_fast_backward
+    (power images recomputed) or bf_fast_backward_stored (store=True)."""
+
+    @staticmethod
+    def forward(ctx, img, sigma_r, kind, N, radius, sigma_s, t_c, store):
+        sr = _sigma_value(sigma_r)
+        if store:
+            out, q, abar = gpa_forward_stored(img, kind, sr, N, radius, sigma_s, t_c)
+        else:
+            out, q = gpa_forward(img, kind, sr, N, radius, sigma_s, t_c, return_q=True)
+            abar = None
+        ctx.cfg = (kind, sr, N, radius, sigma_s, t_c)
+        ctx.abar = abar
+        ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
+        ctx.save_for_backward(img, out, q)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        img, out, q = ctx.saved_tensors
+        kind, sr, N, radius, sigma_s, t_c = ctx.cfg
+        need_s = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
+        gin, gs = gpa_backward(img, out, q, gout.contiguous(), kind, sr, N, radius, sigma_s, t_c,
+                               need_sigma=need_s, abar=ctx.abar)
+        gsig = gs.reshape(()).to(torch.float32) if need_s else None
+        return gin, gsig, None, None, None, None, None, None
+
+
+class DirectBilateral(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, sigma_r, kind, radius, sigma_s, t_c):
+        sr = _sigma_value(sigma_r)
+        out = direct(img, kind, sr, radius, sigma_s, t_c)
+        ctx.cfg = (kind, sr, radius, sigma_s, t_c)
+        ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
+        ctx.save_for_backward(img)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        (img,) = ctx.saved_tensors
+        kind, sr, radius, sigma_s, t_c = ctx.cfg
+        need_s = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
+        gin, gs = direct_backward(img, gout.contiguous(), kind, sr, radius, sigma_s, t_c, need_s)
+        gsig = gs.reshape(()).to(torch.float32) if need_s else None
+        return gin, gsig, None, None, None, None
+
+
+def gpa_bilateral(img, sigma_r, kind=GAUSS, N=None, radius=0, sigma_s=0.0, t_c=128.0,
+                  delta=1.0, store=False):
+    """Differentiable fast bilateral filter; N from delta when not given."""
+    r = resolve_radius(kind, radius, sigma_s)
+    if N is None:
+        N = order_from_delta(kind, r, sigma_s, _sigma_value(sigma_r), delta, t_c)
+    return GPABilateral.apply(img, sigma_r, kind, int(N), r, float(sigma_s), float(t_c),
+                              bool(store))
+
+
+def direct_bilateral(img, sigma_r, kind=GAUSS, radius=0, sigma_s=0.0, t_c=128.0):
+    r = resolve_radius(kind, radius, sigma_s)
+    return DirectBilateral.apply(img, sigma_r, kind, r, float(sigma_s), float(t_c))
+
+
+# ------------------------------------------------------------------ batched
+class BatchPlan:
+    """Persistent batched forward over images of uneven sizes and parameters.
+
+    specs: list of dicts with kind, radius, sigma_s, sigma_r, N (t_c optional).
+    The plan owns its workspace; run() enqueues one memset + one kernel,
+    graph() captures that pair into a CUDA graph for replay."""
+
+    def __init__(self, images, outs, specs, qaux=None):
+        if not (len(images) == len(outs) == len(specs)) or not images:
+            raise ValueError("images, outs and specs must be non-empty lists of equal length")
+        self.device = images[0].device
+        self.images, self.outs, self.qaux = images, outs, qaux
+        descs = (_lib.BfImageDesc * len(images))()
+        for k, (x, o, sp) in enumerate(zip(images, outs, specs)):
+            if x.device != self.device or x.dtype != torch.float32 or x.stride(1) != 1:
+                raise ValueError("image %d must be a float32 CUDA tensor with unit column stride" % k)
+            if o.shape != x.shape or o.stride() != x.stride():
+                raise ValueError("output %d must match its image" % k)
+            q = qaux[k] if qaux is not None else None
+            p = _params(sp["kind"], sp.get("radius", 0), sp.get("sigma_s", 0.0), sp["sigma_r"],
+                        sp["N"], sp.get("t_c", 128.0))
+            descs[k] = _lib.BfImageDesc(x.data_ptr(), o.data_ptr(), q.data_ptr() if q is not None
+                                        else None, x.shape[0], x.shape[1], x.stride(0), p)
+        self._descs = descs
+        plan = ctypes.c_void_p()
+        check(lib().bf_batch_plan_create(descs, len(images), ctypes.byref(plan)),
+              "bf_batch_plan_create")
+        self._plan = plan
+        n = ctypes.c_size_t()
+        check(lib().bf_batch_workspace(plan, ctypes.byref(n)), "bf_batch_workspace")
+        self.ws_bytes = int(n.value)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        check(lib().bf_batch_upload(plan, _ptr(self.ws), ctypes.c_size_t(self.ws_bytes),
+                                    _stream(self.device)), "bf_batch_upload")
+        torch.cuda.current_stream(self.device).synchronize()  # plan tables are now on the device
+        self._graph = None
+
+    def info(self):
+        items, ctas = ctypes.c_int(), ctypes.c_int()
+        check(lib().bf_batch_info(self._plan, ctypes.byref(items), ctypes.byref(ctas)),
+              "bf_batch_info")
+        return items.value, ctas.value
+
+    def run(self):
+        check(lib().bf_batch_forward(self._plan, _ptr(self.ws), ctypes.c_size_t(self.ws_bytes),
+                                     _ptr(self.status), _stream(self.device)), "bf_batch_forward")
+
+    def graph(self):
+        if self._graph is None:
+            g = ctypes.c_void_p()
+            s = torch.cuda.Stream(self.device)
+            s.wait_stream(torch.cuda.current_stream(self.device))
+            check(lib().bf_batch_graph_create(self._plan, _ptr(self.ws),
+                                              ctypes.c_size_t(self.ws_bytes), _ptr(self.status),
+                                              ctypes.c_void_p(s.cuda_stream), ctypes.byref(g)),
+                  "bf_batch_graph_create")
+            s.synchronize()
+            self._graph = g
+        return self._graph
+
+    def replay(self):
+        check(lib().bf_graph_launch(self.graph(), _stream(self.device)), "bf_graph_launch")
+
+    def close(self):
+        if getattr(self, "_graph", None):
+            lib().bf_graph_destroy(self._graph)
+            self._graph = None
+        if getattr(self, "_plan", None):
+            lib().bf_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ tuning
+def variant_count(kind: int = GAUSS) -> int:
+    return int(lib().bf_variant_count(int(kind)))
+
+
+def radius_bucket(radius: int) -> int:
+    return int(lib().bf_tuning_radius_bucket(int(radius)))
+
+
+def order_bucket(N: int) -> int:
+    return int(lib().bf_tuning_order_bucket(int(N)))
+
+
+def tuning_get(kind: int, rb: int, ob: int) -> int:
+    v = ctypes.c_int()
+    check(lib().bf_tuning_get(int(kind), int(rb), int(ob), ctypes.byref(v)), "bf_tuning_get")
+    return v.value
+
+
+def tuning_set(kind: int, rb: int, ob: int, variant: int) -> None:
+    check(lib().bf_tuning_set(int(kind), int(rb), int(ob), int(variant)), "bf_tuning_set")
+
+
+def autotune(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
+             sigma_s: float = 0.0, t_c: float = 128.0, reps: int = 5):
+    """Time every tile variant on this image; record and return (variant, ms)."""
+    x, _ = _as_device_image(img)
+    o = _like(x)
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    best, ms = ctypes.c_int(), ctypes.c_float()
+    check(lib().bf_autotune(_ptr(x), _ptr(o), x.shape[0], x.shape[1], x.stride(0),
+                            ctypes.byref(p), int(reps), _stream(x.device), ctypes.byref(best),
+                            ctypes.byref(ms)), "bf_autotune")
+    return best.value, ms.value

@@ -1,0 +1,250 @@
+// Batched forward: many images of uneven sizes, each with its own spatial
+// kind, W, sigma_s, sigma_r and N, in ONE persistent launch.
+//
+// The host plan splits every image into output tiles (work items), estimates
+// each item's cost from its (N + 1) filterings and tile geometry, and sorts
+// the items longest first.  The grid is sized to the device (SMs x resident
+// CTAs).  Each CTA repeatedly takes the next item index from a device
+// counter (atomicAdd; no CTA ever waits on another) and runs the same tile
+// body as the single-image kernel with that item's parameters.  A launch is
+// a memset of the counter followed by the kernel, so it can be captured in a
+// CUDA graph and replayed.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bf_internal.h"
+#include "gpa_tile.cuh"
+
+namespace {
+
+constexpr int BNT = 256;  // threads per CTA (= region columns)
+
+struct BatchDesc {
+  bfk::TileIO io;
+  bfi::FilterConsts fc;
+  int th;  // output rows per tile for this image (16 or 8)
+  int pad[3];
+};
+
+struct WorkItem {
+  int desc, ty0, tx0, pad;
+};
+
+struct BatchArgs {
+  const BatchDesc *descs;
+  const WorkItem *items;
+  int *counter;
+  int *status;
+  int count, nitems;
+};
+
+__global__ void __launch_bounds__(BNT) gpa_batched_kernel(const __grid_constant__ BatchArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();  // everyone has read s_item before thread 0 may overwrite it
+    if (it >= A.nitems) break;
+    const WorkItem w = A.items[it];
+    if (w.desc < 0 || w.desc >= A.count) {
+      if (threadIdx.x == 0 && A.status) atomicExch(A.status, (int)BF_ERR_INVALID_ARG);
+      continue;
+    }
+    const BatchDesc &d = A.descs[w.desc];
+    const bfi::FilterConsts &fc = d.fc;
+    if (fc.kind == BF_SPATIAL_GAUSS) {
+      if (d.th == 16)
+        bfk::gpa_fwd_tile<1, BNT, 16, 16, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
+      else
+        bfk::gpa_fwd_tile<1, BNT, 8, 8, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
+    } else {
+      if (d.th == 16)
+        bfk::gpa_fwd_tile<0, BNT, 16, 16, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
+      else
+        bfk::gpa_fwd_tile<0, BNT, 8, 8, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
+    }
+    __syncthreads();  // the next item's region load reuses shared memory
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+struct bf_batch_plan {
+  std::vector<BatchDesc> descs;
+  std::vector<WorkItem> items;
+  size_t smem = 0;
+  int ctas = 0;
+  size_t off_descs = 0, off_items = 0, ws_bytes = 0;
+  std::vector<unsigned char> staging;  // descs + items, laid out as in the workspace
+};
+
+extern "C" {
+
+bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_plan **plan_out) {
+  if (!descs || count < 1 || !plan_out) return BF_ERR_INVALID_ARG;
+  *plan_out = nullptr;
+  bf_batch_plan *plan = new (std::nothrow) bf_batch_plan();
+  if (!plan) return BF_ERR_INVALID_ARG;
+  int smem_optin = 232448, dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete plan;
+    return bfi::check_launch();
+  }
+  struct Cost {
+    double c;
+    WorkItem w;
+  };
+  std::vector<Cost> costs;
+  plan->descs.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const bf_image_desc &d = descs[i];
+    bf_status st = bfi::check_image(d.d_in, d.d_out, d.height, d.width, d.pitch);
+    BatchDesc &bd = plan->descs[i];
+    if (st == BF_OK) st = bfi::resolve(&d.params, true, &bd.fc);
+    if (st != BF_OK) {
+      delete plan;
+      return st;
+    }
+    const int R = bd.fc.R;
+    int th = 16;
+    if (BNT - 2 * R < 16 || bfk::fwd_smem_bytes(BNT, 16, R, bd.fc.ntaps_pad) > (size_t)smem_optin)
+      th = 8;
+    if (BNT - 2 * R < 8 || bfk::fwd_smem_bytes(BNT, th, R, bd.fc.ntaps_pad) > (size_t)smem_optin) {
+      delete plan;
+      return BF_ERR_UNSUPPORTED;
+    }
+    bd.th = th;
+    bd.io = {d.d_in, d.d_out, d.d_qaux, nullptr, 0, d.height, d.width, d.pitch};
+    plan->smem = std::max(plan->smem, bfk::fwd_smem_bytes(BNT, th, R, bd.fc.ntaps_pad));
+    const int TW = BNT - 2 * R;
+    // cost model per tile: (N+1) x (region generation + both filter passes)
+    const double taps = bd.fc.kind == BF_SPATIAL_GAUSS ? (double)bd.fc.ntaps_pad : 4.0;
+    const double per_ch = (double)(th + 2 * R) * BNT * 3.0 + (double)th * BNT * taps +
+                          (double)th * TW * (taps + 4.0);
+    const double c = (bd.fc.N + 1.0) * per_ch + (double)(th + 2 * R) * BNT * 8.0;
+    for (int y = 0; y < d.height; y += th)
+      for (int x = 0; x < d.width; x += TW) costs.push_back({c, {i, y, x, 0}});
+  }
+  std::stable_sort(costs.begin(), costs.end(),
+                   [](const Cost &a, const Cost &b) { return a.c > b.c; });
+  plan->items.reserve(costs.size());
+  for (const Cost &c : costs) plan->items.push_back(c.w);
+  if (plan->items.size() > 0x7fffffff) {
+    delete plan;
+    return BF_ERR_UNSUPPORTED;
+  }
+  // grid: every SM filled with as many CTAs as fit
+  cudaError_t e = cudaFuncSetAttribute(gpa_batched_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)plan->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpa_batched_kernel, BNT,
+                                                      plan->smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    delete plan;
+    return e != cudaSuccess ? bfi::cuda_status(e) : BF_ERR_UNSUPPORTED;
+  }
+  plan->ctas = std::min<long long>((long long)sms * per_sm, (long long)plan->items.size());
+  plan->off_descs = 256;
+  plan->off_items = align256(plan->off_descs + sizeof(BatchDesc) * plan->descs.size());
+  plan->ws_bytes = align256(plan->off_items + sizeof(WorkItem) * plan->items.size());
+  plan->staging.assign(plan->ws_bytes - plan->off_descs, 0);
+  memcpy(plan->staging.data(), plan->descs.data(), sizeof(BatchDesc) * plan->descs.size());
+  memcpy(plan->staging.data() + (plan->off_items - plan->off_descs), plan->items.data(),
+         sizeof(WorkItem) * plan->items.size());
+  *plan_out = plan;
+  return BF_OK;
+}
+
+bf_status bf_batch_workspace(const bf_batch_plan *plan, size_t *bytes) {
+  if (!plan || !bytes) return BF_ERR_INVALID_ARG;
+  *bytes = plan->ws_bytes;
+  return BF_OK;
+}
+
+bf_status bf_batch_info(const bf_batch_plan *plan, int *items, int *ctas) {
+  if (!plan) return BF_ERR_INVALID_ARG;
+  if (items) *items = (int)plan->items.size();
+  if (ctas) *ctas = plan->ctas;
+  return BF_OK;
+}
+
+bf_status bf_batch_upload(const bf_batch_plan *plan, void *d_ws, size_t ws_bytes, void *stream) {
+  if (!plan || !d_ws) return BF_ERR_INVALID_ARG;
+  if (ws_bytes < plan->ws_bytes || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+    return BF_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(d_ws);
+  cudaError_t e = cudaMemcpyAsync(base + plan->off_descs, plan->staging.data(),
+                                  plan->staging.size(), cudaMemcpyHostToDevice, s);
+  return bfi::cuda_status(e);
+}
+
+bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_bytes, int *d_status,
+                           void *stream) {
+  if (!plan || !d_ws) return BF_ERR_INVALID_ARG;
+  if (ws_bytes < plan->ws_bytes || (reinterpret_cast<uintptr_t>(d_ws) & 255u))
+    return BF_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(d_ws);
+  BatchArgs A;
+  A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
+  A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items);
+  A.counter = reinterpret_cast<int *>(base);
+  A.status = d_status;
+  A.count = (int)plan->descs.size();
+  A.nitems = (int)plan->items.size();
+  cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return bfi::cuda_status(e);
+  gpa_batched_kernel<<<plan->ctas, BNT, plan->smem, s>>>(A);
+  return bfi::check_launch();
+}
+
+void bf_batch_plan_destroy(bf_batch_plan *plan) { delete plan; }
+
+bf_status bf_batch_graph_create(const bf_batch_plan *plan, void *d_ws, size_t ws_bytes,
+                                int *d_status, void *stream, void **graph_exec_out) {
+  if (!plan || !graph_exec_out || !stream) return BF_ERR_INVALID_ARG;
+  *graph_exec_out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfi::cuda_status(e);
+  bf_status st = bf_batch_forward(plan, d_ws, ws_bytes, d_status, stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(s, &graph);
+  if (st != BF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return bfi::cuda_status(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfi::cuda_status(e);
+  *graph_exec_out = exec;
+  return BF_OK;
+}
+
+bf_status bf_graph_launch(void *graph_exec, void *stream) {
+  if (!graph_exec) return BF_ERR_INVALID_ARG;
+  return bfi::cuda_status(
+      cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)));
+}
+
+void bf_graph_destroy(void *graph_exec) {
+  if (graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
+}
+
+}  // extern "C"

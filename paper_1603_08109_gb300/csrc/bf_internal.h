@@ -1,0 +1,44 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/bf.h"
+
+#define BF_VERSION 10000  // 1.0.0
+
+// Gaussian taps are padded with zeros to a multiple of 16 (the register-window
+// unroll of the separable passes); 2 * BF_MAX_RADIUS + 1 = 193 -> 208 <= 224.
+#define BF_TAPS_MAX 224
+
+namespace bfi {
+
+// One image's filter constants as the device sees them (resolved params).
+struct FilterConsts {
+  int kind;        // BF_SPATIAL_BOX / BF_SPATIAL_GAUSS
+  int R;           // radius W
+  int N;           // number of Taylor terms
+  int ntaps_pad;   // Gaussian: 2R+1 rounded up to a multiple of 16; box: 0
+  float sr;        // sigma_r
+  float inv_sr;    // 1 / sigma_r
+  float tc;        // centre t_c
+  float qscale;    // kernel-sum normalisation: box 1/(2R+1)^2, Gaussian 1
+  float taps[BF_TAPS_MAX];  // normalised 1-D Gaussian taps, taps[k] = w1(k - R)
+};
+
+// Status helpers (bf_host.cpp).
+bf_status cuda_status(cudaError_t e);
+bf_status check_launch();
+void set_error_text(const char *msg);
+
+// Validates image sizes / pointers / params and fills the device constants.
+// `need_order` is false for the direct filter (order_N ignored).
+bf_status resolve(const bf_params *p, bool need_order, FilterConsts *fc);
+bf_status check_image(const void *in, const void *out, int height, int width, int pitch);
+
+// Fastest compiled-in tile variant for (kind, R, N) from the tuning table.
+int tuned_variant(int kind, int R, int N);
+
+}  // namespace bfi

@@ -1,0 +1,446 @@
+// Backward (adjoint) of the fused Gaussian-polynomial bilateral filter.
+//
+// The paper has no backward pass; this is the exact adjoint of
+//   out = t_c + sigma_r P'/Q',  Q' = sum_{n<N} a_n (w*a_n),
+//   P' = sum_{m=1..N} sqrt(m) a_{m-1} (w*a_m),  a_n = e^{-H^2/2} H^n / sqrt(n!).
+// With pbar = g sigma_r / Q' and qbar = -g (out - t_c) / Q' per pixel:
+//   c_n     = qbar a_n [n<N] + pbar sqrt(n) a_{n-1} [n>=1]       (adjoint seeds)
+//   abar_n  = qbar (w*a_n) [n<N] + pbar sqrt(n+1) (w*a_{n+1}) [n<N] + (w*c_n)
+//             (the zero-extended filter is self-adjoint since w is symmetric)
+//   Hbar    = sum_n abar_n (sqrt(n) a_{n-1} - H a_n),   d in = Hbar / sigma_r,
+//   d sigma = sum_i g (out - t_c) / sigma_r - sum_i Hbar H / sigma_r.
+// The tile structure mirrors the forward: phase V streams each region column
+// (advancing a_n in place and forming c_n) through the vertical passes of
+// both channels; phase H applies the horizontal passes and accumulates Hbar.
+// The power images are recomputed (STORED = false) or, for the stored
+// variant, w*a_n is read back from the forward's planes and only c_n is
+// filtered.  sigma_r partials are reduced per CTA in double precision and
+// then summed in a fixed order, so the result is deterministic.
+#include "bf_internal.h"
+#include "gpa_tile.cuh"
+
+namespace {
+
+struct BwdArgs {
+  const float *in, *out, *qaux, *gout, *abar;
+  float *gin;
+  double *partials;  // one per CTA
+  long long plane_stride;
+  int H, W, pitch;
+  bfi::FilterConsts fc;
+};
+
+__host__ __device__ constexpr int VPB(int nt) { return nt + 1; }
+
+size_t bwd_smem_bytes(int NT, int TH, int R, int ntaps_pad, int kind) {
+  const size_t RH = TH + 2 * R;
+  size_t b = RH * (NT + 1) * sizeof(float4) + 2 * (size_t)TH * VPB(NT) * sizeof(float) +
+             (size_t)(ntaps_pad > 0 ? ntaps_pad : 1) * sizeof(float);
+  if (kind == BF_SPATIAL_BOX) b += RH * (NT + 1) * sizeof(float);  // c_n plane (running sums)
+  return b;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+template <int KIND, int NT, int TH, int KH, bool STORED>
+__global__ void __launch_bounds__(NT) gpa_bwd_kernel(const __grid_constant__ BwdArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int IPT = (TH + KH - 1) / KH;
+  constexpr int VP = VPB(NT);
+  constexpr int RP = NT + 1;  // region row pitch (float4): rows land in distinct banks
+  const bfi::FilterConsts &fc = A.fc;
+  const int R = fc.R, RH = TH + 2 * R, TW = NT - 2 * R, N = fc.N;
+  const int ntaps = 2 * R + 1;
+  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+  float4 *sS = reinterpret_cast<float4 *>(smem);         // (a_n, H, qbar, pbar)
+  float *sVa = reinterpret_cast<float *>(sS + RH * RP);  // vertical pass of a_n
+  float *sVc = sVa + TH * VP;                            // vertical pass of c_n
+  float *sT = sVc + TH * VP;
+  float *sC = sT + (fc.ntaps_pad > 0 ? fc.ntaps_pad : 1);  // box only
+  const int tid = threadIdx.x;
+
+  if (KIND == BF_SPATIAL_GAUSS)
+    for (int i = tid; i < fc.ntaps_pad; i += NT) sT[i] = fc.taps[i];
+
+  // ---- region load: (a_0, H, qbar, pbar); qbar/pbar in the kernel's own
+  //      (unnormalised for the box) kernel-sum units: Q_u = Q' / qscale.
+  {
+    const int gx = tx0 - R + tid;
+    const bool colin = gx >= 0 && gx < A.W;
+    for (int r = 0; r < RH; ++r) {
+      const int gy = ty0 - R + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (colin && gy >= 0 && gy < A.H) {
+        const long long o = (long long)gy * A.pitch + gx;
+        const float f = __ldg(A.in + o);
+        const float h = (f - fc.tc) * fc.inv_sr;
+        const float g = __ldg(A.gout + o);
+        const float iq = fc.qscale / __ldg(A.qaux + o);
+        v.x = expf(-0.5f * h * h);
+        v.y = h;
+        v.z = -g * (__ldg(A.out + o) - fc.tc) * iq;
+        v.w = g * fc.sr * iq;
+      }
+      sS[r * RP + tid] = v;
+    }
+  }
+
+  // ---- phase-H items: (row y, segment of KH columns)
+  const int nseg = (TW + KH - 1) / KH;
+  const int items = TH * nseg;
+  float abp[IPT][KH], dAp[IPT][KH], a1[IPT][KH], Hb[IPT][KH];
+#pragma unroll
+  for (int m = 0; m < IPT; ++m)
+#pragma unroll
+    for (int k = 0; k < KH; ++k) abp[m][k] = dAp[m][k] = a1[m][k] = Hb[m][k] = 0.f;
+
+  float4 *col = sS + tid;
+  float *ccol = sC + tid;
+
+  for (int n = 0; n <= N; ++n) {
+    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+    const float sq = __fsqrt_rn((float)n);
+    const float qn = n < N ? 1.f : 0.f;
+    __syncthreads();
+
+    // ---------------- phase V (both channels)
+    auto gen = [&](int r, float &c) -> float {
+      float4 *p = col + r * RP;
+      const float4 v = *p;
+      float a = v.x;
+      if (n > 0) {
+        a = v.x * (v.y * rs);
+        p->x = a;
+      }
+      c = fmaf(v.z * qn, a, v.w * sq * v.x * (n > 0 ? 1.f : 0.f));
+      return a;
+    };
+    if (KIND == BF_SPATIAL_BOX) {
+      float sa = 0.f, sc = 0.f;
+      const int L = 2 * R + 1;
+      for (int r = 0; r < RH; ++r) {
+        float c;
+        const float a = gen(r, c);
+        ccol[r * RP] = c;
+        if (!STORED) sa += a;
+        sc += c;
+        if (r >= L) {
+          if (!STORED) sa -= col[(r - L) * RP].x;
+          sc -= ccol[(r - L) * RP];
+        }
+        if (r >= L - 1) {
+          if (!STORED) sVa[(r - L + 1) * VP + tid] = sa;
+          sVc[(r - L + 1) * VP + tid] = sc;
+        }
+      }
+    } else {
+      float acca[TH], accc[TH], wa[TH], wc[TH];
+#pragma unroll
+      for (int i = 0; i < TH; ++i) {
+        acca[i] = accc[i] = 0.f;
+        wa[i] = gen(i, wc[i]);
+      }
+      for (int kb = 0; kb < ntaps; kb += TH) {
+#pragma unroll
+        for (int u = 0; u < TH; ++u) {
+          if (kb + u < ntaps) {  // warp-uniform: no padded taps
+            const float w = sT[kb + u];
+#pragma unroll
+            for (int y = 0; y < TH; ++y) {
+              if (!STORED) acca[y] = fmaf(w, wa[(u + y) % TH], acca[y]);
+              accc[y] = fmaf(w, wc[(u + y) % TH], accc[y]);
+            }
+            const int r = kb + u + TH;
+            if (r < RH) {
+              wa[u] = gen(r, wc[u]);
+            } else {
+              wa[u] = 0.f;
+              wc[u] = 0.f;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int y = 0; y < TH; ++y) {
+        if (!STORED) sVa[y * VP + tid] = acca[y];
+        sVc[y * VP + tid] = accc[y];
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase H: horizontal passes + adjoint gather
+#pragma unroll
+    for (int m = 0; m < IPT; ++m) {
+      const int it = tid + m * NT;
+      if (it >= items) continue;
+      const int hy = it % TH, hx0 = (it / TH) * KH;
+      float Ab[KH], Cb[KH];
+      const float *ra = sVa + hy * VP, *rc = sVc + hy * VP;
+      if (KIND == BF_SPATIAL_BOX) {
+        float ha[KH], hc[KH], s_a = 0.f, s_c = 0.f;
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+          const int x = min(hx0 + i, NT - 1);
+          if (!STORED) ha[i] = ra[x];
+          hc[i] = rc[x];
+          if (i <= 2 * R) {
+            if (!STORED) s_a += ha[i];
+            s_c += hc[i];
+          }
+        }
+        for (int i = KH; i <= 2 * R; ++i) {
+          if (!STORED) s_a += ra[hx0 + i];
+          s_c += rc[hx0 + i];
+        }
+        Ab[0] = s_a;
+        Cb[0] = s_c;
+#pragma unroll
+        for (int j = 1; j < KH; ++j) {
+          const int x = min(hx0 + j + 2 * R, NT - 1);
+          if (!STORED) s_a += ra[x] - ha[j - 1];
+          s_c += rc[x] - hc[j - 1];
+          Ab[j] = s_a;
+          Cb[j] = s_c;
+        }
+      } else {
+        float wa[KH], wc[KH];
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+          Ab[i] = Cb[i] = 0.f;
+          const int x = min(hx0 + i, NT - 1);
+          if (!STORED) wa[i] = ra[x];
+          wc[i] = rc[x];
+        }
+        for (int kb = 0; kb < ntaps; kb += KH) {
+#pragma unroll
+          for (int u = 0; u < KH; ++u) {
+            if (kb + u < ntaps) {  // warp-uniform
+              const float w = sT[kb + u];
+#pragma unroll
+              for (int i = 0; i < KH; ++i) {
+                if (!STORED) Ab[i] = fmaf(w, wa[(u + i) % KH], Ab[i]);
+                Cb[i] = fmaf(w, wc[(u + i) % KH], Cb[i]);
+              }
+              const int x = min(hx0 + kb + u + KH, NT - 1);
+              if (!STORED) wa[u] = ra[x];
+              wc[u] = rc[x];
+            }
+          }
+        }
+      }
+      if (STORED) {
+        // w*a_n from the forward's plane n (normalised) -> kernel units
+        const int gy = min(ty0 + hy, A.H - 1);
+        const float *src = A.abar + (long long)n * A.plane_stride + (long long)gy * A.pitch;
+        const float inv = 1.0f / fc.qscale;
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+          const int gx = min(tx0 + hx0 + k, A.W - 1);
+          Ab[k] = __ldg(src + gx) * inv;
+        }
+      }
+      const float4 *crow = sS + (hy + R) * RP + R + hx0;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const float4 v = crow[min(k, NT - 1 - R - hx0)];  // (a_n, H, qbar, pbar)
+        if (n > 0) {
+          const float abf = fmaf(v.w * sq, Ab[k], abp[m][k]);  // abar_{n-1} complete
+          Hb[m][k] = fmaf(abf, dAp[m][k], Hb[m][k]);
+        }
+        const float dA = fmaf(sq, a1[m][k], -v.y * v.x);  // d a_n / dH
+        abp[m][k] = fmaf(v.z * qn, Ab[k], Cb[k]);
+        dAp[m][k] = dA;
+        a1[m][k] = v.x;
+      }
+    }
+  }
+
+  // ---- epilogue: d in = Hbar / sigma_r; sigma_r partial sums
+  double part = 0.0;
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    const int it = tid + m * NT;
+    if (it >= items) continue;
+    const int hy = it % TH, hx0 = (it / TH) * KH;
+    const int gy = ty0 + hy;
+    if (gy >= A.H) continue;
+    const float4 *crow = sS + (hy + R) * RP + R + hx0;
+    const long long ro = (long long)gy * A.pitch;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      const int gx = tx0 + hx0 + k;
+      if (hx0 + k < TW && gx < A.W) {
+        const float hbar = Hb[m][k] + abp[m][k] * dAp[m][k];  // abar_N has no pbar term
+        A.gin[ro + gx] = hbar * fc.inv_sr;
+        if (A.partials) {
+          const float H = crow[k].y;
+          const float g = __ldg(A.gout + ro + gx);
+          const float oc = __ldg(A.out + ro + gx) - fc.tc;
+          part += ((double)g * (double)oc - (double)hbar * (double)H) * (double)fc.inv_sr;
+        }
+      }
+    }
+  }
+  if (A.partials) {
+    __shared__ double red[32];
+    const double t = block_sum(part, red);
+    if (threadIdx.x == 0) A.partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Fixed-order sum of the per-CTA partials (one CTA, deterministic).
+__global__ void __launch_bounds__(256) reduce_partials(const double *p, int n, double *out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+  const double t = block_sum(v, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+struct BwdVariant {
+  int NT, TH;
+};
+constexpr BwdVariant kBwd[] = {{128, 16}, {256, 8}, {128, 8}};
+constexpr int kNumBwd = 3;
+
+int smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 232448;
+    cudaGetLastError();
+  }
+  return v;
+}
+
+int pick_bwd(const bfi::FilterConsts &fc) {
+  for (int v = 0; v < kNumBwd; ++v) {
+    const int TW = kBwd[v].NT - 2 * fc.R;
+    if (TW < kBwd[v].TH) continue;
+    if (bwd_smem_bytes(kBwd[v].NT, kBwd[v].TH, fc.R, fc.ntaps_pad, fc.kind) <=
+        (size_t)smem_optin())
+      return v;
+  }
+  return -1;
+}
+
+void grid_for(int v, const bfi::FilterConsts &fc, int H, int W, dim3 *grid) {
+  const int TW = kBwd[v].NT - 2 * fc.R;
+  *grid = dim3((W + TW - 1) / TW, (H + kBwd[v].TH - 1) / kBwd[v].TH);
+}
+
+template <int KIND, int NT, int TH, bool STORED>
+bf_status launch_bwd(const BwdArgs &A, cudaStream_t s) {
+  constexpr int KH = 8;
+  const size_t smem = bwd_smem_bytes(NT, TH, A.fc.R, A.fc.ntaps_pad, KIND);
+  auto kern = gpa_bwd_kernel<KIND, NT, TH, KH, STORED>;
+  static int configured = 0;
+  if ((int)smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    configured = (int)smem;
+  }
+  const int TW = NT - 2 * A.fc.R;
+  dim3 grid((A.W + TW - 1) / TW, (A.H + TH - 1) / TH);
+  kern<<<grid, NT, smem, s>>>(A);
+  return bfi::check_launch();
+}
+
+template <bool STORED>
+bf_status dispatch_bwd(int v, const BwdArgs &A, cudaStream_t s) {
+  const bool g = A.fc.kind == BF_SPATIAL_GAUSS;
+  switch (v) {
+    case 0: return g ? launch_bwd<1, 128, 16, STORED>(A, s) : launch_bwd<0, 128, 16, STORED>(A, s);
+    case 1: return g ? launch_bwd<1, 256, 8, STORED>(A, s) : launch_bwd<0, 256, 8, STORED>(A, s);
+    case 2: return g ? launch_bwd<1, 128, 8, STORED>(A, s) : launch_bwd<0, 128, 8, STORED>(A, s);
+    default: return BF_ERR_INVALID_ARG;
+  }
+}
+
+bf_status workspace_bytes(int height, int width, const bf_params *p, size_t *bytes, int *var,
+                          bfi::FilterConsts *fc) {
+  if (!bytes || height < 1 || width < 1) return BF_ERR_INVALID_ARG;
+  bf_status st = bfi::resolve(p, true, fc);
+  if (st != BF_OK) return st;
+  const int v = pick_bwd(*fc);
+  if (v < 0) return BF_ERR_UNSUPPORTED;
+  dim3 g;
+  grid_for(v, *fc, height, width, &g);
+  *bytes = (size_t)g.x * g.y * sizeof(double);
+  if (var) *var = v;
+  return BF_OK;
+}
+
+bf_status backward_impl(const float *in, const float *out, const float *qaux, const float *abar,
+                        size_t plane_stride, const float *gout, float *gin, double *gsigma,
+                        int height, int width, int pitch, const bf_params *p, void *ws,
+                        size_t ws_bytes, void *stream) {
+  bf_status st = bfi::check_image(in, gin, height, width, pitch);
+  if (st != BF_OK) return st;
+  if (!out || !qaux || !gout) return BF_ERR_INVALID_ARG;
+  BwdArgs A;
+  size_t need = 0;
+  int v = -1;
+  st = workspace_bytes(height, width, p, &need, &v, &A.fc);
+  if (st != BF_OK) return st;
+  if (abar && plane_stride < (size_t)height * (size_t)pitch) return BF_ERR_INVALID_ARG;
+  if (gsigma && (!ws || ws_bytes < need)) return BF_ERR_WORKSPACE;
+  A.in = in;
+  A.out = out;
+  A.qaux = qaux;
+  A.gout = gout;
+  A.abar = abar;
+  A.gin = gin;
+  A.partials = gsigma ? static_cast<double *>(ws) : nullptr;
+  A.plane_stride = (long long)plane_stride;
+  A.H = height;
+  A.W = width;
+  A.pitch = pitch;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = abar ? dispatch_bwd<true>(v, A, s) : dispatch_bwd<false>(v, A, s);
+  if (st != BF_OK || !gsigma) return st;
+  reduce_partials<<<1, 256, 0, s>>>(A.partials, (int)(need / sizeof(double)), gsigma);
+  return bfi::check_launch();
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_fast_backward_workspace(int height, int width, const bf_params *p, size_t *bytes) {
+  bfi::FilterConsts fc;
+  return workspace_bytes(height, width, p, bytes, nullptr, &fc);
+}
+
+bf_status bf_fast_backward(const float *d_in, const float *d_out, const float *d_qaux,
+                           const float *d_gout, float *d_gin, double *d_gsigma, int height,
+                           int width, int pitch, const bf_params *p, void *d_workspace,
+                           size_t workspace_bytes, void *stream) {
+  return backward_impl(d_in, d_out, d_qaux, nullptr, 0, d_gout, d_gin, d_gsigma, height, width,
+                       pitch, p, d_workspace, workspace_bytes, stream);
+}
+
+bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const float *d_qaux,
+                                  const float *d_abar, size_t plane_stride, const float *d_gout,
+                                  float *d_gin, double *d_gsigma, int height, int width, int pitch,
+                                  const bf_params *p, void *d_workspace, size_t workspace_bytes,
+                                  void *stream) {
+  if (!d_abar) return BF_ERR_INVALID_ARG;
+  return backward_impl(d_in, d_out, d_qaux, d_abar, plane_stride, d_gout, d_gin, d_gsigma, height,
+                       width, pitch, p, d_workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Fused forward of the Gaussian-polynomial bilateral filter (Algorithm 2):
+// kernels, tile-variant dispatch and the tile autotuner.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "bf_internal.h"
+#include "gpa_tile.cuh"
+
+namespace {
+
+struct FwdArgs {
+  bfk::TileIO io;
+  bfi::FilterConsts fc;
+};
+
+template <int KIND, int NT, int TH, bool STORE>
+__global__ void __launch_bounds__(NT) gpa_fwd_kernel(const __grid_constant__ FwdArgs args) {
+  extern __shared__ __align__(16) float smem[];
+  const int TW = NT - 2 * args.fc.R;
+  bfk::gpa_fwd_tile<KIND, NT, TH, TH, STORE>(args.io, args.fc, args.fc.taps, blockIdx.y * TH,
+                                             blockIdx.x * TW, smem);
+}
+
+// Tile variants: threads per CTA (= region columns) and output rows per tile.
+struct Variant {
+  int NT, TH;
+};
+constexpr Variant kVariants[] = {{256, 16}, {512, 8}, {256, 8}, {128, 16}, {192, 8}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int max_smem_optin() {
+  static int v = -1;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 232448;
+    cudaGetLastError();
+  });
+  return v;
+}
+
+bool variant_fits(int v, const bfi::FilterConsts &fc) {
+  const Variant &var = kVariants[v];
+  const int TW = var.NT - 2 * fc.R;
+  if (TW < var.TH) return false;
+  return bfk::fwd_smem_bytes(var.NT, var.TH, fc.R, fc.ntaps_pad) <= (size_t)max_smem_optin();
+}
+
+int default_variant(const bfi::FilterConsts &fc) {
+  static const int order[] = {0, 2, 4, 3, 1};
+  for (int v : order)
+    if (variant_fits(v, fc)) return v;
+  return -1;
+}
+
+template <int KIND, int NT, int TH, bool STORE>
+bf_status launch_fwd(const FwdArgs &args, cudaStream_t s) {
+  const int TW = NT - 2 * args.fc.R;
+  const size_t smem = bfk::fwd_smem_bytes(NT, TH, args.fc.R, args.fc.ntaps_pad);
+  auto kern = gpa_fwd_kernel<KIND, NT, TH, STORE>;
+  static int configured = 0;  // bytes of dynamic smem already permitted
+  if ((int)smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    configured = (int)smem;
+  }
+  dim3 grid((args.io.W + TW - 1) / TW, (args.io.H + TH - 1) / TH);
+  kern<<<grid, NT, smem, s>>>(args);
+  return bfi::check_launch();
+}
+
+template <bool STORE>
+bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
+  const bool g = a.fc.kind == BF_SPATIAL_GAUSS;
+  switch (v) {
+    case 0: return g ? launch_fwd<1, 256, 16, STORE>(a, s) : launch_fwd<0, 256, 16, STORE>(a, s);
+    case 1: return g ? launch_fwd<1, 512, 8, STORE>(a, s) : launch_fwd<0, 512, 8, STORE>(a, s);
+    case 2: return g ? launch_fwd<1, 256, 8, STORE>(a, s) : launch_fwd<0, 256, 8, STORE>(a, s);
+    case 3: return g ? launch_fwd<1, 128, 16, STORE>(a, s) : launch_fwd<0, 128, 16, STORE>(a, s);
+    case 4: return g ? launch_fwd<1, 192, 8, STORE>(a, s) : launch_fwd<0, 192, 8, STORE>(a, s);
+    default: return BF_ERR_INVALID_ARG;
+  }
+}
+
+bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, size_t plane_stride,
+                       int height, int width, int pitch, const bf_params *p, int variant,
+                       void *stream) {
+  bf_status st = bfi::check_image(in, out, height, width, pitch);
+  if (st != BF_OK) return st;
+  FwdArgs a;
+  st = bfi::resolve(p, true, &a.fc);
+  if (st != BF_OK) return st;
+  a.io = {in, out, qaux, abar, (long long)plane_stride, height, width, pitch};
+  if (abar && plane_stride < (size_t)height * (size_t)pitch) return BF_ERR_INVALID_ARG;
+  int v = variant;
+  if (v < 0) {
+    v = bfi::tuned_variant(a.fc.kind, a.fc.R, a.fc.N);
+    if (v >= 0 && !variant_fits(v, a.fc)) v = -1;
+    if (v < 0) v = default_variant(a.fc);
+    if (v < 0) return BF_ERR_UNSUPPORTED;
+  } else {
+    if (v >= kNumVariants) return BF_ERR_INVALID_ARG;
+    if (!variant_fits(v, a.fc)) return BF_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return abar ? dispatch<true>(v, a, s) : dispatch<false>(v, a, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int bf_variant_count(int kind) {
+  (void)kind;
+  return kNumVariants;
+}
+
+bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux, int height, int width,
+                          int pitch, const bf_params *p, void *stream) {
+  return forward_impl(d_in, d_out, d_qaux, nullptr, 0, height, width, pitch, p, -1, stream);
+}
+
+bf_status bf_fast_forward_variant(const float *d_in, float *d_out, float *d_qaux, int height,
+                                  int width, int pitch, const bf_params *p, int variant,
+                                  void *stream) {
+  return forward_impl(d_in, d_out, d_qaux, nullptr, 0, height, width, pitch, p, variant, stream);
+}
+
+bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux, float *d_abar,
+                                 size_t plane_stride, int height, int width, int pitch,
+                                 const bf_params *p, void *stream) {
+  if (!d_abar) return BF_ERR_INVALID_ARG;
+  return forward_impl(d_in, d_out, d_qaux, d_abar, plane_stride, height, width, pitch, p, -1,
+                      stream);
+}
+
+// Times every fitting variant (CUDA events on `stream`, after one warm-up
+// launch each) and records the fastest in the tuning table.  Synchronises.
+bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, int pitch,
+                      const bf_params *p, int reps, void *stream, int *best, float *best_ms) {
+  if (!best || reps < 1) return BF_ERR_INVALID_ARG;
+  bfi::FilterConsts fc;
+  bf_status st = bfi::resolve(p, true, &fc);
+  if (st != BF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return bfi::check_launch();
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfi::check_launch();
+  }
+  int bv = -1;
+  float bms = 0.f;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (!variant_fits(v, fc)) continue;
+    st = bf_fast_forward_variant(d_in, d_out, nullptr, height, width, pitch, p, v, stream);
+    if (st != BF_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r)
+      bf_fast_forward_variant(d_in, d_out, nullptr, height, width, pitch, p, v, stream);
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      st = bfi::cuda_status(ce);
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (bv < 0 || ms < bms) {
+      bv = v;
+      bms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BF_OK) return st;
+  if (bv < 0) return BF_ERR_UNSUPPORTED;
+  *best = bv;
+  if (best_ms) *best_ms = bms;
+  return bf_tuning_set(fc.kind, bf_tuning_radius_bucket(fc.R), bf_tuning_order_bucket(fc.N), bv);
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/bf.h declares, validates arguments without touching a GPU, and its
+own host-side order selection reproduces the paper's tables."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bf.h")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _lib():
+    from paper_1603_08109_gb300 import _lib as L
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_08109_gb300 import build
+        build.build()
+    return L
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bf_[a-z0-9_]+)\s*\(", text)))
+
+
+def _rows(name):
+    out = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            out.append([float(v) for v in line.split()])
+    return out
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    L = _lib()
+    handle = ctypes.CDLL(L.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(handle, n), "missing export " + n
+    assert set(names) <= set(L.SIGNATURES), "binding lacks " + str(set(names) - set(L.SIGNATURES))
+    L.lib()
+
+
+def test_version_and_status_strings():
+    L = _lib()
+    assert L.lib().bf_version() == 10000
+    for code, text in L.STATUS.items():
+        assert L.lib().bf_status_string(code).decode() == text
+
+
+def test_library_order_selection_reproduces_table1():
+    """The library's own bracketing + Newton root of nu (App. A) returns the
+    N0' row of Table 1 for eps = 1e-3, T = 128 (independent of the checker)."""
+    L = _lib()
+    from paper_1603_08109_gb300 import api
+    # eps = w(0) delta / (2T + delta): choose delta so that eps = 1e-3 for a box of radius 0
+    for sr, n1, _, _ in _rows("order_vs_sigma_r.txt"):
+        delta = 1e-3 * 256.0 / (1.0 - 1e-3)  # w(0) = 1 for radius 0
+        assert api.order_from_delta(L.BOX, 0, 0.0, sr, delta, 128.0) == int(n1)
+
+
+def test_library_order_vs_delta_table():
+    L = _lib()
+    from paper_1603_08109_gb300 import api
+    for delta, n_lw, _ in _rows("order_vs_delta.txt"):
+        assert api.order_from_delta(L.GAUSS, 15, 5.0, 30.0, delta, 127.0) == int(n_lw)
+        assert abs(api.order_from_delta(L.GAUSS, 0, 5.0, 30.0, delta, 128.0) - int(n_lw)) <= 1
+
+
+def test_library_centre_weight():
+    from paper_1603_08109_gb300 import api
+    assert api.centre_weight(0, 4) == pytest.approx(1.0 / 81.0, rel=1e-15)
+    assert api.centre_weight(1, 15, 5.0) == pytest.approx(6.3905e-3, rel=1e-4)
+
+
+def test_argument_validation_without_gpu():
+    """Invalid arguments are rejected before any CUDA call is made."""
+    L = _lib()
+    lib = L.lib()
+    good = L.make_params(L.GAUSS, 9, 3.0, 30.0, 40)
+    p = ctypes.byref(good)
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.bf_fast_forward(None, fake, None, 8, 8, 8, p, None) == 1
+    assert lib.bf_fast_forward(fake, fake, None, 0, 8, 8, p, None) == 1
+    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 4, p, None) == 1
+    for bad in (L.make_params(L.GAUSS, 9, 3.0, 0.0, 40), L.make_params(L.GAUSS, 9, 3.0, 30.0, 0),
+                L.make_params(7, 9, 3.0, 30.0, 40), L.make_params(L.GAUSS, 0, 0.0, 30.0, 4),
+                L.make_params(L.BOX, -1, 0.0, 30.0, 4)):
+        assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8, ctypes.byref(bad), None) == 1
+    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8,
+                               ctypes.byref(L.make_params(L.BOX, 2, 0.0, 30.0, 5000)), None) == 3
+    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8,
+                               ctypes.byref(L.make_params(L.BOX, 2, 0.0, 5.0, 5)), None) == 3
+    n = ctypes.c_int()
+    assert lib.bf_order_from_delta(0, 2, 0.0, 30.0, 0.0, 128.0, ctypes.byref(n)) == 1
+    assert lib.bf_order_from_delta(0, 2, 0.0, 30.0, 1.0, 128.0, None) == 1
+    sz = ctypes.c_size_t()
+    assert lib.bf_fast_backward_workspace(64, 64, p, ctypes.byref(sz)) == 0 and sz.value > 0
+    assert lib.bf_direct_backward_workspace(64, 64, p, ctypes.byref(sz)) == 0 and sz.value > 0
+    # backward asking for the sigma_r gradient without a workspace
+    assert lib.bf_fast_backward(fake, fake, fake, fake, fake, fake, 8, 8, 8, p, None, 0,
+                                None) in (5, 3)
+    assert lib.bf_batch_plan_create(None, 0, None) == 1
+
+
+def test_tuning_table_roundtrip():
+    from paper_1603_08109_gb300 import api
+    nv = api.variant_count(1)
+    assert nv >= 3
+    rb, ob = api.radius_bucket(9), api.order_bucket(40)
+    old = api.tuning_get(1, rb, ob)
+    api.tuning_set(1, rb, ob, nv - 1)
+    assert api.tuning_get(1, rb, ob) == nv - 1
+    api.tuning_set(1, rb, ob, old)
+    with pytest.raises(Exception):
+        api.tuning_set(1, rb, ob, nv)

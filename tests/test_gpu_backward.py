@@ -1,0 +1,149 @@
+"""GPU gradients: the fast filter's adjoint (recompute and stored variants)
+and the direct filter's gradient, against the checker's exact derivatives
+of eq. GPA / eq. BF, central finite differences of the GPU forward, and the
+direct filter's FP64 gradient."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1603_08109_gb300 as bf
+from helpers import image, needs_gpu, spatial
+from paper_1603_08109_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+GIN_RTOL = 2e-3   # relative to max |gradient|
+GSIG_RTOL = 1e-3
+
+
+def _fast_grads(img, g, kind, r, ss, sr, N, store=False):
+    x = torch.from_numpy(img).cuda()
+    if store:
+        out, q, abar = bf.gpa_forward_stored(x, kind, sr, N, radius=r, sigma_s=ss)
+    else:
+        out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True)
+        abar = None
+    gin, gs = bf.gpa_backward(x, out, q, torch.from_numpy(g).cuda(), kind, sr, N, radius=r,
+                              sigma_s=ss, abar=abar)
+    torch.cuda.synchronize()
+    return gin.cpu().numpy().astype(np.float64), float(gs.item())
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+@pytest.mark.parametrize("case", [
+    (bf.GAUSS, 9, 3.0, 30.0, 40, (40, 300)),
+    (bf.GAUSS, 15, 5.0, 25.0, 54, (40, 130)),
+    (bf.GAUSS, 6, 2.0, 60.0, 8, (25, 90)),
+    (bf.BOX, 5, 0.0, 30.0, 41, (30, 270)),
+    (bf.BOX, 9, 0.0, 40.0, 25, (21, 60)),
+], ids=lambda c: "k%d_r%d_sr%g_N%d" % (c[0], c[1], c[3], c[4]))
+def test_fast_backward_matches_exact_derivatives(case):
+    kind, r, ss, sr, N, (H, W) = case
+    img = image(H, W, seed=H * 31 + W)
+    g = synth.random_like((H, W), seed=H + W)
+    gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+    rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
+    assert _rel(gin, rgin) <= GIN_RTOL
+    assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs)
+    gin2, gs2 = _fast_grads(img, g, kind, r, ss, sr, N, store=True)
+    assert _rel(gin2, gin) <= 1e-4
+    assert abs(gs2 - gs) <= 1e-5 * abs(gs)
+
+
+def test_fast_backward_deterministic_and_autograd():
+    img = image(40, 200, seed=3)
+    g = synth.random_like(img.shape, seed=4)
+    a = _fast_grads(img, g, bf.GAUSS, 9, 3.0, 30.0, 40)
+    b = _fast_grads(img, g, bf.GAUSS, 9, 3.0, 30.0, 40)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    x = torch.from_numpy(img).cuda().requires_grad_(True)
+    s = torch.tensor(30.0, device="cuda", requires_grad=True)
+    out = bf.gpa_bilateral(x, s, kind=bf.GAUSS, N=40, radius=9, sigma_s=3.0)
+    (out * torch.from_numpy(g).cuda()).sum().backward()
+    assert np.array_equal(x.grad.cpu().numpy().astype(np.float64), a[0])
+    assert float(s.grad) == pytest.approx(a[1], rel=1e-6)
+
+
+def test_fast_backward_finite_differences_of_gpu_forward():
+    """Central differences of the GPU forward, loss <r, out> accumulated in
+    FP64.  Image: step h = 1e-2 along a direction d built from the analytic
+    gradient's signs times random magnitudes, so that the directional
+    derivative (order of the pixel count) dominates the float32 rounding
+    noise of the forward (about sqrt(pixels) * 1e-5 / h).  sigma_r: step 0.25
+    (1% of sigma_r; truncation error O(1e-4) relative)."""
+    H, W = 64, 96
+    img = image(H, W, seed=8)
+    kind, r, ss, sr, N = bf.GAUSS, 15, 5.0, 25.0, 54
+    rr = synth.random_like((H, W), seed=9).astype(np.float64)
+
+    def loss(x, s):
+        o = bf.gpa_forward(torch.from_numpy(x).cuda(), kind, s, N, radius=r, sigma_s=ss)
+        return float(np.sum(rr * o.cpu().numpy().astype(np.float64)))
+
+    gin, gs = _fast_grads(img, rr.astype(np.float32), kind, r, ss, sr, N)
+    mag = np.abs(synth.random_like((H, W), seed=10)).astype(np.float64)
+    d = (np.sign(gin) * mag).astype(np.float32)
+    h = 1e-2
+    fd = (loss(img + h * d, sr) - loss(img - h * d, sr)) / (2 * h)
+    an = float(np.sum(gin * d))
+    assert an == pytest.approx(fd, rel=2e-3)
+    hs = 0.25
+    fds = (loss(img, sr + hs) - loss(img, sr - hs)) / (2 * hs)
+    assert gs == pytest.approx(fds, rel=2e-3)
+
+
+def test_fast_gradient_approaches_direct_gradient():
+    """At the order from delta the fast gradient is close to the exact
+    FP64 gradient of eq. BF (and the gap shrinks with N)."""
+    img = image(30, 60, seed=12)
+    g = synth.random_like(img.shape, seed=13)
+    kind, r, ss, sr = bf.GAUSS, 6, 2.0, 30.0
+    w = spatial(kind, r, ss)
+    dgin, dgs = oracle.bf_direct_grad(img, w, sr, g.astype(np.float64))
+    errs = []
+    for N in (25, 40, 55):
+        gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+        errs.append(_rel(gin, dgin))
+    assert errs[2] < errs[0]
+    assert errs[2] <= 5e-3
+
+
+@pytest.mark.parametrize("case", [
+    (bf.GAUSS, 9, 3.0, 30.0, (40, 150)),
+    (bf.BOX, 5, 0.0, 20.0, (30, 100)),
+    (bf.GAUSS, 15, 5.0, 25.0, (33, 70)),
+])
+def test_direct_backward_matches_exact_derivatives(case):
+    kind, r, ss, sr, (H, W) = case
+    img = image(H, W, seed=H + W)
+    g = synth.random_like((H, W), seed=2 * H)
+    x = torch.from_numpy(img).cuda()
+    gin, gs = bf.direct_backward(x, torch.from_numpy(g).cuda(), kind, sr, radius=r, sigma_s=ss)
+    rgin, rgs = oracle.bf_direct_grad(img, spatial(kind, r, ss), sr, g.astype(np.float64))
+    assert _rel(gin.cpu().numpy().astype(np.float64), rgin) <= GIN_RTOL
+    assert abs(float(gs.item()) - rgs) <= GSIG_RTOL * abs(rgs)
+    xs = x.clone().requires_grad_(True)
+    s = torch.tensor(sr, device="cuda", requires_grad=True)
+    (bf.direct_bilateral(xs, s, kind=kind, radius=r, sigma_s=ss) * torch.from_numpy(g).cuda()).sum().backward()
+    assert torch.equal(xs.grad, gin)
+
+
+def test_backward_full_size_512_sampled():
+    """One 512^2 image of the differentiated workload (Gaussian sigma_s = 5,
+    sigma_r = 25, N = 54): image gradient at sampled pixels and sigma_r."""
+    H = W = 512
+    img = image(H, W, seed=4000)
+    g = synth.random_like((H, W), seed=4001)
+    kind, r, ss, sr, N = bf.GAUSS, 15, 5.0, 25.0, 54
+    gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+    rng = np.random.default_rng(5)
+    ys = np.concatenate([rng.integers(0, H, 12), [0, H - 1]])
+    xs = np.concatenate([rng.integers(0, W, 12), [W - 1, 0]])
+    rgin, _ = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64),
+                              samples=(ys, xs))
+    scale = np.abs(gin).max()
+    assert np.abs(gin[ys, xs] - rgin).max() <= GIN_RTOL * scale

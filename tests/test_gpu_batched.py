@@ -1,0 +1,90 @@
+"""GPU batched persistent forward: each image of one launch equals the
+single-image kernel with the same tile shape bit for bit, graph replays are
+identical, and sampled pixels match the checker."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1603_08109_gb300 as bf
+from helpers import compare_forward, image, needs_gpu, scaled_q, spatial
+from paper_1603_08109_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def _batch(specs):
+    imgs, outs, host = [], [], []
+    for sp in specs:
+        a = image(sp["height"], sp["width"], seed=sp["seed"])
+        host.append(a)
+        imgs.append(torch.from_numpy(a).cuda())
+        outs.append(torch.empty_like(imgs[-1]))
+    return host, imgs, outs
+
+
+def _with_order(specs):
+    for sp in specs:
+        sp["N"] = bf.order_from_delta(sp["kind"], sp["radius"], sp["sigma_s"], sp["sigma_r"], 1.0)
+    return specs
+
+
+def _single(img, sp):
+    # the batched kernel uses 256-thread tiles: 16 rows up to radius 44, else 8 rows
+    variant = 0 if sp["radius"] <= 44 else 2
+    return bf.gpa_forward(img, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
+                          sigma_s=sp["sigma_s"], variant=variant)
+
+
+def test_batched_equals_single_image_kernel_and_graph_replays():
+    specs = _with_order(synth.batch_specs(12, seed=77, max_hw=(300, 400)))
+    specs[0].update(radius=45, sigma_s=15.0, kind=bf.GAUSS)
+    specs[1].update(height=1, width=1)
+    specs[2].update(height=3, width=700, kind=bf.BOX, radius=30)
+    _with_order(specs)
+    host, imgs, outs = _batch(specs)
+    plan = bf.BatchPlan(imgs, outs, specs)
+    items, ctas = plan.info()
+    assert items >= len(specs) and 1 <= ctas <= items
+    plan.run()
+    torch.cuda.synchronize()
+    assert int(plan.status.item()) == 0
+    first = [o.clone() for o in outs]
+    for x, o, sp in zip(imgs, first, specs):
+        assert torch.equal(o, _single(x, sp)), sp
+    for _ in range(3):
+        for o in outs:
+            o.fill_(-1.0)
+        plan.replay()
+        torch.cuda.synchronize()
+        for o, f in zip(outs, first):
+            assert torch.equal(o, f)
+    for k in (0, 3):
+        sp = specs[k]
+        w = spatial(sp["kind"], sp["radius"], sp["sigma_s"])
+        ro, P, Q = oracle.gpa_alg2(host[k], w, sp["sigma_r"], sp["N"], return_parts=True)
+        compare_forward(first[k].cpu().numpy(), None, ro, scaled_q(host[k], Q, sp["sigma_r"]),
+                        w[sp["radius"], sp["radius"]], "batched %d" % k)
+    plan.close()
+
+
+def test_batched_full_256_workload():
+    """The uneven 256-image batch: every image equals the single-image kernel."""
+    specs = _with_order(synth.batch_specs(256, seed=3000))
+    host, imgs, outs = _batch(specs)
+    plan = bf.BatchPlan(imgs, outs, specs)
+    plan.replay()
+    torch.cuda.synchronize()
+    for x, o, sp in zip(imgs, outs, specs):
+        assert torch.equal(o, _single(x, sp))
+    k = int(np.argmax([sp["N"] for sp in specs]))
+    sp = specs[k]
+    rng = np.random.default_rng(1)
+    ys = rng.integers(0, sp["height"], 40)
+    xs = rng.integers(0, sp["width"], 40)
+    w = spatial(sp["kind"], sp["radius"], sp["sigma_s"])
+    ro, P, Q = oracle.gpa_alg2_at(host[k], w, sp["sigma_r"], sp["N"], (ys, xs), return_parts=True)
+    compare_forward(outs[k].cpu().numpy()[ys, xs], None, ro,
+                    scaled_q(host[k][ys, xs], Q, sp["sigma_r"]), w[sp["radius"], sp["radius"]],
+                    "batched max-N image")
+    plan.close()

@@ -1,0 +1,136 @@
+"""GPU parity of the fused forward (bf_fast_forward) against the checker's
+Algorithm 2 at the same N, element by element, at sizes spanning several
+tiles with ragged tails; plus every tile variant, edge cases, the stored
+planes, and sampled pixels at the full 2048^2 / 4096^2 workload sizes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1603_08109_gb300 as bf
+from helpers import compare_forward, image, needs_gpu, scaled_q, spatial
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+CASES = [
+    # kind, radius, sigma_s, sigma_r, N, (H, W)
+    (bf.GAUSS, 9, 3.0, 30.0, 40, (70, 500)),     # 256^2 workload's filter, several tiles
+    (bf.GAUSS, 9, 3.0, 30.0, 2, (40, 300)),
+    (bf.GAUSS, 30, 10.0, 60.0, 19, (90, 260)),
+    (bf.GAUSS, 15, 5.0, 25.0, 54, (45, 470)),
+    (bf.GAUSS, 9, 3.0, 10.0, 223, (34, 260)),
+    (bf.BOX, 5, 0.0, 30.0, 41, (70, 520)),
+    (bf.BOX, 20, 0.0, 60.0, 20, (60, 300)),
+    (bf.BOX, 5, 0.0, 10.0, 226, (30, 270)),
+    (bf.BOX, 50, 0.0, 60.0, 21, (40, 200)),
+    (bf.BOX, 3, 0.0, 40.0, 1, (33, 100)),
+]
+
+
+def _run(img, kind, r, ss, sr, N, variant=-1):
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True, variant=variant)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), q.cpu().numpy()
+
+
+def _ref(img, kind, r, ss, sr, N):
+    w = spatial(kind, r, ss)
+    o, P, Q = oracle.gpa_alg2(img, w, sr, N, return_parts=True)
+    return o, scaled_q(img, Q, sr), w[r, r]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "k%d_r%d_sr%g_N%d" % (c[0], c[1], c[3], c[4]))
+def test_forward_matches_algorithm2(case):
+    kind, r, ss, sr, N, (H, W) = case
+    img = image(H, W, seed=H * 1000 + W)
+    out, q = _run(img, kind, r, ss, sr, N)
+    ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
+    compare_forward(out, q, ro, rq, w0, str(case))
+
+
+@pytest.mark.parametrize("variant", range(5))
+def test_every_tile_variant(variant):
+    img = image(50, 330, seed=77)
+    for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 7, 0.0)):
+        ro, rq, w0 = _ref(img, kind, r, ss, 30.0, 40)
+        out, q = _run(img, kind, r, ss, 30.0, 40, variant=variant)
+        compare_forward(out, q, ro, rq, w0, "variant %d kind %d" % (variant, kind))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (5, 7), (3, 400), (300, 3)])
+def test_tiny_and_thin_images_radius_beyond_image(shape):
+    img = image(*shape, seed=5, block=2)
+    for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 12, 0.0)):
+        ro, rq, w0 = _ref(img, kind, r, ss, 30.0, 40)
+        out, q = _run(img, kind, r, ss, 30.0, 40)
+        compare_forward(out, q, ro, rq, w0, "shape %s kind %d" % (shape, kind))
+
+
+def test_constant_image_is_fixed_point():
+    img = np.full((40, 300), 201.0, np.float32)
+    for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 5, 0.0)):
+        out, _ = _run(img, kind, r, ss, 30.0, 40)
+        assert np.abs(out - 201.0).max() <= 1e-3
+
+
+def test_pitched_input_and_cpu_tensor_roundtrip():
+    img = image(40, 150, seed=9)
+    base = torch.zeros((40, 160), dtype=torch.float32, device="cuda")
+    base[:, :150] = torch.from_numpy(img).cuda()
+    view = base[:, :150]
+    assert view.stride(0) == 160
+    out = bf.gpa_forward(view, bf.GAUSS, 30.0, 40, radius=9, sigma_s=3.0)
+    ro, rq, w0 = _ref(img, bf.GAUSS, 9, 3.0, 30.0, 40)
+    compare_forward(out.cpu().numpy(), None, ro, rq, w0, "pitched")
+    out_cpu = bf.gpa_forward(torch.from_numpy(img), bf.GAUSS, 30.0, 40, radius=9, sigma_s=3.0)
+    assert out_cpu.device.type == "cpu"
+    assert torch.equal(out_cpu, out.cpu())
+
+
+def test_stored_planes_match_filtered_images():
+    """bf_fast_forward_stored plane n = Fbar_n / sqrt(n!) (the rescaled
+    filtered image of Algorithm 2), and out is bitwise the plain forward's."""
+    img = image(40, 280, seed=31)
+    kind, r, ss, sr, N = bf.GAUSS, 6, 2.0, 30.0, 30
+    w = spatial(kind, r, ss)
+    _, _, _, planes = oracle.gpa_alg2(img, w, sr, N, return_parts=True, return_planes=True)
+    x = torch.from_numpy(img).cuda()
+    out_s, q_s, abar = bf.gpa_forward_stored(x, kind, sr, N, radius=r, sigma_s=ss)
+    out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True)
+    assert torch.equal(out_s, out) and torch.equal(q_s, q)
+    ab = abar.cpu().numpy()
+    from math import lgamma, exp
+    for n in range(N + 1):
+        ref = planes[n] / np.sqrt(exp(lgamma(n + 1)))
+        assert np.abs(ab[n] - ref).max() <= 2e-6 + 1e-5 * np.abs(ref).max(), n
+
+
+def _sampled_case(H, W, gen, kind, r, ss, sr, N, nsamp, seed):
+    img = gen(H, W, seed)
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    ys = np.concatenate([rng.integers(0, H, nsamp), [0, 0, H - 1, H - 1, H // 2]])
+    xs = np.concatenate([rng.integers(0, W, nsamp), [0, W - 1, 0, W - 1, W // 2]])
+    w = spatial(kind, r, ss)
+    ro, P, Q = oracle.gpa_alg2_at(img, w, sr, N, (ys, xs), return_parts=True)
+    rq = scaled_q(img[ys, xs], Q, sr)
+    o = out[ys, xs].cpu().numpy()
+    qq = q[ys, xs].cpu().numpy()
+    return compare_forward(o, qq, ro, rq, w[r, r], "sampled %dx%d" % (H, W))
+
+
+def test_full_size_2048_sampled():
+    """2048^2 blocks (64) + noise 10 at the benchmark's launch configuration."""
+    gen = lambda h, w, s: image(h, w, s, block=64, noise=10.0)  # noqa: E731
+    _sampled_case(2048, 2048, gen, bf.GAUSS, 9, 3.0, 30.0, 40, 400, 1000)
+    _sampled_case(2048, 2048, gen, bf.BOX, 20, 0.0, 30.0, 44, 300, 1001)
+
+
+def test_full_size_4096_sampled_gradient_polygons():
+    from paper_1603_08109_gb300 import synth
+    gen = lambda h, w, s: synth.gradient_polygons_image(h, w, 64, 15.0, seed=s)  # noqa: E731
+    _sampled_case(4096, 4096, gen, bf.BOX, 5, 0.0, 40.0, 3, 300, 2000)
+    _sampled_case(4096, 4096, gen, bf.GAUSS, 60, 20.0, 40.0, 32, 60, 2001)
