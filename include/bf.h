@@ -162,6 +162,32 @@ bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const f
                                   int height, int width, int pitch, const bf_params *p,
                                   void *d_workspace, size_t workspace_bytes, void *stream);
 
+/* Allocation-free variant of bf_fast_backward (the paper has no counterpart;
+ * it exists for callers of this library, not for the method).  Some callers
+ * cannot call cudaMalloc: plug-ins hosted by an application that owns the
+ * device allocator, and real-time pipelines that must not allocate after
+ * start-up because cudaMalloc can synchronise the device and take an
+ * unbounded time.  This entry point needs no workspace: the per-CTA sigma_r
+ * partial sums go to a fixed 65536-entry (512 KiB) static device array that
+ * every GPU loading the library holds until the process exits.  The caller
+ * still passes every input and output, as for bf_fast_backward, and gets the
+ * same results.
+ *  - The first call on a device (with d_gsigma non-NULL) looks up the
+ *    array's device address for that device, so make that first call before
+ *    any stream capture.
+ *  - All calls share the array and it keeps the last call's partial sums;
+ *    each call writes every entry it reads, so nothing needs clearing, but
+ *    calls that overlap on the GPU (e.g. on two streams) race on it.
+ *  - An image that needs more than 65536 partial sums (one per CTA of the
+ *    backward grid: roughly beyond 1.1e8 pixels at W = 9, e.g. above
+ *    10000 x 10000) is rejected with BF_ERR_UNSUPPORTED before any
+ *    GPU work.  Nothing here calls cudaMalloc, cudaFree or any allocating
+ *    library routine. */
+bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_out, const float *d_qaux,
+                                   const float *d_gout, float *d_gin, double *d_gsigma,
+                                   int height, int width, int pitch, const bf_params *p,
+                                   void *stream);
+
 /* ------------------------------------------------------ direct filter
  * eq. BF computed directly, O((2W+1)^2) exponentials per pixel (Sec. I-A),
  * float32 accumulation; order_N is ignored.  The same-GPU comparison. */

@@ -58,6 +58,7 @@ SIGNATURES = {
     "bf_fast_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_backward_stored": (_i, [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _i, _pp,
                                      _vp, _sz, _vp]),
+    "bf_fast_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp]),
     "bf_direct": (_i, [_vp, _vp, _i, _i, _i, _pp, _vp]),
     "bf_direct_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_direct_backward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),

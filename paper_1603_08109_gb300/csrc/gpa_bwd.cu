@@ -16,6 +16,8 @@
 // variant, w*a_n is read back from the forward's planes and only c_n is
 // filtered.  sigma_r partials are reduced per CTA in double precision and
 // then summed in a fixed order, so the result is deterministic.
+#include <mutex>
+
 #include "bf_internal.h"
 #include "gpa_tile.cuh"
 
@@ -444,3 +446,65 @@ bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free backward.
+//
+// Some callers cannot call cudaMalloc: plug-ins hosted by an application that
+// owns the device allocator and does not let them allocate, and real-time
+// pipelines that must not allocate after start-up (cudaMalloc can
+// synchronise the device and take an unbounded time).  For them the per-CTA
+// sigma_r partial sums, the backward's only scratch memory, live in the
+// file-scope device array below instead of a caller workspace.  Every GPU
+// that loads this library holds the array (512 KiB) until the process exits.
+namespace {
+constexpr int kNoAllocPartials = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+// Device address of g_noalloc_partials on the current device.  In host code
+// the symbol's name is only a host-side stand-in, so its address is looked up
+// once per device (with that device current) and cached.
+static bf_status noalloc_partials(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return bfi::cuda_status(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return BF_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return BF_OK;
+}
+
+extern "C" bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_out,
+                                              const float *d_qaux, const float *d_gout,
+                                              float *d_gin, double *d_gsigma, int height,
+                                              int width, int pitch, const bf_params *p,
+                                              void *stream) {
+  size_t need = 0;
+  bf_status st = bf_fast_backward_workspace(height, width, p, &need);
+  if (st != BF_OK) return st;
+  if (need > sizeof(double) * (size_t)kNoAllocPartials) {
+    bfi::set_error_text("image too large for the allocation-free backward: it needs more "
+                        "sigma_r partial sums than the 65536 of its static scratch");
+    return BF_ERR_UNSUPPORTED;
+  }
+  double *scratch = nullptr;
+  if (d_gsigma) {
+    st = noalloc_partials(&scratch);
+    if (st != BF_OK) return st;
+  }
+  // Every partial the reduction reads is written earlier in this same call,
+  // so the array needs no clearing between calls.
+  return backward_impl(d_in, d_out, d_qaux, nullptr, 0, d_gout, d_gin, d_gsigma, height, width,
+                       pitch, p, scratch, scratch ? need : 0, stream);
+}
