@@ -44,8 +44,8 @@ L2_NOTE = "L2 flushed between timed steps (512 MB write, outside the per-step ev
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048, help="image side (profiling runs only)")
     ap.add_argument("--kind", default="gauss", choices=["gauss", "box"])

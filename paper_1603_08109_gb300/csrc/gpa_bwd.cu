@@ -309,6 +309,258 @@ __global__ void __launch_bounds__(256) reduce_partials(const double *p, int n, d
   if (threadIdx.x == 0) *out = t;
 }
 
+// ---------------------------------------------------------------------------
+// Backward specialised for a compile-time radius R (same math, same result
+// up to rounding).  Each column thread keeps its RH = TH + 2R power-image
+// values in registers; H and (qbar, pbar) of the region stay in shared
+// memory; taps are constant-bank FMA operands.  The adjoint gather is
+// re-associated: with D_n = d a_n / dH = sqrt(n) a_{n-1} - H a_n,
+//   Hbar = qbar * sum_{n<N} (w*a_n) D_n + sum_n (w*c_n) D_n
+//          + pbar * sum_{m>=1} sqrt(m) (w*a_m) D_{m-1},
+// so phase H keeps three running sums per output and reads only D_n, which
+// phase V computes for the centre rows.
+template <int R, int NT, int TH>
+struct BwdFixedGeom {
+  static constexpr int RH = TH + 2 * R;
+  static constexpr int TW = NT - 2 * R;
+  static constexpr int KH = 16;
+  static constexpr int IPT = TH / KH;
+  static constexpr int L = 2 * R + 1;
+  // Row pitch = 17 (mod 32): the 16 rows of one half-warp and the next
+  // segment (+16 columns) of the other half fall in 32 distinct banks.
+  static constexpr int VP = NT + KH + 1;
+  static_assert(VP % 32 == 17, "phase-H row pitch must be 17 mod 32");
+  static constexpr size_t smem_bytes() {
+    return (3 * (size_t)TH * VP + (size_t)RH * NT) * sizeof(float) +
+           (size_t)RH * NT * sizeof(float2);
+  }
+};
+
+template <int KIND, int R, int NT, int TH>
+__global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant__ BwdArgs A) {
+  using G = BwdFixedGeom<R, NT, TH>;
+  constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L, VP = G::VP;
+  static_assert(TH % KH == 0 && NT % TH == 0 && TW >= KH, "tile geometry");
+  extern __shared__ __align__(16) float smem[];
+  const bfi::FilterConsts &fc = A.fc;
+  const int N = fc.N;
+  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+  float *sVa = smem;               // TH x VP: vertical pass of a_n
+  float *sVc = sVa + TH * VP;      // TH x VP: vertical pass of c_n
+  float *sD = sVc + TH * VP;       // TH x VP: D_n of the centre rows
+  float *sH = sD + TH * VP;        // RH x NT: H
+  float2 *sQP = reinterpret_cast<float2 *>(sH + RH * NT);  // RH x NT: (qbar, pbar)
+  const int c = threadIdx.x;
+
+  float a[RH];
+  {
+    const int gx = tx0 - R + c;
+    const bool colin = gx >= 0 && gx < A.W;
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+      const int gy = ty0 - R + r;
+      float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
+      if (colin && gy >= 0 && gy < A.H) {
+        const long long o = (long long)gy * A.pitch + gx;
+        h = (__ldg(A.in + o) - fc.tc) * fc.inv_sr;
+        a0 = expf(-0.5f * h * h);
+        const float g = __ldg(A.gout + o);
+        const float iq = fc.qscale / __ldg(A.qaux + o);  // kernel-sum units: Q_u = Q' / qscale
+        qb = -g * (__ldg(A.out + o) - fc.tc) * iq;
+        pb = g * fc.sr * iq;
+      }
+      a[r] = a0;
+      sH[r * NT + c] = h;
+      sQP[r * NT + c] = make_float2(qb, pb);
+    }
+  }
+
+  float X[IPT][KH], Y[IPT][KH], Z[IPT][KH], Dp[IPT][KH];
+#pragma unroll
+  for (int m = 0; m < IPT; ++m)
+#pragma unroll
+    for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
+
+  for (int n = 0; n <= N; ++n) {
+    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+    const float sq = __fsqrt_rn((float)n);
+    const float qn = n < N ? 1.f : 0.f;
+    __syncthreads();
+
+    // ---------------- phase V: advance, seeds c_n, D_n of centre rows, vertical passes
+    float acca[TH], accc[TH];
+#pragma unroll
+    for (int y = 0; y < TH; ++y) acca[y] = accc[y] = 0.f;
+    float cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+      const float h = sH[r * NT + c];
+      const float aold = a[r];
+      const float an = n > 0 ? aold * (h * rs) : aold;
+      a[r] = an;
+      const float2 qp = sQP[r * NT + c];
+      const float cn = fmaf(qp.x * qn, an, qp.y * sq * aold);
+      if (r >= R && r < R + TH) sD[(r - R) * VP + c] = fmaf(sq, aold, -h * an);
+      if (KIND == BF_SPATIAL_GAUSS) {
+#pragma unroll
+        for (int y = 0; y < TH; ++y) {
+          if (r - y >= 0 && r - y < L) {
+            acca[y] = fmaf(fc.taps[r - y], an, acca[y]);
+            accc[y] = fmaf(fc.taps[r - y], cn, accc[y]);
+          }
+        }
+      } else {
+        cbox[KIND == BF_SPATIAL_BOX ? r : 0] = cn;
+      }
+    }
+    if (KIND == BF_SPATIAL_BOX) {
+      float sa = 0.f, sc = 0.f;
+#pragma unroll
+      for (int r = 0; r < L; ++r) {
+        sa += a[r];
+        sc += cbox[KIND == BF_SPATIAL_BOX ? r : 0];
+      }
+      acca[0] = sa;
+      accc[0] = sc;
+#pragma unroll
+      for (int y = 1; y < TH; ++y) {
+        sa += a[y + 2 * R] - a[y - 1];
+        sc += cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0] - cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
+        acca[y] = sa;
+        accc[y] = sc;
+      }
+    }
+#pragma unroll
+    for (int y = 0; y < TH; ++y) {
+      sVa[y * VP + c] = acca[y];
+      sVc[y * VP + c] = accc[y];
+    }
+    __syncthreads();
+
+    // ---------------- phase H: horizontal passes + running sums
+#pragma unroll
+    for (int m = 0; m < IPT; ++m) {
+      const int it = c + m * NT;
+      const int hy = it % TH, hx0 = (it / TH) * KH;
+      if (hx0 >= TW) continue;
+      const float *ra = sVa + hy * VP + hx0, *rc = sVc + hy * VP + hx0;
+      float Ab[KH], Cb[KH];
+      if (KIND == BF_SPATIAL_GAUSS) {
+        float wa[KH], wc[KH];
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+          Ab[i] = Cb[i] = 0.f;
+          wa[i] = ra[i];
+          wc[i] = rc[i];
+        }
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          const float w = fc.taps[t];
+#pragma unroll
+          for (int i = 0; i < KH; ++i) {
+            Ab[i] = fmaf(w, wa[(t + i) % KH], Ab[i]);
+            Cb[i] = fmaf(w, wc[(t + i) % KH], Cb[i]);
+          }
+          wa[t % KH] = ra[t + KH];
+          wc[t % KH] = rc[t + KH];
+        }
+      } else {
+        float va[KH + 2 * R], vc[KH + 2 * R];
+#pragma unroll
+        for (int i = 0; i < KH + 2 * R; ++i) {
+          va[i] = ra[i];
+          vc[i] = rc[i];
+        }
+        float sa = 0.f, sc = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          sa += va[i];
+          sc += vc[i];
+        }
+        Ab[0] = sa;
+        Cb[0] = sc;
+#pragma unroll
+        for (int j = 1; j < KH; ++j) {
+          sa += va[j + 2 * R] - va[j - 1];
+          sc += vc[j + 2 * R] - vc[j - 1];
+          Ab[j] = sa;
+          Cb[j] = sc;
+        }
+      }
+      const float *drow = sD + hy * VP + R + hx0;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const float D = drow[k];
+        X[m][k] = fmaf(Ab[k] * qn, D, X[m][k]);
+        Y[m][k] = fmaf(Cb[k], D, Y[m][k]);
+        Z[m][k] = fmaf(Ab[k] * sq, Dp[m][k], Z[m][k]);
+        Dp[m][k] = D;
+      }
+    }
+  }
+
+  // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
+  double part = 0.0;
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    const int it = c + m * NT;
+    const int hy = it % TH, hx0 = (it / TH) * KH;
+    const int gy = ty0 + hy;
+    if (hx0 >= TW || gy >= A.H) continue;
+    const long long ro = (long long)gy * A.pitch;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      const int gx = tx0 + hx0 + k;
+      if (hx0 + k < TW && gx < A.W) {
+        const int ci = (hy + R) * NT + R + hx0 + k;
+        const float2 qp = sQP[ci];
+        const float hbar = fmaf(qp.x, X[m][k], fmaf(qp.y, Z[m][k], Y[m][k]));
+        A.gin[ro + gx] = hbar * fc.inv_sr;
+        if (A.partials) {
+          const float g = __ldg(A.gout + ro + gx);
+          const float oc = __ldg(A.out + ro + gx) - fc.tc;
+          part += ((double)g * (double)oc - (double)hbar * (double)sH[ci]) * (double)fc.inv_sr;
+        }
+      }
+    }
+  }
+  if (A.partials) {
+    __shared__ double red[32];
+    const double t = block_sum(part, red);
+    if (threadIdx.x == 0) A.partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+constexpr int kBwdFixedNT = 128, kBwdFixedTH = 16;
+bool bwd_fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
+
+template <int KIND, int R>
+bf_status launch_bwd_fixed_r(const BwdArgs &A, cudaStream_t s) {
+  using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
+  auto kern = gpa_bwd_fixed_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem_bytes());
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    configured = true;
+  }
+  dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
+  kern<<<grid, kBwdFixedNT, G::smem_bytes(), s>>>(A);
+  return bfi::check_launch();
+}
+
+template <int KIND>
+bf_status launch_bwd_fixed(const BwdArgs &A, cudaStream_t s) {
+  switch (A.fc.R) {
+    case 3: return launch_bwd_fixed_r<KIND, 3>(A, s);
+    case 5: return launch_bwd_fixed_r<KIND, 5>(A, s);
+    case 9: return launch_bwd_fixed_r<KIND, 9>(A, s);
+    case 15: return launch_bwd_fixed_r<KIND, 15>(A, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
+}
+
 struct BwdVariant {
   int NT, TH;
 };
@@ -412,7 +664,12 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   A.W = width;
   A.pitch = pitch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = abar ? dispatch_bwd<true>(v, A, s) : dispatch_bwd<false>(v, A, s);
+  // The compile-time-radius kernel has the geometry of variant 0 (128 threads,
+  // 16-row tiles), so the partial-sum count (workspace size) is the same.
+  if (!abar && v == 0 && bwd_fixed_radius(A.fc.R))
+    st = A.fc.kind == BF_SPATIAL_GAUSS ? launch_bwd_fixed<1>(A, s) : launch_bwd_fixed<0>(A, s);
+  else
+    st = abar ? dispatch_bwd<true>(v, A, s) : dispatch_bwd<false>(v, A, s);
   if (st != BF_OK || !gsigma) return st;
   reduce_partials<<<1, 256, 0, s>>>(A.partials, (int)(need / sizeof(double)), gsigma);
   return bfi::check_launch();

@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "bf_internal.h"
+#include "gpa_fixed.cuh"
 #include "gpa_tile.cuh"
 
 namespace {
@@ -22,12 +23,27 @@ __global__ void __launch_bounds__(NT) gpa_fwd_kernel(const __grid_constant__ Fwd
                                              blockIdx.x * TW, smem);
 }
 
-// Tile variants: threads per CTA (= region columns) and output rows per tile.
+// Compile-time-radius kernel (gpa_fixed.cuh): 256 threads, 16-row tiles.
+template <int KIND, int R>
+__global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constant__ FwdArgs args) {
+  extern __shared__ __align__(16) float smem[];
+  using G = bfk::FixedGeom<R, 256, 16>;
+  bfk::gpa_fwd_tile_fixed<KIND, R, 256, 16>(args.io, args.fc, blockIdx.y * 16, blockIdx.x * G::TW,
+                                            smem);
+}
+
+// Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
+// columns, output rows per tile).  Variant 5: the compile-time-radius kernel
+// for the radii in kFixedRadii (forward without stored planes only).
 struct Variant {
   int NT, TH;
 };
 constexpr Variant kVariants[] = {{256, 16}, {512, 8}, {256, 8}, {128, 16}, {192, 8}};
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kNumGeneric = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int kFixedVariant = kNumGeneric;
+constexpr int kNumVariants = kNumGeneric + 1;
+
+bool fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 
 int max_smem_optin() {
   static int v = -1;
@@ -42,18 +58,47 @@ int max_smem_optin() {
   return v;
 }
 
-bool variant_fits(int v, const bfi::FilterConsts &fc) {
+bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
+  if (v == kFixedVariant) return !store && fixed_radius(fc.R);
   const Variant &var = kVariants[v];
   const int TW = var.NT - 2 * fc.R;
   if (TW < var.TH) return false;
   return bfk::fwd_smem_bytes(var.NT, var.TH, fc.R, fc.ntaps_pad) <= (size_t)max_smem_optin();
 }
 
-int default_variant(const bfi::FilterConsts &fc) {
-  static const int order[] = {0, 2, 4, 3, 1};
+int default_variant(const bfi::FilterConsts &fc, bool store) {
+  static const int order[] = {kFixedVariant, 0, 2, 4, 3, 1};
   for (int v : order)
-    if (variant_fits(v, fc)) return v;
+    if (variant_fits(v, fc, store)) return v;
   return -1;
+}
+
+template <int KIND, int R>
+bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
+  using G = bfk::FixedGeom<R, 256, 16>;
+  const size_t smem = G::smem_bytes();
+  auto kern = gpa_fwd_fixed_kernel<KIND, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    configured = true;
+  }
+  dim3 grid((args.io.W + G::TW - 1) / G::TW, (args.io.H + 15) / 16);
+  kern<<<grid, 256, smem, s>>>(args);
+  return bfi::check_launch();
+}
+
+template <int KIND>
+bf_status launch_fixed(const FwdArgs &a, cudaStream_t s) {
+  switch (a.fc.R) {
+    case 3: return launch_fixed_r<KIND, 3>(a, s);
+    case 5: return launch_fixed_r<KIND, 5>(a, s);
+    case 9: return launch_fixed_r<KIND, 9>(a, s);
+    case 15: return launch_fixed_r<KIND, 15>(a, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
 }
 
 template <int KIND, int NT, int TH, bool STORE>
@@ -76,6 +121,10 @@ bf_status launch_fwd(const FwdArgs &args, cudaStream_t s) {
 template <bool STORE>
 bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
   const bool g = a.fc.kind == BF_SPATIAL_GAUSS;
+  if (v == kFixedVariant) {
+    if (STORE) return BF_ERR_UNSUPPORTED;
+    return g ? launch_fixed<1>(a, s) : launch_fixed<0>(a, s);
+  }
   switch (v) {
     case 0: return g ? launch_fwd<1, 256, 16, STORE>(a, s) : launch_fwd<0, 256, 16, STORE>(a, s);
     case 1: return g ? launch_fwd<1, 512, 8, STORE>(a, s) : launch_fwd<0, 512, 8, STORE>(a, s);
@@ -96,15 +145,16 @@ bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, si
   if (st != BF_OK) return st;
   a.io = {in, out, qaux, abar, (long long)plane_stride, height, width, pitch};
   if (abar && plane_stride < (size_t)height * (size_t)pitch) return BF_ERR_INVALID_ARG;
+  const bool store = abar != nullptr;
   int v = variant;
   if (v < 0) {
     v = bfi::tuned_variant(a.fc.kind, a.fc.R, a.fc.N);
-    if (v >= 0 && !variant_fits(v, a.fc)) v = -1;
-    if (v < 0) v = default_variant(a.fc);
+    if (v >= 0 && !variant_fits(v, a.fc, store)) v = -1;
+    if (v < 0) v = default_variant(a.fc, store);
     if (v < 0) return BF_ERR_UNSUPPORTED;
   } else {
     if (v >= kNumVariants) return BF_ERR_INVALID_ARG;
-    if (!variant_fits(v, a.fc)) return BF_ERR_UNSUPPORTED;
+    if (!variant_fits(v, a.fc, store)) return BF_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return abar ? dispatch<true>(v, a, s) : dispatch<false>(v, a, s);

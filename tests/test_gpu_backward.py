@@ -49,9 +49,12 @@ def test_fast_backward_matches_exact_derivatives(case):
     rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
     assert _rel(gin, rgin) <= GIN_RTOL
     assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs)
+    # stored planes (runtime-radius kernel) vs recompute (possibly the
+    # compile-time-radius kernel with re-associated sums): same math, float32
     gin2, gs2 = _fast_grads(img, g, kind, r, ss, sr, N, store=True)
     assert _rel(gin2, gin) <= 1e-4
-    assert abs(gs2 - gs) <= 1e-5 * abs(gs)
+    assert abs(gs2 - gs) <= 1e-4 * abs(gs)
+    assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
 
 
 def test_fast_backward_deterministic_and_autograd():

@@ -46,16 +46,36 @@ def test_forward_matches_algorithm2(case):
     img = image(H, W, seed=H * 1000 + W)
     out, q = _run(img, kind, r, ss, sr, N)
     ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
-    compare_forward(out, q, ro, rq, w0, str(case))
+    compare_forward(out, q, ro, rq, w0, str(case), sigma_r=sr, N=N)
 
 
-@pytest.mark.parametrize("variant", range(5))
+@pytest.mark.parametrize("variant", range(6))
 def test_every_tile_variant(variant):
     img = image(50, 330, seed=77)
-    for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 7, 0.0)):
+    ran = 0
+    for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 7, 0.0), (bf.BOX, 5, 0.0)):
         ro, rq, w0 = _ref(img, kind, r, ss, 30.0, 40)
-        out, q = _run(img, kind, r, ss, 30.0, 40, variant=variant)
+        try:
+            out, q = _run(img, kind, r, ss, 30.0, 40, variant=variant)
+        except bf._lib.BFError as e:  # the fixed-radius variant covers W in {3, 5, 9, 15} only
+            assert e.status == 3 and variant == 5 and r == 7
+            continue
         compare_forward(out, q, ro, rq, w0, "variant %d kind %d" % (variant, kind))
+        ran += 1
+    assert ran >= 2
+
+
+@pytest.mark.parametrize("r", [3, 5, 9, 15])
+def test_fixed_radius_kernel(r):
+    """The compile-time-radius kernel at every radius it is built for, both
+    kinds, ragged sizes, small and large N (including N = 1 and 2)."""
+    img = image(45, 600, seed=r)
+    for kind, ss in ((bf.GAUSS, r / 3.0), (bf.BOX, 0.0)):
+        for sr, N in ((30.0, 40), (60.0, 2), (40.0, 1), (12.0, 180)):
+            ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
+            out, q = _run(img, kind, r, ss, sr, N, variant=5)
+            compare_forward(out, q, ro, rq, w0, "fixed r=%d kind %d N=%d" % (r, kind, N),
+                            sigma_r=sr, N=N)
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (5, 7), (3, 400), (300, 3)])
