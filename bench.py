@@ -57,6 +57,9 @@ def parse():
                     help="restrict the timed step (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--sweep", default="",
+                    help="comma list of extra studies, one JSON line per point: "
+                         "grid2048, roofline4096, large8192, batch256, grad512 (or 'all')")
     return ap.parse_args()
 
 
@@ -260,10 +263,188 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+# ----------------------------------------------------------------- studies
+def _time_ms(fn, reps, stream, flush=None):
+    """Mean CUDA-event time of fn() over reps calls (L2 flushed between)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(reps):
+        if flush is not None:
+            flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
+
+
+def run_sweeps(args):
+    """Extra studies behind the headline: one JSON line per measured point."""
+    import numpy as np
+    import torch
+
+    import paper_1603_08109_gb300 as bf
+    from paper_1603_08109_gb300 import synth
+    names = set(args.sweep.split(",")) if args.sweep != "all" else {
+        "grid2048", "roofline4096", "large8192", "batch256", "grad512"}
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pk, pk_src = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    if "grid2048" in names:
+        # 2048^2 blocks(64)+N(0,10^2); box W in {5,20,50}, Gaussian sigma_s in {3,10};
+        # sigma_r in {10,30,60}; N in {2, bound/2, bound}; fast vs direct, forward only
+        x = torch.from_numpy(synth.blocks_image(2048, 2048, 64, 10.0, seed=1000)).to(dev)
+        o = torch.empty_like(x)
+        d = torch.empty_like(x)
+        for kind, R, ss in ((bf.BOX, 5, 0.0), (bf.BOX, 20, 0.0), (bf.BOX, 50, 0.0),
+                            (bf.GAUSS, 9, 3.0), (bf.GAUSS, 30, 10.0)):
+            for sr in (10.0, 30.0, 60.0):
+                nb = bf.order_from_delta(kind, R, ss, sr, 1.0)
+                dms = _time_ms(lambda: bf.direct(x, kind, sr, radius=R, sigma_s=ss, out=d),
+                               3, stream, flush)
+                for N in sorted({2, max(2, nb // 2), nb}):
+                    try:
+                        fms = _time_ms(lambda: bf.gpa_forward(x, kind, sr, N, radius=R,
+                                                              sigma_s=ss, out=o), 5, stream, flush)
+                    except bf._lib.BFError as e:
+                        emit({"sweep": "grid2048", "kind": kind, "radius": R, "sigma_r": sr,
+                              "N": N, "error": str(e)})
+                        continue
+                    err = float((o.double() - d.double()).abs().max()) if N == nb else None
+                    emit({"sweep": "grid2048", "kind": "box" if kind == 0 else "gaussian",
+                          "radius": R, "sigma_s": ss, "sigma_r": sr, "N": N, "N_bound": nb,
+                          "fast_fwd_ms": fms, "fast_fwd_mpx_s": 4.194304 / fms * 1e3,
+                          "direct_fwd_ms": dms, "direct_fwd_mpx_s": 4.194304 / dms * 1e3,
+                          "speedup_vs_direct": dms / fms, "max_abs_fast_vs_direct": err})
+    if "roofline4096" in names:
+        # 4096^2 gradient + polygons; HBM fraction of the fused forward (8 B/px: f in, out)
+        x = torch.from_numpy(synth.gradient_polygons_image(4096, 4096, 64, 15.0, seed=2000)).to(dev)
+        o = torch.empty_like(x)
+        px = 4096.0 * 4096.0
+        cms = _time_ms(lambda: o.copy_(x), 10, stream, flush)
+        emit({"sweep": "roofline4096", "kernel": "torch copy (reference)", "ms": cms,
+              "gbs": 8 * px / cms / 1e6, "frac_of_measured_hbm": 8 * px / cms / 1e6 / hbm_peak})
+        for kind, R, ss in ((bf.BOX, 5, 0.0), (bf.GAUSS, 9, 3.0)):
+            nb = bf.order_from_delta(kind, R, ss, 40.0, 1.0)
+            for N in (1, 2, 3, 5, 8, nb):
+                fms = _time_ms(lambda: bf.gpa_forward(x, kind, 40.0, N, radius=R, sigma_s=ss,
+                                                      out=o), 10, stream, flush)
+                gbs = 8 * px / fms / 1e6
+                emit({"sweep": "roofline4096", "kind": "box" if kind == 0 else "gaussian",
+                      "radius": R, "sigma_r": 40.0, "N": N, "fwd_ms": fms,
+                      "fwd_mpx_s": px / fms / 1e3, "algorithmic_gbs": gbs,
+                      "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src,
+                      "alu_ops_frac": fwd_ops_per_pixel(kind, R, N) * px / (fms * 1e-3) /
+                      fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+    if "large8192" in names:
+        # 8192^2 gradient + polygons; Gaussian sigma_s=20 (W=60), sigma_r=40, N from delta=0.5
+        x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)
+        o = torch.empty_like(x)
+        d = torch.empty_like(x)
+        N = bf.order_from_delta(bf.GAUSS, 60, 20.0, 40.0, 0.5)
+        fms = _time_ms(lambda: bf.gpa_forward(x, bf.GAUSS, 40.0, N, radius=60, sigma_s=20.0,
+                                              out=o), 3, stream, flush)
+        dms = _time_ms(lambda: bf.direct(x, bf.GAUSS, 40.0, radius=60, sigma_s=20.0, out=d),
+                       1, stream, flush)
+        px = 8192.0 * 8192.0
+        emit({"sweep": "large8192", "kind": "gaussian", "radius": 60, "sigma_s": 20.0,
+              "sigma_r": 40.0, "N": N, "fast_fwd_ms": fms, "fast_fwd_mpx_s": px / fms / 1e3,
+              "direct_fwd_ms": dms, "direct_fwd_mpx_s": px / dms / 1e3,
+              "speedup_vs_direct": dms / fms,
+              "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max()),
+              "fwd_alu_ops_frac": fwd_ops_per_pixel(1, 60, N) * px / (fms * 1e-3) /
+              fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+    if "batch256" in names:
+        specs = synth.batch_specs(256, seed=3000)
+        for sp in specs:
+            sp["N"] = bf.order_from_delta(sp["kind"], sp["radius"], sp["sigma_s"], sp["sigma_r"], 1.0)
+        imgs = [torch.from_numpy(synth.blocks_image(sp["height"], sp["width"], 16, 20.0,
+                                                    seed=sp["seed"])).to(dev) for sp in specs]
+        outs = [torch.empty_like(t) for t in imgs]
+        plan = bf.BatchPlan(imgs, outs, specs)
+        items, ctas = plan.info()
+        gms = _time_ms(plan.replay, 5, stream, flush)
+
+        def loop():
+            for x, o, sp in zip(imgs, outs, specs):
+                bf.gpa_forward(x, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
+                               sigma_s=sp["sigma_s"], out=o)
+        lms = _time_ms(loop, 3, stream, flush)
+        px = float(sum(sp["height"] * sp["width"] for sp in specs))
+        emit({"sweep": "batch256", "images": 256, "megapixels": px / 1e6, "work_items": items,
+              "ctas": ctas, "graph_ms": gms, "graph_mpx_s": px / gms / 1e3,
+              "per_image_launches_ms": lms, "per_image_mpx_s": px / lms / 1e3,
+              "N_range": [min(s["N"] for s in specs), max(s["N"] for s in specs)]})
+        plan.close()
+    if "grad512" in names:
+        # 32 x 512^2, Gaussian sigma_s=5 (W=15), sigma_r=25, N from delta=1: fwd+bwd
+        N = bf.order_from_delta(bf.GAUSS, 15, 5.0, 25.0, 1.0)
+        xs = [torch.from_numpy(synth.blocks_image(512, 512, 16, 20.0, seed=4000 + k)).to(dev)
+              for k in range(32)]
+        gs = [torch.from_numpy(synth.random_like((512, 512), seed=5000 + k)).to(dev)
+              for k in range(32)]
+
+        def fb(store):
+            def run():
+                for x, g in zip(xs, gs):
+                    if store:
+                        o, q, ab = bf.gpa_forward_stored(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0)
+                    else:
+                        o, q = bf.gpa_forward(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
+                                              return_q=True)
+                        ab = None
+                    bf.gpa_backward(x, o, q, g, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
+                                    abar=ab)
+            return run
+
+        def dfb():
+            for x, g in zip(xs, gs):
+                bf.direct(x, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
+                bf.direct_backward(x, g, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
+        def graphed(fn):
+            # capture the 32-image loop once (the library never allocates or
+            # synchronises), then time replays: no Python launch gaps
+            s = torch.cuda.Stream(dev)
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                fn()
+                fn()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            torch.cuda.synchronize()
+            return g
+
+        px = 32 * 512.0 * 512.0
+        g_r, g_s, g_d = graphed(fb(False)), graphed(fb(True)), graphed(dfb)
+        rms = _time_ms(g_r.replay, 3, stream, flush)
+        sms = _time_ms(g_s.replay, 3, stream, flush)
+        dms = _time_ms(g_d.replay, 2, stream, flush)
+        emit({"sweep": "grad512", "images": 32, "N": N, "recompute_fwd_bwd_ms": rms,
+              "recompute_mpx_s": px / rms / 1e3, "stored_fwd_bwd_ms": sms,
+              "stored_mpx_s": px / sms / 1e3, "stored_plane_bytes_per_image": 4 * (N + 1) * 512 * 512,
+              "direct_fwd_bwd_ms": dms, "direct_mpx_s": px / dms / 1e3})
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweeps(args)
 
     import numpy as np
     import torch

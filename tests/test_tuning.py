@@ -1,0 +1,42 @@
+"""Tile-shape tuning table: JSON cache round trip (CPU) and a small on-GPU
+autotune whose chosen variant still meets the parity bar."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1603_08109_gb300 as bf
+from helpers import compare_forward, image, needs_gpu, scaled_q, spatial
+from paper_1603_08109_gb300 import tuning
+
+
+def test_json_cache_roundtrip(tmp_path):
+    path = tmp_path / "tune.json"
+    rb, ob = bf.radius_bucket(20), bf.order_bucket(100)
+    old = bf.tuning_get(0, rb, ob)
+    entries = [{"kind": 0, "radius_bucket": rb, "order_bucket": ob, "variant": 2, "ms": 1.0}]
+    path.write_text(json.dumps({"device": "test", "entries": entries}))
+    try:
+        assert tuning.load(str(path)) == 1
+        assert bf.tuning_get(0, rb, ob) == 2
+    finally:
+        bf.tuning_set(0, rb, ob, old)
+    assert tuning.load(str(tmp_path / "missing.json")) == 0
+
+
+@pytest.mark.gpu
+@needs_gpu
+def test_autotune_then_forward_meets_parity(tmp_path):
+    entries = tuning.autotune_grid(128, 300, kinds=(bf.GAUSS,), radii=(12,), orders=(24,), reps=2)
+    assert len(entries) == 1 and 0 <= entries[0]["variant"] < bf.variant_count()
+    tuning.save(entries, str(tmp_path / "t.json"))
+    assert tuning.load(str(tmp_path / "t.json")) == 1
+    img = image(60, 300, seed=21)
+    out, q = bf.gpa_forward(torch.from_numpy(img).cuda(), bf.GAUSS, 30.0, 24, radius=12,
+                            sigma_s=4.0, return_q=True)
+    w = spatial(bf.GAUSS, 12, 4.0)
+    ro, P, Q = oracle.gpa_alg2(img, w, 30.0, 24, return_parts=True)
+    compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, 30.0), w[12, 12],
+                    "tuned", sigma_r=30.0, N=24)
