@@ -395,23 +395,37 @@ def run_sweeps(args):
         gs = [torch.from_numpy(synth.random_like((512, 512), seed=5000 + k)).to(dev)
               for k in range(32)]
 
-        def fb(store):
+        # a 512^2 image alone fills only part of the GPU: the 32 images run on 8
+        # streams (parallel branches of the captured graph)
+        side = [torch.cuda.Stream(dev) for _ in range(8)]
+
+        def fanout(body):
             def run():
-                for x, g in zip(xs, gs):
-                    if store:
-                        o, q, ab = bf.gpa_forward_stored(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0)
-                    else:
-                        o, q = bf.gpa_forward(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
-                                              return_q=True)
-                        ab = None
-                    bf.gpa_backward(x, o, q, g, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
-                                    abar=ab)
+                cur = torch.cuda.current_stream(dev)
+                for k, (x, g) in enumerate(zip(xs, gs)):
+                    s = side[k % len(side)]
+                    s.wait_stream(cur)
+                    with torch.cuda.stream(s):
+                        body(x, g)
+                for s in side:
+                    cur.wait_stream(s)
             return run
 
-        def dfb():
-            for x, g in zip(xs, gs):
-                bf.direct(x, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
-                bf.direct_backward(x, g, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
+        def fb(store):
+            def body(x, g):
+                if store:
+                    o, q, ab = bf.gpa_forward_stored(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0)
+                else:
+                    o, q = bf.gpa_forward(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
+                                          return_q=True)
+                    ab = None
+                bf.gpa_backward(x, o, q, g, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0, abar=ab)
+            return fanout(body)
+
+        def dbody(x, g):
+            bf.direct(x, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
+            bf.direct_backward(x, g, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
+        dfb = fanout(dbody)
         def graphed(fn):
             # capture the 32-image loop once (the library never allocates or
             # synchronises), then time replays: no Python launch gaps

@@ -44,19 +44,22 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
 
   float a[RH];
   {
+    // all loads of the column first (RH independent loads in flight), then
+    // the arithmetic; out-of-image pixels read as t_c with a_0 = 0
     const int gx = tx0 - R + c;
     const bool colin = gx >= 0 && gx < io.W;
     const float *src = io.in + gx;
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
       const int gy = ty0 - R + r;
-      float h = 0.f, a0 = 0.f;
-      if (colin && gy >= 0 && gy < io.H) {
-        const float f = __ldg(src + (long long)gy * io.pitch);
-        h = (f - fc.tc) * fc.inv_sr;
-        a0 = expf(-0.5f * h * h);  // the one transcendental of Algorithm 2
-      }
-      a[r] = a0;
+      a[r] = (colin && gy >= 0 && gy < io.H) ? __ldg(src + (long long)gy * io.pitch) : fc.tc;
+    }
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+      const int gy = ty0 - R + r;
+      const bool in = colin && gy >= 0 && gy < io.H;
+      const float h = (a[r] - fc.tc) * fc.inv_sr;
+      a[r] = in ? expf(-0.5f * h * h) : 0.f;  // the one transcendental of Algorithm 2
       sH[r * NT + c] = h;
     }
   }
