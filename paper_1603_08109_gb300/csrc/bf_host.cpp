@@ -88,6 +88,7 @@ bf_status resolve(const bf_params *p, bool need_order, FilterConsts *fc) {
   fc->N = p->order_N;
   fc->sr = p->sigma_r;
   fc->inv_sr = (float)(1.0 / (double)p->sigma_r);
+  fc->e2c = (float)(-1.4426950408889634 / (2.0 * (double)p->sigma_r * (double)p->sigma_r));
   fc->tc = p->t_c;
   if (p->kind == BF_SPATIAL_GAUSS) {
     fc->ntaps_pad = ((2 * R + 1) + 15) / 16 * 16;

@@ -25,6 +25,7 @@ struct FilterConsts {
   float inv_sr;    // 1 / sigma_r
   float tc;        // centre t_c
   float qscale;    // kernel-sum normalisation: box 1/(2R+1)^2, Gaussian 1
+  float e2c;       // -log2(e) / (2 sigma_r^2): a_0 = 2^(e2c (f - t_c)^2)
   float taps[BF_TAPS_MAX];  // normalised 1-D Gaussian taps, taps[k] = w1(k - R)
 };
 

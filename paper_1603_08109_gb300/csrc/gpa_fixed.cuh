@@ -11,6 +11,12 @@
 //  - the shared rows are padded so that no index needs clamping.
 // Phase V also copies the TH centre rows of a_n to shared memory (sC) for the
 // recombination in phase H.
+//
+// The kernel is persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...
+// and copies the next tile's region (f) into a second shared buffer with
+// cp.async while it computes the current tile, so the HBM latency of the
+// load overlaps the arithmetic.  Outputs are staged in shared memory and
+// written row by row (coalesced).
 #pragma once
 
 #include "gpa_tile.cuh"
@@ -23,43 +29,71 @@ struct FixedGeom {
   static constexpr int TW = NT - 2 * R;
   static constexpr int KH = TH;
   static constexpr int L = 2 * R + 1;
-  static constexpr int VP = NT + KH + 1;  // odd; phase-H windows never need clamping
-  static constexpr size_t smem_bytes() {
-    return ((size_t)2 * TH * VP + (size_t)RH * NT) * sizeof(float);
+  static constexpr int VP = NT + KH + 1;  // 17 mod 32; phase-H windows never need clamping
+  // sV, sC, two region buffers, and the (1/sqrt(n), sqrt(n)) table for n <= N
+  static constexpr size_t smem_bytes(int N) {
+    return ((size_t)2 * TH * VP + (size_t)2 * RH * NT) * sizeof(float) +
+           (size_t)(N + 1) * sizeof(float2);
   }
 };
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Copy the f column of region column c of the tile at (ty0, tx0) into buf
+// (RH x NT floats).  Out-of-image pixels are not copied (the consumer masks
+// them by their coordinates).
+template <int R, int NT, int TH>
+__device__ __forceinline__ void prefetch_region(const TileIO &io, int ty0, int tx0, float *buf) {
+  using G = FixedGeom<R, NT, TH>;
+  const int c = threadIdx.x;
+  const int gx = tx0 - R + c;
+  if (gx < 0 || gx >= io.W) return;
+  const float *src = io.in + gx;
+  if (ty0 - R >= 0 && ty0 - R + G::RH <= io.H) {  // interior rows: no per-row test
+#pragma unroll
+    for (int r = 0; r < G::RH; ++r)
+      cp_async4(buf + r * NT + c, src + (long long)(ty0 - R + r) * io.pitch);
+  } else {
+#pragma unroll
+    for (int r = 0; r < G::RH; ++r) {
+      const int gy = ty0 - R + r;
+      if (gy >= 0 && gy < io.H) cp_async4(buf + r * NT + c, src + (long long)gy * io.pitch);
+    }
+  }
+}
+
 template <int KIND, int R, int NT, int TH>
 __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::FilterConsts &fc,
-                                                   int ty0, int tx0, float *smem) {
+                                                   int ty0, int tx0, float *sH, float *sV,
+                                                   float *sC, const float2 *sRS) {
   using G = FixedGeom<R, NT, TH>;
   constexpr int RH = G::RH, TW = G::TW, KH = G::KH, L = G::L, VP = G::VP;
   static_assert(TW >= KH, "tile too narrow for this radius");
   static_assert(NT % TH == 0, "NT must be a multiple of TH");
-  float *sV = smem;            // TH x VP   vertical-pass results
-  float *sC = sV + TH * VP;    // TH x VP   centre rows of a_n
-  float *sH = sC + TH * VP;    // RH x NT   H of the region
   const int c = threadIdx.x;
   const int N = fc.N;
 
+  // sH holds this column's f (copied asynchronously); turn it into H in place
   float a[RH];
   {
-    // all loads of the column first (RH independent loads in flight), then
-    // the arithmetic; out-of-image pixels read as t_c with a_0 = 0
     const int gx = tx0 - R + c;
     const bool colin = gx >= 0 && gx < io.W;
-    const float *src = io.in + gx;
-#pragma unroll
-    for (int r = 0; r < RH; ++r) {
-      const int gy = ty0 - R + r;
-      a[r] = (colin && gy >= 0 && gy < io.H) ? __ldg(src + (long long)gy * io.pitch) : fc.tc;
-    }
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
       const int gy = ty0 - R + r;
       const bool in = colin && gy >= 0 && gy < io.H;
-      const float h = (a[r] - fc.tc) * fc.inv_sr;
-      a[r] = in ? expf(-0.5f * h * h) : 0.f;  // the one transcendental of Algorithm 2
+      const float d = sH[r * NT + c] - fc.tc;
+      const float h = in ? d * fc.inv_sr : 0.f;
+      // the one transcendental of Algorithm 2: exp(-H^2/2) = 2^(e2c d^2)
+      a[r] = in ? exp2f(d * d * fc.e2c) : 0.f;
       sH[r * NT + c] = h;
     }
   }
@@ -74,9 +108,9 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
   const float *crow = sC + hy * VP + R + hx0;
 
   for (int n = 0; n <= N; ++n) {
-    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
-    const float sq = __fsqrt_rn((float)n);
-    __syncthreads();  // phase H of the previous channel is done with sV / sC
+    const float2 rsq = sRS[n];  // (1/sqrt(n), sqrt(n)), correctly rounded
+    const float rs = rsq.x, sq = rsq.y;
+    __syncthreads();  // phase H of the previous channel (or tile) is done with sV / sC
 
     // ---------------- phase V (registers): advance, centre copy, vertical pass
     if (n > 0) {
@@ -148,20 +182,64 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
     }
   }
 
+  // ---- epilogue: f_GPA = t_c + sigma_r P'/Q', staged in sV / sC, stored row-wise
+  __syncthreads();  // every thread is done reading sV / sC
   if (hact) {
-    const int gy = ty0 + hy;
-    if (gy < io.H) {
-      float *orow = io.out + (long long)gy * io.pitch;
-      float *qrow = io.qaux ? io.qaux + (long long)gy * io.pitch : nullptr;
 #pragma unroll
-      for (int k = 0; k < KH; ++k) {
-        const int gx = tx0 + hx0 + k;
-        if (hx0 + k < TW && gx < io.W) {
-          orow[gx] = fmaf(fc.sr, P[k] / Q[k], fc.tc);
-          if (qrow) qrow[gx] = Q[k] * fc.qscale;
-        }
-      }
+    for (int k = 0; k < KH; ++k) {
+      // approximate division (2 ulp): <= 3e-5 on the 0..255 scale
+      sV[hy * VP + hx0 + k] = fmaf(fc.sr, __fdividef(P[k], Q[k]), fc.tc);
+      sC[hy * VP + hx0 + k] = Q[k] * fc.qscale;
     }
+  }
+  __syncthreads();
+  const int wmax = min(TW, io.W - tx0);
+  for (int y = 0; y < TH; ++y) {
+    const int gy = ty0 + y;
+    if (gy >= io.H) break;
+    if (c < wmax) {
+      io.out[(long long)gy * io.pitch + tx0 + c] = sV[y * VP + c];
+      if (io.qaux) io.qaux[(long long)gy * io.pitch + tx0 + c] = sC[y * VP + c];
+    }
+  }
+}
+
+// Persistent driver: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (row-major over the tile grid), double-buffered region copies.
+template <int KIND, int R, int NT, int TH>
+__device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
+                                                         const bfi::FilterConsts &fc, float *smem) {
+  using G = FixedGeom<R, NT, TH>;
+  float *sV = smem;
+  float *sC = sV + TH * G::VP;
+  float *sF0 = sC + TH * G::VP;
+  float *sF1 = sF0 + G::RH * NT;
+  float2 *sRS = reinterpret_cast<float2 *>(sF1 + G::RH * NT);
+  const int ntx = (io.W + G::TW - 1) / G::TW;
+  const int nty = (io.H + TH - 1) / TH;
+  const int ntiles = ntx * nty;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  prefetch_region<R, NT, TH>(io, (t / ntx) * TH, (t % ntx) * G::TW, sF0);
+  cp_async_commit();
+  // channel constants 1/sqrt(n), sqrt(n), correctly rounded, once per CTA
+  for (int n = threadIdx.x; n <= fc.N; n += NT)
+    sRS[n] = make_float2(n > 0 ? __frsqrt_rn((float)n) : 0.f, __fsqrt_rn((float)n));
+  __syncthreads();
+  int buf = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int next = t + gridDim.x;
+    float *cur = buf ? sF1 : sF0;
+    if (next < ntiles) {
+      prefetch_region<R, NT, TH>(io, (next / ntx) * TH, (next % ntx) * G::TW, buf ? sF0 : sF1);
+      cp_async_commit();
+      cp_async_wait<1>();  // the current tile's copies are complete
+    } else {
+      cp_async_wait<0>();
+    }
+    gpa_fwd_tile_fixed<KIND, R, NT, TH>(io, fc, (t / ntx) * TH, (t % ntx) * G::TW, cur, sV, sC,
+                                        sRS);
+    buf ^= 1;
   }
 }
 

@@ -2,6 +2,7 @@
 // kernels, tile-variant dispatch and the tile autotuner.
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bf_internal.h"
@@ -23,13 +24,12 @@ __global__ void __launch_bounds__(NT) gpa_fwd_kernel(const __grid_constant__ Fwd
                                              blockIdx.x * TW, smem);
 }
 
-// Compile-time-radius kernel (gpa_fixed.cuh): 256 threads, 16-row tiles.
+// Compile-time-radius kernel (gpa_fixed.cuh): persistent, 256 threads,
+// 16-row tiles, double-buffered region copies.
 template <int KIND, int R>
 __global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constant__ FwdArgs args) {
   extern __shared__ __align__(16) float smem[];
-  using G = bfk::FixedGeom<R, 256, 16>;
-  bfk::gpa_fwd_tile_fixed<KIND, R, 256, 16>(args.io, args.fc, blockIdx.y * 16, blockIdx.x * G::TW,
-                                            smem);
+  bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16>(args.io, args.fc, smem);
 }
 
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
@@ -76,16 +76,26 @@ int default_variant(const bfi::FilterConsts &fc, bool store) {
 template <int KIND, int R>
 bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   using G = bfk::FixedGeom<R, 256, 16>;
-  const size_t smem = G::smem_bytes();
+  const size_t smem = G::smem_bytes(args.fc.N);
   auto kern = gpa_fwd_fixed_kernel<KIND, R>;
-  static bool configured = false;
-  if (!configured) {
+  // resident CTAs (per SM x SMs) for this shared-memory size, cached
+  static size_t cached_smem = 0;
+  static int resident = 0;
+  if (smem != cached_smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)G::smem_bytes(BF_MAX_ORDER));
+    int per_sm = 0, sms = 0, dev = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = true;
+    if (per_sm < 1) return BF_ERR_UNSUPPORTED;
+    resident = per_sm * sms;
+    cached_smem = smem;
   }
-  dim3 grid((args.io.W + G::TW - 1) / G::TW, (args.io.H + 15) / 16);
+  const long long tiles = (long long)((args.io.W + G::TW - 1) / G::TW) * ((args.io.H + 15) / 16);
+  if (tiles > 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
+  const int grid = (int)std::min<long long>(tiles, resident);
   kern<<<grid, 256, smem, s>>>(args);
   return bfi::check_launch();
 }
