@@ -179,8 +179,8 @@ bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const f
  *    each call writes every entry it reads, so nothing needs clearing, but
  *    calls that overlap on the GPU (e.g. on two streams) race on it.
  *  - An image that needs more than 65536 partial sums (one per CTA of the
- *    backward grid: roughly beyond 1.1e8 pixels at W = 9, e.g. above
- *    10000 x 10000) is rejected with BF_ERR_UNSUPPORTED before any
+ *    backward grid: roughly beyond 5.7e7 pixels at W = 9, e.g. above
+ *    7500 x 7500) is rejected with BF_ERR_UNSUPPORTED before any
  *    GPU work.  Nothing here calls cudaMalloc, cudaFree or any allocating
  *    library routine. */
 bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_out, const float *d_qaux,

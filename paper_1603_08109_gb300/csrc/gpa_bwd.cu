@@ -323,13 +323,17 @@ template <int R, int NT, int TH>
 struct BwdFixedGeom {
   static constexpr int RH = TH + 2 * R;
   static constexpr int TW = NT - 2 * R;
-  static constexpr int KH = 16;
+  static constexpr int KH = TH >= 16 ? 16 : 8;
   static constexpr int IPT = TH / KH;
   static constexpr int L = 2 * R + 1;
-  // Row pitch = 17 (mod 32): the 16 rows of one half-warp and the next
-  // segment (+16 columns) of the other half fall in 32 distinct banks.
-  static constexpr int VP = NT + KH + 1;
-  static_assert(VP % 32 == 17, "phase-H row pitch must be 17 mod 32");
+  // Phase-H lanes: (row = lane % TH, segment = lane / TH), segments KH
+  // columns apart.  Row pitch 17 (mod 32) for 16-row tiles (two segments of
+  // 16 rows per warp), 1 (mod 32) for 8-row tiles (four segments of 8 rows):
+  // every lane of a warp falls in its own bank.  Reads run up to column
+  // NT + KH - 2.
+  static constexpr int VP = TH >= 16 ? NT + 17 : NT + 33;
+  static_assert(VP % 32 == (TH >= 16 ? 17 : 1), "phase-H row pitch");
+  static_assert(VP >= NT + KH - 1, "phase-H window reads stay inside the row");
   static constexpr size_t smem_bytes() {
     return (3 * (size_t)TH * VP + (size_t)RH * NT) * sizeof(float) +
            (size_t)RH * NT * sizeof(float2);
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   }
 }
 
-constexpr int kBwdFixedNT = 128, kBwdFixedTH = 16;
+constexpr int kBwdFixedNT = 128, kBwdFixedTH = 8;
 bool bwd_fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 
 template <int KIND, int R>
@@ -633,7 +637,13 @@ bf_status workspace_bytes(int height, int width, const bf_params *p, size_t *byt
   if (v < 0) return BF_ERR_UNSUPPORTED;
   dim3 g;
   grid_for(v, *fc, height, width, &g);
-  *bytes = (size_t)g.x * g.y * sizeof(double);
+  size_t ctas = (size_t)g.x * g.y;
+  if (bwd_fixed_radius(fc->R)) {  // room for either kernel's per-CTA partials
+    const size_t fx = (size_t)((width + kBwdFixedNT - 2 * fc->R - 1) / (kBwdFixedNT - 2 * fc->R)) *
+                      ((height + kBwdFixedTH - 1) / kBwdFixedTH);
+    ctas = fx > ctas ? fx : ctas;
+  }
+  *bytes = ctas * sizeof(double);
   if (var) *var = v;
   return BF_OK;
 }
@@ -664,14 +674,20 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   A.W = width;
   A.pitch = pitch;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // The compile-time-radius kernel has the geometry of variant 0 (128 threads,
-  // 16-row tiles), so the partial-sum count (workspace size) is the same.
-  if (!abar && v == 0 && bwd_fixed_radius(A.fc.R))
+  // The reduction sums exactly the partials of the grid that was launched.
+  int ctas = 0;
+  if (!abar && bwd_fixed_radius(A.fc.R)) {
     st = A.fc.kind == BF_SPATIAL_GAUSS ? launch_bwd_fixed<1>(A, s) : launch_bwd_fixed<0>(A, s);
-  else
+    const int TWf = kBwdFixedNT - 2 * A.fc.R;
+    ctas = ((width + TWf - 1) / TWf) * ((height + kBwdFixedTH - 1) / kBwdFixedTH);
+  } else {
     st = abar ? dispatch_bwd<true>(v, A, s) : dispatch_bwd<false>(v, A, s);
+    dim3 g;
+    grid_for(v, A.fc, height, width, &g);
+    ctas = (int)(g.x * g.y);
+  }
   if (st != BF_OK || !gsigma) return st;
-  reduce_partials<<<1, 256, 0, s>>>(A.partials, (int)(need / sizeof(double)), gsigma);
+  reduce_partials<<<1, 256, 0, s>>>(A.partials, ctas, gsigma);
   return bfi::check_launch();
 }
 
