@@ -65,8 +65,11 @@ def _load():
         lib.orc_gpa_alg2_at.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_double, ip, ip,
                                         ctypes.c_long, dp, dp, dp]
+        lib.orc_joint_filter.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, dp,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ip, ip, ctypes.c_long, dp, dp, dp]
         for fn in ("orc_spatial_kernel", "orc_range_filter", "orc_range_filter_grad",
-                   "orc_gpa_alg2", "orc_gpa_alg2_at"):
+                   "orc_gpa_alg2", "orc_gpa_alg2_at", "orc_joint_filter"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -141,6 +144,40 @@ def gpa_definition(img, w, sigma_r, N, T=128.0, samples=None, return_parts=False
     brute force. Parts: num = P_2, den = Q_2 of App. C."""
     out, num, den = _range_filter(1, img, w, sigma_r, N, T, samples)
     return (out, num, den) if return_parts else out
+
+
+def _joint(kind, img, guide, w, sigma_r, N, T, samples):
+    f = _f64(img)
+    e = _f64(guide)
+    assert f.shape == e.shape
+    H, W = f.shape
+    r = (w.shape[0] - 1) // 2
+    ys, xs, ns = _samples(samples)
+    n = ns if ys is not None else H * W
+    out = np.empty(n)
+    num = np.empty(n)
+    den = np.empty(n)
+    rc = _load().orc_joint_filter(kind, _dp(f), _dp(e), H, W, _dp(np.ascontiguousarray(w)), r,
+                                  float(sigma_r), int(N), float(T), _ip(ys), _ip(xs), ns,
+                                  _dp(out), _dp(num), _dp(den))
+    _check(rc, "joint_filter")
+    if ys is None:
+        return out.reshape(H, W), num.reshape(H, W), den.reshape(H, W)
+    return out, num, den
+
+
+def joint_direct(img, guide, w, sigma_r, T=128.0, samples=None, return_parts=False):
+    """Cross (joint) bilateral filter (Sec. I, Sec. V): exact Gaussian range
+    kernel on the guide, average of img."""
+    res = _joint(0, img, guide, w, sigma_r, 1, T, samples)
+    return res if return_parts else res[0]
+
+
+def joint_gpa(img, guide, w, sigma_r, N, T=128.0, samples=None, return_parts=False):
+    """Cross bilateral filter with the range kernel replaced by phi_N
+    (eq. GaussPolynomial) on guide values, brute force."""
+    res = _joint(1, img, guide, w, sigma_r, N, T, samples)
+    return res if return_parts else res[0]
 
 
 def gpa_alg2(img, w, sigma_r, N, T=128.0, return_parts=False, return_planes=False):

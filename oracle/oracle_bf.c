@@ -177,6 +177,60 @@ int orc_range_filter(int kind, const double *f, int H, int W, const double *w, i
     return bad ? ORC_NONFINITE : ORC_OK;
 }
 
+/* Cross (joint) bilateral filter, the extension named in Sec. I and Sec. V:
+ * the range kernel compares guide values e while the data f is averaged,
+ *   out(i) = T + sum_j w(j) k(e(i-j)-T, e(i)-T) (f(i-j)-T) / sum_j w(j) k(...),
+ * with k the exact Gaussian range kernel (kind 0) or phi_N (kind 1, the
+ * Gaussian-polynomial approximation of eq. GaussPolynomial).  Same sample
+ * conventions as orc_range_filter; num/den may be NULL. */
+int orc_joint_filter(int kind, const double *f, const double *e, int H, int W, const double *w,
+                     int r, double sr, int N, double T, const int *iy, const int *ix, long nsamp,
+                     double *out, double *num, double *den)
+{
+    if (!f || !e || !w || !out || H < 1 || W < 1 || r < 0 || !(sr > 0.0)) return ORC_BAD_ARG;
+    if (kind != 0 && kind != 1) return ORC_BAD_ARG;
+    if (kind == 1 && N < 1) return ORC_BAD_ARG;
+    int S = 2 * r + 1;
+    long npix = (long)H * W;
+    long count = iy ? nsamp : npix;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (long k = 0; k < count; ++k) {
+        int y, x;
+        if (iy) {
+            y = iy[k];
+            x = ix[k];
+        } else {
+            y = (int)(k / W);
+            x = (int)(k % W);
+        }
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            bad |= 2;
+            continue;
+        }
+        double tau = e[IDX(y, x, W)] - T, nsum = 0.0, dsum = 0.0, d[4];
+        for (int dy = -r; dy <= r; ++dy) {
+            int yy = y - dy;
+            if (yy < 0 || yy >= H) continue;
+            for (int dx = -r; dx <= r; ++dx) {
+                int xx = x - dx;
+                if (xx < 0 || xx >= W) continue;
+                range_kernel(kind, e[IDX(yy, xx, W)] - T, tau, sr, N, d);
+                double wk = w[(dy + r) * S + (dx + r)];
+                nsum += wk * d[0] * (f[IDX(yy, xx, W)] - T);
+                dsum += wk * d[0];
+            }
+        }
+        double o = T + nsum / dsum;
+        out[k] = o;
+        if (num) num[k] = nsum;
+        if (den) den[k] = dsum;
+        if (!isfinite(o)) bad |= 1;
+    }
+    if (bad & 2) return ORC_BAD_ARG;
+    return bad ? ORC_NONFINITE : ORC_OK;
+}
+
 /* Gradient of the same ratio with respect to the input image and sigma_r,
  * for a loss with d(loss)/d(out) = gout.  Exact partial derivatives of the
  * definition (chain rule on the ratio), evaluated brute force:

@@ -57,6 +57,19 @@ def test_fast_backward_matches_exact_derivatives(case):
     assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (5, 7), (3, 300), (260, 3)])
+def test_fast_backward_tiny_and_thin_images(shape):
+    """Radius beyond the image, single rows/columns, ragged tiles: both the
+    compile-time-radius (W=9) and the runtime-radius (W=12) backward."""
+    img = image(*shape, seed=7, block=2)
+    g = synth.random_like(shape, seed=8)
+    for kind, r, ss, sr, N in ((bf.GAUSS, 9, 3.0, 30.0, 40), (bf.BOX, 12, 0.0, 30.0, 44)):
+        gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+        rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
+        assert _rel(gin, rgin) <= GIN_RTOL, (shape, kind)
+        assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs) + 1e-9, (shape, kind)
+
+
 def test_fast_backward_deterministic_and_autograd():
     img = image(40, 200, seed=3)
     g = synth.random_like(img.shape, seed=4)
