@@ -292,7 +292,7 @@ def run_sweeps(args):
     import paper_1603_08109_gb300 as bf
     from paper_1603_08109_gb300 import synth
     names = set(args.sweep.split(",")) if args.sweep != "all" else {
-        "grid2048", "roofline4096", "large8192", "batch256", "grad512"}
+        "grid2048", "roofline4096", "large8192", "batch256", "grad512", "joint2048"}
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -388,6 +388,24 @@ def run_sweeps(args):
               "per_image_launches_ms": lms, "per_image_mpx_s": px / lms / 1e3,
               "N_range": [min(s["N"] for s in specs), max(s["N"] for s in specs)]})
         plan.close()
+    if "joint2048" in names:
+        # cross (joint) filter: 2048^2 blocks(64) image, gradient+polygons guide
+        x = torch.from_numpy(synth.blocks_image(2048, 2048, 64, 10.0, seed=1000)).to(dev)
+        e = torch.from_numpy(synth.gradient_polygons_image(2048, 2048, 64, 15.0, seed=1001)).to(dev)
+        o = torch.empty_like(x)
+        d = torch.empty_like(x)
+        for kind, R, ss, sr in ((bf.GAUSS, 9, 3.0, 30.0), (bf.GAUSS, 30, 10.0, 30.0),
+                                (bf.BOX, 20, 0.0, 30.0)):
+            N = bf.order_from_delta(kind, R, ss, sr, 1.0)
+            fms = _time_ms(lambda: bf.joint_forward(x, e, kind, sr, N, radius=R, sigma_s=ss, out=o),
+                           5, stream, flush)
+            dms = _time_ms(lambda: bf.joint_direct(x, e, kind, sr, radius=R, sigma_s=ss, out=d),
+                           3, stream, flush)
+            emit({"sweep": "joint2048", "kind": "box" if kind == 0 else "gaussian", "radius": R,
+                  "sigma_r": sr, "N": N, "fast_fwd_ms": fms, "fast_fwd_mpx_s": 4.194304 / fms * 1e3,
+                  "direct_fwd_ms": dms, "direct_fwd_mpx_s": 4.194304 / dms * 1e3,
+                  "speedup_vs_direct": dms / fms,
+                  "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max())})
     if "grad512" in names:
         # 32 x 512^2, Gaussian sigma_s=5 (W=15), sigma_r=25, N from delta=1: fwd+bwd
         N = bf.order_from_delta(bf.GAUSS, 15, 5.0, 25.0, 1.0)

@@ -205,6 +205,24 @@ bf_status bf_direct_backward(const float *d_in, const float *d_gout, float *d_gi
                              const bf_params *p, void *d_workspace,
                              size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------ cross (joint) filter
+ * The cross (joint) bilateral filter, named as an extension in Sec. I and
+ * Sec. V: the range kernel compares a guide image e while the data f is
+ * averaged,
+ *   out(i) = t_c + sum_j w(j) k(e(i-j), e(i)) (f(i-j) - t_c) / sum_j w(j) k(e(i-j), e(i)).
+ * bf_joint_forward uses k = phi_N on centred guide values (eq. GaussPolynomial):
+ * with b_n the guide's rescaled power images, out = t_c + U'/Q',
+ * Q' = sum_{n<N} b_n (w*b_n), U' = sum_{n<N} b_n (w*(b_n (f - t_c))): 2N
+ * spatial filterings in one fused pass.  For e = f it equals bf_fast_forward.
+ * d_qaux (optional) receives Q' as in bf_fast_forward.  The guide follows the
+ * image's layout (same height, width, pitch).  Radius limit: W <= 56.
+ * bf_joint_direct computes the same filter with the exact Gaussian range
+ * kernel, O((2W+1)^2) per pixel (the same-GPU comparison). */
+bf_status bf_joint_forward(const float *d_in, const float *d_guide, float *d_out, float *d_qaux,
+                           int height, int width, int pitch, const bf_params *p, void *stream);
+bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out, int height,
+                          int width, int pitch, const bf_params *p, void *stream);
+
 /* --------------------------------------------------- batched forward
  * Many images of uneven sizes, each with its own spatial kind, W, sigma_s,
  * sigma_r and N, filtered by ONE persistent launch: CTAs take output tiles

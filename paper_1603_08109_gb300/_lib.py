@@ -60,6 +60,8 @@ SIGNATURES = {
                                      _vp, _sz, _vp]),
     "bf_fast_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp]),
     "bf_direct": (_i, [_vp, _vp, _i, _i, _i, _pp, _vp]),
+    "bf_joint_forward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp]),
+    "bf_joint_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp]),
     "bf_direct_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_direct_backward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_batch_plan_create": (_i, [ctypes.POINTER(BfImageDesc), _i, ctypes.POINTER(_vp)]),

@@ -20,6 +20,7 @@ __all__ = [
     "gpa_forward_stored", "gpa_backward", "direct", "direct_backward", "GPABilateral",
     "DirectBilateral", "gpa_bilateral", "direct_bilateral", "BatchPlan", "autotune",
     "variant_count", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
+    "joint_forward", "joint_direct",
 ]
 
 
@@ -177,6 +178,47 @@ def direct(img: torch.Tensor, kind: int, sigma_r: float, radius: int = 0, sigma_
     H, W = x.shape
     check(lib().bf_direct(_ptr(x), _ptr(o), H, W, x.stride(0), ctypes.byref(p), _stream(x.device)),
           "bf_direct")
+    return o.cpu() if on_cpu else o
+
+
+def _guide_like(x: torch.Tensor, guide: torch.Tensor) -> torch.Tensor:
+    g, _ = _as_device_image(guide)
+    if g.shape != x.shape or g.device != x.device:
+        raise ValueError("guide must have the image's shape and device")
+    if g.stride() != x.stride():
+        g = torch.empty_strided(x.shape, x.stride(), dtype=x.dtype, device=x.device).copy_(g)
+    return g
+
+
+def joint_forward(img: torch.Tensor, guide: torch.Tensor, kind: int, sigma_r: float, N: int,
+                  radius: int = 0, sigma_s: float = 0.0, t_c: float = 128.0,
+                  return_q: bool = False, out: Optional[torch.Tensor] = None):
+    """Cross (joint) bilateral filter, Gaussian-polynomial form (range kernel on guide)."""
+    x, on_cpu = _as_device_image(img)
+    g = _guide_like(x, guide)
+    o = _image_like(x, out if not on_cpu else None)
+    q = _like(x) if return_q else None
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    H, W = x.shape
+    check(lib().bf_joint_forward(_ptr(x), _ptr(g), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                 ctypes.byref(p), _stream(x.device)), "bf_joint_forward")
+    if on_cpu:
+        o = o.cpu()
+        q = q.cpu() if q is not None else None
+    return (o, q) if return_q else o
+
+
+def joint_direct(img: torch.Tensor, guide: torch.Tensor, kind: int, sigma_r: float,
+                 radius: int = 0, sigma_s: float = 0.0, t_c: float = 128.0,
+                 out: Optional[torch.Tensor] = None):
+    """Cross (joint) bilateral filter with the exact range kernel (comparison)."""
+    x, on_cpu = _as_device_image(img)
+    g = _guide_like(x, guide)
+    o = _image_like(x, out if not on_cpu else None)
+    p = _params(kind, radius, sigma_s, sigma_r, 1, t_c)
+    H, W = x.shape
+    check(lib().bf_joint_direct(_ptr(x), _ptr(g), _ptr(o), H, W, x.stride(0), ctypes.byref(p),
+                                _stream(x.device)), "bf_joint_direct")
     return o.cpu() if on_cpu else o
 
 
