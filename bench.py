@@ -292,7 +292,7 @@ def run_sweeps(args):
     import paper_1603_08109_gb300 as bf
     from paper_1603_08109_gb300 import synth
     names = set(args.sweep.split(",")) if args.sweep != "all" else {
-        "grid2048", "roofline4096", "large8192", "batch256", "grad512", "joint2048"}
+        "grid2048", "roofline4096", "large8192", "batch256", "grad512", "joint2048", "tightness"}
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -388,6 +388,21 @@ def run_sweeps(args):
               "per_image_launches_ms": lms, "per_image_mpx_s": px / lms / 1e3,
               "N_range": [min(s["N"] for s in specs), max(s["N"] for s in specs)]})
         plan.close()
+    if "tightness" in names:
+        # Fig. tightness: orders from Chebyshev / Chernoff / exact Poisson / exhaustive grid
+        # search, and the grid sup-norm error each order achieves (1025^2 grid of [-T, T]^2)
+        for eps in (0.1, 1e-3):
+            for sr in (10.0, 20.0, 30.0, 40.0, 50.0, 60.0):
+                ch, cn, po = bf.order_estimates(sr, eps, 128.0)
+                ex = bf.exhaustive_order(sr, eps, 128.0, grid=1025)
+                t0 = time.perf_counter()
+                errs = {k: bf.kernel_error_max(n, sr, 128.0, 1025)
+                        for k, n in (("chebyshev", ch), ("chernoff", cn), ("poisson", po),
+                                     ("exhaustive", ex))}
+                gpu_s = (time.perf_counter() - t0) / 4
+                emit({"sweep": "tightness", "eps": eps, "sigma_r": sr, "N_chebyshev": ch,
+                      "N_chernoff": cn, "N_poisson": po, "N_exhaustive": ex,
+                      "grid_error": errs, "s_per_grid_eval_gpu": gpu_s})
     if "joint2048" in names:
         # cross (joint) filter: 2048^2 blocks(64) image, gradient+polygons guide
         x = torch.from_numpy(synth.blocks_image(2048, 2048, 64, 10.0, seed=1000)).to(dev)

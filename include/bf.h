@@ -104,6 +104,22 @@ bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out);
 bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r,
                               float delta, float T, int *N_out);
 
+/* -------------------------------------------- kernel-error analysis (Sec. II)
+ * bf_kernel_error_max: sup-norm of the kernel error (eq. Linf),
+ *   max |g(t - tau) - phi_N(t, tau)|  (eq. error)
+ * over a grid x grid lattice of [-T, T]^2 (end points included), evaluated
+ * in double precision on the GPU; writes one double to d_out (device).
+ * BF_ERR_INVALID_ARG for N < 1, sigma_r <= 0, T <= 0, grid outside [1, 65536].
+ * bf_order_estimates (host only): for a kernel-error budget eps in (0, 1),
+ * the Chebyshev order (eq. cheby2), the Chernoff order (eq. LambW, the
+ * root of nu above lambda = T^2/sigma_r^2, App. A) and the exact Poisson
+ * order (smallest N with P(X >= N) <= eps, Prop. upperBound); any output
+ * pointer may be NULL. */
+bf_status bf_kernel_error_max(int N, double sigma_r, double T, int grid, double *d_out,
+                              void *stream);
+bf_status bf_order_estimates(double sigma_r, double eps, double T, int *N_chebyshev,
+                             int *N_chernoff, int *N_poisson);
+
 /* ---------------------------------------------------------- fast forward
  * f_GPA of eq. GPA via Algorithm 2 (eqs. intImg, spatialFiltering, PbyQ,
  * P, Q), fused: each output tile reads its input tile plus a W-pixel halo

@@ -20,7 +20,7 @@ __all__ = [
     "gpa_forward_stored", "gpa_backward", "direct", "direct_backward", "GPABilateral",
     "DirectBilateral", "gpa_bilateral", "direct_bilateral", "BatchPlan", "autotune",
     "variant_count", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
-    "joint_forward", "joint_direct",
+    "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
 ]
 
 
@@ -45,6 +45,40 @@ def order_from_delta(kind: int, radius: int, sigma_s: float, sigma_r: float, del
     check(lib().bf_order_from_delta(int(kind), int(radius), float(sigma_s), float(sigma_r),
                                     float(delta), float(T), ctypes.byref(n)), "bf_order_from_delta")
     return n.value
+
+
+def order_estimates(sigma_r: float, eps: float, T: float = 128.0):
+    """(Chebyshev, Chernoff, exact Poisson) orders for kernel-error budget eps."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().bf_order_estimates(float(sigma_r), float(eps), float(T), ctypes.byref(a),
+                                   ctypes.byref(b), ctypes.byref(c)), "bf_order_estimates")
+    return a.value, b.value, c.value
+
+
+def kernel_error_max(N: int, sigma_r: float, T: float = 128.0, grid: int = 1025,
+                     device="cuda") -> float:
+    """sup |g - phi_N| over a grid x grid lattice of [-T, T]^2 (eq. Linf), on the GPU."""
+    out = torch.empty(1, dtype=torch.float64, device=device)
+    check(lib().bf_kernel_error_max(int(N), float(sigma_r), float(T), int(grid), _ptr(out),
+                                    _stream(out.device)), "bf_kernel_error_max")
+    return float(out.item())
+
+
+def exhaustive_order(sigma_r: float, eps: float, T: float = 128.0, grid: int = 1025) -> int:
+    """Smallest N whose grid sup-norm kernel error is <= eps (the 'exhaustive
+    search' order of Sec. II-B), found by bisection between 1 and the exact
+    Poisson order (the error decreases with N)."""
+    _, _, hi = order_estimates(sigma_r, eps, T)
+    lo = 1
+    if kernel_error_max(lo, sigma_r, T, grid) <= eps:
+        return lo
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if kernel_error_max(mid, sigma_r, T, grid) <= eps:
+            hi = mid
+        else:
+            lo = mid
+    return hi
 
 
 def _stream(dev: torch.device) -> ctypes.c_void_p:

@@ -119,3 +119,18 @@ def test_tuning_table_roundtrip():
     api.tuning_set(1, rb, ob, old)
     with pytest.raises(Exception):
         api.tuning_set(1, rb, ob, nv)
+
+
+def test_library_order_estimates_match_checker():
+    """bf_order_estimates (C++, own root finder and tail sum) vs the
+    checker's Chebyshev formula, Lambert-W order and Poisson order."""
+    from oracle import order
+    from paper_1603_08109_gb300 import api
+    for sr in (10.0, 17.0, 30.0, 55.0):
+        lam = (128.0 / sr) ** 2
+        for eps in (1e-1, 1e-3, 1e-7):
+            ch, cn, po = api.order_estimates(sr, eps, 128.0)
+            assert ch == order.chebyshev_order(lam, eps)
+            assert cn == order.chernoff_order_lambertw(lam, eps)[0]
+            assert po == order.poisson_order(lam, eps)
+            assert po <= cn <= ch or eps > 0.05
