@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "bf_internal.h"
+#include "box_stream.cuh"
 #include "gpa_fixed.cuh"
 #include "gpa_tile.cuh"
 
@@ -32,18 +33,33 @@ __global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constan
   bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16>(args.io, args.fc, smem);
 }
 
+// Streaming box kernel for small N (box_stream.cuh): strips of 240 columns,
+// bands of 64 rows.
+template <int R, int NN>
+__global__ void __launch_bounds__(256) box_stream_kernel(const __grid_constant__ bfk::StreamArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  using G = bfk::StreamGeom<R, NN>;
+  const int yo0 = blockIdx.y * G::BAND;
+  bfk::box_stream_band<R, NN>(A, blockIdx.x * G::TW, yo0, min(A.io.H, yo0 + G::BAND), smem);
+}
+
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
 // columns, output rows per tile).  Variant 5: the compile-time-radius kernel
 // for the radii in kFixedRadii (forward without stored planes only).
+// Variant 6: the streaming box kernel (box, W in {3, 5}, N <= 5).
 struct Variant {
   int NT, TH;
 };
 constexpr Variant kVariants[] = {{256, 16}, {512, 8}, {256, 8}, {128, 16}, {192, 8}};
 constexpr int kNumGeneric = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kFixedVariant = kNumGeneric;
-constexpr int kNumVariants = kNumGeneric + 1;
+constexpr int kStreamVariant = kNumGeneric + 1;
+constexpr int kNumVariants = kNumGeneric + 2;
 
 bool fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
+bool stream_fits(const bfi::FilterConsts &fc) {
+  return fc.kind == BF_SPATIAL_BOX && (fc.R == 3 || fc.R == 5) && fc.N >= 1 && fc.N <= 5;
+}
 
 int max_smem_optin() {
   static int v = -1;
@@ -60,6 +76,7 @@ int max_smem_optin() {
 
 bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
   if (v == kFixedVariant) return !store && fixed_radius(fc.R);
+  if (v == kStreamVariant) return !store && stream_fits(fc);
   const Variant &var = kVariants[v];
   const int TW = var.NT - 2 * fc.R;
   if (TW < var.TH) return false;
@@ -67,7 +84,7 @@ bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
 }
 
 int default_variant(const bfi::FilterConsts &fc, bool store) {
-  static const int order[] = {kFixedVariant, 0, 2, 4, 3, 1};
+  static const int order[] = {kStreamVariant, kFixedVariant, 0, 2, 4, 3, 1};
   for (int v : order)
     if (variant_fits(v, fc, store)) return v;
   return -1;
@@ -98,6 +115,50 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   const int grid = (int)std::min<long long>(tiles, resident);
   kern<<<grid, 256, smem, s>>>(args);
   return bfi::check_launch();
+}
+
+template <int R, int NN>
+bf_status launch_stream_rn(const FwdArgs &a, cudaStream_t s) {
+  using G = bfk::StreamGeom<R, NN>;
+  bfk::StreamArgs A;
+  A.io = a.io;
+  A.fc = a.fc;
+  for (int n = 0; n < 8; ++n) {
+    A.rsq[n] = n > 0 ? (float)(1.0 / sqrt((double)n)) : 0.f;
+    A.sq[n] = (float)sqrt((double)n);
+  }
+  const bool out_al = (reinterpret_cast<uintptr_t>(a.io.out) & 15u) == 0;
+  const bool q_al = !a.io.qaux || (reinterpret_cast<uintptr_t>(a.io.qaux) & 15u) == 0;
+  A.vec_ok = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  auto kern = box_stream_kernel<R, NN>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem_bytes());
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    configured = true;
+  }
+  dim3 grid((a.io.W + G::TW - 1) / G::TW, (a.io.H + G::BAND - 1) / G::BAND);
+  kern<<<grid, G::NT, G::smem_bytes(), s>>>(A);
+  return bfi::check_launch();
+}
+
+template <int R>
+bf_status launch_stream_r(const FwdArgs &a, cudaStream_t s) {
+  switch (a.fc.N + 1) {
+    case 2: return launch_stream_rn<R, 2>(a, s);
+    case 3: return launch_stream_rn<R, 3>(a, s);
+    case 4: return launch_stream_rn<R, 4>(a, s);
+    case 5: return launch_stream_rn<R, 5>(a, s);
+    case 6: return launch_stream_rn<R, 6>(a, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
+}
+
+bf_status launch_stream(const FwdArgs &a, cudaStream_t s) {
+  if (a.fc.R == 3) return launch_stream_r<3>(a, s);
+  if (a.fc.R == 5) return launch_stream_r<5>(a, s);
+  return BF_ERR_UNSUPPORTED;
 }
 
 template <int KIND>
@@ -134,6 +195,10 @@ bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
   if (v == kFixedVariant) {
     if (STORE) return BF_ERR_UNSUPPORTED;
     return g ? launch_fixed<1>(a, s) : launch_fixed<0>(a, s);
+  }
+  if (v == kStreamVariant) {
+    if (STORE) return BF_ERR_UNSUPPORTED;
+    return launch_stream(a, s);
   }
   switch (v) {
     case 0: return g ? launch_fwd<1, 256, 16, STORE>(a, s) : launch_fwd<0, 256, 16, STORE>(a, s);

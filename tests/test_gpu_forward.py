@@ -65,6 +65,26 @@ def test_every_tile_variant(variant):
     assert ran >= 2
 
 
+@pytest.mark.parametrize("r", [3, 5])
+def test_streaming_box_kernel(r):
+    """Variant 6 (streaming box, N <= 5): several strips and 64-row bands with
+    ragged tails, every supported N, aligned (vector stores) and odd-pitch
+    (scalar stores) outputs."""
+    H, W = 150, 500
+    img = image(H, W, seed=40 + r)
+    for sr, N in ((40.0, 1), (40.0, 2), (60.0, 3), (80.0, 5), (30.0, 4)):
+        ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, sr, N)
+        out, q = _run(img, bf.BOX, r, 0.0, sr, N, variant=6)
+        compare_forward(out, q, ro, rq, w0, "stream r=%d N=%d" % (r, N), sigma_r=sr, N=N)
+    base = torch.zeros((H, W + 1), dtype=torch.float32, device="cuda")
+    base[:, :W] = torch.from_numpy(img).cuda()
+    o = bf.gpa_forward(base[:, :W], bf.BOX, 60.0, 3, radius=r, variant=6)
+    ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, 60.0, 3)
+    compare_forward(o.cpu().numpy(), None, ro, rq, w0, "stream odd pitch", sigma_r=60.0, N=3)
+    with pytest.raises(bf._lib.BFError):
+        bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=6)
+
+
 @pytest.mark.parametrize("r", [3, 5, 9, 15])
 def test_fixed_radius_kernel(r):
     """The compile-time-radius kernel at every radius it is built for, both
