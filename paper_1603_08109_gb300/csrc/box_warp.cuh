@@ -1,0 +1,337 @@
+// Warp-strip streaming forward for the box spatial kernel at small order
+// (N <= 5) and small radius (W <= 8): the memory-bound regime of Algorithm 2.
+//
+// Each warp owns a strip of 256 region columns, 8 consecutive columns per
+// lane (lanes 1..30 produce the strip's 240 output columns, lanes 0 and 31
+// carry the W-column halos), and a band of output rows.  It streams down the
+// band two rows at a time with no block barrier and no value passed through
+// shared memory from one thread to another:
+//   * input rows are copied with cp.async into a per-lane ring in shared
+//     memory one row pair ahead of use; every lane reads back only the bytes
+//     it copied itself;
+//   * per column and channel n the running vertical window sum
+//     V_n = sum of u_n over the 2W + 1 rows of the window stays in registers,
+//     u_n = e^{-H^2/2} H^n being the power image F_n of Algorithm 2 (unscaled:
+//     |u_n| <= (n/e)^{n/2} <= 4.6 for n <= 5).  A row leaving the window is
+//     regenerated from its ring entry by the same instructions that produced
+//     it on entry, so what is subtracted is bitwise what was added;
+//   * horizontal window sums S_n take the W halo columns of the neighbouring
+//     lanes by warp shuffles;
+//   * Algorithm 2's sums at the centre pixel are P = sum_{n<N} H^n S_{n+1}/n!
+//     and Q = sum_{n<N} H^n S_n/n! (Horner form); the centre's factor
+//     e^{-H^2/2} of Q' and P' cancels in f_GPA = t_c + sigma_r P/Q and is
+//     computed only when Q' = e^{-H^2/2} Q w(0) is requested.
+// Column pairs go through the packed two-lane FP32 instructions (fma / add /
+// mul on float2, each lane rounded exactly as the scalar operation).
+// Out-of-image columns of the ring hold a sentinel intensity whose u_n are
+// exactly 0 (zero extension of the power images); out-of-image rows are
+// skipped by warp-uniform branches.  Strips and bands that touch no image
+// edge run a loop without any of these checks.
+#pragma once
+
+#include "gpa_fixed.cuh"
+#include "gpa_tile.cuh"
+
+namespace bfk {
+
+struct WarpStripArgs {
+  TileIO io;
+  float tc, sr;
+  float kg, kg0;    // g = f kg + kg0 = (f - t_c) sqrt(log2(e)/2) / sigma_r; u_0 = 2^(-g^2)
+  float hs, hs0;    // H = f hs + hs0 = (f - t_c) / sigma_r
+  float qscale;     // w(0) = 1 / (2W + 1)^2: normalised Q'
+  float sentinel;   // intensity with u_n = 0 exactly (t_c + 1e4 sigma_r)
+  float inv_n[8];   // 1 / n (entry 0 unused)
+  int band;         // output rows per warp (even)
+  int nstrips, nbands;
+  int vec_in;       // input rows 16-byte aligned: 16-byte copies
+  int vec_out;      // out (and Q') rows 16-byte aligned: 16-byte stores
+};
+
+template <int R>
+struct WarpStripGeom {
+  static constexpr int C = 8, SW = 32 * C, TW = SW - 2 * C;  // 256 region, 240 output columns
+  static constexpr int L = 2 * R + 1;
+  // ring rows: the L + 2 rows a row pair reads (two leave, two enter) plus
+  // the next pair in flight
+  static constexpr int RS = L + 4;
+  static constexpr size_t warp_floats = (size_t)RS * SW;
+};
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ float ws_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float ws_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Per-warp constants as packed pairs.
+struct WsConst {
+  float2 kg, kg0, hs, hs0;
+};
+
+// u_0 of two intensities: 2^(-g^2) by the hardware base-2 exponential (<= 2 ulp
+// relative).  The same instruction sequence serves a row entering and leaving,
+// so the two results are bitwise equal.
+__device__ __forceinline__ float2 ws_u0(const WsConst &K, float2 f) {
+  const float2 g = __ffma2_rn(f, K.kg, K.kg0);
+  const float2 t = __fmul2_rn(g, g);
+  return make_float2(ws_ex2(-t.x), ws_ex2(-t.y));
+}
+
+__device__ __forceinline__ void ws_load8(const float *slot, float2 (&f)[4]) {
+  const float4 lo = *reinterpret_cast<const float4 *>(slot);
+  const float4 hi = *reinterpret_cast<const float4 *>(slot + 128);
+  f[0] = make_float2(lo.x, lo.y);
+  f[1] = make_float2(lo.z, lo.w);
+  f[2] = make_float2(hi.x, hi.y);
+  f[3] = make_float2(hi.z, hi.w);
+}
+
+// V_n += u_n (ADD) or V_n -= u_n for the 8 intensities of one row.  The
+// subtraction adds the chain started from -u_0, which is exactly -u_n.
+template <int NN, bool ADD>
+__device__ __forceinline__ void ws_update(const WsConst &K, float2 (&V)[NN][4],
+                                          const float2 (&f)[4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float2 u = ws_u0(K, f[p]);
+    if (!ADD) u = make_float2(-u.x, -u.y);
+    const float2 h = __ffma2_rn(f[p], K.hs, K.hs0);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+      if (n > 0) u = __fmul2_rn(u, h);
+      V[n][p] = __fadd2_rn(V[n][p], u);
+    }
+  }
+}
+
+template <int M>
+__device__ __forceinline__ float ws_tree_sum(const float *e) {
+  if constexpr (M == 1) {
+    return e[0];
+  } else {
+    return ws_tree_sum<M / 2>(e) + ws_tree_sum<M - M / 2>(e + M / 2);
+  }
+}
+
+// Box sums over 2W + 1 columns of v at the lane's 8 columns; the W columns on
+// each side come from the neighbouring lanes.
+template <int R>
+__device__ __forceinline__ void ws_hsum(const float2 (&v2)[4], float2 (&S2)[4]) {
+  constexpr unsigned FULL = 0xffffffffu;
+  float v[8];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    v[2 * p] = v2[p].x;
+    v[2 * p + 1] = v2[p].y;
+  }
+  float e[8 + 2 * R];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) e[R + k] = v[k];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    e[k] = __shfl_up_sync(FULL, v[8 - R + k], 1);
+    e[R + 8 + k] = __shfl_down_sync(FULL, v[k], 1);
+  }
+  float S[8];
+  float s = ws_tree_sum<2 * R + 1>(e);
+  S[0] = s;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    s += e[k + 2 * R] - e[k - 1];
+    S[k] = s;
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) S2[p] = make_float2(S[2 * p], S[2 * p + 1]);
+}
+
+// f_GPA (and optionally Q') of one output row from the window sums V and the
+// centre intensities fc.
+template <int R, int NN, bool FULL>
+__device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst &K,
+                                           const float2 (&V)[NN][4], const float2 (&fc)[4],
+                                           int yo, int x0, bool store) {
+  constexpr int N = NN - 1;
+  float2 H[4], Pa[4], Qa[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) H[p] = __ffma2_rn(fc[p], K.hs, K.hs0);
+#pragma unroll
+  for (int m = NN - 1; m >= 0; --m) {
+    float2 S[4];
+    ws_hsum<R>(V[m], S);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (m == N) {
+        Pa[p] = S[p];
+      } else {
+        if (m >= 1) Pa[p] = __ffma2_rn(__fmul2_rn(H[p], f2(A.inv_n[m])), Pa[p], S[p]);
+        Qa[p] = m == N - 1 ? S[p]
+                           : __ffma2_rn(__fmul2_rn(H[p], f2(A.inv_n[m + 1])), Qa[p], S[p]);
+      }
+    }
+  }
+  if (!store) return;
+  const TileIO &io = A.io;
+  float2 o[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    // P/Q by the approximate reciprocal (<= 2 ulp, as __fdividef)
+    const float2 r = __fmul2_rn(Pa[p], make_float2(ws_rcp(Qa[p].x), ws_rcp(Qa[p].y)));
+    o[p] = __ffma2_rn(f2(A.sr), r, f2(A.tc));
+  }
+  float *orow = io.out + (long long)yo * io.pitch + x0;
+  const bool full = FULL || (A.vec_out && x0 + 8 <= io.W);
+  if (full) {
+    reinterpret_cast<float4 *>(orow)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    reinterpret_cast<float4 *>(orow)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (x0 + k < io.W) orow[k] = k & 1 ? o[k / 2].y : o[k / 2].x;
+  }
+  if (io.qaux) {
+    float2 q[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) q[p] = __fmul2_rn(__fmul2_rn(ws_u0(K, fc[p]), Qa[p]), f2(A.qscale));
+    float *qrow = io.qaux + (long long)yo * io.pitch + x0;
+    if (full) {
+      reinterpret_cast<float4 *>(qrow)[0] = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+      reinterpret_cast<float4 *>(qrow)[1] = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (x0 + k < io.W) qrow[k] = k & 1 ? q[k / 2].y : q[k / 2].x;
+    }
+  }
+}
+
+// The band loop.  FAST: every row the loop touches is inside the image and
+// every lane's 8 columns are inside the image with 16-byte aligned rows.
+template <int R, int NN, bool FAST>
+__device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K, float *my,
+                                        int x0, int yo0, int yo1, int cnt0, int cnt1) {
+  using G = WarpStripGeom<R>;
+  constexpr int SW = G::SW, L = G::L, RS = G::RS;
+  const TileIO &io = A.io;
+  const bool vec0 = FAST || (A.vec_in && cnt0 == 4), vec1 = FAST || (A.vec_in && cnt1 == 4);
+  auto issue = [&](int y, int slot) {
+    if (FAST || (y >= 0 && y < io.H)) {
+      const float *src = io.in + (long long)y * io.pitch + x0;
+      float *dst = my + slot * SW;
+      if (vec0) {
+        cp_async16(dst, src);
+      } else {
+        for (int e = 0; e < cnt0; ++e) cp_async4(dst + e, src + e);
+      }
+      if (vec1) {
+        cp_async16(dst + 128, src + 4);
+      } else {
+        for (int e = 0; e < cnt1; ++e) cp_async4(dst + 128 + e, src + 4 + e);
+      }
+    }
+  };
+  auto wrap = [](int s) { return s >= RS ? s - RS : s; };  // s < 2 RS
+
+  float2 V[NN][4];
+#pragma unroll
+  for (int n = 0; n < NN; ++n)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) V[n][p] = make_float2(0.f, 0.f);
+
+  const int lane = threadIdx.x & 31;
+  const bool writer = lane >= 1 && lane <= 30;
+  // region row rho = 0.. is image row yo0 - R + rho and lives in ring slot
+  // rho mod RS; rows rho >= 2W complete the window of output row rho - 2W
+  const int nrows = (yo1 - yo0) + 2 * R;
+  issue(yo0 - R, 0);
+  issue(yo0 - R + 1, 1);
+  cp_async_commit();
+  int s0 = 0;  // slot of row rho
+  for (int rho = 0; rho < nrows; rho += 2) {
+    const int y = yo0 - R + rho;
+    // the next pair goes to the slots of rows rho + 2 - RS and rho + 3 - RS,
+    // which left the window in the previous iteration
+    issue(y + 2, wrap(s0 + 2));
+    issue(y + 3, wrap(s0 + 3));
+    cp_async_commit();
+    cp_async_wait<1>();  // rows rho and rho + 1 have landed
+    const int s1 = wrap(s0 + 1);
+    float2 fe0[4], fe1[4];
+    ws_load8(my + s0 * SW, fe0);
+    ws_load8(my + s1 * SW, fe1);
+    if (rho < 2 * R) {  // warm-up: the window above the band's first output row
+      if (FAST || (y >= 0 && y < io.H)) ws_update<NN, true>(K, V, fe0);
+      if (FAST || (y + 1 >= 0 && y + 1 < io.H)) ws_update<NN, true>(K, V, fe1);
+    } else {
+      const int sl0 = wrap(s0 + RS - L), sl1 = wrap(s1 + RS - L);
+      const int sc0 = wrap(s0 + RS - R), sc1 = wrap(s1 + RS - R);
+      float2 fl0[4], fl1[4], fc0[4], fc1[4];
+      ws_load8(my + sl0 * SW, fl0);
+      ws_load8(my + sl1 * SW, fl1);
+      ws_load8(my + sc0 * SW, fc0);
+      ws_load8(my + sc1 * SW, fc1);
+      const int yo = y - R;  // output rows yo, yo + 1 (the second may be past the band)
+      // entering rows y, y + 1; leaving rows y - L, y + 1 - L (entered in this band
+      // when rho >= L)
+      if (FAST || y < io.H) ws_update<NN, true>(K, V, fe0);
+      if (rho >= L && (FAST || y - L >= 0)) ws_update<NN, false>(K, V, fl0);
+      ws_row_out<R, NN, FAST>(A, K, V, fc0, yo, x0, writer);
+      if (FAST || y + 1 < io.H) ws_update<NN, true>(K, V, fe1);
+      if (FAST || y + 1 - L >= 0) ws_update<NN, false>(K, V, fl1);
+      ws_row_out<R, NN, FAST>(A, K, V, fc1, yo + 1, x0, writer && yo + 1 < yo1);
+    }
+    s0 = wrap(s0 + 2);
+  }
+  cp_async_wait<0>();
+}
+
+template <int R, int NN>
+__device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip, int band,
+                                               float *ring) {
+  using G = WarpStripGeom<R>;
+  constexpr int SW = G::SW, RS = G::RS;
+  static_assert(R >= 1 && R <= 8, "the halo must come from one neighbouring lane");
+  static_assert(NN >= 2 && NN <= 6, "order range of the warp-strip kernel");
+  const TileIO &io = A.io;
+  const int lane = threadIdx.x & 31;
+  const int x0 = strip * G::TW - 8 + 8 * lane;  // first region column of this lane
+  const int yo0 = band * A.band, yo1 = min(io.H, yo0 + A.band);
+  float *my = ring + 4 * lane;  // ring row r, chunk j: my[r * SW + 128 * j + 0..3]
+  WsConst K;
+  K.kg = f2(A.kg);
+  K.kg0 = f2(A.kg0);
+  K.hs = f2(A.hs);
+  K.hs0 = f2(A.hs0);
+
+  // per chunk of 4 columns: valid column count (chunks start on multiples of 4);
+  // out-of-image columns of every ring row hold the sentinel
+  const int cnt0 = x0 < 0 ? 0 : max(0, min(4, io.W - x0));
+  const int cnt1 = x0 + 4 < 0 ? 0 : max(0, min(4, io.W - x0 - 4));
+  for (int e = cnt0; e < 4; ++e)
+    for (int r = 0; r < RS; ++r) my[r * SW + e] = A.sentinel;
+  for (int e = cnt1; e < 4; ++e)
+    for (int r = 0; r < RS; ++r) my[r * SW + 128 + e] = A.sentinel;
+  // rows touched: yo0 - W .. yo1 + W + 1 (the last pair's prefetch)
+  const bool rows_in = yo0 - R >= 0 && yo1 + R + 2 <= io.H;
+  const bool fast = __all_sync(0xffffffffu, rows_in && A.vec_in && A.vec_out && cnt0 == 4 &&
+                                                cnt1 == 4);
+  if (fast)
+    ws_band<R, NN, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+  else
+    ws_band<R, NN, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+}
+
+}  // namespace bfk

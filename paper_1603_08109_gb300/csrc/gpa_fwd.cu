@@ -6,7 +6,7 @@
 #include <mutex>
 
 #include "bf_internal.h"
-#include "box_stream.cuh"
+#include "box_warp.cuh"
 #include "gpa_fixed.cuh"
 #include "gpa_tile.cuh"
 
@@ -33,20 +33,24 @@ __global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constan
   bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16>(args.io, args.fc, smem);
 }
 
-// Streaming box kernel for small N (box_stream.cuh): strips of 240 columns,
-// bands of 64 rows.
+// Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of 240
+// output columns and band of rows, one warp per CTA.
+constexpr int kWarpWPB = 1;
 template <int R, int NN>
-__global__ void __launch_bounds__(256) box_stream_kernel(const __grid_constant__ bfk::StreamArgs A) {
+__global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid_constant__ bfk::WarpStripArgs A) {
   extern __shared__ __align__(16) float smem[];
-  using G = bfk::StreamGeom<R, NN>;
-  const int yo0 = blockIdx.y * G::BAND;
-  bfk::box_stream_band<R, NN>(A, blockIdx.x * G::TW, yo0, min(A.io.H, yo0 + G::BAND), smem);
+  using G = bfk::WarpStripGeom<R>;
+  const int w = threadIdx.x >> 5;
+  const int wid = blockIdx.x * kWarpWPB + w;
+  const int strip = wid % A.nstrips, band = wid / A.nstrips;
+  if (band >= A.nbands) return;
+  bfk::box_warp_strip<R, NN>(A, strip, band, smem + w * G::warp_floats);
 }
 
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
 // columns, output rows per tile).  Variant 5: the compile-time-radius kernel
 // for the radii in kFixedRadii (forward without stored planes only).
-// Variant 6: the streaming box kernel (box, W in {3, 5}, N <= 5).
+// Variant 6: the warp-strip streaming box kernel (box, W in {3, 5}, N <= 5).
 struct Variant {
   int NT, TH;
 };
@@ -117,47 +121,75 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   return bfi::check_launch();
 }
 
+// Rows per warp band (even, 16..64): about one wave of resident warps.  The
+// 2W warm-up rows of a band are read and entered but produce no output, so
+// bands are kept long where the image allows.
 template <int R, int NN>
-bf_status launch_stream_rn(const FwdArgs &a, cudaStream_t s) {
-  using G = bfk::StreamGeom<R, NN>;
-  bfk::StreamArgs A;
+bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
+  using G = bfk::WarpStripGeom<R>;
+  constexpr size_t smem = kWarpWPB * G::warp_floats * sizeof(float);
+  auto kern = box_warp_kernel<R, NN>;
+  static std::once_flag once;
+  static cudaError_t init_err = cudaSuccess;
+  static int resident_warps = 0;
+  std::call_once(once, [&] {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kWarpWPB, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    init_err = e;
+    resident_warps = per_sm * sms * kWarpWPB;
+  });
+  if (init_err != cudaSuccess) return bfi::cuda_status(init_err);
+  if (resident_warps < 1) return BF_ERR_UNSUPPORTED;
+  bfk::WarpStripArgs A;
   A.io = a.io;
-  A.fc = a.fc;
-  for (int n = 0; n < 8; ++n) {
-    A.rsq[n] = n > 0 ? (float)(1.0 / sqrt((double)n)) : 0.f;
-    A.sq[n] = (float)sqrt((double)n);
-  }
+  const double sr = a.fc.sr, tc = a.fc.tc;
+  const double kg = sqrt(1.4426950408889634 / 2.0) / sr;
+  A.tc = a.fc.tc;
+  A.sr = a.fc.sr;
+  A.kg = (float)kg;
+  A.kg0 = (float)(-tc * kg);
+  A.hs = (float)(1.0 / sr);
+  A.hs0 = (float)(-tc / sr);
+  A.qscale = a.fc.qscale;
+  A.sentinel = (float)(tc + 1e4 * sr);
+  for (int n = 0; n < 8; ++n) A.inv_n[n] = n > 0 ? (float)(1.0 / n) : 0.f;
+  const bool in_al = (reinterpret_cast<uintptr_t>(a.io.in) & 15u) == 0;
   const bool out_al = (reinterpret_cast<uintptr_t>(a.io.out) & 15u) == 0;
   const bool q_al = !a.io.qaux || (reinterpret_cast<uintptr_t>(a.io.qaux) & 15u) == 0;
-  A.vec_ok = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
-  auto kern = box_stream_kernel<R, NN>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes());
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = true;
-  }
-  dim3 grid((a.io.W + G::TW - 1) / G::TW, (a.io.H + G::BAND - 1) / G::BAND);
-  kern<<<grid, G::NT, G::smem_bytes(), s>>>(A);
+  A.vec_in = (in_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  A.vec_out = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  A.nstrips = (a.io.W + G::TW - 1) / G::TW;
+  const long long per_strip = std::max(1, resident_warps / A.nstrips);
+  const int band = (int)std::min<long long>(64, std::max<long long>(16, (a.io.H + per_strip - 1) / per_strip));
+  A.band = (band + 1) & ~1;
+  A.nbands = (a.io.H + A.band - 1) / A.band;
+  const long long warps = (long long)A.nstrips * A.nbands;
+  const long long ctas = (warps + kWarpWPB - 1) / kWarpWPB;
+  if (ctas > 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
+  kern<<<(int)ctas, 32 * kWarpWPB, smem, s>>>(A);
   return bfi::check_launch();
 }
 
 template <int R>
-bf_status launch_stream_r(const FwdArgs &a, cudaStream_t s) {
+bf_status launch_warp_r(const FwdArgs &a, cudaStream_t s) {
   switch (a.fc.N + 1) {
-    case 2: return launch_stream_rn<R, 2>(a, s);
-    case 3: return launch_stream_rn<R, 3>(a, s);
-    case 4: return launch_stream_rn<R, 4>(a, s);
-    case 5: return launch_stream_rn<R, 5>(a, s);
-    case 6: return launch_stream_rn<R, 6>(a, s);
+    case 2: return launch_warp_rn<R, 2>(a, s);
+    case 3: return launch_warp_rn<R, 3>(a, s);
+    case 4: return launch_warp_rn<R, 4>(a, s);
+    case 5: return launch_warp_rn<R, 5>(a, s);
+    case 6: return launch_warp_rn<R, 6>(a, s);
     default: return BF_ERR_UNSUPPORTED;
   }
 }
 
-bf_status launch_stream(const FwdArgs &a, cudaStream_t s) {
-  if (a.fc.R == 3) return launch_stream_r<3>(a, s);
-  if (a.fc.R == 5) return launch_stream_r<5>(a, s);
+bf_status launch_warp(const FwdArgs &a, cudaStream_t s) {
+  if (a.fc.R == 3) return launch_warp_r<3>(a, s);
+  if (a.fc.R == 5) return launch_warp_r<5>(a, s);
   return BF_ERR_UNSUPPORTED;
 }
 
@@ -198,7 +230,7 @@ bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
   }
   if (v == kStreamVariant) {
     if (STORE) return BF_ERR_UNSUPPORTED;
-    return launch_stream(a, s);
+    return launch_warp(a, s);
   }
   switch (v) {
     case 0: return g ? launch_fwd<1, 256, 16, STORE>(a, s) : launch_fwd<0, 256, 16, STORE>(a, s);
