@@ -18,6 +18,8 @@
 // then summed in a fixed order, so the result is deterministic.
 #include <mutex>
 
+#include <type_traits>
+
 #include "bf_internal.h"
 #include "gpa_tile.cuh"
 
@@ -318,7 +320,10 @@ __global__ void __launch_bounds__(256) reduce_partials(const double *p, int n, d
 //   Hbar = qbar * sum_{n<N} (w*a_n) D_n + sum_n (w*c_n) D_n
 //          + pbar * sum_{m>=1} sqrt(m) (w*a_m) D_{m-1},
 // so phase H keeps three running sums per output and reads only D_n, which
-// phase V computes for the centre rows.
+// phase V computes for the centre rows.  The two filterings of a channel
+// (w*a_n and w*c_n) share every tap, so they run as one filtering of the pair
+// (a_n, c_n) with the packed two-lane FP32 instructions (each lane rounded
+// exactly as the scalar operation).
 template <int R, int NT, int TH>
 struct BwdFixedGeom {
   static constexpr int RH = TH + 2 * R;
@@ -327,16 +332,16 @@ struct BwdFixedGeom {
   static constexpr int IPT = TH / KH;
   static constexpr int L = 2 * R + 1;
   // Phase-H lanes: (row = lane % TH, segment = lane / TH), segments KH
-  // columns apart.  Row pitch 17 (mod 32) for 16-row tiles (two segments of
-  // 16 rows per warp), 1 (mod 32) for 8-row tiles (four segments of 8 rows):
-  // every lane of a warp falls in its own bank.  Reads run up to column
-  // NT + KH - 2.
-  static constexpr int VP = TH >= 16 ? NT + 17 : NT + 33;
-  static_assert(VP % 32 == (TH >= 16 ? 17 : 1), "phase-H row pitch");
+  // columns apart, reading 8-byte (a, c) pairs.  Row pitch 1 (mod 16) pairs
+  // for 8-row tiles (four segments of 8 rows), 9 (mod 16) for 16-row tiles
+  // (two segments of 16 rows): the 16 lanes of each half-warp access
+  // distinct bank pairs.  Reads run up to column NT + KH - 2.
+  static constexpr int VP = TH >= 16 ? NT + 25 : NT + 33;
+  static_assert(VP % 16 == (TH >= 16 ? 9 : 1), "phase-H row pitch");
   static_assert(VP >= NT + KH - 1, "phase-H window reads stay inside the row");
   static constexpr size_t smem_bytes() {
-    return (3 * (size_t)TH * VP + (size_t)RH * NT) * sizeof(float) +
-           (size_t)RH * NT * sizeof(float2);
+    return ((size_t)TH * VP + (size_t)RH * NT) * sizeof(float2) +
+           ((size_t)TH * VP + (size_t)RH * NT) * sizeof(float);
   }
 };
 
@@ -349,11 +354,10 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   const bfi::FilterConsts &fc = A.fc;
   const int N = fc.N;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-  float *sVa = smem;               // TH x VP: vertical pass of a_n
-  float *sVc = sVa + TH * VP;      // TH x VP: vertical pass of c_n
-  float *sD = sVc + TH * VP;       // TH x VP: D_n of the centre rows
-  float *sH = sD + TH * VP;        // RH x NT: H
-  float2 *sQP = reinterpret_cast<float2 *>(sH + RH * NT);  // RH x NT: (qbar, pbar)
+  float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (a_n, c_n)
+  float2 *sQP = sV + TH * VP;                     // RH x NT: (qbar, pbar)
+  float *sD = reinterpret_cast<float *>(sQP + RH * NT);  // TH x VP: D_n of the centre rows
+  float *sH = sD + TH * VP;                       // RH x NT: H
   const int c = threadIdx.x;
 
   float a[RH];
@@ -385,125 +389,124 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
 #pragma unroll
     for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
 
-  for (int n = 0; n <= N; ++n) {
-    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+  // One channel n.  FIRST (n = 0): a_0 as loaded, no p-bar term; LAST (n = N):
+  // no q-bar term (the sums of Q' stop at N - 1).
+  auto channel = [&](int n, auto first_tag, auto last_tag) {
+    constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
+    const float rs = FIRST ? 0.f : __frsqrt_rn((float)n);
     const float sq = __fsqrt_rn((float)n);
-    const float qn = n < N ? 1.f : 0.f;
     __syncthreads();
 
-    // ---------------- phase V: advance, seeds c_n, D_n of centre rows, vertical passes
-    float acca[TH], accc[TH];
+    // ---------------- phase V: advance, seeds c_n, D_n of centre rows, vertical pass of (a_n, c_n)
+    float2 acc[TH];
 #pragma unroll
-    for (int y = 0; y < TH; ++y) acca[y] = accc[y] = 0.f;
-    float cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
+    for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
+    float2 cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
       const float h = sH[r * NT + c];
       const float aold = a[r];
-      const float an = n > 0 ? aold * (h * rs) : aold;
-      a[r] = an;
       const float2 qp = sQP[r * NT + c];
-      const float cn = fmaf(qp.x * qn, an, qp.y * sq * aold);
-      if (r >= R && r < R + TH) sD[(r - R) * VP + c] = fmaf(sq, aold, -h * an);
+      // (a_n, pbar sqrt(n) a_{n-1}) = a_{n-1} (H / sqrt(n), pbar sqrt(n))
+      float2 ac;
+      if (FIRST) {
+        ac = make_float2(aold, 0.f);
+      } else {
+        ac = __fmul2_rn(make_float2(aold, aold), __fmul2_rn(make_float2(h, qp.y), make_float2(rs, sq)));
+      }
+      // c_n = qbar a_n [n < N] + pbar sqrt(n) a_{n-1}, in place of the second lane
+      if (!LAST) ac.y = fmaf(qp.x, ac.x, ac.y);
+      a[r] = ac.x;
+      if (r >= R && r < R + TH) sD[(r - R) * VP + c] = fmaf(sq, aold, -h * ac.x);
       if (KIND == BF_SPATIAL_GAUSS) {
 #pragma unroll
         for (int y = 0; y < TH; ++y) {
           if (r - y >= 0 && r - y < L) {
-            acca[y] = fmaf(fc.taps[r - y], an, acca[y]);
-            accc[y] = fmaf(fc.taps[r - y], cn, accc[y]);
+            const float w = fc.taps[r - y];
+            acc[y] = __ffma2_rn(make_float2(w, w), ac, acc[y]);
           }
         }
       } else {
-        cbox[KIND == BF_SPATIAL_BOX ? r : 0] = cn;
+        cbox[KIND == BF_SPATIAL_BOX ? r : 0] = ac;
       }
     }
     if (KIND == BF_SPATIAL_BOX) {
-      float sa = 0.f, sc = 0.f;
+      float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int r = 0; r < L; ++r) {
-        sa += a[r];
-        sc += cbox[KIND == BF_SPATIAL_BOX ? r : 0];
-      }
-      acca[0] = sa;
-      accc[0] = sc;
+      for (int r = 0; r < L; ++r) s2 = __fadd2_rn(s2, cbox[KIND == BF_SPATIAL_BOX ? r : 0]);
+      acc[0] = s2;
 #pragma unroll
       for (int y = 1; y < TH; ++y) {
-        sa += a[y + 2 * R] - a[y - 1];
-        sc += cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0] - cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
-        acca[y] = sa;
-        accc[y] = sc;
+        const float2 in = cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0];
+        const float2 out = cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
+        s2 = __fadd2_rn(s2, __fadd2_rn(in, make_float2(-out.x, -out.y)));
+        acc[y] = s2;
       }
     }
 #pragma unroll
-    for (int y = 0; y < TH; ++y) {
-      sVa[y * VP + c] = acca[y];
-      sVc[y * VP + c] = accc[y];
-    }
+    for (int y = 0; y < TH; ++y) sV[y * VP + c] = acc[y];
     __syncthreads();
 
-    // ---------------- phase H: horizontal passes + running sums
+    // ---------------- phase H: horizontal pass of (a_n, c_n) + running sums
 #pragma unroll
     for (int m = 0; m < IPT; ++m) {
       const int it = c + m * NT;
       const int hy = it % TH, hx0 = (it / TH) * KH;
       if (hx0 >= TW) continue;
-      const float *ra = sVa + hy * VP + hx0, *rc = sVc + hy * VP + hx0;
-      float Ab[KH], Cb[KH];
+      const float2 *rv = sV + hy * VP + hx0;
+      float2 AC[KH];
       if (KIND == BF_SPATIAL_GAUSS) {
-        float wa[KH], wc[KH];
+        float2 win[KH];
 #pragma unroll
         for (int i = 0; i < KH; ++i) {
-          Ab[i] = Cb[i] = 0.f;
-          wa[i] = ra[i];
-          wc[i] = rc[i];
+          AC[i] = make_float2(0.f, 0.f);
+          win[i] = rv[i];
         }
 #pragma unroll
         for (int t = 0; t < L; ++t) {
           const float w = fc.taps[t];
 #pragma unroll
-          for (int i = 0; i < KH; ++i) {
-            Ab[i] = fmaf(w, wa[(t + i) % KH], Ab[i]);
-            Cb[i] = fmaf(w, wc[(t + i) % KH], Cb[i]);
-          }
-          wa[t % KH] = ra[t + KH];
-          wc[t % KH] = rc[t + KH];
+          for (int i = 0; i < KH; ++i) AC[i] = __ffma2_rn(make_float2(w, w), win[(t + i) % KH], AC[i]);
+          win[t % KH] = rv[t + KH];
         }
       } else {
-        float va[KH + 2 * R], vc[KH + 2 * R];
+        float2 v[KH + 2 * R];
 #pragma unroll
-        for (int i = 0; i < KH + 2 * R; ++i) {
-          va[i] = ra[i];
-          vc[i] = rc[i];
-        }
-        float sa = 0.f, sc = 0.f;
+        for (int i = 0; i < KH + 2 * R; ++i) v[i] = rv[i];
+        float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < L; ++i) {
-          sa += va[i];
-          sc += vc[i];
-        }
-        Ab[0] = sa;
-        Cb[0] = sc;
+        for (int i = 0; i < L; ++i) s2 = __fadd2_rn(s2, v[i]);
+        AC[0] = s2;
 #pragma unroll
         for (int j = 1; j < KH; ++j) {
-          sa += va[j + 2 * R] - va[j - 1];
-          sc += vc[j + 2 * R] - vc[j - 1];
-          Ab[j] = sa;
-          Cb[j] = sc;
+          s2 = __fadd2_rn(s2, __fadd2_rn(v[j + 2 * R], make_float2(-v[j - 1].x, -v[j - 1].y)));
+          AC[j] = s2;
         }
       }
       const float *drow = sD + hy * VP + R + hx0;
 #pragma unroll
       for (int k = 0; k < KH; ++k) {
         const float D = drow[k];
-        X[m][k] = fmaf(Ab[k] * qn, D, X[m][k]);
-        Y[m][k] = fmaf(Cb[k], D, Y[m][k]);
-        Z[m][k] = fmaf(Ab[k] * sq, Dp[m][k], Z[m][k]);
+        if (!LAST) X[m][k] = fmaf(AC[k].x, D, X[m][k]);
+        Y[m][k] = fmaf(AC[k].y, D, Y[m][k]);
+        if (!FIRST) Z[m][k] = fmaf(AC[k].x * sq, Dp[m][k], Z[m][k]);
         Dp[m][k] = D;
       }
     }
+  };
+  using F = std::false_type;
+  using T = std::true_type;
+  if (N == 0) {
+    channel(0, T{}, T{});
+  } else {
+    channel(0, T{}, F{});
+    for (int n = 1; n < N; ++n) channel(n, F{}, F{});
+    channel(N, F{}, T{});
   }
 
   // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
+  // sigma_r partial: the thread's (at most KH) terms summed in float, the
+  // CTA's in double
   double part = 0.0;
 #pragma unroll
   for (int m = 0; m < IPT; ++m) {
@@ -512,6 +515,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
     const int gy = ty0 + hy;
     if (hx0 >= TW || gy >= A.H) continue;
     const long long ro = (long long)gy * A.pitch;
+    float pf = 0.f;
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
       const int gx = tx0 + hx0 + k;
@@ -523,10 +527,11 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
         if (A.partials) {
           const float g = __ldg(A.gout + ro + gx);
           const float oc = __ldg(A.out + ro + gx) - fc.tc;
-          part += ((double)g * (double)oc - (double)hbar * (double)sH[ci]) * (double)fc.inv_sr;
+          pf += fmaf(g, oc, -hbar * sH[ci]);
         }
       }
     }
+    part += (double)pf * (double)fc.inv_sr;
   }
   if (A.partials) {
     __shared__ double red[32];
