@@ -360,22 +360,30 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   float *sH = sD + TH * VP;                       // RH x NT: H
   const int c = threadIdx.x;
 
+  // Region inputs.  The sigma_r partial's first term, sum g (out - t_c) over
+  // the tile's own pixels, is taken here while g and out are in registers.
   float a[RH];
+  float pf_go = 0.f;
   {
     const int gx = tx0 - R + c;
     const bool colin = gx >= 0 && gx < A.W;
+    const bool colown = c >= R && c < R + TW && gx < A.W;
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
       const int gy = ty0 - R + r;
       float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
       if (colin && gy >= 0 && gy < A.H) {
         const long long o = (long long)gy * A.pitch + gx;
-        h = (__ldg(A.in + o) - fc.tc) * fc.inv_sr;
-        a0 = expf(-0.5f * h * h);
+        const float d = __ldg(A.in + o) - fc.tc;
+        h = d * fc.inv_sr;
+        a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
         const float g = __ldg(A.gout + o);
-        const float iq = fc.qscale / __ldg(A.qaux + o);  // kernel-sum units: Q_u = Q' / qscale
-        qb = -g * (__ldg(A.out + o) - fc.tc) * iq;
+        const float go = g * (__ldg(A.out + o) - fc.tc);
+        // kernel-sum units: Q_u = Q' / qscale; approximate division (2 ulp)
+        const float iq = __fdividef(fc.qscale, __ldg(A.qaux + o));
+        qb = -go * iq;
         pb = g * fc.sr * iq;
+        if (r >= R && r < R + TH && colown) pf_go += go;
       }
       a[r] = a0;
       sH[r * NT + c] = h;
@@ -505,9 +513,9 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   }
 
   // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
-  // sigma_r partial: the thread's (at most KH) terms summed in float, the
-  // CTA's in double
-  double part = 0.0;
+  // sigma_r partial: sum over the tile's pixels of (g (out - t_c) - Hbar H) / sigma_r;
+  // each thread's terms summed in float, the CTA's in double
+  double part = (double)pf_go * (double)fc.inv_sr;
 #pragma unroll
   for (int m = 0; m < IPT; ++m) {
     const int it = c + m * NT;
@@ -524,11 +532,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
         const float2 qp = sQP[ci];
         const float hbar = fmaf(qp.x, X[m][k], fmaf(qp.y, Z[m][k], Y[m][k]));
         A.gin[ro + gx] = hbar * fc.inv_sr;
-        if (A.partials) {
-          const float g = __ldg(A.gout + ro + gx);
-          const float oc = __ldg(A.out + ro + gx) - fc.tc;
-          pf += fmaf(g, oc, -hbar * sH[ci]);
-        }
+        pf = fmaf(-hbar, sH[ci], pf);
       }
     }
     part += (double)pf * (double)fc.inv_sr;
