@@ -136,6 +136,28 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
                           int height, int width, int pitch,
                           const bf_params *p, void *stream);
 
+/* Forward with a caller-provided workspace, for large radii (W > 15).  The
+ * spatial filter is separable (eq. spatial_kernel1 on the square Omega), so
+ * the image is processed in bands of rows, two kernels per band: the first
+ * filters the columns of every power image a_0..a_N of the band (with the
+ * W-row halos) into the workspace, the second filters those planes along the
+ * rows (with the W-column halos) and forms P', Q' and f_GPA (Algorithm 2).
+ * Results equal bf_fast_forward's up to float rounding.
+ * bf_fast_forward_workspace: the workspace in bytes for bands tall enough
+ *   to give each launch several waves of CTAs (at most 2 GiB unless 64 rows
+ *   need more); 0 when the radius is 15 or less (bf_fast_forward_ws then
+ *   runs bf_fast_forward).
+ * bf_fast_forward_ws: d_workspace device memory, 16-byte aligned, owned by
+ *   the caller, of ws_bytes >= 64 rows of N + 1 planes, i.e. 64 (N+1) Wp
+ *   floats with Wp = width rounded up to a multiple of 4; a larger workspace
+ *   gives taller bands.  Same arguments and outputs as bf_fast_forward.
+ *   BF_ERR_WORKSPACE for a missing or too small workspace when W > 15. */
+bf_status bf_fast_forward_workspace(int height, int width, const bf_params *p,
+                                    size_t *bytes);
+bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux,
+                             int height, int width, int pitch, const bf_params *p,
+                             void *d_workspace, size_t ws_bytes, void *stream);
+
 /* Same as bf_fast_forward, and also stores the N+1 filtered power images
  * w * a_n (normalised kernel) to d_abar: plane n at d_abar + n * plane_stride,
  * each plane height x width with row pitch `pitch`; plane_stride >=

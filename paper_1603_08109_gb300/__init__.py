@@ -10,7 +10,8 @@ signatures), ``build`` (nvcc), ``synth`` (seeded synthetic inputs).
 """
 from .api import (BOX, GAUSS, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
                   centre_weight, direct, direct_backward, direct_bilateral, gpa_backward,
-                  exhaustive_order, gpa_bilateral, gpa_forward, gpa_forward_stored, joint_direct,
+                  exhaustive_order, forward_workspace_bytes, gpa_bilateral, gpa_forward,
+                  gpa_forward_stored, joint_direct,
                   joint_forward, kernel_error_max, order_bucket, order_estimates, order_from_delta,
                   radius_bucket, resolve_radius, tuning_get, tuning_set, variant_count)
 

@@ -19,7 +19,7 @@ __all__ = [
     "BOX", "GAUSS", "resolve_radius", "centre_weight", "order_from_delta", "gpa_forward",
     "gpa_forward_stored", "gpa_backward", "direct", "direct_backward", "GPABilateral",
     "DirectBilateral", "gpa_bilateral", "direct_bilateral", "BatchPlan", "autotune",
-    "variant_count", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
+    "variant_count", "forward_workspace_bytes", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
 ]
 
@@ -124,17 +124,46 @@ def _params(kind, radius, sigma_s, sigma_r, N, t_c):
     return make_params(kind, radius, sigma_s, float(sigma_r), N, t_c)
 
 
+def forward_workspace_bytes(H: int, W: int, kind: int, sigma_r: float, N: int, radius: int = 0,
+                            sigma_s: float = 0.0, t_c: float = 128.0) -> int:
+    """Workspace of the banded two-pass forward (0 when the radius is <= 15)."""
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    n = ctypes.c_size_t(0)
+    check(lib().bf_fast_forward_workspace(H, W, ctypes.byref(p), ctypes.byref(n)),
+          "bf_fast_forward_workspace")
+    return int(n.value)
+
+
 def gpa_forward(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
                 sigma_s: float = 0.0, t_c: float = 128.0, return_q: bool = False,
-                out: Optional[torch.Tensor] = None, variant: int = -1):
-    """f_GPA of eq. GPA (Algorithm 2, fused).  Returns out, or (out, Q')."""
+                out: Optional[torch.Tensor] = None, variant: int = -1,
+                band_rows: Optional[int] = None):
+    """f_GPA of eq. GPA (Algorithm 2).  Returns out, or (out, Q').
+
+    variant -1 picks the kernel: for radii above 15 the banded two-pass
+    forward with a workspace from torch's allocator (band_rows, a multiple of
+    64, overrides its band height); otherwise, or for an explicit variant,
+    the fused single-pass kernels."""
     x, on_cpu = _as_device_image(img)
     o = _image_like(x, out if not on_cpu else None)
     q = _like(x) if return_q else None
     p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
     H, W = x.shape
-    st = lib().bf_fast_forward_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
-                                       ctypes.byref(p), int(variant), _stream(x.device))
+    nbytes = 0
+    if variant < 0:
+        n = ctypes.c_size_t(0)
+        check(lib().bf_fast_forward_workspace(H, W, ctypes.byref(p), ctypes.byref(n)),
+              "bf_fast_forward_workspace")
+        nbytes = int(n.value)
+    if nbytes > 0:
+        if band_rows is not None:
+            nbytes = int(band_rows) * (int(N) + 1) * ((W + 3) // 4 * 4) * 4
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+        st = lib().bf_fast_forward_ws(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                      ctypes.byref(p), _ptr(ws), nbytes, _stream(x.device))
+    else:
+        st = lib().bf_fast_forward_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                           ctypes.byref(p), int(variant), _stream(x.device))
     check(st, "bf_fast_forward")
     if on_cpu:
         o = o.cpu()

@@ -106,6 +106,17 @@ def test_argument_validation_without_gpu():
     assert lib.bf_fast_backward(fake, fake, fake, fake, fake, fake, 8, 8, 8, p, None, 0,
                                 None) in (5, 3)
     assert lib.bf_batch_plan_create(None, 0, None) == 1
+    # banded forward: no workspace for radius <= 15; for W = 60 a workspace of
+    # at least 64 rows of N + 1 planes, checked before any launch
+    assert lib.bf_fast_forward_workspace(64, 64, p, ctypes.byref(sz)) == 0 and sz.value == 0
+    big = ctypes.byref(L.make_params(L.GAUSS, 60, 20.0, 40.0, 32))
+    assert lib.bf_fast_forward_workspace(8192, 8192, big, ctypes.byref(sz)) == 0
+    assert sz.value >= 64 * 33 * 8192 * 4 and sz.value % (33 * 8192 * 4) == 0
+    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big, None, 0, None) == 5
+    too_small = 63 * 33 * 200 * 4
+    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big, fake, too_small, None) == 5
+    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big,
+                                  ctypes.c_void_p(0x1004), 64 * 33 * 200 * 4, None) == 1
 
 
 def test_tuning_table_roundtrip():

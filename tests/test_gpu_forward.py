@@ -91,6 +91,24 @@ def test_streaming_box_kernel(r):
         bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=6)
 
 
+@pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 20, 20 / 3.0), (bf.GAUSS, 60, 20.0),
+                                       (bf.BOX, 20, 0.0), (bf.BOX, 50, 0.0)])
+def test_banded_two_pass(kind, r, ss):
+    """The banded two-pass forward (radius > 15): several bands of 64 rows with
+    a ragged last band, several column tiles with ragged edges, the band
+    height from the default workspace, and Q'."""
+    H, W = 150, 301
+    img = image(H, W, seed=r + 7)
+    sr, N = 60.0, 18
+    ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
+    x = torch.from_numpy(img).cuda()
+    assert bf.forward_workspace_bytes(H, W, kind, sr, N, radius=r, sigma_s=ss) > 0
+    for band in (64, 128, None):
+        out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True, band_rows=band)
+        compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, rq, w0,
+                        "banded kind %d r %d band %s" % (kind, r, band), sigma_r=sr, N=N)
+
+
 @pytest.mark.parametrize("r", [3, 5, 9, 15])
 def test_fixed_radius_kernel(r):
     """The compile-time-radius kernel at every radius it is built for, both
