@@ -263,14 +263,19 @@ bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out,
 
 /* --------------------------------------------------- batched forward
  * Many images of uneven sizes, each with its own spatial kind, W, sigma_s,
- * sigma_r and N, filtered by ONE persistent launch: CTAs take output tiles
- * from a device work queue (longest work first) until it is empty.
+ * sigma_r and N.  Images with W <= 15 are filtered by ONE persistent launch:
+ * CTAs take output tiles from a device work queue (longest work first) until
+ * it is empty.  Images with W > 15 take the two-pass banded forward (see
+ * bf_fast_forward_ws): one column-pass launch and one row-pass launch over
+ * the tiles of a group of images, their planes in the plan's workspace
+ * (groups keep the plane region at most 4 GiB, reused group after group).
+ * Results equal the single-image paths bit for bit.
  * Usage: bf_batch_plan_create (host: validates, picks tile shapes, orders
  * the work) -> bf_batch_workspace -> bf_batch_upload (enqueue the plan's
  * tables into the workspace; the plan must stay alive until that copy has
  * completed) -> bf_batch_forward, any number of times (graph-capturable: a
- * memset node and one kernel node; no allocation, no host synchronisation)
- * -> bf_batch_plan_destroy. */
+ * memset node, the persistent kernel and two kernels per banded group; no
+ * allocation, no host synchronisation) -> bf_batch_plan_destroy. */
 typedef struct {
     const float *d_in;   /* device input image                    */
     float *d_out;        /* device output image                   */

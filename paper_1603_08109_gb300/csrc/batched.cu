@@ -1,22 +1,33 @@
 // Batched forward: many images of uneven sizes, each with its own spatial
-// kind, W, sigma_s, sigma_r and N, in ONE persistent launch.
+// kind, W, sigma_s, sigma_r and N.
 //
-// The host plan splits every image into output tiles (work items), estimates
-// each item's cost from its (N + 1) filterings and tile geometry, and sorts
-// the items longest first.  The grid is sized to the device (SMs x resident
-// CTAs).  Each CTA repeatedly takes the next item index from a device
-// counter (atomicAdd; no CTA ever waits on another) and runs the same tile
-// body as the single-image kernel with that item's parameters.  A launch is
-// a memset of the counter followed by the kernel, so it can be captured in a
-// CUDA graph and replayed.
+// Images with W <= 15 go through ONE persistent launch: the host plan splits
+// them into output tiles (work items), estimates each item's cost from its
+// (N + 1) filterings and tile geometry, and sorts the items longest first.
+// The grid is sized to the device (SMs x resident CTAs).  Each CTA
+// repeatedly takes the next item index from a device counter (atomicAdd; no
+// CTA ever waits on another) and runs the same tile body as the single-image
+// kernel with that item's parameters.
+//
+// Images with W > 15 take the two-pass banded forward (gpa_banded.cuh), one
+// launch per pass over the tiles of a group of images (longest first); each
+// image's N + 1 column-filtered planes live in the plan's workspace, groups
+// are formed so that one group's planes fit a 4 GiB region that the next
+// group reuses.
+//
+// A launch is a memset of the counter, the persistent kernel and the
+// per-group pass launches, so it can be captured in a CUDA graph and
+// replayed.
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "bf_internal.h"
+#include "gpa_banded.cuh"
 #include "gpa_tile.cuh"
 
 namespace {
@@ -73,6 +84,51 @@ __global__ void __launch_bounds__(BNT) gpa_batched_kernel(const __grid_constant_
   }
 }
 
+// ---- banded items (W > 15)
+struct BandItem {
+  int desc, bx, by, pad;
+};
+
+struct BandBatchArgs {
+  const bfk::BandArgs *descs;  // .ws holds the byte offset of the image's planes
+  const BandItem *items;       // this launch's items, one per CTA
+  char *planes;                // the workspace's plane region
+};
+
+template <bool VPASS>
+__global__ void __launch_bounds__(bfk::kBandNT) gpa_batched_band_kernel(
+    const __grid_constant__ BandBatchArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ bfk::BandArgs sA;
+  const BandItem it = A.items[blockIdx.x];
+  const int *src = reinterpret_cast<const int *>(A.descs + it.desc);
+  int *dst = reinterpret_cast<int *>(&sA);
+  for (int i = threadIdx.x; i < (int)(sizeof(bfk::BandArgs) / sizeof(int)); i += blockDim.x)
+    dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    sA.ws = reinterpret_cast<float *>(A.planes + reinterpret_cast<uintptr_t>(sA.ws));
+  __syncthreads();
+  if (VPASS) {
+    if (sA.fc.kind == BF_SPATIAL_GAUSS)
+      bfk::band_vpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem);
+    else
+      bfk::band_vpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem);
+  } else {
+    if (sA.fc.kind == BF_SPATIAL_GAUSS)
+      bfk::band_hpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem);
+    else
+      bfk::band_hpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem);
+  }
+}
+
+struct BandGroup {
+  int v0, nv, h0, nh;
+  size_t vsmem, hsmem;
+};
+
+constexpr size_t kBatchPlaneCap = 4ull << 30;  // plane bytes per group
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
@@ -80,10 +136,14 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 struct bf_batch_plan {
   std::vector<BatchDesc> descs;
   std::vector<WorkItem> items;
+  std::vector<bfk::BandArgs> bdescs;
+  std::vector<BandItem> bitems;
+  std::vector<BandGroup> groups;
   size_t smem = 0;
   int ctas = 0;
-  size_t off_descs = 0, off_items = 0, ws_bytes = 0;
-  std::vector<unsigned char> staging;  // descs + items, laid out as in the workspace
+  size_t off_descs = 0, off_items = 0, off_bdescs = 0, off_bitems = 0, off_planes = 0;
+  size_t ws_bytes = 0;
+  std::vector<unsigned char> staging;  // tables, laid out as in the workspace
 };
 
 extern "C" {
@@ -106,6 +166,7 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
     WorkItem w;
   };
   std::vector<Cost> costs;
+  std::vector<int> large;  // images for the banded path
   plan->descs.resize(count);
   for (int i = 0; i < count; ++i) {
     const bf_image_desc &d = descs[i];
@@ -116,7 +177,13 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
       delete plan;
       return st;
     }
+    bd.io = {d.d_in, d.d_out, d.d_qaux, nullptr, 0, d.height, d.width, d.pitch};
     const int R = bd.fc.R;
+    if (R > 15) {
+      bd.th = 0;
+      large.push_back(i);
+      continue;
+    }
     int th = 16;
     if (BNT - 2 * R < 16 || bfk::fwd_smem_bytes(BNT, 16, R, bd.fc.ntaps_pad) > (size_t)smem_optin)
       th = 8;
@@ -125,7 +192,6 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
       return BF_ERR_UNSUPPORTED;
     }
     bd.th = th;
-    bd.io = {d.d_in, d.d_out, d.d_qaux, nullptr, 0, d.height, d.width, d.pitch};
     plan->smem = std::max(plan->smem, bfk::fwd_smem_bytes(BNT, th, R, bd.fc.ntaps_pad));
     const int TW = BNT - 2 * R;
     // cost model per tile: (N+1) x (region generation + both filter passes)
@@ -140,30 +206,121 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
                    [](const Cost &a, const Cost &b) { return a.c > b.c; });
   plan->items.reserve(costs.size());
   for (const Cost &c : costs) plan->items.push_back(c.w);
-  if (plan->items.size() > 0x7fffffff) {
+
+  // banded images: descriptors, groups of planes, tile items (longest first)
+  size_t planes_max = 0;
+  {
+    struct BCost {
+      double c;
+      BandItem it;
+    };
+    size_t cur = 0;
+    std::vector<BCost> vq, hq;
+    auto close_group = [&]() {
+      if (vq.empty()) return;
+      auto by_cost = [](const BCost &a, const BCost &b) { return a.c > b.c; };
+      std::stable_sort(vq.begin(), vq.end(), by_cost);
+      std::stable_sort(hq.begin(), hq.end(), by_cost);
+      BandGroup g{};
+      g.v0 = (int)plan->bitems.size();
+      g.nv = (int)vq.size();
+      for (const BCost &b : vq) plan->bitems.push_back(b.it);
+      g.h0 = (int)plan->bitems.size();
+      g.nh = (int)hq.size();
+      for (const BCost &b : hq) plan->bitems.push_back(b.it);
+      for (const BCost &b : vq) {
+        const bfi::FilterConsts &fc = plan->bdescs[b.it.desc].fc;
+        g.vsmem = std::max(g.vsmem, bfk::vpass_smem(fc.kind, fc.R, fc.ntaps_pad));
+        g.hsmem = std::max(g.hsmem, bfk::hpass_smem(fc.kind, fc.R, fc.ntaps_pad));
+      }
+      plan->groups.push_back(g);
+      planes_max = std::max(planes_max, cur);
+      vq.clear();
+      hq.clear();
+      cur = 0;
+    };
+    for (int i : large) {
+      const BatchDesc &bd = plan->descs[i];
+      const int H = bd.io.H, W = bd.io.W, Wp = (W + 3) / 4 * 4, N = bd.fc.N;
+      const size_t pbytes = align256((size_t)(N + 1) * (size_t)H * (size_t)Wp * sizeof(float));
+      if (cur > 0 && cur + pbytes > kBatchPlaneCap) close_group();
+      bfk::BandArgs a{};
+      a.in = bd.io.in;
+      a.out = bd.io.out;
+      a.qaux = bd.io.qaux;
+      a.ws = reinterpret_cast<float *>(static_cast<uintptr_t>(cur));  // offset, patched on device
+      a.plane = (long long)H * Wp;
+      a.Wp = Wp;
+      a.H = H;
+      a.W = W;
+      a.pitch = bd.io.pitch;
+      a.y0 = 0;
+      a.rows = H;
+      a.fc = bd.fc;
+      const int di = (int)plan->bdescs.size();
+      plan->bdescs.push_back(a);
+      cur += pbytes;
+      const double c = (N + 1.0) * (bd.fc.kind == BF_SPATIAL_GAUSS ? bd.fc.ntaps_pad : 8.0);
+      for (int by = 0; by < (H + bfk::kVB - 1) / bfk::kVB; ++by)
+        for (int bx = 0; bx < (Wp + bfk::kVC - 1) / bfk::kVC; ++bx) vq.push_back({c, {di, bx, by, 0}});
+      for (int by = 0; by < (H + bfk::kHT - 1) / bfk::kHT; ++by)
+        for (int bx = 0; bx < (W + bfk::kHW - 1) / bfk::kHW; ++bx) hq.push_back({c, {di, bx, by, 0}});
+    }
+    close_group();
+  }
+  if (plan->items.size() > 0x7fffffff || plan->bitems.size() > 0x7fffffff) {
     delete plan;
     return BF_ERR_UNSUPPORTED;
   }
-  // grid: every SM filled with as many CTAs as fit
-  cudaError_t e = cudaFuncSetAttribute(gpa_batched_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)plan->smem);
-  int per_sm = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpa_batched_kernel, BNT,
-                                                      plan->smem);
-  if (e != cudaSuccess || per_sm < 1) {
-    delete plan;
-    return e != cudaSuccess ? bfi::cuda_status(e) : BF_ERR_UNSUPPORTED;
+  cudaError_t e = cudaSuccess;
+  if (!large.empty()) {
+    static std::once_flag once;
+    static cudaError_t band_err = cudaSuccess;
+    std::call_once(once, [] {
+      const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
+      const size_t vs = std::max(bfk::vpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
+                                 bfk::vpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
+      const size_t hs = std::max(bfk::hpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
+                                 bfk::hpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
+      cudaError_t err = cudaFuncSetAttribute(gpa_batched_band_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(gpa_batched_band_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+      band_err = err;
+    });
+    e = band_err;
   }
-  plan->ctas = std::min<long long>((long long)sms * per_sm, (long long)plan->items.size());
+  // fused launch: every SM filled with as many CTAs as fit
+  if (e == cudaSuccess && !plan->items.empty()) {
+    e = cudaFuncSetAttribute(gpa_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)plan->smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpa_batched_kernel, BNT,
+                                                        plan->smem);
+    if (e == cudaSuccess && per_sm < 1) {
+      delete plan;
+      return BF_ERR_UNSUPPORTED;
+    }
+    plan->ctas = (int)std::min<long long>((long long)sms * per_sm, (long long)plan->items.size());
+  }
+  if (e != cudaSuccess) {
+    delete plan;
+    return bfi::cuda_status(e);
+  }
   plan->off_descs = 256;
   plan->off_items = align256(plan->off_descs + sizeof(BatchDesc) * plan->descs.size());
-  plan->ws_bytes = align256(plan->off_items + sizeof(WorkItem) * plan->items.size());
-  plan->staging.assign(plan->ws_bytes - plan->off_descs, 0);
-  memcpy(plan->staging.data(), plan->descs.data(), sizeof(BatchDesc) * plan->descs.size());
-  memcpy(plan->staging.data() + (plan->off_items - plan->off_descs), plan->items.data(),
-         sizeof(WorkItem) * plan->items.size());
+  plan->off_bdescs = align256(plan->off_items + sizeof(WorkItem) * plan->items.size());
+  plan->off_bitems = align256(plan->off_bdescs + sizeof(bfk::BandArgs) * plan->bdescs.size());
+  plan->off_planes = align256(plan->off_bitems + sizeof(BandItem) * plan->bitems.size());
+  plan->ws_bytes = plan->off_planes + planes_max;
+  plan->staging.assign(plan->off_planes - plan->off_descs, 0);
+  unsigned char *st0 = plan->staging.data() - plan->off_descs;  // workspace offset -> staging
+  memcpy(st0 + plan->off_descs, plan->descs.data(), sizeof(BatchDesc) * plan->descs.size());
+  memcpy(st0 + plan->off_items, plan->items.data(), sizeof(WorkItem) * plan->items.size());
+  memcpy(st0 + plan->off_bdescs, plan->bdescs.data(), sizeof(bfk::BandArgs) * plan->bdescs.size());
+  memcpy(st0 + plan->off_bitems, plan->bitems.data(), sizeof(BandItem) * plan->bitems.size());
   *plan_out = plan;
   return BF_OK;
 }
@@ -176,7 +333,7 @@ bf_status bf_batch_workspace(const bf_batch_plan *plan, size_t *bytes) {
 
 bf_status bf_batch_info(const bf_batch_plan *plan, int *items, int *ctas) {
   if (!plan) return BF_ERR_INVALID_ARG;
-  if (items) *items = (int)plan->items.size();
+  if (items) *items = (int)(plan->items.size() + plan->bitems.size());
   if (ctas) *ctas = plan->ctas;
   return BF_OK;
 }
@@ -199,17 +356,34 @@ bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_byte
     return BF_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_ws);
-  BatchArgs A;
-  A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
-  A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items);
-  A.counter = reinterpret_cast<int *>(base);
-  A.status = d_status;
-  A.count = (int)plan->descs.size();
-  A.nitems = (int)plan->items.size();
-  cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), s);
-  if (e != cudaSuccess) return bfi::cuda_status(e);
-  gpa_batched_kernel<<<plan->ctas, BNT, plan->smem, s>>>(A);
-  return bfi::check_launch();
+  if (!plan->items.empty()) {
+    BatchArgs A;
+    A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
+    A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items);
+    A.counter = reinterpret_cast<int *>(base);
+    A.status = d_status;
+    A.count = (int)plan->descs.size();
+    A.nitems = (int)plan->items.size();
+    cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    gpa_batched_kernel<<<plan->ctas, BNT, plan->smem, s>>>(A);
+    bf_status st = bfi::check_launch();
+    if (st != BF_OK) return st;
+  }
+  for (const BandGroup &g : plan->groups) {
+    BandBatchArgs B;
+    B.descs = reinterpret_cast<const bfk::BandArgs *>(base + plan->off_bdescs);
+    B.planes = base + plan->off_planes;
+    B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.v0;
+    gpa_batched_band_kernel<true><<<g.nv, bfk::kBandNT, g.vsmem, s>>>(B);
+    bf_status st = bfi::check_launch();
+    if (st != BF_OK) return st;
+    B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.h0;
+    gpa_batched_band_kernel<false><<<g.nh, bfk::kBandNT, g.hsmem, s>>>(B);
+    st = bfi::check_launch();
+    if (st != BF_OK) return st;
+  }
+  return BF_OK;
 }
 
 void bf_batch_plan_destroy(bf_batch_plan *plan) { delete plan; }

@@ -1,0 +1,263 @@
+// Device side of the two-pass banded forward (Algorithm 2 for large radii):
+// the tile bodies of the column pass (pass V) and the row pass (pass H),
+// shared by the single-image launches and the batched plan.
+//   pass V  per tile of 64 columns x 64 output rows: loads f for the tile's
+//           rows plus the W-row halos, generates a_0 and then a_n in shared
+//           memory (Algorithm 2's recursion, rescaled by 1/sqrt(n!)), and
+//           writes the vertical filtering (w_1 * a_n) of every channel
+//           n = 0..N to a workspace of N + 1 planes covering the band;
+//   pass H  per tile of 32 rows x 128 output columns: for each channel reads
+//           the plane with the W-column halos (cp.async, one channel ahead),
+//           filters along the rows, regenerates a_n at the tile's pixels and
+//           accumulates Q' and P' (eqs. P, Q), then f_GPA = t_c + sigma_r P'/Q'.
+// Out-of-image pixels carry a_n = 0 (zero extension), as in the fused kernels.
+#pragma once
+
+#include "bf_internal.h"
+#include "gpa_fixed.cuh"
+
+namespace bfk {
+
+constexpr int kBandNT = 256;
+constexpr int kVC = 64, kVB = 64;   // pass V tile: columns, output rows
+constexpr int kHT = 32, kHW = 128;  // pass H tile: rows, output columns
+
+struct BandArgs {
+  const float *in;
+  float *out, *qaux;
+  float *ws;        // N + 1 planes of rows x Wp floats
+  long long plane;  // floats per plane
+  int Wp;           // workspace row pitch: W rounded up to a multiple of 4
+  int H, W, pitch;
+  int y0, rows;     // the band: image rows y0 .. y0 + rows - 1
+  bfi::FilterConsts fc;
+};
+
+// Region rows of a pass-V tile: the rotating 16-tap windows read up to row
+// 63 + ntaps_pad (taps padded with zeros); a box reads 64 + 2W rows.
+__host__ __device__ inline int vpass_rows(int kind, int R, int ntp) {
+  return kind == BF_SPATIAL_GAUSS ? kVB + ntp : kVB + 2 * R;
+}
+// Region columns of a pass-H tile, and the row pitch (1 mod 32: the 32 lanes
+// of a warp, one row each, read distinct banks).
+__host__ __device__ inline int hpass_cols(int kind, int R, int ntp) {
+  return kind == BF_SPATIAL_GAUSS ? kHW + ntp : kHW + 2 * R;
+}
+__host__ __device__ inline int hpass_pitch(int cols) { return (cols + 31) / 32 * 32 + 1; }
+
+inline size_t vpass_smem(int kind, int R, int ntp) { return 2 * (size_t)vpass_rows(kind, R, ntp) * kVC * sizeof(float); }
+inline size_t hpass_smem(int kind, int R, int ntp) {
+  return 2 * (size_t)kHT * hpass_pitch(hpass_cols(kind, R, ntp)) * sizeof(float);
+}
+
+// Pass V of tile (bx, by): columns 64 bx.., band rows 64 by.. .
+template <int KIND>
+__device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int by, float *sm) {
+  const bfi::FilterConsts &fc = A.fc;
+  const int R = fc.R, N = fc.N;
+  const int RR = vpass_rows(KIND, R, fc.ntaps_pad);
+  float *sH = sm, *sA = sm + RR * kVC;
+  const int tx = bx * kVC;
+  const int tyb = by * kVB;  // band-relative first output row
+  const int ty = A.y0 + tyb;
+  const int halo = kVB + 2 * R;      // rows of real data; the rest are zero padding
+  for (int i = threadIdx.x; i < RR * kVC; i += kBandNT) {
+    const int r = i / kVC, c = i % kVC;
+    const int gy = ty - R + r, gx = tx + c;
+    float h = 0.f, a0 = 0.f;
+    if (r < halo && gy >= 0 && gy < A.H && gx < A.W) {
+      const float d = __ldg(A.in + (long long)gy * A.pitch + gx) - fc.tc;
+      h = d * fc.inv_sr;
+      a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2)
+    }
+    sH[i] = h;
+    sA[i] = a0;
+  }
+  const int c = threadIdx.x % kVC, yb = threadIdx.x / kVC;  // 4 blocks of 16 output rows
+  const int gx = tx + c;
+  const float *col = sA + 16 * yb * kVC + c;
+  for (int n = 0; n <= N; ++n) {
+    __syncthreads();  // region loaded / previous channel's filtering done
+    if (n > 0) {
+      const float rs = __frsqrt_rn((float)n);
+      float4 *a4 = reinterpret_cast<float4 *>(sA);
+      const float4 *h4 = reinterpret_cast<const float4 *>(sH);
+      for (int i = threadIdx.x; i < RR * kVC / 4; i += kBandNT) {
+        const float4 h = h4[i];
+        float4 v = a4[i];
+        v.x *= h.x * rs;
+        v.y *= h.y * rs;
+        v.z *= h.z * rs;
+        v.w *= h.w * rs;
+        a4[i] = v;
+      }
+      __syncthreads();
+    }
+    float acc[16];
+    if (KIND == BF_SPATIAL_GAUSS) {
+      float win[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        acc[i] = 0.f;
+        win[i] = col[i * kVC];
+      }
+      for (int k = 0; k < fc.ntaps_pad; k += 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float w = fc.taps[k + j];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[i] = fmaf(w, win[(j + i) & 15], acc[i]);
+          win[j] = col[(k + j + 16) * kVC];
+        }
+      }
+    } else {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int r = 0;
+      for (; r + 3 <= 2 * R; r += 4) {
+        s0 += col[r * kVC];
+        s1 += col[(r + 1) * kVC];
+        s2 += col[(r + 2) * kVC];
+        s3 += col[(r + 3) * kVC];
+      }
+      for (; r <= 2 * R; ++r) s0 += col[r * kVC];
+      float s = (s0 + s1) + (s2 + s3);
+      acc[0] = s;
+#pragma unroll
+      for (int i = 1; i < 16; ++i) {
+        s += col[(i + 2 * R) * kVC] - col[(i - 1) * kVC];
+        acc[i] = s;
+      }
+    }
+    if (c < A.Wp - tx) {  // columns W..Wp-1 of the workspace are written as zeros
+      float *dst = A.ws + (long long)n * A.plane + gx;
+      const bool colin = gx < A.W;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int orow = tyb + 16 * yb + i;
+        if (orow < A.rows) dst[(long long)orow * A.Wp] = colin ? acc[i] : 0.f;
+      }
+    }
+  }
+}
+
+// Pass H of tile (bx, by): output columns 128 bx.., band rows 32 by.. .
+template <int KIND>
+__device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int by, float *sm) {
+  const bfi::FilterConsts &fc = A.fc;
+  const int R = fc.R, N = fc.N;
+  const int RC = hpass_cols(KIND, R, fc.ntaps_pad), P = hpass_pitch(RC);
+  float *const buf0 = sm, *const buf1 = sm + kHT * P;
+  const int tx = bx * kHW;
+  const int tyb = by * kHT;
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;  // row lane, 16 columns seg
+
+  // plane n of rows tyb.., columns tx - W.., into b; each warp copies four
+  // rows, its lanes consecutive columns (zeros outside the image / band)
+  auto load = [&](int n, float *b) {
+    const float *src = A.ws + (long long)n * A.plane;
+    for (int r = seg; r < kHT; r += kBandNT / 32) {
+      const int orow = tyb + r;
+      const float *srow = src + (long long)orow * A.Wp;
+      float *drow = b + r * P;
+      for (int j = lane; j < RC; j += 32) {
+        const int gx = tx - R + j;
+        if (orow < A.rows && gx >= 0 && gx < A.W)
+          bfk::cp_async4(drow + j, srow + gx);
+        else
+          drow[j] = 0.f;
+      }
+    }
+  };
+
+  // the thread's 16 pixels: row ty + lane, columns tx + 16 seg + i
+  const int gy = A.y0 + tyb + lane;
+  const bool rowin = tyb + lane < A.rows;
+  float a[16], H[16], Q[16], Pp[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int gx = tx + 16 * seg + i;
+    float h = 0.f, a0 = 0.f;
+    if (rowin && gx < A.W) {
+      const float d = __ldg(A.in + (long long)gy * A.pitch + gx) - fc.tc;
+      h = d * fc.inv_sr;
+      a0 = exp2f(d * d * fc.e2c);
+    }
+    a[i] = a0;
+    H[i] = h;
+    Q[i] = Pp[i] = 0.f;
+  }
+
+  load(0, buf0);
+  bfk::cp_async_commit();
+  const float *vrow0 = nullptr;
+  for (int n = 0; n <= N; ++n) {
+    if (n < N) {
+      load(n + 1, (n & 1) ? buf0 : buf1);
+      bfk::cp_async_commit();
+      bfk::cp_async_wait<1>();
+    } else {
+      bfk::cp_async_wait<0>();
+    }
+    __syncthreads();  // plane n is in buffer n & 1 for every thread
+    vrow0 = ((n & 1) ? buf1 : buf0) + lane * P + 16 * seg;
+    float Ab[16];
+    if (KIND == BF_SPATIAL_GAUSS) {
+      float win[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        Ab[i] = 0.f;
+        win[i] = vrow0[i];
+      }
+      for (int k = 0; k < fc.ntaps_pad; k += 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float w = fc.taps[k + j];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) Ab[i] = fmaf(w, win[(j + i) & 15], Ab[i]);
+          win[j] = vrow0[k + j + 16];
+        }
+      }
+    } else {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int j = 0;
+      for (; j + 3 <= 2 * R; j += 4) {
+        s0 += vrow0[j];
+        s1 += vrow0[j + 1];
+        s2 += vrow0[j + 2];
+        s3 += vrow0[j + 3];
+      }
+      for (; j <= 2 * R; ++j) s0 += vrow0[j];
+      float s = (s0 + s1) + (s2 + s3);
+      Ab[0] = s;
+#pragma unroll
+      for (int i = 1; i < 16; ++i) {
+        s += vrow0[i + 2 * R] - vrow0[i - 1];
+        Ab[i] = s;
+      }
+    }
+    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+    const float sq = __fsqrt_rn((float)n);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float aold = a[i];  // a_{n-1}
+      const float an = n > 0 ? aold * (H[i] * rs) : aold;
+      if (n < N) Q[i] = fmaf(an, Ab[i], Q[i]);
+      if (n > 0) Pp[i] = fmaf(sq * aold, Ab[i], Pp[i]);
+      a[i] = an;
+    }
+    __syncthreads();  // buffer n & 1 is free for plane n + 2
+  }
+
+  if (!rowin) return;
+  const long long ro = (long long)gy * A.pitch;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int gx = tx + 16 * seg + i;
+    if (gx < A.W) {
+      A.out[ro + gx] = fmaf(fc.sr, __fdividef(Pp[i], Q[i]), fc.tc);  // 2-ulp division
+      if (A.qaux) A.qaux[ro + gx] = Q[i] * fc.qscale;
+    }
+  }
+}
+
+}  // namespace bfk

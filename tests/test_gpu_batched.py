@@ -1,6 +1,7 @@
-"""GPU batched persistent forward: each image of one launch equals the
-single-image kernel with the same tile shape bit for bit, graph replays are
-identical, and sampled pixels match the checker."""
+"""GPU batched forward: each image of one plan equals the single-image path
+bit for bit (the 256-thread, 16-row fused tile for W <= 15; the two-pass
+banded forward for W > 15), graph replays are identical, and sampled pixels
+match the checker."""
 import numpy as np
 import pytest
 import torch
@@ -30,8 +31,9 @@ def _with_order(specs):
 
 
 def _single(img, sp):
-    # the batched kernel uses 256-thread tiles: 16 rows up to radius 44, else 8 rows
-    variant = 0 if sp["radius"] <= 44 else 2
+    # W <= 15: the persistent launch's 256-thread, 16-row tile (variant 0);
+    # W > 15: the banded two-pass forward (the default path for such radii)
+    variant = 0 if sp["radius"] <= 15 else -1
     return bf.gpa_forward(img, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
                           sigma_s=sp["sigma_s"], variant=variant)
 
