@@ -360,34 +360,51 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   float *sH = sD + TH * VP;                       // RH x NT: H
   const int c = threadIdx.x;
 
-  // Region inputs.  The sigma_r partial's first term, sum g (out - t_c) over
-  // the tile's own pixels, is taken here while g and out are in registers.
+  // Region inputs, in groups of rows whose loads are all issued before any
+  // is used (out-of-image pixels load the image origin and are masked).  The
+  // sigma_r partial's first term, sum g (out - t_c) over the tile's own
+  // pixels, is taken here while g and out are in registers.
   float a[RH];
   float pf_go = 0.f;
   {
     const int gx = tx0 - R + c;
     const bool colin = gx >= 0 && gx < A.W;
     const bool colown = c >= R && c < R + TW && gx < A.W;
+    constexpr int GR = 7;  // rows per load group
 #pragma unroll
-    for (int r = 0; r < RH; ++r) {
-      const int gy = ty0 - R + r;
-      float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
-      if (colin && gy >= 0 && gy < A.H) {
-        const long long o = (long long)gy * A.pitch + gx;
-        const float d = __ldg(A.in + o) - fc.tc;
-        h = d * fc.inv_sr;
-        a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
-        const float g = __ldg(A.gout + o);
-        const float go = g * (__ldg(A.out + o) - fc.tc);
-        // kernel-sum units: Q_u = Q' / qscale; approximate division (2 ulp)
-        const float iq = __fdividef(fc.qscale, __ldg(A.qaux + o));
-        qb = -go * iq;
-        pb = g * fc.sr * iq;
-        if (r >= R && r < R + TH && colown) pf_go += go;
+    for (int r0 = 0; r0 < RH; r0 += GR) {
+      float fv[GR], gv[GR], ov[GR], qv[GR];
+      bool in[GR];
+#pragma unroll
+      for (int j = 0; j < GR; ++j) {
+        const int r = r0 + j, gy = ty0 - R + r;
+        in[j] = r < RH && colin && gy >= 0 && gy < A.H;
+        const long long o = in[j] ? (long long)gy * A.pitch + gx : 0;
+        fv[j] = __ldg(A.in + o);
+        gv[j] = __ldg(A.gout + o);
+        ov[j] = __ldg(A.out + o);
+        qv[j] = __ldg(A.qaux + o);
       }
-      a[r] = a0;
-      sH[r * NT + c] = h;
-      sQP[r * NT + c] = make_float2(qb, pb);
+#pragma unroll
+      for (int j = 0; j < GR; ++j) {
+        const int r = r0 + j;
+        if (r >= RH) break;
+        float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
+        if (in[j]) {
+          const float d = fv[j] - fc.tc;
+          h = d * fc.inv_sr;
+          a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
+          const float go = gv[j] * (ov[j] - fc.tc);
+          // kernel-sum units: Q_u = Q' / qscale; approximate division (2 ulp)
+          const float iq = __fdividef(fc.qscale, qv[j]);
+          qb = -go * iq;
+          pb = gv[j] * fc.sr * iq;
+          if (r >= R && r < R + TH && colown) pf_go += go;
+        }
+        a[r] = a0;
+        sH[r * NT + c] = h;
+        sQP[r * NT + c] = make_float2(qb, pb);
+      }
     }
   }
 
