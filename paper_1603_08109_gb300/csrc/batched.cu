@@ -96,7 +96,7 @@ struct BandBatchArgs {
 };
 
 template <bool VPASS>
-__global__ void __launch_bounds__(bfk::kBandNT) gpa_batched_band_kernel(
+__global__ void __launch_bounds__(VPASS ? bfk::kVNT : bfk::kBandNT) gpa_batched_band_kernel(
     const __grid_constant__ BandBatchArgs A) {
   extern __shared__ __align__(16) float smem[];
   __shared__ bfk::BandArgs sA;
@@ -375,7 +375,7 @@ bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_byte
     B.descs = reinterpret_cast<const bfk::BandArgs *>(base + plan->off_bdescs);
     B.planes = base + plan->off_planes;
     B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.v0;
-    gpa_batched_band_kernel<true><<<g.nv, bfk::kBandNT, g.vsmem, s>>>(B);
+    gpa_batched_band_kernel<true><<<g.nv, bfk::kVNT, g.vsmem, s>>>(B);
     bf_status st = bfi::check_launch();
     if (st != BF_OK) return st;
     B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.h0;

@@ -24,7 +24,7 @@ constexpr size_t kBandCap = 2ull << 30;   // default workspace cap (bytes)
 constexpr long long kBandCTAs = 8 * 152;   // pass-V CTAs per band wanted
 
 template <int KIND>
-__global__ void __launch_bounds__(kBandNT) band_vpass(const __grid_constant__ BandArgs A) {
+__global__ void __launch_bounds__(kVNT) band_vpass(const __grid_constant__ BandArgs A) {
   extern __shared__ __align__(16) float sm[];
   band_vpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm);
 }
@@ -80,7 +80,7 @@ bf_status launch_band(BandArgs &A, cudaStream_t s) {
     A.y0 = y0;
     A.rows = std::min(band, A.H - y0);
     dim3 gv((A.Wp + kVC - 1) / kVC, (A.rows + kVB - 1) / kVB);
-    band_vpass<KIND><<<gv, kBandNT, vs, s>>>(A);
+    band_vpass<KIND><<<gv, kVNT, vs, s>>>(A);
     bf_status st = bfi::check_launch();
     if (st != BF_OK) return st;
     dim3 gh((A.W + kHW - 1) / kHW, (A.rows + kHT - 1) / kHT);

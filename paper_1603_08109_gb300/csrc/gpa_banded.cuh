@@ -18,7 +18,8 @@
 
 namespace bfk {
 
-constexpr int kBandNT = 256;
+constexpr int kBandNT = 256;        // pass H threads per CTA
+constexpr int kVNT = 128;           // pass V threads per CTA (two columns each)
 constexpr int kVC = 64, kVB = 64;   // pass V tile: columns, output rows
 constexpr int kHT = 32, kHW = 128;  // pass H tile: rows, output columns
 
@@ -61,7 +62,7 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
   const int tyb = by * kVB;  // band-relative first output row
   const int ty = A.y0 + tyb;
   const int halo = kVB + 2 * R;      // rows of real data; the rest are zero padding
-  for (int i = threadIdx.x; i < RR * kVC; i += kBandNT) {
+  for (int i = threadIdx.x; i < RR * kVC; i += kVNT) {
     const int r = i / kVC, c = i % kVC;
     const int gy = ty - R + r, gx = tx + c;
     float h = 0.f, a0 = 0.f;
@@ -73,16 +74,18 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
     sH[i] = h;
     sA[i] = a0;
   }
-  const int c = threadIdx.x % kVC, yb = threadIdx.x / kVC;  // 4 blocks of 16 output rows
-  const int gx = tx + c;
-  const float *col = sA + 16 * yb * kVC + c;
+  // each thread: two adjacent columns (a packed pair) x 16 output rows
+  constexpr int CS = kVC / 2;  // row stride in column pairs
+  const int cp = threadIdx.x % CS, yb = threadIdx.x / CS;  // 4 blocks of 16 output rows
+  const int gx = tx + 2 * cp;
+  const float2 *col = reinterpret_cast<const float2 *>(sA + 16 * yb * kVC) + cp;
   for (int n = 0; n <= N; ++n) {
     __syncthreads();  // region loaded / previous channel's filtering done
     if (n > 0) {
       const float rs = __frsqrt_rn((float)n);
       float4 *a4 = reinterpret_cast<float4 *>(sA);
       const float4 *h4 = reinterpret_cast<const float4 *>(sH);
-      for (int i = threadIdx.x; i < RR * kVC / 4; i += kBandNT) {
+      for (int i = threadIdx.x; i < RR * kVC / 4; i += kVNT) {
         const float4 h = h4[i];
         float4 v = a4[i];
         v.x *= h.x * rs;
@@ -93,48 +96,50 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
       }
       __syncthreads();
     }
-    float acc[16];
+    float2 acc[16];
     if (KIND == BF_SPATIAL_GAUSS) {
-      float win[16];
+      float2 win[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        acc[i] = 0.f;
-        win[i] = col[i * kVC];
+        acc[i] = make_float2(0.f, 0.f);
+        win[i] = col[i * CS];
       }
       for (int k = 0; k < fc.ntaps_pad; k += 16) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float w = fc.taps[k + j];
+          const float2 w2 = make_float2(w, w);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] = fmaf(w, win[(j + i) & 15], acc[i]);
-          win[j] = col[(k + j + 16) * kVC];
+          for (int i = 0; i < 16; ++i) acc[i] = __ffma2_rn(w2, win[(j + i) & 15], acc[i]);
+          win[j] = col[(k + j + 16) * CS];
         }
       }
     } else {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
       int r = 0;
       for (; r + 3 <= 2 * R; r += 4) {
-        s0 += col[r * kVC];
-        s1 += col[(r + 1) * kVC];
-        s2 += col[(r + 2) * kVC];
-        s3 += col[(r + 3) * kVC];
+        s0 = __fadd2_rn(s0, col[r * CS]);
+        s1 = __fadd2_rn(s1, col[(r + 1) * CS]);
+        s2 = __fadd2_rn(s2, col[(r + 2) * CS]);
+        s3 = __fadd2_rn(s3, col[(r + 3) * CS]);
       }
-      for (; r <= 2 * R; ++r) s0 += col[r * kVC];
-      float s = (s0 + s1) + (s2 + s3);
+      for (; r <= 2 * R; ++r) s0 = __fadd2_rn(s0, col[r * CS]);
+      float2 s = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
       acc[0] = s;
 #pragma unroll
       for (int i = 1; i < 16; ++i) {
-        s += col[(i + 2 * R) * kVC] - col[(i - 1) * kVC];
+        const float2 in = col[(i + 2 * R) * CS], out = col[(i - 1) * CS];
+        s = __fadd2_rn(s, __fadd2_rn(in, make_float2(-out.x, -out.y)));
         acc[i] = s;
       }
     }
-    if (c < A.Wp - tx) {  // columns W..Wp-1 of the workspace are written as zeros
+    // columns W..Wp-1 of the workspace receive zeros (their a_n are 0)
+    if (gx < A.Wp) {
       float *dst = A.ws + (long long)n * A.plane + gx;
-      const bool colin = gx < A.W;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int orow = tyb + 16 * yb + i;
-        if (orow < A.rows) dst[(long long)orow * A.Wp] = colin ? acc[i] : 0.f;
+        if (orow < A.rows) *reinterpret_cast<float2 *>(dst + (long long)orow * A.Wp) = acc[i];
       }
     }
   }
