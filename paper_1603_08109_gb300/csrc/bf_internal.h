@@ -39,6 +39,16 @@ void set_error_text(const char *msg);
 bf_status resolve(const bf_params *p, bool need_order, FilterConsts *fc);
 bf_status check_image(const void *in, const void *out, int height, int width, int pitch);
 
+// Two-pass banded backward for W > 15 (gpa_banded_bwd.cu): whether it applies,
+// the workspace it prefers, and the launch sequence (prep, per band a column
+// and a row pass, the sigma_r reduce).  BF_ERR_WORKSPACE when ws holds fewer
+// than 64 band rows.
+bool banded_backward_fits(const FilterConsts &fc);
+size_t banded_backward_bytes(int height, int width, const FilterConsts &fc);
+bf_status banded_backward(const float *in, const float *out, const float *qaux, const float *gout,
+                          float *gin, double *gsigma, int height, int width, int pitch,
+                          const FilterConsts &fc, void *ws, size_t ws_bytes, void *stream);
+
 // Fastest compiled-in tile variant for (kind, R, N) from the tuning table.
 int tuned_variant(int kind, int R, int N);
 

@@ -16,6 +16,7 @@
 // variant, w*a_n is read back from the forward's planes and only c_n is
 // filtered.  sigma_r partials are reduced per CTA in double precision and
 // then summed in a fixed order, so the result is deterministic.
+#include <algorithm>
 #include <mutex>
 
 #include <type_traits>
@@ -654,12 +655,14 @@ bf_status dispatch_bwd(int v, const BwdArgs &A, cudaStream_t s) {
   }
 }
 
+// Workspace of the fused kernels (their per-CTA sigma_r partials).
 bf_status workspace_bytes(int height, int width, const bf_params *p, size_t *bytes, int *var,
                           bfi::FilterConsts *fc) {
   if (!bytes || height < 1 || width < 1) return BF_ERR_INVALID_ARG;
   bf_status st = bfi::resolve(p, true, fc);
   if (st != BF_OK) return st;
   const int v = pick_bwd(*fc);
+  if (var) *var = v;
   if (v < 0) return BF_ERR_UNSUPPORTED;
   dim3 g;
   grid_for(v, *fc, height, width, &g);
@@ -685,6 +688,14 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   size_t need = 0;
   int v = -1;
   st = workspace_bytes(height, width, p, &need, &v, &A.fc);
+  if (st != BF_OK && st != BF_ERR_UNSUPPORTED) return st;
+  // W > 15 without stored planes: the banded two-pass backward when the
+  // workspace holds at least 64 band rows; the fused runtime-W kernel otherwise
+  if (!abar && bfi::banded_backward_fits(A.fc) && ws) {
+    const bf_status sb = bfi::banded_backward(in, out, qaux, gout, gin, gsigma, height, width,
+                                              pitch, A.fc, ws, ws_bytes, stream);
+    if (sb != BF_ERR_WORKSPACE || st != BF_OK) return sb;
+  }
   if (st != BF_OK) return st;
   if (abar && plane_stride < (size_t)height * (size_t)pitch) return BF_ERR_INVALID_ARG;
   if (gsigma && (!ws || ws_bytes < need)) return BF_ERR_WORKSPACE;
@@ -723,7 +734,14 @@ extern "C" {
 
 bf_status bf_fast_backward_workspace(int height, int width, const bf_params *p, size_t *bytes) {
   bfi::FilterConsts fc;
-  return workspace_bytes(height, width, p, bytes, nullptr, &fc);
+  bf_status st = workspace_bytes(height, width, p, bytes, nullptr, &fc);
+  if (st != BF_OK && st != BF_ERR_UNSUPPORTED) return st;
+  if (bfi::banded_backward_fits(fc)) {  // W > 15: room for the banded backward
+    const size_t b = bfi::banded_backward_bytes(height, width, fc);
+    *bytes = st == BF_OK ? std::max(*bytes, b) : b;
+    return BF_OK;
+  }
+  return st;
 }
 
 bf_status bf_fast_backward(const float *d_in, const float *d_out, const float *d_qaux,
@@ -790,7 +808,8 @@ extern "C" bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_
                                               int width, int pitch, const bf_params *p,
                                               void *stream) {
   size_t need = 0;
-  bf_status st = bf_fast_backward_workspace(height, width, p, &need);
+  bfi::FilterConsts fc;
+  bf_status st = workspace_bytes(height, width, p, &need, nullptr, &fc);  // the fused kernels'
   if (st != BF_OK) return st;
   if (need > sizeof(double) * (size_t)kNoAllocPartials) {
     bfi::set_error_text("image too large for the allocation-free backward: it needs more "

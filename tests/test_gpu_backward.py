@@ -57,6 +57,55 @@ def test_fast_backward_matches_exact_derivatives(case):
     assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
 
 
+@pytest.mark.parametrize("case", [
+    (bf.GAUSS, 20, 20 / 3.0, 60.0, 18, (150, 173)),
+    (bf.GAUSS, 60, 20.0, 60.0, 12, (140, 150)),
+    (bf.BOX, 25, 0.0, 60.0, 18, (150, 131)),
+], ids=lambda c: "k%d_r%d" % (c[0], c[1]))
+def test_banded_backward(case):
+    """The banded two-pass backward (radius > 15) against the checker's exact
+    derivatives, with the workspace from the query (one band) and with smaller
+    workspaces (several bands of 64 or 128 rows); W = 60 is beyond what the
+    fused runtime-radius backward supports."""
+    import ctypes
+    from paper_1603_08109_gb300 import _lib
+    kind, r, ss, sr, N, (H, W) = case
+    img = image(H, W, seed=H * 7 + W)
+    g = synth.random_like((H, W), seed=H + 2 * W)
+    rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True)
+    gt = torch.from_numpy(g).cuda()
+    p = _lib.make_params(kind, r, ss, sr, N)
+    lib = _lib.lib()
+    need = ctypes.c_size_t()
+    assert lib.bf_fast_backward_workspace(H, W, ctypes.byref(p), ctypes.byref(need)) == 0
+    band_bytes = 3 * (N + 1) * 64 * ((W + 3) // 4 * 4) * 4   # 64 rows of band planes
+    ran = 0
+    for nbytes in (need.value, need.value - band_bytes, need.value - 2 * band_bytes):
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        gin = torch.empty_like(x)
+        gs = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = lib.bf_fast_backward(x.data_ptr(), out.data_ptr(), q.data_ptr(), gt.data_ptr(),
+                                  gin.data_ptr(), gs.data_ptr(), H, W, W, ctypes.byref(p),
+                                  ws.data_ptr(), nbytes, torch.cuda.current_stream().cuda_stream)
+        if st == 5 and r > 52:
+            continue  # below 64 band rows, and no fused fallback at this radius
+        assert st == 0, st
+        torch.cuda.synchronize()
+        assert _rel(gin.cpu().numpy().astype(np.float64), rgin) <= GIN_RTOL, nbytes
+        assert abs(float(gs.item()) - rgs) <= GSIG_RTOL * abs(rgs), nbytes
+        ran += 1
+    assert ran >= 2
+    # through autograd: the default path for this radius
+    xg = x.clone().requires_grad_(True)
+    srt = torch.tensor(sr, dtype=torch.float64, device="cuda", requires_grad=True)
+    y = bf.gpa_bilateral(xg, srt, kind, N, radius=r, sigma_s=ss)
+    (y * gt).sum().backward()
+    assert _rel(xg.grad.cpu().numpy().astype(np.float64), rgin) <= GIN_RTOL
+    assert abs(float(srt.grad.item()) - rgs) <= GSIG_RTOL * abs(rgs)
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (5, 7), (3, 300), (260, 3)])
 def test_fast_backward_tiny_and_thin_images(shape):
     """Radius beyond the image, single rows/columns, ragged tiles: both the
