@@ -181,8 +181,15 @@ bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux,
  *  d_gout               dL/d out.           d_gin: dL/d in (written).
  *  d_gsigma             optional: one double on the device, written (not added).
  *  d_workspace          >= bf_fast_backward_workspace() bytes (may be NULL
- *                       only if d_gsigma is NULL).  The sigma_r sum is reduced
- *                       deterministically in a fixed order.
+ *                       only if d_gsigma is NULL), 256-byte aligned.  The
+ *                       sigma_r sum is reduced deterministically in a fixed
+ *                       order.
+ * For W > 15 the gradient is computed by a two-pass banded backward (a column
+ * pass of a_n, qbar a_n and pbar a_n into workspace planes, then a row pass
+ * that forms the sums above), the adjoint of bf_fast_forward_ws; its
+ * workspace (the query's value) also holds the qbar and pbar planes.  With a
+ * workspace too small for 64 band rows, or none, the fused runtime-W kernel
+ * runs instead where its tile fits (W up to about 52).
  * BF_ERR_WORKSPACE if the workspace is missing or too small. */
 bf_status bf_fast_backward_workspace(int height, int width, const bf_params *p,
                                      size_t *bytes);
