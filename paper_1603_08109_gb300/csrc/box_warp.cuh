@@ -7,7 +7,7 @@
 // band two rows at a time with no block barrier and no value passed through
 // shared memory from one thread to another:
 //   * input rows are copied with cp.async into a per-lane ring in shared
-//     memory one row pair ahead of use; every lane reads back only the bytes
+//     memory DP row pairs ahead of use; every lane reads back only the bytes
 //     it copied itself;
 //   * per column and channel n the running vertical window sum
 //     V_n = sum of u_n over the 2W + 1 rows of the window stays in registers,
@@ -48,13 +48,13 @@ struct WarpStripArgs {
   int vec_out;      // out (and Q') rows 16-byte aligned: 16-byte stores
 };
 
-template <int R>
+template <int R, int DP = 1>
 struct WarpStripGeom {
   static constexpr int C = 8, SW = 32 * C, TW = SW - 2 * C;  // 256 region, 240 output columns
   static constexpr int L = 2 * R + 1;
   // ring rows: the L + 2 rows a row pair reads (two leave, two enter) plus
-  // the next pair in flight
-  static constexpr int RS = L + 4;
+  // the DP pairs in flight
+  static constexpr int RS = L + 2 + 2 * DP;
   static constexpr size_t warp_floats = (size_t)RS * SW;
 };
 
@@ -220,10 +220,10 @@ __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst
 
 // The band loop.  FAST: every row the loop touches is inside the image and
 // every lane's 8 columns are inside the image with 16-byte aligned rows.
-template <int R, int NN, bool FAST>
+template <int R, int NN, int DP, bool FAST>
 __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K, float *my,
                                         int x0, int yo0, int yo1, int cnt0, int cnt1) {
-  using G = WarpStripGeom<R>;
+  using G = WarpStripGeom<R, DP>;
   constexpr int SW = G::SW, L = G::L, RS = G::RS;
   const TileIO &io = A.io;
   const bool vec0 = FAST || (A.vec_in && cnt0 == 4), vec1 = FAST || (A.vec_in && cnt1 == 4);
@@ -256,18 +256,21 @@ __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K
   // region row rho = 0.. is image row yo0 - R + rho and lives in ring slot
   // rho mod RS; rows rho >= 2W complete the window of output row rho - 2W
   const int nrows = (yo1 - yo0) + 2 * R;
-  issue(yo0 - R, 0);
-  issue(yo0 - R + 1, 1);
-  cp_async_commit();
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {  // the first DP pairs
+    issue(yo0 - R + 2 * k, 2 * k);
+    issue(yo0 - R + 2 * k + 1, 2 * k + 1);
+    cp_async_commit();
+  }
   int s0 = 0;  // slot of row rho
   for (int rho = 0; rho < nrows; rho += 2) {
     const int y = yo0 - R + rho;
-    // the next pair goes to the slots of rows rho + 2 - RS and rho + 3 - RS,
+    // pair rho + 2 DP goes to the slots of rows rho - L - 2 and rho - L - 1,
     // which left the window in the previous iteration
-    issue(y + 2, wrap(s0 + 2));
-    issue(y + 3, wrap(s0 + 3));
+    issue(y + 2 * DP, wrap(s0 + 2 * DP));
+    issue(y + 2 * DP + 1, wrap(s0 + 2 * DP + 1));
     cp_async_commit();
-    cp_async_wait<1>();  // rows rho and rho + 1 have landed
+    cp_async_wait<DP>();  // rows rho and rho + 1 have landed
     const int s1 = wrap(s0 + 1);
     float2 fe0[4], fe1[4];
     ws_load8(my + s0 * SW, fe0);
@@ -298,10 +301,10 @@ __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K
   cp_async_wait<0>();
 }
 
-template <int R, int NN>
+template <int R, int NN, int DP = 1>
 __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip, int band,
                                                float *ring) {
-  using G = WarpStripGeom<R>;
+  using G = WarpStripGeom<R, DP>;
   constexpr int SW = G::SW, RS = G::RS;
   static_assert(R >= 1 && R <= 8, "the halo must come from one neighbouring lane");
   static_assert(NN >= 2 && NN <= 6, "order range of the warp-strip kernel");
@@ -324,14 +327,14 @@ __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip
     for (int r = 0; r < RS; ++r) my[r * SW + e] = A.sentinel;
   for (int e = cnt1; e < 4; ++e)
     for (int r = 0; r < RS; ++r) my[r * SW + 128 + e] = A.sentinel;
-  // rows touched: yo0 - W .. yo1 + W + 1 (the last pair's prefetch)
-  const bool rows_in = yo0 - R >= 0 && yo1 + R + 2 <= io.H;
+  // rows touched: yo0 - W .. yo1 + W + 2 DP - 1 (the last prefetches)
+  const bool rows_in = yo0 - R >= 0 && yo1 + R + 2 * DP <= io.H;
   const bool fast = __all_sync(0xffffffffu, rows_in && A.vec_in && A.vec_out && cnt0 == 4 &&
                                                 cnt1 == 4);
   if (fast)
-    ws_band<R, NN, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
   else
-    ws_band<R, NN, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
 }
 
 }  // namespace bfk

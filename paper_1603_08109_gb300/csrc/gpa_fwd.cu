@@ -121,9 +121,11 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   return bfi::check_launch();
 }
 
-// Rows per warp band (even, 16..64): about one wave of resident warps.  The
-// 2W warm-up rows of a band are read and entered but produce no output, so
-// bands are kept long where the image allows.
+// Rows per warp band (even, 16..64): about one wave of resident warps, or
+// half a wave for N <= 2.  The 2W warm-up rows of a band are read and entered
+// but produce no output, so bands are kept long where the image allows
+// (measured at 4096^2: 64-row bands beat one full wave of shorter bands for
+// N = 1, 2; for larger N one wave is faster).
 template <int R, int NN>
 bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   using G = bfk::WarpStripGeom<R>;
@@ -165,7 +167,9 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   A.vec_out = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
   A.nstrips = (a.io.W + G::TW - 1) / G::TW;
   const long long per_strip = std::max(1, resident_warps / A.nstrips);
-  const int band = (int)std::min<long long>(64, std::max<long long>(16, (a.io.H + per_strip - 1) / per_strip));
+  const int waves = NN <= 3 ? 2 : 1;  // fewer channels: fewer registers, more warps per SM
+  const int band = (int)std::min<long long>(
+      64, std::max<long long>(16, waves * ((a.io.H + per_strip - 1) / per_strip)));
   A.band = (band + 1) & ~1;
   A.nbands = (a.io.H + A.band - 1) / A.band;
   const long long warps = (long long)A.nstrips * A.nbands;
