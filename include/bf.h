@@ -261,10 +261,21 @@ bf_status bf_direct_backward(const float *d_in, const float *d_gout, float *d_gi
  * spatial filterings in one fused pass.  For e = f it equals bf_fast_forward.
  * d_qaux (optional) receives Q' as in bf_fast_forward.  The guide follows the
  * image's layout (same height, width, pitch).  Radius limit: W <= 56.
+ * bf_joint_forward_workspace / bf_joint_forward_ws: the same filter for
+ * Gaussian W > 15 and box W > 24 (where the fused box tile stops being the
+ * faster form) by the two-pass banded split (see bf_fast_forward_ws): a column pass
+ * of b_n and b_n (f - t_c) into 2N workspace planes per band, then a row pass
+ * forming Q' and U'.  Workspace rule as for bf_fast_forward_ws with 2N planes
+ * per band row (64 rows at least); radii up to BF_MAX_RADIUS; below those
+ * radii the workspace query returns 0 and the call runs bf_joint_forward.
  * bf_joint_direct computes the same filter with the exact Gaussian range
  * kernel, O((2W+1)^2) per pixel (the same-GPU comparison). */
 bf_status bf_joint_forward(const float *d_in, const float *d_guide, float *d_out, float *d_qaux,
                            int height, int width, int pitch, const bf_params *p, void *stream);
+bf_status bf_joint_forward_workspace(int height, int width, const bf_params *p, size_t *bytes);
+bf_status bf_joint_forward_ws(const float *d_in, const float *d_guide, float *d_out,
+                              float *d_qaux, int height, int width, int pitch, const bf_params *p,
+                              void *d_workspace, size_t ws_bytes, void *stream);
 bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out, int height,
                           int width, int pitch, const bf_params *p, void *stream);
 

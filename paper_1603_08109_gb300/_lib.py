@@ -57,6 +57,8 @@ SIGNATURES = {
     "bf_fast_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp]),
     "bf_fast_forward_stored": (_i, [_vp, _vp, _vp, _vp, _sz, _i, _i, _i, _pp, _vp]),
     "bf_fast_forward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
+    "bf_joint_forward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
+    "bf_joint_forward_ws": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_forward_ws": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_fast_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),

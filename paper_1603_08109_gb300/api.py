@@ -255,16 +255,32 @@ def _guide_like(x: torch.Tensor, guide: torch.Tensor) -> torch.Tensor:
 
 def joint_forward(img: torch.Tensor, guide: torch.Tensor, kind: int, sigma_r: float, N: int,
                   radius: int = 0, sigma_s: float = 0.0, t_c: float = 128.0,
-                  return_q: bool = False, out: Optional[torch.Tensor] = None):
-    """Cross (joint) bilateral filter, Gaussian-polynomial form (range kernel on guide)."""
+                  return_q: bool = False, out: Optional[torch.Tensor] = None,
+                  band_rows: Optional[int] = None):
+    """Cross (joint) bilateral filter, Gaussian-polynomial form (range kernel on guide).
+
+    For radii above 15 the banded two-pass form with a workspace from torch's
+    allocator (band_rows, a multiple of 64, overrides its band height)."""
     x, on_cpu = _as_device_image(img)
     g = _guide_like(x, guide)
     o = _image_like(x, out if not on_cpu else None)
     q = _like(x) if return_q else None
     p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
     H, W = x.shape
-    check(lib().bf_joint_forward(_ptr(x), _ptr(g), _ptr(o), _ptr(q), H, W, x.stride(0),
-                                 ctypes.byref(p), _stream(x.device)), "bf_joint_forward")
+    n = ctypes.c_size_t(0)
+    check(lib().bf_joint_forward_workspace(H, W, ctypes.byref(p), ctypes.byref(n)),
+          "bf_joint_forward_workspace")
+    nbytes = int(n.value)
+    if nbytes > 0:
+        if band_rows is not None:
+            nbytes = int(band_rows) * 2 * int(N) * ((W + 3) // 4 * 4) * 4
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+        check(lib().bf_joint_forward_ws(_ptr(x), _ptr(g), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                        ctypes.byref(p), _ptr(ws), nbytes, _stream(x.device)),
+              "bf_joint_forward")
+    else:
+        check(lib().bf_joint_forward(_ptr(x), _ptr(g), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                     ctypes.byref(p), _stream(x.device)), "bf_joint_forward")
     if on_cpu:
         o = o.cpu()
         q = q.cpu() if q is not None else None

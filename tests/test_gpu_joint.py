@@ -43,6 +43,26 @@ def test_joint_forward_matches_definition(case):
     assert np.abs(out.cpu().numpy() - ro)[mask].max() <= OUT_TOL
 
 
+@pytest.mark.parametrize("case", [(bf.GAUSS, 20, 20 / 3.0, 45.0, 25), (bf.GAUSS, 60, 20.0, 60.0, 12),
+                                  (bf.BOX, 30, 0.0, 60.0, 19)], ids=lambda c: "k%d_r%d" % c[:2])
+def test_joint_banded_two_pass(case):
+    """The banded joint filter (radius > 15): several bands (64 rows, ragged last
+    band), several column tiles, against the checker's definition."""
+    kind, r, ss, sr, N = case
+    H, W = 150, 181
+    f, e = _pair(H, W, seed=r + 3)
+    w = spatial(kind, r, ss)
+    ro, num, den = oracle.joint_gpa(f, e, w, sr, N, return_parts=True)
+    mask = den >= 0.5 * w[r, r]
+    for band in (64, None):
+        out, q = bf.joint_forward(torch.from_numpy(f).cuda(), torch.from_numpy(e).cuda(), kind, sr,
+                                  N, radius=r, sigma_s=ss, return_q=True, band_rows=band)
+        qg = q.cpu().numpy().astype(np.float64)
+        assert (np.abs(qg - den) <= Q_ATOL + Q_RTOL * np.abs(den)).all()
+        og = out.cpu().numpy().astype(np.float64)
+        assert np.abs(og - ro)[mask].max() <= OUT_TOL
+
+
 def test_joint_with_guide_equal_to_image_is_plain_filter():
     f = image(45, 280, seed=3)
     x = torch.from_numpy(f).cuda()
