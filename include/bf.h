@@ -136,7 +136,8 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
                           int height, int width, int pitch,
                           const bf_params *p, void *stream);
 
-/* Forward with a caller-provided workspace, for large radii (W > 15).  The
+/* Forward with a caller-provided workspace, for large radii (Gaussian W >= 12
+ * except 15, box W > 15, where it is faster than the fused kernels).  The
  * spatial filter is separable (eq. spatial_kernel1 on the square Omega), so
  * the image is processed in bands of rows, two kernels per band: the first
  * filters the columns of every power image a_0..a_N of the band (with the
@@ -145,13 +146,13 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
  * Results equal bf_fast_forward's up to float rounding.
  * bf_fast_forward_workspace: the workspace in bytes for bands tall enough
  *   to give each launch several waves of CTAs (at most 2 GiB unless 64 rows
- *   need more); 0 when the radius is 15 or less (bf_fast_forward_ws then
- *   runs bf_fast_forward).
+ *   need more); 0 below those radii (bf_fast_forward_ws then runs
+ *   bf_fast_forward).
  * bf_fast_forward_ws: d_workspace device memory, 16-byte aligned, owned by
  *   the caller, of ws_bytes >= 64 rows of N + 1 planes, i.e. 64 (N+1) Wp
  *   floats with Wp = width rounded up to a multiple of 4; a larger workspace
  *   gives taller bands.  Same arguments and outputs as bf_fast_forward.
- *   BF_ERR_WORKSPACE for a missing or too small workspace when W > 15. */
+ *   BF_ERR_WORKSPACE for a missing or too small workspace at those radii. */
 bf_status bf_fast_forward_workspace(int height, int width, const bf_params *p,
                                     size_t *bytes);
 bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux,
@@ -281,9 +282,10 @@ bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out,
 
 /* --------------------------------------------------- batched forward
  * Many images of uneven sizes, each with its own spatial kind, W, sigma_s,
- * sigma_r and N.  Images with W <= 15 are filtered by ONE persistent launch:
+ * sigma_r and N.  Images below the banded radii (see bf_fast_forward_ws) are
+ * filtered by ONE persistent launch:
  * CTAs take output tiles from a device work queue (longest work first) until
- * it is empty.  Images with W > 15 take the two-pass banded forward (see
+ * it is empty.  The others take the two-pass banded forward (see
  * bf_fast_forward_ws): one column-pass launch and one row-pass launch over
  * the tiles of a group of images, their planes in the plan's workspace
  * (groups keep the plane region at most 4 GiB, reused group after group).

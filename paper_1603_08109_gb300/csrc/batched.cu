@@ -1,7 +1,8 @@
 // Batched forward: many images of uneven sizes, each with its own spatial
 // kind, W, sigma_s, sigma_r and N.
 //
-// Images with W <= 15 go through ONE persistent launch: the host plan splits
+// Images below the banded path's radii (Gaussian W < 12 or W = 15, box
+// W <= 15) go through ONE persistent launch: the host plan splits
 // them into output tiles (work items), estimates each item's cost from its
 // (N + 1) filterings and tile geometry, and sorts the items longest first.
 // The grid is sized to the device (SMs x resident CTAs).  Each CTA
@@ -9,7 +10,7 @@
 // CTA ever waits on another) and runs the same tile body as the single-image
 // kernel with that item's parameters.
 //
-// Images with W > 15 take the two-pass banded forward (gpa_banded.cuh), one
+// The other images take the two-pass banded forward (gpa_banded.cuh), one
 // launch per pass over the tiles of a group of images (longest first); each
 // image's N + 1 column-filtered planes live in the plan's workspace, groups
 // are formed so that one group's planes fit a 4 GiB region that the next
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(BNT) gpa_batched_kernel(const __grid_constant_
   }
 }
 
-// ---- banded items (W > 15)
+// ---- banded items (the banded path's radii)
 struct BandItem {
   int desc, bx, by, pad;
 };
@@ -179,7 +180,7 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
     }
     bd.io = {d.d_in, d.d_out, d.d_qaux, nullptr, 0, d.height, d.width, d.pitch};
     const int R = bd.fc.R;
-    if (R > 15) {
+    if (bfk::banded_forward_preferred(bd.fc.kind, R)) {
       bd.th = 0;
       large.push_back(i);
       continue;

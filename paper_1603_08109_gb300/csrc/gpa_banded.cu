@@ -1,6 +1,6 @@
-// Two-pass banded forward of Algorithm 2 for large radii (W > 15): single-
-// image launches and the workspace entry points (tile bodies in
-// gpa_banded.cuh).
+// Two-pass banded forward of Algorithm 2 for large radii (Gaussian W >= 12
+// except 15, box W > 15): single-image launches and the workspace entry
+// points (tile bodies in gpa_banded.cuh).
 //
 // A fused 2-D tile needs a 2W halo in both directions: at W = 60 its region
 // is tens of times the tile, does not fit shared memory at a useful size, and
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kBandNT) band_hpass(const __grid_constant__ Ba
   band_hpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm);
 }
 
-bool banded_fits(const bfi::FilterConsts &fc) { return fc.R > 15; }
+bool banded_fits(const bfi::FilterConsts &fc) { return banded_forward_preferred(fc.kind, fc.R); }
 
 int round_up4(int w) { return (w + 3) / 4 * 4; }
 

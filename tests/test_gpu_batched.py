@@ -1,6 +1,6 @@
 """GPU batched forward: each image of one plan equals the single-image path
-bit for bit (the 256-thread, 16-row fused tile for W <= 15; the two-pass
-banded forward for W > 15), graph replays are identical, and sampled pixels
+bit for bit (the 256-thread, 16-row fused tile below the banded radii; the
+two-pass banded forward at them), graph replays are identical, and sampled pixels
 match the checker."""
 import numpy as np
 import pytest
@@ -31,9 +31,12 @@ def _with_order(specs):
 
 
 def _single(img, sp):
-    # W <= 15: the persistent launch's 256-thread, 16-row tile (variant 0);
-    # W > 15: the banded two-pass forward (the default path for such radii)
-    variant = 0 if sp["radius"] <= 15 else -1
+    # the banded two-pass forward (the default path) at Gaussian radii >= 12
+    # except 15 and box radii > 15; else the persistent launch's 256-thread,
+    # 16-row tile (variant 0)
+    r = sp["radius"]
+    banded = (r >= 12 and r != 15) if sp["kind"] == bf.GAUSS else r > 15
+    variant = -1 if banded else 0
     return bf.gpa_forward(img, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
                           sigma_s=sp["sigma_s"], variant=variant)
 

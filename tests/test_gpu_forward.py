@@ -91,10 +91,10 @@ def test_streaming_box_kernel(r):
         bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=6)
 
 
-@pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 20, 20 / 3.0), (bf.GAUSS, 60, 20.0),
-                                       (bf.BOX, 20, 0.0), (bf.BOX, 50, 0.0)])
+@pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 12, 4.0), (bf.GAUSS, 20, 20 / 3.0),
+                                       (bf.GAUSS, 60, 20.0), (bf.BOX, 20, 0.0), (bf.BOX, 50, 0.0)])
 def test_banded_two_pass(kind, r, ss):
-    """The banded two-pass forward (radius > 15): several bands of 64 rows with
+    """The banded two-pass forward (Gaussian radius >= 12, box > 15): several bands of 64 rows with
     a ragged last band, several column tiles with ragged edges, the band
     height from the default workspace, and Q'."""
     H, W = 150, 301
