@@ -275,36 +275,30 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
   }
   cudaError_t e = cudaSuccess;
   if (!large.empty()) {
-    static std::once_flag once;
-    static cudaError_t band_err = cudaSuccess;
-    std::call_once(once, [] {
-      const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
-      const size_t vs = std::max(bfk::vpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
-                                 bfk::vpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
-      const size_t hs = std::max(bfk::hpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
-                                 bfk::hpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
-      cudaError_t err = cudaFuncSetAttribute(gpa_batched_band_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vs);
-      if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(gpa_batched_band_kernel<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
-      band_err = err;
-    });
-    e = band_err;
+    const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
+    const size_t vs = std::max(bfk::vpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
+                               bfk::vpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
+    const size_t hs = std::max(bfk::hpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
+                               bfk::hpass_smem(BF_SPATIAL_BOX, BF_MAX_RADIUS, 0));
+    bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_band_kernel<true>), vs);
+    if (st == BF_OK)
+      st = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_band_kernel<false>), hs);
+    if (st != BF_OK) {
+      delete plan;
+      return st;
+    }
   }
   // fused launch: every SM filled with as many CTAs as fit
   if (e == cudaSuccess && !plan->items.empty()) {
-    e = cudaFuncSetAttribute(gpa_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)plan->smem);
-    int per_sm = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpa_batched_kernel, BNT,
-                                                        plan->smem);
-    if (e == cudaSuccess && per_sm < 1) {
+    const void *fn = reinterpret_cast<const void *>(gpa_batched_kernel);
+    int resident = 0;
+    bf_status st = bfi::ensure_smem(fn, plan->smem);
+    if (st == BF_OK) st = bfi::resident_ctas(fn, BNT, plan->smem, &resident);
+    if (st != BF_OK || resident < 1) {
       delete plan;
-      return BF_ERR_UNSUPPORTED;
+      return st != BF_OK ? st : BF_ERR_UNSUPPORTED;
     }
-    plan->ctas = (int)std::min<long long>((long long)sms * per_sm, (long long)plan->items.size());
+    plan->ctas = (int)std::min<long long>((long long)resident, (long long)plan->items.size());
   }
   if (e != cudaSuccess) {
     delete plan;
@@ -358,6 +352,9 @@ bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_byte
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_ws);
   if (!plan->items.empty()) {
+    const bf_status sm = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_kernel),
+                                          plan->smem);
+    if (sm != BF_OK) return sm;
     BatchArgs A;
     A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
     A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items);

@@ -5,6 +5,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "bf_internal.h"
 
@@ -41,6 +44,44 @@ bf_status cuda_status(cudaError_t e) {
 }
 
 bf_status check_launch() { return cuda_status(cudaGetLastError()); }
+
+bf_status ensure_smem(const void *func, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> set;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, func);
+  const auto it = set.find(key);
+  if (it != set.end() && it->second >= bytes) return BF_OK;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  set[key] = bytes;
+  return BF_OK;
+}
+
+bf_status resident_ctas(const void *func, int threads, size_t smem, int *ctas) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, func, threads, smem);
+  const auto it = cache.find(key);
+  if (it != cache.end()) {
+    *ctas = it->second;
+    return BF_OK;
+  }
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  cache[key] = per_sm * sms;
+  *ctas = per_sm * sms;
+  return BF_OK;
+}
 
 bf_status check_image(const void *in, const void *out, int height, int width, int pitch) {
   if (!in || !out) return BF_ERR_INVALID_ARG;

@@ -32,6 +32,12 @@ struct FilterConsts {
 // Status helpers (bf_host.cpp).
 bf_status cuda_status(cudaError_t e);
 bf_status check_launch();
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device (cached per device and kernel; thread-safe).
+bf_status ensure_smem(const void *func, size_t bytes);
+// Resident CTAs of a kernel on the current device (SMs x CTAs per SM) for a
+// block size and dynamic shared memory (cached; thread-safe).
+bf_status resident_ctas(const void *func, int threads, size_t smem, int *ctas);
 void set_error_text(const char *msg);
 
 // Validates image sizes / pointers / params and fills the device constants.

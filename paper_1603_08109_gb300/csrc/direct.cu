@@ -246,14 +246,8 @@ bf_status fill_args(const bf_params *p, int H, int W, int pitch, DirectArgs *A) 
 }
 
 template <typename K>
-bf_status set_smem(K kern, size_t bytes, int *configured) {
-  if ((int)bytes > *configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    *configured = (int)bytes;
-  }
-  return BF_OK;
+bf_status set_smem(K kern, size_t bytes) {
+  return bfi::ensure_smem(reinterpret_cast<const void *>(kern), bytes);
 }
 
 dim3 direct_grid(int H, int W) { return dim3((W + DTW - 1) / DTW, (H + DTH - 1) / DTH); }
@@ -272,8 +266,7 @@ bf_status bf_direct(const float *d_in, float *d_out, int height, int width, int 
   A.in = d_in;
   A.out = d_out;
   const size_t smem = region_floats(A.R) * sizeof(float);
-  static int configured = 0;
-  st = set_smem(direct_kernel<0>, smem, &configured);
+  st = set_smem(direct_kernel<0>, smem);
   if (st != BF_OK) return st;
   direct_kernel<0><<<direct_grid(height, width), DNT, smem, static_cast<cudaStream_t>(stream)>>>(A);
   return bfi::check_launch();
@@ -318,15 +311,14 @@ bf_status bf_direct_backward(const float *d_in, const float *d_gout, float *d_gi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const dim3 g = direct_grid(height, width);
   const size_t smem1 = region_floats(A.R) * sizeof(float);
-  static int conf1 = 0, conf2 = 0;
-  st = set_smem(direct_kernel<1>, smem1, &conf1);
+  st = set_smem(direct_kernel<1>, smem1);
   if (st != BF_OK) return st;
   direct_kernel<1><<<g, DNT, smem1, s>>>(A);
   st = bfi::check_launch();
   if (st != BF_OK) return st;
   const size_t smem2 = 3 * region_floats(A.R) * sizeof(float);
   if (smem2 > 232448) return BF_ERR_UNSUPPORTED;
-  st = set_smem(direct_bwd_gather, smem2, &conf2);
+  st = set_smem(direct_bwd_gather, smem2);
   if (st != BF_OK) return st;
   direct_bwd_gather<<<g, DNT, smem2, s>>>(A);
   st = bfi::check_launch();

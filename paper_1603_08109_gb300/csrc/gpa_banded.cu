@@ -61,18 +61,13 @@ int preferred_band_rows(int height, int width, int N) {
 
 template <int KIND>
 bf_status launch_band(BandArgs &A, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t init_err = cudaSuccess;
-  std::call_once(once, [] {
-    const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
-    cudaError_t e = cudaFuncSetAttribute(band_vpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)vpass_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(band_hpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)hpass_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    init_err = e;
-  });
-  if (init_err != cudaSuccess) return bfi::cuda_status(init_err);
+  const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
+  bf_status est = bfi::ensure_smem(reinterpret_cast<const void *>(band_vpass<KIND>),
+                                   vpass_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est == BF_OK)
+    est = bfi::ensure_smem(reinterpret_cast<const void *>(band_hpass<KIND>),
+                           hpass_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est != BF_OK) return est;
   const int R = A.fc.R, ntp = A.fc.ntaps_pad;
   const size_t vs = vpass_smem(KIND, R, ntp), hs = hpass_smem(KIND, R, ntp);
   const int band = A.rows;

@@ -387,18 +387,13 @@ BwdLayout layout(int height, int width, int N, size_t ws_bytes) {
 
 template <int KIND>
 bf_status run_banded_bwd(BandBwdArgs &A, const BwdLayout &L, double *gsigma, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t init_err = cudaSuccess;
-  std::call_once(once, [] {
-    const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
-    cudaError_t e = cudaFuncSetAttribute(band_bwd_vpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bv_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(band_bwd_hpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)bh_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    init_err = e;
-  });
-  if (init_err != cudaSuccess) return bfi::cuda_status(init_err);
+  const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
+  bf_status est = bfi::ensure_smem(reinterpret_cast<const void *>(band_bwd_vpass<KIND>),
+                                   bv_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est == BF_OK)
+    est = bfi::ensure_smem(reinterpret_cast<const void *>(band_bwd_hpass<KIND>),
+                           bh_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est != BF_OK) return est;
   const int R = A.fc.R, ntp = A.fc.ntaps_pad;
   const size_t vs = bv_smem(KIND, R, ntp), hs = bh_smem(KIND, R, ntp);
   const long long n = (long long)A.H * A.Wp;

@@ -569,13 +569,8 @@ template <int KIND, int R>
 bf_status launch_bwd_fixed_r(const BwdArgs &A, cudaStream_t s) {
   using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
   auto kern = gpa_bwd_fixed_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes());
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = true;
-  }
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), G::smem_bytes());
+  if (st != BF_OK) return st;
   dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
   kern<<<grid, kBwdFixedNT, G::smem_bytes(), s>>>(A);
   return bfi::check_launch();
@@ -631,13 +626,8 @@ bf_status launch_bwd(const BwdArgs &A, cudaStream_t s) {
   constexpr int KH = 8;
   const size_t smem = bwd_smem_bytes(NT, TH, A.fc.R, A.fc.ntaps_pad, KIND);
   auto kern = gpa_bwd_kernel<KIND, NT, TH, KH, STORED>;
-  static int configured = 0;
-  if ((int)smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = (int)smem;
-  }
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
+  if (st != BF_OK) return st;
   const int TW = NT - 2 * A.fc.R;
   dim3 grid((A.W + TW - 1) / TW, (A.H + TH - 1) / TH);
   kern<<<grid, NT, smem, s>>>(A);

@@ -99,21 +99,12 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   using G = bfk::FixedGeom<R, 256, 16>;
   const size_t smem = G::smem_bytes(args.fc.N);
   auto kern = gpa_fwd_fixed_kernel<KIND, R>;
-  // resident CTAs (per SM x SMs) for this shared-memory size, cached
-  static size_t cached_smem = 0;
-  static int resident = 0;
-  if (smem != cached_smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes(BF_MAX_ORDER));
-    int per_sm = 0, sms = 0, dev = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    if (per_sm < 1) return BF_ERR_UNSUPPORTED;
-    resident = per_sm * sms;
-    cached_smem = smem;
-  }
+  const void *fn = reinterpret_cast<const void *>(kern);
+  bf_status st = bfi::ensure_smem(fn, G::smem_bytes(BF_MAX_ORDER));
+  int resident = 0;  // resident CTAs (SMs x CTAs per SM) at this shared-memory size
+  if (st == BF_OK) st = bfi::resident_ctas(fn, 256, smem, &resident);
+  if (st != BF_OK) return st;
+  if (resident < 1) return BF_ERR_UNSUPPORTED;
   const long long tiles = (long long)((args.io.W + G::TW - 1) / G::TW) * ((args.io.H + 15) / 16);
   if (tiles > 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
   const int grid = (int)std::min<long long>(tiles, resident);
@@ -131,21 +122,12 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   using G = bfk::WarpStripGeom<R>;
   constexpr size_t smem = kWarpWPB * G::warp_floats * sizeof(float);
   auto kern = box_warp_kernel<R, NN>;
-  static std::once_flag once;
-  static cudaError_t init_err = cudaSuccess;
-  static int resident_warps = 0;
-  std::call_once(once, [&] {
-    int per_sm = 0, sms = 0, dev = 0;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kWarpWPB, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    init_err = e;
-    resident_warps = per_sm * sms * kWarpWPB;
-  });
-  if (init_err != cudaSuccess) return bfi::cuda_status(init_err);
+  const void *fn = reinterpret_cast<const void *>(kern);
+  bf_status st = bfi::ensure_smem(fn, smem);
+  int resident_ctas = 0;
+  if (st == BF_OK) st = bfi::resident_ctas(fn, 32 * kWarpWPB, smem, &resident_ctas);
+  if (st != BF_OK) return st;
+  const int resident_warps = resident_ctas * kWarpWPB;
   if (resident_warps < 1) return BF_ERR_UNSUPPORTED;
   bfk::WarpStripArgs A;
   A.io = a.io;
@@ -213,13 +195,8 @@ bf_status launch_fwd(const FwdArgs &args, cudaStream_t s) {
   const int TW = NT - 2 * args.fc.R;
   const size_t smem = bfk::fwd_smem_bytes(NT, TH, args.fc.R, args.fc.ntaps_pad);
   auto kern = gpa_fwd_kernel<KIND, NT, TH, STORE>;
-  static int configured = 0;  // bytes of dynamic smem already permitted
-  if ((int)smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = (int)smem;
-  }
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
+  if (st != BF_OK) return st;
   dim3 grid((args.io.W + TW - 1) / TW, (args.io.H + TH - 1) / TH);
   kern<<<grid, NT, smem, s>>>(args);
   return bfi::check_launch();

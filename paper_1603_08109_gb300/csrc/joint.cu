@@ -392,13 +392,8 @@ template <int KIND, int R>
 bf_status launch_joint_fixed_r(const JointArgs &A, cudaStream_t s) {
   using G = JointFixedGeom<R>;
   auto kern = joint_fixed_kernel<KIND, R>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::smem_bytes());
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = true;
-  }
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), G::smem_bytes());
+  if (st != BF_OK) return st;
   dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + G::TH - 1) / G::TH);
   kern<<<grid, G::NT, G::smem_bytes(), s>>>(A);
   return bfi::check_launch();
@@ -500,13 +495,8 @@ template <int KIND, int NT, int TH>
 bf_status launch_joint(const JointArgs &A, cudaStream_t s) {
   const size_t smem = joint_smem(NT, TH, A.fc.R, A.fc.ntaps_pad);
   auto kern = joint_kernel<KIND, NT, TH>;
-  static int configured = 0;
-  if ((int)smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = (int)smem;
-  }
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
+  if (st != BF_OK) return st;
   const int TW = NT - 2 * A.fc.R;
   dim3 grid((A.W + TW - 1) / TW, (A.H + TH - 1) / TH);
   kern<<<grid, NT, smem, s>>>(A);
@@ -569,13 +559,8 @@ bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out,
                          : 0.f;
   const size_t smem = 2 * jd_plane(fc.R) * sizeof(float);
   if (smem > (size_t)smem_optin_j()) return BF_ERR_UNSUPPORTED;
-  static int configured = 0;
-  if ((int)smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(joint_direct_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return bfi::cuda_status(e);
-    configured = (int)smem;
-  }
+  st = bfi::ensure_smem(reinterpret_cast<const void *>(joint_direct_kernel), smem);
+  if (st != BF_OK) return st;
   dim3 grid((width + DTW - 1) / DTW, (height + DTH - 1) / DTH);
   joint_direct_kernel<<<grid, DNT, smem, static_cast<cudaStream_t>(stream)>>>(A);
   return bfi::check_launch();

@@ -286,18 +286,13 @@ int joint_band_rows(int height, int width, int N, size_t ws_bytes) {
 
 template <int KIND>
 bf_status run_joint_band(JointBandArgs &A, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t init_err = cudaSuccess;
-  std::call_once(once, [] {
-    const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
-    cudaError_t e = cudaFuncSetAttribute(joint_band_vpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)jv_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(joint_band_hpass<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)jh_smem(KIND, BF_MAX_RADIUS, ntp_max));
-    init_err = e;
-  });
-  if (init_err != cudaSuccess) return bfi::cuda_status(init_err);
+  const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
+  bf_status est = bfi::ensure_smem(reinterpret_cast<const void *>(joint_band_vpass<KIND>),
+                                   jv_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est == BF_OK)
+    est = bfi::ensure_smem(reinterpret_cast<const void *>(joint_band_hpass<KIND>),
+                           jh_smem(KIND, BF_MAX_RADIUS, ntp_max));
+  if (est != BF_OK) return est;
   const int R = A.fc.R, ntp = A.fc.ntaps_pad;
   const size_t vs = jv_smem(KIND, R, ntp), hs = jh_smem(KIND, R, ntp);
   const int band = A.rows;
