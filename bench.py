@@ -336,7 +336,7 @@ def run_sweeps(args):
         cms = _time_ms(lambda: o.copy_(x), 10, stream, flush)
         emit({"sweep": "roofline4096", "kernel": "torch copy (reference)", "ms": cms,
               "gbs": 8 * px / cms / 1e6, "frac_of_measured_hbm": 8 * px / cms / 1e6 / hbm_peak})
-        for kind, R, ss in ((bf.BOX, 5, 0.0), (bf.GAUSS, 9, 3.0)):
+        for kind, R, ss in ((bf.BOX, 3, 0.0), (bf.BOX, 5, 0.0), (bf.GAUSS, 9, 3.0)):
             nb = bf.order_from_delta(kind, R, ss, 40.0, 1.0)
             for N in (1, 2, 3, 5, 8, nb):
                 fms = _time_ms(lambda: bf.gpa_forward(x, kind, 40.0, N, radius=R, sigma_s=ss,
@@ -348,6 +348,21 @@ def run_sweeps(args):
                       "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src,
                       "alu_ops_frac": fwd_ops_per_pixel(kind, R, N) * px / (fms * 1e-3) /
                       fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+        # the same generator at 8192^2: the small-N box forward past the launch ramp and tail
+        x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)
+        o = torch.empty_like(x)
+        px = 8192.0 * 8192.0
+        cms = _time_ms(lambda: o.copy_(x), 10, stream, flush)
+        emit({"sweep": "roofline4096", "size": 8192, "kernel": "torch copy (reference)", "ms": cms,
+              "gbs": 8 * px / cms / 1e6, "frac_of_measured_hbm": 8 * px / cms / 1e6 / hbm_peak})
+        for R in (3, 5):
+            fms = _time_ms(lambda: bf.gpa_forward(x, bf.BOX, 40.0, 1, radius=R, out=o), 10, stream,
+                           flush)
+            gbs = 8 * px / fms / 1e6
+            emit({"sweep": "roofline4096", "size": 8192, "kind": "box", "radius": R, "sigma_r": 40.0,
+                  "N": 1, "fwd_ms": fms, "fwd_mpx_s": px / fms / 1e3, "algorithmic_gbs": gbs,
+                  "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src})
+        del x, o
     if "large8192" in names:
         # 8192^2 gradient + polygons; Gaussian sigma_s=20 (W=60), sigma_r=40, N from delta=0.5
         x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)

@@ -1,9 +1,13 @@
 // Warp-strip streaming forward for the box spatial kernel at small order
 // (N <= 5) and small radius (W <= 8): the memory-bound regime of Algorithm 2.
 //
-// Each warp owns a strip of 256 region columns, 8 consecutive columns per
-// lane (lanes 1..30 produce the strip's 240 output columns, lanes 0 and 31
-// carry the W-column halos), and a band of output rows.  It streams down the
+// Each warp owns a strip of 32 C region columns, C = 8 or 4 consecutive
+// columns per lane (the ceil(W / C) lanes at each end carry the W-column
+// halos, the others produce the strip's output columns: 240 for C = 8, 120
+// or 112 for C = 4 and W = 3 or 5), and a band of output rows.  Four columns
+// per lane halve the per-warp ring and the registers, so about twice as many
+// warps are resident per SM, for twice the halo shuffles per pixel and more
+// halo lanes.  It streams down the
 // band two rows at a time with no block barrier and no value passed through
 // shared memory from one thread to another:
 //   * input rows are copied with cp.async into a per-lane ring in shared
@@ -15,8 +19,8 @@
 //     |u_n| <= (n/e)^{n/2} <= 4.6 for n <= 5).  A row leaving the window is
 //     regenerated from its ring entry by the same instructions that produced
 //     it on entry, so what is subtracted is bitwise what was added;
-//   * horizontal window sums S_n take the W halo columns of the neighbouring
-//     lanes by warp shuffles;
+//   * horizontal window sums S_n take the W halo columns from the lanes one
+//     (or, for C = 4 and W > 4, two) positions away by warp shuffles;
 //   * Algorithm 2's sums at the centre pixel are P = sum_{n<N} H^n S_{n+1}/n!
 //     and Q = sum_{n<N} H^n S_n/n! (Horner form); the centre's factor
 //     e^{-H^2/2} of Q' and P' cancels in f_GPA = t_c + sigma_r P/Q and is
@@ -48,9 +52,13 @@ struct WarpStripArgs {
   int vec_out;      // out (and Q') rows 16-byte aligned: 16-byte stores
 };
 
-template <int R, int DP = 1>
+template <int R, int DP = 1, int C = 8>
 struct WarpStripGeom {
-  static constexpr int C = 8, SW = 32 * C, TW = SW - 2 * C;  // 256 region, 240 output columns
+  static_assert(C == 4 || C == 8, "4 or 8 columns per lane");
+  static constexpr int SW = 32 * C;             // region columns of a strip
+  static constexpr int HL = (R + C - 1) / C;    // halo lanes on each side
+  static constexpr int TW = SW - 2 * HL * C;    // output columns of a strip
+  static constexpr int NCH = C / 4;             // 16-byte chunks per lane and row
   static constexpr int L = 2 * R + 1;
   // ring rows: the L + 2 rows a row pair reads (two leave, two enter) plus
   // the DP pairs in flight
@@ -91,29 +99,31 @@ __device__ __forceinline__ float2 ws_u0(const WsConst &K, float2 f) {
   return make_float2(ws_ex2(-t.x), ws_ex2(-t.y));
 }
 
-__device__ __forceinline__ void ws_load8(const float *slot, float2 (&f)[4]) {
-  const float4 lo = *reinterpret_cast<const float4 *>(slot);
-  const float4 hi = *reinterpret_cast<const float4 *>(slot + 128);
-  f[0] = make_float2(lo.x, lo.y);
-  f[1] = make_float2(lo.z, lo.w);
-  f[2] = make_float2(hi.x, hi.y);
-  f[3] = make_float2(hi.z, hi.w);
+// The lane's C intensities of one ring row (chunk j at slot + 128 j).
+template <int C>
+__device__ __forceinline__ void ws_load(const float *slot, float2 (&f)[C / 2]) {
+#pragma unroll
+  for (int j = 0; j < C / 4; ++j) {
+    const float4 v = *reinterpret_cast<const float4 *>(slot + 128 * j);
+    f[2 * j] = make_float2(v.x, v.y);
+    f[2 * j + 1] = make_float2(v.z, v.w);
+  }
 }
 
-// V_n += u_n (ADD) or V_n -= u_n for the 8 intensities of one row.  The
-// subtraction adds the chain started from -u_0, which is exactly -u_n.
-template <int NN, bool ADD>
-__device__ __forceinline__ void ws_update(const WsConst &K, float2 (&V)[NN][4],
-                                          const float2 (&f)[4]) {
+// V_n += u_n (ADD) or V_n -= u_n for the lane's intensities of one row.  The
+// subtraction is fma(u_n, -1, V_n), rounded as V_n + (-u_n), with u_n from
+// the same instructions as on entry.
+template <int NN, int NP, bool ADD>
+__device__ __forceinline__ void ws_update(const WsConst &K, float2 (&V)[NN][NP],
+                                          const float2 (&f)[NP]) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < NP; ++p) {
     float2 u = ws_u0(K, f[p]);
-    if (!ADD) u = make_float2(-u.x, -u.y);
     const float2 h = __ffma2_rn(f[p], K.hs, K.hs0);
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
       if (n > 0) u = __fmul2_rn(u, h);
-      V[n][p] = __fadd2_rn(V[n][p], u);
+      V[n][p] = ADD ? __fadd2_rn(V[n][p], u) : __ffma2_rn(u, f2(-1.f), V[n][p]);
     }
   }
 }
@@ -127,53 +137,55 @@ __device__ __forceinline__ float ws_tree_sum(const float *e) {
   }
 }
 
-// Box sums over 2W + 1 columns of v at the lane's 8 columns; the W columns on
-// each side come from the neighbouring lanes.
-template <int R>
-__device__ __forceinline__ void ws_hsum(const float2 (&v2)[4], float2 (&S2)[4]) {
+// Box sums over 2W + 1 columns of v at the lane's C columns; the W columns on
+// each side come from the neighbouring lanes (one or two lanes away).
+template <int R, int C>
+__device__ __forceinline__ void ws_hsum(const float2 (&v2)[C / 2], float2 (&S2)[C / 2]) {
   constexpr unsigned FULL = 0xffffffffu;
-  float v[8];
+  float v[C];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < C / 2; ++p) {
     v[2 * p] = v2[p].x;
     v[2 * p + 1] = v2[p].y;
   }
-  float e[8 + 2 * R];
+  float e[C + 2 * R];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) e[R + k] = v[k];
+  for (int k = 0; k < C; ++k) e[R + k] = v[k];
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    e[k] = __shfl_up_sync(FULL, v[8 - R + k], 1);
-    e[R + 8 + k] = __shfl_down_sync(FULL, v[k], 1);
+  for (int d = 1; d <= R; ++d) {  // column d to the left / right of the lane's columns
+    const int m = (d + C - 1) / C;  // lanes away (compile-time after unrolling)
+    e[R - d] = __shfl_up_sync(FULL, v[C * m - d], m);
+    e[R + C - 1 + d] = __shfl_down_sync(FULL, v[d - 1 - C * (m - 1)], m);
   }
-  float S[8];
+  float S[C];
   float s = ws_tree_sum<2 * R + 1>(e);
   S[0] = s;
 #pragma unroll
-  for (int k = 1; k < 8; ++k) {
+  for (int k = 1; k < C; ++k) {
     s += e[k + 2 * R] - e[k - 1];
     S[k] = s;
   }
 #pragma unroll
-  for (int p = 0; p < 4; ++p) S2[p] = make_float2(S[2 * p], S[2 * p + 1]);
+  for (int p = 0; p < C / 2; ++p) S2[p] = make_float2(S[2 * p], S[2 * p + 1]);
 }
 
 // f_GPA (and optionally Q') of one output row from the window sums V and the
 // centre intensities fc.
-template <int R, int NN, bool FULL>
+template <int R, int NN, int C, bool FULL>
 __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst &K,
-                                           const float2 (&V)[NN][4], const float2 (&fc)[4],
-                                           int yo, int x0, bool store) {
-  constexpr int N = NN - 1;
-  float2 H[4], Pa[4], Qa[4];
+                                           const float2 (&V)[NN][C / 2],
+                                           const float2 (&fc)[C / 2], int yo, int x0,
+                                           bool store) {
+  constexpr int N = NN - 1, NP = C / 2;
+  float2 H[NP], Pa[NP], Qa[NP];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) H[p] = __ffma2_rn(fc[p], K.hs, K.hs0);
+  for (int p = 0; p < NP; ++p) H[p] = __ffma2_rn(fc[p], K.hs, K.hs0);
 #pragma unroll
   for (int m = NN - 1; m >= 0; --m) {
-    float2 S[4];
-    ws_hsum<R>(V[m], S);
+    float2 S[NP];
+    ws_hsum<R, C>(V[m], S);
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < NP; ++p) {
       if (m == N) {
         Pa[p] = S[p];
       } else {
@@ -185,46 +197,50 @@ __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst
   }
   if (!store) return;
   const TileIO &io = A.io;
-  float2 o[4];
+  float2 o[NP];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < NP; ++p) {
     // P/Q by the approximate reciprocal (<= 2 ulp, as __fdividef)
     const float2 r = __fmul2_rn(Pa[p], make_float2(ws_rcp(Qa[p].x), ws_rcp(Qa[p].y)));
     o[p] = __ffma2_rn(f2(A.sr), r, f2(A.tc));
   }
   float *orow = io.out + (long long)yo * io.pitch + x0;
-  const bool full = FULL || (A.vec_out && x0 + 8 <= io.W);
+  const bool full = FULL || (A.vec_out && x0 + C <= io.W);
   if (full) {
-    reinterpret_cast<float4 *>(orow)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-    reinterpret_cast<float4 *>(orow)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+#pragma unroll
+    for (int j = 0; j < C / 4; ++j)
+      reinterpret_cast<float4 *>(orow)[j] =
+          make_float4(o[2 * j].x, o[2 * j].y, o[2 * j + 1].x, o[2 * j + 1].y);
   } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < C; ++k)
       if (x0 + k < io.W) orow[k] = k & 1 ? o[k / 2].y : o[k / 2].x;
   }
   if (io.qaux) {
-    float2 q[4];
+    float2 q[NP];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) q[p] = __fmul2_rn(__fmul2_rn(ws_u0(K, fc[p]), Qa[p]), f2(A.qscale));
+    for (int p = 0; p < NP; ++p) q[p] = __fmul2_rn(__fmul2_rn(ws_u0(K, fc[p]), Qa[p]), f2(A.qscale));
     float *qrow = io.qaux + (long long)yo * io.pitch + x0;
     if (full) {
-      reinterpret_cast<float4 *>(qrow)[0] = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
-      reinterpret_cast<float4 *>(qrow)[1] = make_float4(q[2].x, q[2].y, q[3].x, q[3].y);
+#pragma unroll
+      for (int j = 0; j < C / 4; ++j)
+        reinterpret_cast<float4 *>(qrow)[j] =
+            make_float4(q[2 * j].x, q[2 * j].y, q[2 * j + 1].x, q[2 * j + 1].y);
     } else {
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < C; ++k)
         if (x0 + k < io.W) qrow[k] = k & 1 ? q[k / 2].y : q[k / 2].x;
     }
   }
 }
 
 // The band loop.  FAST: every row the loop touches is inside the image and
-// every lane's 8 columns are inside the image with 16-byte aligned rows.
-template <int R, int NN, int DP, bool FAST>
+// every lane's C columns are inside the image with 16-byte aligned rows.
+template <int R, int NN, int DP, int C, bool FAST>
 __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K, float *my,
                                         int x0, int yo0, int yo1, int cnt0, int cnt1) {
-  using G = WarpStripGeom<R, DP>;
-  constexpr int SW = G::SW, L = G::L, RS = G::RS;
+  using G = WarpStripGeom<R, DP, C>;
+  constexpr int SW = G::SW, L = G::L, RS = G::RS, NP = C / 2, HL = G::HL;
   const TileIO &io = A.io;
   const bool vec0 = FAST || (A.vec_in && cnt0 == 4), vec1 = FAST || (A.vec_in && cnt1 == 4);
   auto issue = [&](int y, int slot) {
@@ -236,23 +252,25 @@ __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K
       } else {
         for (int e = 0; e < cnt0; ++e) cp_async4(dst + e, src + e);
       }
-      if (vec1) {
-        cp_async16(dst + 128, src + 4);
-      } else {
-        for (int e = 0; e < cnt1; ++e) cp_async4(dst + 128 + e, src + 4 + e);
+      if constexpr (C == 8) {
+        if (vec1) {
+          cp_async16(dst + 128, src + 4);
+        } else {
+          for (int e = 0; e < cnt1; ++e) cp_async4(dst + 128 + e, src + 4 + e);
+        }
       }
     }
   };
   auto wrap = [](int s) { return s >= RS ? s - RS : s; };  // s < 2 RS
 
-  float2 V[NN][4];
+  float2 V[NN][NP];
 #pragma unroll
   for (int n = 0; n < NN; ++n)
 #pragma unroll
-    for (int p = 0; p < 4; ++p) V[n][p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < NP; ++p) V[n][p] = make_float2(0.f, 0.f);
 
   const int lane = threadIdx.x & 31;
-  const bool writer = lane >= 1 && lane <= 30;
+  const bool writer = lane >= HL && lane < 32 - HL;
   // region row rho = 0.. is image row yo0 - R + rho and lives in ring slot
   // rho mod RS; rows rho >= 2W complete the window of output row rho - 2W
   const int nrows = (yo1 - yo0) + 2 * R;
@@ -272,47 +290,50 @@ __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K
     cp_async_commit();
     cp_async_wait<DP>();  // rows rho and rho + 1 have landed
     const int s1 = wrap(s0 + 1);
-    float2 fe0[4], fe1[4];
-    ws_load8(my + s0 * SW, fe0);
-    ws_load8(my + s1 * SW, fe1);
+    float2 fe0[NP], fe1[NP];
+    ws_load<C>(my + s0 * SW, fe0);
+    ws_load<C>(my + s1 * SW, fe1);
     if (rho < 2 * R) {  // warm-up: the window above the band's first output row
-      if (FAST || (y >= 0 && y < io.H)) ws_update<NN, true>(K, V, fe0);
-      if (FAST || (y + 1 >= 0 && y + 1 < io.H)) ws_update<NN, true>(K, V, fe1);
+      if (FAST || (y >= 0 && y < io.H)) ws_update<NN, NP, true>(K, V, fe0);
+      if (FAST || (y + 1 >= 0 && y + 1 < io.H)) ws_update<NN, NP, true>(K, V, fe1);
     } else {
       const int sl0 = wrap(s0 + RS - L), sl1 = wrap(s1 + RS - L);
       const int sc0 = wrap(s0 + RS - R), sc1 = wrap(s1 + RS - R);
-      float2 fl0[4], fl1[4], fc0[4], fc1[4];
-      ws_load8(my + sl0 * SW, fl0);
-      ws_load8(my + sl1 * SW, fl1);
-      ws_load8(my + sc0 * SW, fc0);
-      ws_load8(my + sc1 * SW, fc1);
+      float2 fl0[NP], fl1[NP], fc0[NP], fc1[NP];
+      ws_load<C>(my + sl0 * SW, fl0);
+      ws_load<C>(my + sl1 * SW, fl1);
+      ws_load<C>(my + sc0 * SW, fc0);
+      ws_load<C>(my + sc1 * SW, fc1);
       const int yo = y - R;  // output rows yo, yo + 1 (the second may be past the band)
       // entering rows y, y + 1; leaving rows y - L, y + 1 - L (entered in this band
       // when rho >= L)
-      if (FAST || y < io.H) ws_update<NN, true>(K, V, fe0);
-      if (rho >= L && (FAST || y - L >= 0)) ws_update<NN, false>(K, V, fl0);
-      ws_row_out<R, NN, FAST>(A, K, V, fc0, yo, x0, writer);
-      if (FAST || y + 1 < io.H) ws_update<NN, true>(K, V, fe1);
-      if (FAST || y + 1 - L >= 0) ws_update<NN, false>(K, V, fl1);
-      ws_row_out<R, NN, FAST>(A, K, V, fc1, yo + 1, x0, writer && yo + 1 < yo1);
+      if (FAST || y < io.H) ws_update<NN, NP, true>(K, V, fe0);
+      if (rho >= L && (FAST || y - L >= 0)) ws_update<NN, NP, false>(K, V, fl0);
+      ws_row_out<R, NN, C, FAST>(A, K, V, fc0, yo, x0, writer);
+      if (FAST || y + 1 < io.H) ws_update<NN, NP, true>(K, V, fe1);
+      if (FAST || y + 1 - L >= 0) ws_update<NN, NP, false>(K, V, fl1);
+      ws_row_out<R, NN, C, FAST>(A, K, V, fc1, yo + 1, x0, writer && yo + 1 < yo1);
     }
     s0 = wrap(s0 + 2);
   }
   cp_async_wait<0>();
 }
 
-template <int R, int NN, int DP = 1>
+// One warp: strip `strip` (TW output columns), band `band` (A.band output rows).
+// The warp's ring holds RS rows of SW floats, lane l's chunk j of a row at
+// offset 128 j + 4 l.
+template <int R, int NN, int DP = 1, int C = 8>
 __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip, int band,
                                                float *ring) {
-  using G = WarpStripGeom<R, DP>;
+  using G = WarpStripGeom<R, DP, C>;
   constexpr int SW = G::SW, RS = G::RS;
-  static_assert(R >= 1 && R <= 8, "the halo must come from one neighbouring lane");
+  static_assert(R >= 1 && R <= 8 && G::HL <= 2, "the halo comes from at most two lanes");
   static_assert(NN >= 2 && NN <= 6, "order range of the warp-strip kernel");
   const TileIO &io = A.io;
   const int lane = threadIdx.x & 31;
-  const int x0 = strip * G::TW - 8 + 8 * lane;  // first region column of this lane
+  const int x0 = strip * G::TW - G::HL * C + C * lane;  // first region column of this lane
   const int yo0 = band * A.band, yo1 = min(io.H, yo0 + A.band);
-  float *my = ring + 4 * lane;  // ring row r, chunk j: my[r * SW + 128 * j + 0..3]
+  float *my = ring + 4 * lane;
   WsConst K;
   K.kg = f2(A.kg);
   K.kg0 = f2(A.kg0);
@@ -322,19 +343,20 @@ __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip
   // per chunk of 4 columns: valid column count (chunks start on multiples of 4);
   // out-of-image columns of every ring row hold the sentinel
   const int cnt0 = x0 < 0 ? 0 : max(0, min(4, io.W - x0));
-  const int cnt1 = x0 + 4 < 0 ? 0 : max(0, min(4, io.W - x0 - 4));
+  const int cnt1 = C == 4 ? 4 : (x0 + 4 < 0 ? 0 : max(0, min(4, io.W - x0 - 4)));
   for (int e = cnt0; e < 4; ++e)
     for (int r = 0; r < RS; ++r) my[r * SW + e] = A.sentinel;
-  for (int e = cnt1; e < 4; ++e)
-    for (int r = 0; r < RS; ++r) my[r * SW + 128 + e] = A.sentinel;
+  if constexpr (C == 8)
+    for (int e = cnt1; e < 4; ++e)
+      for (int r = 0; r < RS; ++r) my[r * SW + 128 + e] = A.sentinel;
   // rows touched: yo0 - W .. yo1 + W + 2 DP - 1 (the last prefetches)
   const bool rows_in = yo0 - R >= 0 && yo1 + R + 2 * DP <= io.H;
   const bool fast = __all_sync(0xffffffffu, rows_in && A.vec_in && A.vec_out && cnt0 == 4 &&
                                                 cnt1 == 4);
   if (fast)
-    ws_band<R, NN, DP, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, C, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
   else
-    ws_band<R, NN, DP, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, C, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
 }
 
 }  // namespace bfk

@@ -33,24 +33,25 @@ __global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constan
   bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16>(args.io, args.fc, smem);
 }
 
-// Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of 240
-// output columns and band of rows, one warp per CTA.
+// Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of
+// output columns (C columns per lane) and band of rows, one warp per CTA.
 constexpr int kWarpWPB = 1;
-template <int R, int NN>
+template <int R, int NN, int C>
 __global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid_constant__ bfk::WarpStripArgs A) {
   extern __shared__ __align__(16) float smem[];
-  using G = bfk::WarpStripGeom<R>;
+  using G = bfk::WarpStripGeom<R, 1, C>;
   const int w = threadIdx.x >> 5;
   const int wid = blockIdx.x * kWarpWPB + w;
   const int strip = wid % A.nstrips, band = wid / A.nstrips;
   if (band >= A.nbands) return;
-  bfk::box_warp_strip<R, NN>(A, strip, band, smem + w * G::warp_floats);
+  bfk::box_warp_strip<R, NN, 1, C>(A, strip, band, smem + w * G::warp_floats);
 }
 
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
 // columns, output rows per tile).  Variant 5: the compile-time-radius kernel
 // for the radii in kFixedRadii (forward without stored planes only).
-// Variant 6: the warp-strip streaming box kernel (box, W in {3, 5}, N <= 5).
+// Variants 6 and 7: the warp-strip streaming box kernel (box, W in {3, 5},
+// N <= 5) with 8 and 4 columns per lane.
 struct Variant {
   int NT, TH;
 };
@@ -58,7 +59,8 @@ constexpr Variant kVariants[] = {{256, 16}, {512, 8}, {256, 8}, {128, 16}, {192,
 constexpr int kNumGeneric = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kFixedVariant = kNumGeneric;
 constexpr int kStreamVariant = kNumGeneric + 1;
-constexpr int kNumVariants = kNumGeneric + 2;
+constexpr int kStream4Variant = kNumGeneric + 2;
+constexpr int kNumVariants = kNumGeneric + 3;
 
 bool fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 bool stream_fits(const bfi::FilterConsts &fc) {
@@ -80,15 +82,20 @@ int max_smem_optin() {
 
 bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
   if (v == kFixedVariant) return !store && fixed_radius(fc.R);
-  if (v == kStreamVariant) return !store && stream_fits(fc);
+  if (v == kStreamVariant || v == kStream4Variant) return !store && stream_fits(fc);
   const Variant &var = kVariants[v];
   const int TW = var.NT - 2 * fc.R;
   if (TW < var.TH) return false;
   return bfk::fwd_smem_bytes(var.NT, var.TH, fc.R, fc.ntaps_pad) <= (size_t)max_smem_optin();
 }
 
+// Measured at 2048^2, 4096^2 and 8192^2: 4 columns per lane is faster for
+// W = 3 at every N <= 5 and for W = 5 at N <= 3; at W = 5, N in {4, 5} the
+// extra halo shuffles and halo lanes of 4 columns per lane cost more than
+// the added resident warps gain.
 int default_variant(const bfi::FilterConsts &fc, bool store) {
-  static const int order[] = {kStreamVariant, kFixedVariant, 0, 2, 4, 3, 1};
+  if (!store && stream_fits(fc)) return fc.R == 3 || fc.N <= 3 ? kStream4Variant : kStreamVariant;
+  static const int order[] = {kFixedVariant, 0, 2, 4, 3, 1};
   for (int v : order)
     if (variant_fits(v, fc, store)) return v;
   return -1;
@@ -112,16 +119,17 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   return bfi::check_launch();
 }
 
-// Rows per warp band (even, 16..64): about one wave of resident warps, or
-// half a wave for N <= 2.  The 2W warm-up rows of a band are read and entered
-// but produce no output, so bands are kept long where the image allows
-// (measured at 4096^2: 64-row bands beat one full wave of shorter bands for
-// N = 1, 2; for larger N one wave is faster).
-template <int R, int NN>
+// Rows per warp band (even, 16..64).  The 2W warm-up rows of a band are read
+// and entered but produce no output.  Measured at 4096^2 (W in {3, 5},
+// N in {1, 3}): with 8 columns per lane (14-16 resident warps per SM) about
+// one wave of warps, or half a wave for N <= 2, is fastest; with 4 columns
+// per lane (20-28 resident warps per SM) short bands filling two or more
+// waves are fastest, the warm-up rows being mostly L2 hits.
+template <int R, int NN, int C>
 bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
-  using G = bfk::WarpStripGeom<R>;
+  using G = bfk::WarpStripGeom<R, 1, C>;
   constexpr size_t smem = kWarpWPB * G::warp_floats * sizeof(float);
-  auto kern = box_warp_kernel<R, NN>;
+  auto kern = box_warp_kernel<R, NN, C>;
   const void *fn = reinterpret_cast<const void *>(kern);
   bf_status st = bfi::ensure_smem(fn, smem);
   int resident_ctas = 0;
@@ -149,9 +157,9 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   A.vec_out = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
   A.nstrips = (a.io.W + G::TW - 1) / G::TW;
   const long long per_strip = std::max(1, resident_warps / A.nstrips);
-  const int waves = NN <= 3 ? 2 : 1;  // fewer channels: fewer registers, more warps per SM
-  const int band = (int)std::min<long long>(
-      64, std::max<long long>(16, waves * ((a.io.H + per_strip - 1) / per_strip)));
+  const long long one_wave = (a.io.H + per_strip - 1) / per_strip;  // band rows for one wave
+  const long long rows = C == 4 ? (one_wave + 1) / 2 : (NN <= 3 ? 2 : 1) * one_wave;
+  const int band = (int)std::min<long long>(64, std::max<long long>(16, rows));
   A.band = (band + 1) & ~1;
   A.nbands = (a.io.H + A.band - 1) / A.band;
   const long long warps = (long long)A.nstrips * A.nbands;
@@ -161,21 +169,22 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   return bfi::check_launch();
 }
 
-template <int R>
+template <int R, int C>
 bf_status launch_warp_r(const FwdArgs &a, cudaStream_t s) {
   switch (a.fc.N + 1) {
-    case 2: return launch_warp_rn<R, 2>(a, s);
-    case 3: return launch_warp_rn<R, 3>(a, s);
-    case 4: return launch_warp_rn<R, 4>(a, s);
-    case 5: return launch_warp_rn<R, 5>(a, s);
-    case 6: return launch_warp_rn<R, 6>(a, s);
+    case 2: return launch_warp_rn<R, 2, C>(a, s);
+    case 3: return launch_warp_rn<R, 3, C>(a, s);
+    case 4: return launch_warp_rn<R, 4, C>(a, s);
+    case 5: return launch_warp_rn<R, 5, C>(a, s);
+    case 6: return launch_warp_rn<R, 6, C>(a, s);
     default: return BF_ERR_UNSUPPORTED;
   }
 }
 
+template <int C>
 bf_status launch_warp(const FwdArgs &a, cudaStream_t s) {
-  if (a.fc.R == 3) return launch_warp_r<3>(a, s);
-  if (a.fc.R == 5) return launch_warp_r<5>(a, s);
+  if (a.fc.R == 3) return launch_warp_r<3, C>(a, s);
+  if (a.fc.R == 5) return launch_warp_r<5, C>(a, s);
   return BF_ERR_UNSUPPORTED;
 }
 
@@ -209,9 +218,9 @@ bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
     if (STORE) return BF_ERR_UNSUPPORTED;
     return g ? launch_fixed<1>(a, s) : launch_fixed<0>(a, s);
   }
-  if (v == kStreamVariant) {
+  if (v == kStreamVariant || v == kStream4Variant) {
     if (STORE) return BF_ERR_UNSUPPORTED;
-    return launch_warp(a, s);
+    return v == kStreamVariant ? launch_warp<8>(a, s) : launch_warp<4>(a, s);
   }
   switch (v) {
     case 0: return g ? launch_fwd<1, 256, 16, STORE>(a, s) : launch_fwd<0, 256, 16, STORE>(a, s);

@@ -65,9 +65,11 @@ def test_every_tile_variant(variant):
     assert ran >= 2
 
 
+@pytest.mark.parametrize("variant", [6, 7])
 @pytest.mark.parametrize("r", [3, 5])
-def test_streaming_box_kernel(r):
-    """Variant 6 (warp-strip streaming box, N <= 5): several strips and bands with
+def test_streaming_box_kernel(r, variant):
+    """Variants 6 and 7 (warp-strip streaming box, N <= 5, 8 and 4 columns per
+    lane, halos from one or two lanes away): several strips and bands with
     ragged tails, every supported N, aligned (vector copies and stores) and
     odd-pitch (scalar) rows, widths that end inside a 4-column chunk, and
     images smaller than one strip or band."""
@@ -75,20 +77,20 @@ def test_streaming_box_kernel(r):
     img = image(H, W, seed=40 + r)
     for sr, N in ((40.0, 1), (40.0, 2), (60.0, 3), (80.0, 5), (30.0, 4)):
         ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, sr, N)
-        out, q = _run(img, bf.BOX, r, 0.0, sr, N, variant=6)
-        compare_forward(out, q, ro, rq, w0, "stream r=%d N=%d" % (r, N), sigma_r=sr, N=N)
+        out, q = _run(img, bf.BOX, r, 0.0, sr, N, variant=variant)
+        compare_forward(out, q, ro, rq, w0, "stream v%d r=%d N=%d" % (variant, r, N), sigma_r=sr, N=N)
     base = torch.zeros((H, W + 1), dtype=torch.float32, device="cuda")
     base[:, :W] = torch.from_numpy(img).cuda()
-    o = bf.gpa_forward(base[:, :W], bf.BOX, 60.0, 3, radius=r, variant=6)
+    o = bf.gpa_forward(base[:, :W], bf.BOX, 60.0, 3, radius=r, variant=variant)
     ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, 60.0, 3)
     compare_forward(o.cpu().numpy(), None, ro, rq, w0, "stream odd pitch", sigma_r=60.0, N=3)
     for shape in ((70, 517), (37, 243), (9, 5), (1, 1), (300, 3)):
         im = image(*shape, seed=shape[0] + shape[1], block=4)
         ro, rq, w0 = _ref(im, bf.BOX, r, 0.0, 70.0, 4)
-        out, q = _run(im, bf.BOX, r, 0.0, 70.0, 4, variant=6)
-        compare_forward(out, q, ro, rq, w0, "stream shape %s" % (shape,), sigma_r=70.0, N=4)
+        out, q = _run(im, bf.BOX, r, 0.0, 70.0, 4, variant=variant)
+        compare_forward(out, q, ro, rq, w0, "stream v%d shape %s" % (variant, shape), sigma_r=70.0, N=4)
     with pytest.raises(bf._lib.BFError):
-        bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=6)
+        bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=variant)
 
 
 @pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 12, 4.0), (bf.GAUSS, 20, 20 / 3.0),
