@@ -10,6 +10,8 @@ Provably Accurate Bilateral Filtering" (arXiv 1603.08109):
 * ``*_grad``             -- exact derivatives of eq. BF / eq. GPA with respect
                             to the image and sigma_r (chain rule on the ratio).
 * ``order``              -- order selection and kernel error (Sec. II).
+* ``recursive``          -- Algorithm 2 with the recursive (Deriche) Gaussian
+                            as the spatial filter, the O(1) route of Sec. III-A.
 
 Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
 this package. It shares no code with the GPU library. Parity status of each
