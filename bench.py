@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--sweep", default="",
                     help="comma list of extra studies, one JSON line per point: "
-                         "grid2048, roofline4096, large8192, batch256, grad512 (or 'all')")
+                         "grid2048, roofline4096, large8192, recursive, batch256, grad512, "
+                         "joint2048, tightness (or 'all')")
     return ap.parse_args()
 
 
@@ -147,6 +148,23 @@ def fwd_ops_per_pixel(kind: int, R: int, N: int) -> float:
     box running sums; plus ~12 per pixel (centre, exp, ratio)."""
     filt = 2 * (2 * R + 1) if kind == 1 else 4
     return (N + 1) * (2 + filt + 3) + 12
+
+
+def rec_ops_per_pixel(N: int) -> float:
+    """The recursive-Gaussian forward: per channel, rows 18 (zero-state finals
+    of both directions, advance a_n) + 27 (both recursions with their outputs,
+    advance a_n), columns 16 + 29 (with the recombination), the two tile scans
+    ~2; plus ~20 per pixel (centre, exp, ratio)."""
+    return (N + 1) * 92 + 20
+
+
+def rec_bytes_per_pixel(N: int) -> float:
+    """DRAM bytes per pixel the recursive forward's decomposition moves: per
+    channel the row pass's plane (4 written) and the column pass's two reads of
+    it (8), and the 32-pixel tile carries (1 B/px per channel, written, scanned
+    in place, read: 4 per direction); per pixel f read by three kernels (12)
+    and out written (4)."""
+    return (N + 1) * 20 + 16
 
 
 def bwd_ops_per_pixel(kind: int, R: int, N: int) -> float:
@@ -292,7 +310,8 @@ def run_sweeps(args):
     import paper_1603_08109_gb300 as bf
     from paper_1603_08109_gb300 import synth
     names = set(args.sweep.split(",")) if args.sweep != "all" else {
-        "grid2048", "roofline4096", "large8192", "batch256", "grad512", "joint2048", "tightness"}
+        "grid2048", "roofline4096", "large8192", "recursive", "batch256", "grad512", "joint2048",
+        "tightness"}
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -381,6 +400,65 @@ def run_sweeps(args):
               "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max()),
               "fwd_alu_ops_frac": fwd_ops_per_pixel(1, 60, N) * px / (fms * 1e-3) /
               fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+    if "recursive" in names:
+        # Algorithm 2 with the recursive (Deriche) Gaussian: cost independent of
+        # sigma_s, against the truncated-Gaussian FIR forward (fused tile or banded
+        # two-pass) at the same sigma_s; gradient + polygons, sigma_r=40, delta=0.5
+        fp32 = fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))
+        for size in (2048, 8192):
+            x = torch.from_numpy(synth.gradient_polygons_image(size, size, 64, 15.0,
+                                                               seed=2001)).to(dev)
+            o = torch.empty_like(x)
+            o2 = torch.empty_like(x)
+            px = float(size * size)
+            for ss in (3.0, 10.0, 20.0, 40.0):
+                N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, ss, 40.0, 0.5)
+                ws = torch.empty(bf.recursive_workspace_bytes(size, size, N) // 4, device=dev)
+                rms = _time_ms(lambda: bf.recursive_forward(x, 40.0, N, ss, out=o, ws=ws), 5,
+                               stream, flush)
+                row = {"sweep": "recursive", "size": size, "sigma_s": ss, "sigma_r": 40.0, "N": N,
+                       "rec_fwd_ms": rms, "rec_fwd_mpx_s": px / rms / 1e3,
+                       "rec_algorithmic_gbs": rec_bytes_per_pixel(N) * px / rms / 1e6,
+                       "rec_frac_of_measured_hbm": rec_bytes_per_pixel(N) * px / rms / 1e6 / hbm_peak,
+                       "rec_alu_ops_frac": rec_ops_per_pixel(N) * px / (rms * 1e-3) / fp32}
+                del ws
+                R = int(math.ceil(3.0 * ss - 1e-9))
+                if R <= 96:
+                    Nf = bf.order_from_delta(bf.GAUSS, R, ss, 40.0, 0.5)
+                    fms = _time_ms(lambda: bf.gpa_forward(x, bf.GAUSS, 40.0, Nf, radius=R,
+                                                          sigma_s=ss, out=o2), 3, stream, flush)
+                    row.update({"fir_radius": R, "fir_N": Nf, "fir_fwd_ms": fms,
+                                "speedup_vs_fir": fms / rms,
+                                "max_abs_rec_vs_fir": float((o - o2).abs().max())})
+                    if size == 2048 and ss in (3.0, 20.0):
+                        d = torch.empty_like(x)
+                        dms = _time_ms(lambda: bf.direct(x, bf.GAUSS, 40.0, radius=R, sigma_s=ss,
+                                                         out=d), 1, stream, flush)
+                        row.update({"direct_ms": dms, "speedup_vs_direct": dms / rms,
+                                    "max_abs_rec_vs_direct": float((o - d).abs().max()),
+                                    "max_abs_fir_vs_direct": float((o2 - d).abs().max())})
+                        del d
+                emit(row)
+            # the spatial operator alone, and its kernel against the sampled Gaussian
+            ws = torch.empty(bf.recursive_workspace_bytes(size, size, 0) // 4, device=dev)
+            for ss in (3.0, 40.0):
+                ms = _time_ms(lambda: bf.recursive_gauss(x, ss, out=o, ws=ws), 10, stream, flush)
+                emit({"sweep": "recursive", "size": size, "filter_only_sigma_s": ss, "ms": ms,
+                      "mpx_s": px / ms / 1e3})
+            del ws, x, o, o2
+            torch.cuda.empty_cache()
+        for ss in (3.0, 20.0):
+            n = int(math.ceil(12 * ss)) * 2 + 1
+            imp = torch.zeros((n, n), device=dev)
+            imp[n // 2, n // 2] = 1.0
+            hh = bf.recursive_gauss(imp, ss).double().cpu().numpy()
+            k = np.arange(n) - n // 2
+            g = np.exp(-k * k / (2.0 * ss * ss))
+            g2 = np.outer(g, g) / g.sum() ** 2
+            emit({"sweep": "recursive", "kernel_vs_sampled_gaussian_sigma_s": ss,
+                  "max_abs_dev_rel_to_peak": float(np.abs(hh - g2).max() / g2.max()),
+                  "centre_weight_recursive": bf.centre_weight(bf.GAUSS_RECURSIVE, 0, ss),
+                  "centre_weight_truncated": bf.centre_weight(bf.GAUSS, int(math.ceil(3 * ss)), ss)})
     if "batch256" in names:
         specs = synth.batch_specs(256, seed=3000)
         for sp in specs:

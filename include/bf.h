@@ -53,7 +53,10 @@ typedef enum {
 
 typedef enum {
     BF_SPATIAL_BOX = 0,      /* eq. spatial_kernel2: w = 1/|Omega|            */
-    BF_SPATIAL_GAUSS = 1     /* eq. spatial_kernel1: w = exp(-|j|^2 / 2 s^2)  */
+    BF_SPATIAL_GAUSS = 1,    /* eq. spatial_kernel1: w = exp(-|j|^2 / 2 s^2)  */
+    BF_SPATIAL_GAUSS_RECURSIVE = 2  /* Deriche's recursive Gaussian (Sec. I,
+                                       Sec. III-A); only bf_recursive_* and the
+                                       order-selection helpers accept it      */
 } bf_spatial_kind;
 
 /* Filter parameters (Sec. I, Sec. III).
@@ -90,7 +93,9 @@ int bf_version(void);
 /* --------------------------------------------------- order selection (host)
  * Centre weight w(0) of the normalised spatial kernel (eq. normal):
  * 1/(2W+1)^2 for the box, 1/(sum_k exp(-k^2/2 sigma_s^2))^2 for the
- * Gaussian on [-W, W]^2.  Host only; no GPU work. */
+ * Gaussian on [-W, W]^2, h(0)^2 for the recursive Gaussian (radius ignored;
+ * h is its normalised 1-D impulse response, see bf_recursive_forward).
+ * Host only; no GPU work. */
 bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out);
 
 /* Order N for a filter accuracy delta (Sec. III-C): eps from eq. eps,
@@ -349,6 +354,43 @@ int bf_tuning_radius_bucket(int radius);
 int bf_tuning_order_bucket(int order_N);
 bf_status bf_tuning_get(int kind, int radius_bucket, int order_bucket, int *variant);
 bf_status bf_tuning_set(int kind, int radius_bucket, int order_bucket, int variant);
+
+/* ------------------------------------------- recursive Gaussian (Sec. III-A)
+ * The paper notes (Sec. I, Sec. III-A) that the N + 1 spatial filterings of
+ * Algorithm 2 cost O(1) per pixel, independent of the filter size, when the
+ * Gaussian is implemented by recursion (Deriche).  These entry points use
+ * Deriche's fourth-order fit: the 1-D impulse response
+ *     h(k) = (1.680 cos(0.6318 k/s) + 3.735 sin(0.6318 k/s)) exp(-1.783 k/s)
+ *          - (0.6803 cos(1.997 k/s) + 0.2598 sin(1.997 k/s)) exp(-1.723 k/s)
+ * for k >= 0, mirrored for k < 0, s = sigma_s, normalised to unit sum over
+ * all integers (within 5e-4 of the sampled Gaussian's peak).  Its causal and
+ * anticausal recursions start from zero state at both ends of every row and
+ * column, which is exactly the convolution of the zero-extended image with
+ * w(j) = h(j_y) h(j_x) over the whole image (the in-image-neighbours rule of
+ * the other kinds, with unbounded support); the cost per pixel and channel
+ * does not depend on sigma_s.  Floating point: FP32, each mode a complex
+ * one-pole recursion; rows and columns cut into 32-pixel tiles made exact by
+ * a carry pass (no halos).
+ *
+ * bf_recursive_workspace: bytes of the caller-owned device workspace for an
+ *   image of height x width and order N (N = 0: the plain filter):
+ *   1.25 (N + 1) 4 Hp P bytes (Hp, P = height, width rounded up to 32),
+ *   rounded to 256-byte blocks.
+ * bf_recursive_gauss: d_out = w * d_in (the plain filter, one image), for
+ *   tests and as a building block.  sigma_s >= 0.5.
+ * bf_recursive_forward: Algorithm 2 (f_GPA, optional Q') with w the
+ *   recursive Gaussian; p->kind must be BF_SPATIAL_GAUSS_RECURSIVE,
+ *   p->sigma_s >= 0.5, p->radius is ignored; otherwise as bf_fast_forward
+ *   (the same sigma_r limit).  Choose N with bf_order_from_delta (kind 2:
+ *   w(0) = h(0)^2).
+ * Workspace: 256-byte aligned, at least the queried size, else
+ * BF_ERR_WORKSPACE / BF_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *bytes);
+bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int width, int pitch,
+                             float sigma_s, void *d_ws, size_t ws_bytes, void *stream);
+bf_status bf_recursive_forward(const float *d_in, float *d_out, float *d_qaux, int height,
+                               int width, int pitch, const bf_params *p, void *d_ws,
+                               size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -8,11 +8,12 @@ behind the C ABI in include/bf.h.  This package is the thin Python layer:
 ``api`` (PyTorch tensors in, library calls out), ``_lib`` (ctypes
 signatures), ``build`` (nvcc), ``synth`` (seeded synthetic inputs).
 """
-from .api import (BOX, GAUSS, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
+from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
                   centre_weight, direct, direct_backward, direct_bilateral, gpa_backward,
                   exhaustive_order, forward_workspace_bytes, gpa_bilateral, gpa_forward,
                   gpa_forward_stored, joint_direct,
                   joint_forward, kernel_error_max, order_bucket, order_estimates, order_from_delta,
-                  radius_bucket, resolve_radius, tuning_get, tuning_set, variant_count)
+                  radius_bucket, recursive_forward, recursive_gauss, recursive_workspace_bytes,
+                  resolve_radius, tuning_get, tuning_set, variant_count)
 
 __version__ = "1.0.0"

@@ -15,7 +15,7 @@ BF_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "unsupported parameters",
           4: "device wait timed out", 5: "workspace missing or too small", 6: "non-finite result"}
 
-BOX, GAUSS = 0, 1
+BOX, GAUSS, GAUSS_RECURSIVE = 0, 1, 2
 MAX_ORDER = 1024
 MAX_RADIUS = 96
 
@@ -60,6 +60,9 @@ SIGNATURES = {
     "bf_joint_forward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_joint_forward_ws": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_forward_ws": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
+    "bf_recursive_workspace": (_i, [_i, _i, _i, ctypes.POINTER(_sz)]),
+    "bf_recursive_gauss": (_i, [_vp, _vp, _i, _i, _i, ctypes.c_float, _vp, _sz, _vp]),
+    "bf_recursive_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_fast_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_backward_stored": (_i, [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _i, _pp,

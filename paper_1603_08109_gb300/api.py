@@ -13,7 +13,7 @@ from typing import Optional
 import torch
 
 from . import _lib
-from ._lib import BOX, GAUSS, check, lib, make_params
+from ._lib import BOX, GAUSS, GAUSS_RECURSIVE, check, lib, make_params
 
 __all__ = [
     "BOX", "GAUSS", "resolve_radius", "centre_weight", "order_from_delta", "gpa_forward",
@@ -21,6 +21,7 @@ __all__ = [
     "DirectBilateral", "gpa_bilateral", "direct_bilateral", "BatchPlan", "autotune",
     "variant_count", "forward_workspace_bytes", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
+    "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
 ]
 
 
@@ -165,6 +166,52 @@ def gpa_forward(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: in
         st = lib().bf_fast_forward_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
                                            ctypes.byref(p), int(variant), _stream(x.device))
     check(st, "bf_fast_forward")
+    if on_cpu:
+        o = o.cpu()
+        q = q.cpu() if q is not None else None
+    return (o, q) if return_q else o
+
+
+def recursive_workspace_bytes(H: int, W: int, N: int = 0) -> int:
+    """Workspace of the recursive-Gaussian path (N = 0: the plain filter)."""
+    n = ctypes.c_size_t(0)
+    check(lib().bf_recursive_workspace(int(H), int(W), int(N), ctypes.byref(n)),
+          "bf_recursive_workspace")
+    return int(n.value)
+
+
+def _recursive_ws(H, W, N, dev, ws):
+    nbytes = recursive_workspace_bytes(H, W, N)
+    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != dev:
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=dev)
+    return ws, ws.numel() * ws.element_size()
+
+
+def recursive_gauss(img: torch.Tensor, sigma_s: float, out: Optional[torch.Tensor] = None,
+                    ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """w * img with w the recursive (Deriche) Gaussian over the whole image."""
+    x, on_cpu = _as_device_image(img)
+    o = _image_like(x, out if not on_cpu else None)
+    H, W = x.shape
+    ws, nbytes = _recursive_ws(H, W, 0, x.device, ws)
+    check(lib().bf_recursive_gauss(_ptr(x), _ptr(o), H, W, x.stride(0), float(sigma_s), _ptr(ws),
+                                   nbytes, _stream(x.device)), "bf_recursive_gauss")
+    return o.cpu() if on_cpu else o
+
+
+def recursive_forward(img: torch.Tensor, sigma_r: float, N: int, sigma_s: float,
+                      t_c: float = 128.0, return_q: bool = False,
+                      out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None):
+    """f_GPA (Algorithm 2) with the recursive Gaussian as the spatial filter.
+    Returns out, or (out, Q').  `ws` may hold a reusable workspace tensor."""
+    x, on_cpu = _as_device_image(img)
+    o = _image_like(x, out if not on_cpu else None)
+    q = _like(x) if return_q else None
+    H, W = x.shape
+    ws, nbytes = _recursive_ws(H, W, N, x.device, ws)
+    p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_recursive_forward(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0), ctypes.byref(p),
+                                     _ptr(ws), nbytes, _stream(x.device)), "bf_recursive_forward")
     if on_cpu:
         o = o.cpu()
         q = q.cpu() if q is not None else None

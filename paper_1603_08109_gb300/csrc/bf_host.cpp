@@ -178,6 +178,11 @@ bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out) 
     *w0_out = 1.0 / (s * s);
     return BF_OK;
   }
+  if (kind == BF_SPATIAL_GAUSS_RECURSIVE) {
+    if (!(sigma_s >= 0.5f) || !isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
+    *w0_out = recursive_centre_weight(sigma_s);
+    return BF_OK;
+  }
   if (kind != BF_SPATIAL_GAUSS || !(sigma_s > 0.0f)) return BF_ERR_INVALID_ARG;
   if (radius > 100000) return BF_ERR_UNSUPPORTED;
   double z = 0.0;
@@ -194,7 +199,7 @@ bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out) 
 bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r, float delta,
                               float T, int *N_out) {
   if (!N_out || !(delta > 0.0f) || !(T > 0.0f) || !(sigma_r > 0.0f)) return BF_ERR_INVALID_ARG;
-  int R = radius;
+  int R = kind == BF_SPATIAL_GAUSS_RECURSIVE ? 0 : radius;
   if (kind == BF_SPATIAL_GAUSS && R <= 0) {
     if (!(sigma_s > 0.0f)) return BF_ERR_INVALID_ARG;
     R = (int)ceil(3.0 * (double)sigma_s - 1e-9);

@@ -55,6 +55,9 @@ bf_status banded_backward(const float *in, const float *out, const float *qaux, 
                           float *gin, double *gsigma, int height, int width, int pitch,
                           const FilterConsts &fc, void *ws, size_t ws_bytes, void *stream);
 
+// w(0) = h(0)^2 of the normalised recursive (Deriche) Gaussian (recursive.cu).
+double recursive_centre_weight(double sigma_s);
+
 // Fastest compiled-in tile variant for (kind, R, N) from the tuning table.
 int tuned_variant(int kind, int R, int N);
 

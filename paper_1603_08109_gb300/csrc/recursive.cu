@@ -1,0 +1,688 @@
+// Algorithm 2 with the recursive (Deriche) Gaussian as the spatial filter:
+// the O(1)-per-pixel route of Sec. I and Sec. III-A.
+//
+// The spatial operator.  Deriche's fourth-order fit of the Gaussian has the
+// impulse response h(k) = sum_j 2 Re(alpha_j r_j^|k|) over two modes j (two
+// damped cosine/sine pairs), normalised here to unit sum over all integers.
+// With s_j[i] = x[i] + r_j s_j[i-1] (causal, s_j[-1] = 0) and
+// q_j[i] = x[i] + r_j q_j[i+1] (anticausal, q_j[L] = 0), the zero-extended
+// convolution of a line x[0..L) with h is
+//      y[i] = sum_j Re(A_j (s_j[i] + q_j[i])) - h(0) x[i],   A_j = 2 alpha_j,
+// since s_j + q_j counts the centre twice.  Each mode is a complex one-pole
+// recursion (four FP32 operations per step): unlike a fourth-order direct
+// form its rounding noise is amplified only by 1/|1 - r_j| (about 10 at
+// sigma_s = 20), so FP32 holds the 1e-3 parity bar at any sigma_s.
+//
+// Line parallelism.  A line is cut into tiles of 32 pixels, each handled by
+// two lanes of one warp (pixels 0-15 and 16-31).  Three kernels per
+// direction make every tile exact without halos:
+//   carry  : each tile's zero-state final states (causal at its last pixel,
+//            anticausal at its first), per mode and channel;
+//   scan   : one thread per (line, channel) walks the tiles and turns them
+//            into the true incoming states (S_in(t+1) = r^32 S_in(t) + e(t),
+//            and mirrored for the anticausal side);
+//   apply  : each tile re-runs both recursions from its incoming states.
+// In `apply` both lanes of a tile run the same instruction stream: the second
+// lane holds its 16 pixels in reverse order, so phase 1 is the first lane's
+// causal pass and the second lane's anticausal pass; the two swap their final
+// states with one shuffle and phase 2 runs the other direction.
+//
+// Data flow of Algorithm 2 (N + 1 channels F_n, rescaled as
+// a_n = e^{-H^2/2} H^n / sqrt(n!), so |a_n| <= 1):
+//   rows    : a_n from f (through a shared-memory transpose of a 16 x 32
+//             tile of f), filtered along rows -> planes X_n in the workspace;
+//   columns : X_n filtered along columns -> A_n = w * a_n; the recombination
+//             Q' = sum_{n<N} a_n A_n, P' = sum_{n<N} sqrt(n+1) a_n A_{n+1}
+//             accumulates in registers over the channel loop, then
+//             out = t_c + sigma_r P'/Q' (and Q').
+// Out-of-image pixels enter as exact zeros (zero extension): their centred
+// intensity is replaced by a sentinel H = 1e4, whose e^{-H^2/2} is 0.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "bf_internal.h"
+
+namespace {
+
+constexpr int kTileLen = 32;       // pixels per carry tile
+constexpr int kHalf = 16;          // pixels per lane
+constexpr int kWarpsPerBlock = 4;  // 128-thread blocks
+constexpr float kSentinelH = 1.0e4f;
+
+struct RecConsts {
+  float pr[2], pi[2];      // poles r_j
+  float ar[2], ai[2];      // A_j = 2 alpha_j (normalised)
+  float h0;                // h(0)
+  float p16r[2], p16i[2];  // r_j^16
+  float p32r[2], p32i[2];  // r_j^32
+};
+
+struct RecArgs {
+  RecConsts K;
+  const float *in;  // image (pitch elements per row)
+  float *out;       // result (pitch)
+  float *qaux;      // Q' (pitch) or null
+  float *planes;    // (nch) planes of Hp x P floats
+  float *carry;     // nch * (lines of the direction) * tiles * 8 floats
+  int H, W, pitch;
+  int Hp, P;        // rows and pitch of a plane (multiples of 32)
+  int nch;          // channels: N + 1 (GPA) or 1 (plain filter)
+  int N;
+  float tc, sr, inv_sr;
+  float e2c;        // -log2(e) / 2: a_0 = 2^(e2c H^2)
+};
+
+struct Cx {
+  float r, i;
+};
+
+// s <- x + r s for one mode.
+__device__ __forceinline__ Cx step(Cx s, float x, float pr, float pi) {
+  Cx o;
+  o.r = fmaf(pr, s.r, fmaf(-pi, s.i, x));
+  o.i = fmaf(pr, s.i, pi * s.r);
+  return o;
+}
+
+__device__ __forceinline__ Cx cmul(Cx a, float br, float bi) {
+  Cx o;
+  o.r = fmaf(a.r, br, -a.i * bi);
+  o.i = fmaf(a.r, bi, a.i * br);
+  return o;
+}
+
+__device__ __forceinline__ Cx cadd(Cx a, Cx b) { return Cx{a.r + b.r, a.i + b.i}; }
+
+__device__ __forceinline__ Cx shfl16(Cx a) {
+  return Cx{__shfl_xor_sync(0xffffffffu, a.r, 16), __shfl_xor_sync(0xffffffffu, a.i, 16)};
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Zero-state final states of one lane's 16 inputs walked in register order
+// (fw) and in reverse register order (bw).
+__device__ __forceinline__ void zero_state_finals(const RecConsts &K, const float (&x)[kHalf],
+                                                  Cx (&fw)[2], Cx (&bw)[2]) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    Cx s{0.f, 0.f}, q{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      s = step(s, x[k], K.pr[j], K.pi[j]);
+      q = step(q, x[kHalf - 1 - k], K.pr[j], K.pi[j]);
+    }
+    fw[j] = s;
+    bw[j] = q;
+  }
+}
+
+// Tile carries from the two lanes' zero-state finals: written by the first
+// lane of the pair.  First lane: fw = causal final at pixel 15, bw =
+// anticausal final at pixel 0.  Second lane (reversed): fw = anticausal final
+// at pixel 16, bw = causal final at pixel 31.
+__device__ __forceinline__ void write_carry(const RecConsts &K, const Cx (&fw)[2], const Cx (&bw)[2],
+                                            bool first, float *dst) {
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const Cx pf = shfl16(fw[j]), pb = shfl16(bw[j]);
+    const Cx e = cadd(cmul(fw[j], K.p16r[j], K.p16i[j]), pb);  // causal at pixel 31
+    const Cx g = cadd(bw[j], cmul(pf, K.p16r[j], K.p16i[j]));  // anticausal at pixel 0
+    v[2 * j] = e.r;
+    v[2 * j + 1] = e.i;
+    v[4 + 2 * j] = g.r;
+    v[4 + 2 * j + 1] = g.i;
+  }
+  if (first) {
+    reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+// Both recursions over one tile from its incoming states; y = the filtered
+// values in the lane's register order.
+__device__ __forceinline__ void apply_tile(const RecConsts &K, const float (&x)[kHalf], float4 c0,
+                                           float4 c1, bool first, float (&y)[kHalf]) {
+  // c0: causal incoming state S_in, c1: anticausal incoming state Q_in
+  Cx st[2];
+  st[0] = first ? Cx{c0.x, c0.y} : Cx{c1.x, c1.y};
+  st[1] = first ? Cx{c0.z, c0.w} : Cx{c1.z, c1.w};
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) {
+    float c = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      st[j] = step(st[j], x[k], K.pr[j], K.pi[j]);
+      c = fmaf(K.ar[j], st[j].r, fmaf(-K.ai[j], st[j].i, c));
+    }
+    y[k] = c;
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) st[j] = shfl16(st[j]);
+#pragma unroll
+  for (int k = kHalf - 1; k >= 0; --k) {
+    float c = fmaf(-K.h0, x[k], y[k]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      st[j] = step(st[j], x[k], K.pr[j], K.pi[j]);
+      c = fmaf(K.ar[j], st[j].r, fmaf(-K.ai[j], st[j].i, c));
+    }
+    y[k] = c;
+  }
+}
+
+// Carry slot of (channel, tile, line).
+__device__ __forceinline__ float *carry_at(const RecArgs &a, int ch, int tile, int ntiles, int nlines,
+                                           int line) {
+  return a.carry + (((size_t)ch * ntiles + tile) * nlines + line) * 8;
+}
+
+// ------------------------------------------------------------ rows (first)
+// Warp w: rows 16 ry .. 16 ry + 15, tile tx (columns 32 tx .. 32 tx + 31).
+// Loads the tile's centred intensities H (sentinel outside the image) into
+// the lane's registers: first lane of a pair pixels 0..15 of row 16ry + l,
+// second lane pixels 31..16 of row 16ry + l - 16.
+template <bool GPA>
+__device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, float (&Hv)[kHalf],
+                                         int &y, int &x0, bool &first) {
+  const int ntx = a.P / kTileLen;
+  const int tx = w % ntx, ry = w / ntx;
+  if (ry * 16 >= a.Hp) return false;
+  const int lane = threadIdx.x & 31;
+  x0 = tx * kTileLen;
+  const int y0 = ry * 16;
+  for (int r = 0; r < 16; ++r) {
+    const int yy = y0 + r, xx = x0 + lane;
+    float v = kSentinelH;
+    if (yy < a.H && xx < a.W) {
+      const float f = __ldg(a.in + (size_t)yy * a.pitch + xx);
+      v = GPA ? (f - a.tc) * a.inv_sr : f;
+    } else if (!GPA) {
+      v = 0.f;
+    }
+    sm[r * 33 + lane] = v;
+  }
+  __syncwarp();
+  first = lane < 16;
+  const int r = lane & 15;
+  y = y0 + r;
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) Hv[k] = sm[r * 33 + (first ? k : kTileLen - 1 - k)];
+  return true;
+}
+
+__device__ __forceinline__ void a0_from_H(const RecArgs &a, const float (&Hv)[kHalf], float (&x)[kHalf]) {
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) x[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
+}
+
+template <bool GPA>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __grid_constant__ RecArgs a) {
+  __shared__ float smem[kWarpsPerBlock][16 * 33];
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  float Hv[kHalf];
+  int y, x0;
+  bool first;
+  if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
+  const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
+  float x[kHalf];
+  if (GPA) a0_from_H(a, Hv, x);
+  else
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) x[k] = Hv[k];
+  for (int n = 0; n < a.nch; ++n) {
+    if (GPA && n > 0) {
+      const float is = 1.0f / sqrtf((float)n);
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
+    }
+    Cx fw[2], bw[2];
+    zero_state_finals(a.K, x, fw, bw);
+    write_carry(a.K, fw, bw, first, carry_at(a, n, tx, ntx, a.Hp, y));
+  }
+}
+
+template <bool GPA>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __grid_constant__ RecArgs a) {
+  __shared__ float smem[kWarpsPerBlock][16 * 33];
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  float Hv[kHalf];
+  int y, x0;
+  bool first;
+  if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
+  const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
+  float x[kHalf];
+  if (GPA) a0_from_H(a, Hv, x);
+  else
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) x[k] = Hv[k];
+  const size_t plane = (size_t)a.Hp * a.P;
+  const float4 *cp = reinterpret_cast<const float4 *>(carry_at(a, 0, tx, ntx, a.Hp, y));
+  float4 c0 = cp[0], c1 = cp[1];
+  for (int n = 0; n < a.nch; ++n) {
+    if (GPA && n > 0) {
+      const float is = 1.0f / sqrtf((float)n);
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
+    }
+    // the next channel's incoming states, loaded while this one computes
+    const float4 *cn = reinterpret_cast<const float4 *>(
+        carry_at(a, min(n + 1, a.nch - 1), tx, ntx, a.Hp, y));
+    const float4 n0 = cn[0], n1 = cn[1];
+    float yv[kHalf];
+    apply_tile(a.K, x, c0, c1, first, yv);
+    c0 = n0;
+    c1 = n1;
+    // first lane: columns x0 + k; second lane: columns x0 + 31 - k
+    float *dst = a.planes + n * plane + (size_t)y * a.P + x0 + (first ? 0 : kHalf);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      float4 v;
+      v.x = first ? yv[4 * m] : yv[15 - 4 * m];
+      v.y = first ? yv[4 * m + 1] : yv[14 - 4 * m];
+      v.z = first ? yv[4 * m + 2] : yv[13 - 4 * m];
+      v.w = first ? yv[4 * m + 3] : yv[12 - 4 * m];
+      reinterpret_cast<float4 *>(dst)[m] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- scan
+// One thread per (line, channel): zero-state tile finals -> incoming states.
+// The loads of kScanChunk tiles are issued together before their sequential
+// updates, so a line costs ntiles / kScanChunk memory latencies per side.
+constexpr int kScanChunk = 8;
+
+__global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, int nlines, int ntiles) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nlines * a.nch) return;
+  const int line = (int)(i % nlines), ch = (int)(i / nlines);
+  const size_t step = (size_t)nlines * 2;  // float4 stride between consecutive tiles
+  float4 *base = reinterpret_cast<float4 *>(carry_at(a, ch, 0, ntiles, nlines, line));
+  Cx S[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int t0 = 0; t0 < ntiles; t0 += kScanChunk) {
+    float4 e[kScanChunk];
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u)
+      if (t0 + u < ntiles) e[u] = base[(t0 + u) * step];
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u) {
+      if (t0 + u < ntiles) {
+        base[(t0 + u) * step] = make_float4(S[0].r, S[0].i, S[1].r, S[1].i);
+        S[0] = cadd(cmul(S[0], a.K.p32r[0], a.K.p32i[0]), Cx{e[u].x, e[u].y});
+        S[1] = cadd(cmul(S[1], a.K.p32r[1], a.K.p32i[1]), Cx{e[u].z, e[u].w});
+      }
+    }
+  }
+  Cx Q[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int t0 = ntiles - 1; t0 >= 0; t0 -= kScanChunk) {
+    float4 g[kScanChunk];
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u)
+      if (t0 - u >= 0) g[u] = base[(t0 - u) * step + 1];
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u) {
+      if (t0 - u >= 0) {
+        base[(t0 - u) * step + 1] = make_float4(Q[0].r, Q[0].i, Q[1].r, Q[1].i);
+        Q[0] = cadd(cmul(Q[0], a.K.p32r[0], a.K.p32i[0]), Cx{g[u].x, g[u].y});
+        Q[1] = cadd(cmul(Q[1], a.K.p32r[1], a.K.p32i[1]), Cx{g[u].z, g[u].w});
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------- columns (second)
+// Warp w: columns 16 cx .. 16 cx + 15, tile ty (rows 32 ty .. 32 ty + 31).
+// First lane of a pair: rows 0..15 of the tile; second lane rows 31..16.
+__device__ __forceinline__ bool col_tile(const RecArgs &a, int w, int &x, int &y0, bool &first) {
+  const int ncx = a.P / 16;
+  const int cx = w % ncx, ty = w / ncx;
+  if (ty * kTileLen >= a.Hp) return false;
+  const int lane = threadIdx.x & 31;
+  first = lane < 16;
+  x = cx * 16 + (lane & 15);
+  y0 = ty * kTileLen;
+  return true;
+}
+
+__device__ __forceinline__ int col_row(int y0, bool first, int k) {
+  return y0 + (first ? k : kTileLen - 1 - k);
+}
+
+// Per-warp ring of kColDepth channels in shared memory: the 32 x 16 plane
+// tile of a channel and (apply pass) the 16 columns' incoming states, copied
+// with cp.async kColDepth - 1 channels ahead of use.
+constexpr int kColDepth = 3;
+struct ColRing {
+  float tile[kColDepth][kTileLen * 16];  // row-major, 16 floats per row
+  float carry[kColDepth][16 * 8];
+};
+
+__device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, int xb, int y0,
+                                          int ty, int nty, bool with_carry) {
+  const int lane = threadIdx.x & 31;
+  const int slot = n % kColDepth;
+  const float *src = a.planes + (size_t)n * a.Hp * a.P + (size_t)y0 * a.P + xb;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // 128 chunks of 16 bytes
+    const int c = lane + 32 * j, row = c >> 2, col = (c & 3) * 4;
+    cp_async16(&R.tile[slot][row * 16 + col], src + (size_t)row * a.P + col);
+  }
+  if (with_carry) cp_async16(&R.carry[slot][lane * 4], carry_at(a, n, ty, nty, a.P, xb) + lane * 4);
+}
+
+// The lane's 16 inputs of channel n from the ring (call after col_wait).
+__device__ __forceinline__ void col_read(const ColRing &R, int n, bool first, float (&v)[kHalf]) {
+  const int c = threadIdx.x & 15, slot = n % kColDepth;
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) v[k] = R.tile[slot][(first ? k : kTileLen - 1 - k) * 16 + c];
+}
+
+// Before channel n: queue channel n + kColDepth - 1 (into the slot channel
+// n - 1 used; every lane finished reading it), then wait for channel n.
+__device__ __forceinline__ void col_advance(const RecArgs &a, ColRing &R, int n, int xb, int y0,
+                                            int ty, int nty, bool with_carry) {
+  __syncwarp();
+  if (n + kColDepth - 1 < a.nch) col_issue(a, R, n + kColDepth - 1, xb, y0, ty, nty, with_carry);
+  cp_commit();
+  cp_wait<kColDepth - 1>();
+  __syncwarp();
+}
+
+__device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing &R, int xb, int y0, int ty,
+                                             int nty, bool with_carry) {
+#pragma unroll
+  for (int q = 0; q < kColDepth - 1; ++q) {
+    if (q < a.nch) col_issue(a, R, q, xb, y0, ty, nty, with_carry);
+    cp_commit();
+  }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_cols_carry(const __grid_constant__ RecArgs a) {
+  __shared__ ColRing ring[kWarpsPerBlock];
+  ColRing &R = ring[threadIdx.x >> 5];
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  int x, y0;
+  bool first;
+  if (!col_tile(a, w, x, y0, first)) return;
+  const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
+  col_prologue(a, R, xb, y0, ty, nty, false);
+  for (int n = 0; n < a.nch; ++n) {
+    col_advance(a, R, n, xb, y0, ty, nty, false);
+    float v[kHalf];
+    col_read(R, n, first, v);
+    Cx fw[2], bw[2];
+    zero_state_finals(a.K, v, fw, bw);
+    write_carry(a.K, fw, bw, first, carry_at(a, n, ty, nty, a.P, x));
+  }
+  cp_wait<0>();
+}
+
+// Column pass.  Plain filter: the filtered plane is the output.  Algorithm 2:
+// A_n = w * a_n, accumulated into P' and Q' over the channel loop.
+template <bool GPA>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) rec_cols_apply(const __grid_constant__ RecArgs a) {
+  __shared__ ColRing ring[kWarpsPerBlock];
+  ColRing &R = ring[threadIdx.x >> 5];
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  int x, y0;
+  bool first;
+  if (!col_tile(a, w, x, y0, first)) return;
+  const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
+  const bool xin = x < a.W;
+  const int cs = (threadIdx.x & 15) * 8;  // this column's carry slot in the ring
+  col_prologue(a, R, xb, y0, ty, nty, true);
+  if constexpr (!GPA) {
+    col_advance(a, R, 0, xb, y0, ty, nty, true);
+    float v[kHalf], yv[kHalf];
+    col_read(R, 0, first, v);
+    const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
+    const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][cs + 4]);
+    apply_tile(a.K, v, c0, c1, first, yv);
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      const int yy = col_row(y0, first, k);
+      if (xin && yy < a.H) a.out[(size_t)yy * a.pitch + x] = yv[k];
+    }
+  } else {
+    // centred intensities of the lane's pixels (sentinel outside the image)
+    float Hv[kHalf], av[kHalf], Pa[kHalf], Qa[kHalf];
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      const int yy = col_row(y0, first, k);
+      Hv[k] = (xin && yy < a.H) ? (__ldg(a.in + (size_t)yy * a.pitch + x) - a.tc) * a.inv_sr
+                                : kSentinelH;
+      av[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
+      Pa[k] = 0.f;
+      Qa[k] = 0.f;
+    }
+    for (int n = 0; n <= a.N; ++n) {
+      col_advance(a, R, n, xb, y0, ty, nty, true);
+      float v[kHalf], An[kHalf];
+      col_read(R, n, first, v);
+      const int slot = n % kColDepth;
+      const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs]);
+      const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs + 4]);
+      apply_tile(a.K, v, c0, c1, first, An);
+      if (n > 0) {  // P' += sqrt(n) a_{n-1} A_n, then a_n = a_{n-1} H / sqrt(n)
+        const float sq = sqrtf((float)n), is = 1.0f / sq;
+#pragma unroll
+        for (int k = 0; k < kHalf; ++k) {
+          Pa[k] = fmaf(sq * av[k], An[k], Pa[k]);
+          av[k] *= Hv[k] * is;
+        }
+      }
+      if (n < a.N) {  // Q' += a_n A_n
+#pragma unroll
+        for (int k = 0; k < kHalf; ++k) Qa[k] = fmaf(av[k], An[k], Qa[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      const int yy = col_row(y0, first, k);
+      if (xin && yy < a.H) {
+        a.out[(size_t)yy * a.pitch + x] = fmaf(a.sr, __fdividef(Pa[k], Qa[k]), a.tc);
+        if (a.qaux) a.qaux[(size_t)yy * a.pitch + x] = Qa[k];
+      }
+    }
+  }
+  cp_wait<0>();
+}
+
+// ------------------------------------------------------------------ host
+struct Cd {
+  double r, i;
+};
+Cd cd_mul(Cd a, Cd b) { return Cd{a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+Cd cd_div(Cd a, Cd b) {
+  const double d = b.r * b.r + b.i * b.i;
+  return Cd{(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+Cd cd_pow(Cd a, int n) {
+  Cd o{1.0, 0.0};
+  for (int k = 0; k < n; ++k) o = cd_mul(o, a);
+  return o;
+}
+
+// Modes of Deriche's fourth-order Gaussian fit at sigma_s: poles r_j =
+// exp((-b_j + i w_j) / s) and weights alpha_j = (c_cos - i c_sin) / 2, so that
+// c_cos cos(w k/s) + c_sin sin(w k/s) times exp(-b k/s) = 2 Re(alpha r^k).
+// Normalised by the sum over all integers, 2 sum_{k>=0} h(k) - h(0), with the
+// geometric series sum_{k>=0} r^k = 1 / (1 - r).
+struct Modes {
+  Cd r[2], alpha[2];
+  double h0;
+};
+
+Modes deriche_modes(double s) {
+  const double a0 = 1.680, a1 = 3.735, b0 = 1.783, w0 = 0.6318;
+  const double c0 = -0.6803, c1 = -0.2598, b1 = 1.723, w1 = 1.997;
+  Modes m;
+  const double b[2] = {b0, b1}, w[2] = {w0, w1}, cc[2] = {a0, c0}, cs[2] = {a1, c1};
+  double sum_pos = 0.0, raw0 = 0.0;
+  for (int j = 0; j < 2; ++j) {
+    const double mag = exp(-b[j] / s);
+    m.r[j] = Cd{mag * cos(w[j] / s), mag * sin(w[j] / s)};
+    m.alpha[j] = Cd{0.5 * cc[j], -0.5 * cs[j]};
+    const Cd g = cd_div(m.alpha[j], Cd{1.0 - m.r[j].r, -m.r[j].i});
+    sum_pos += 2.0 * g.r;
+    raw0 += 2.0 * m.alpha[j].r;
+  }
+  const double total = 2.0 * sum_pos - raw0;
+  for (int j = 0; j < 2; ++j) m.alpha[j] = Cd{m.alpha[j].r / total, m.alpha[j].i / total};
+  m.h0 = raw0 / total;
+  return m;
+}
+
+RecConsts make_consts(double sigma_s) {
+  const Modes m = deriche_modes(sigma_s);
+  RecConsts K;
+  for (int j = 0; j < 2; ++j) {
+    K.pr[j] = (float)m.r[j].r;
+    K.pi[j] = (float)m.r[j].i;
+    K.ar[j] = (float)(2.0 * m.alpha[j].r);
+    K.ai[j] = (float)(2.0 * m.alpha[j].i);
+    const Cd p16 = cd_pow(m.r[j], 16), p32 = cd_pow(m.r[j], 32);
+    K.p16r[j] = (float)p16.r;
+    K.p16i[j] = (float)p16.i;
+    K.p32r[j] = (float)p32.r;
+    K.p32i[j] = (float)p32.i;
+  }
+  K.h0 = (float)m.h0;
+  return K;
+}
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+struct Layout {
+  int Hp, P;
+  size_t plane_floats, planes_bytes, carry_bytes, total;
+};
+
+Layout layout(int height, int width, int nch) {
+  Layout L;
+  L.Hp = (int)round_up((size_t)height, kTileLen);
+  L.P = (int)round_up((size_t)width, kTileLen);
+  L.plane_floats = (size_t)L.Hp * L.P;
+  L.planes_bytes = round_up(L.plane_floats * nch * sizeof(float), 256);
+  // one carry slot (8 floats) per 32 pixels of a line per channel; rows and
+  // columns need the same count, and the row carries are dead once the row
+  // pass has run, so the column pass reuses them
+  L.carry_bytes = round_up(L.plane_floats / kTileLen * 8 * nch * sizeof(float), 256);
+  L.total = L.planes_bytes + L.carry_bytes;
+  return L;
+}
+
+constexpr double kMinSigmaS = 0.5;
+
+bf_status run(const float *in, float *out, float *qaux, int height, int width, int pitch,
+              double sigma_s, bool gpa, int N, float tc, float sr, void *ws, size_t ws_bytes,
+              void *stream) {
+  bf_status st = bfi::check_image(in, out, height, width, pitch);
+  if (st != BF_OK) return st;
+  if (!(sigma_s >= kMinSigmaS) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
+  const int nch = gpa ? N + 1 : 1;
+  const Layout L = layout(height, width, nch);
+  if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
+  RecArgs a;
+  a.K = make_consts(sigma_s);
+  a.in = in;
+  a.out = out;
+  a.qaux = qaux;
+  a.planes = static_cast<float *>(ws);
+  a.carry = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes);
+  a.H = height;
+  a.W = width;
+  a.pitch = pitch;
+  a.Hp = L.Hp;
+  a.P = L.P;
+  a.nch = nch;
+  a.N = N;
+  a.tc = tc;
+  a.sr = sr;
+  a.inv_sr = (float)(1.0 / (double)sr);
+  a.e2c = (float)(-1.4426950408889634 / 2.0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int threads = 32 * kWarpsPerBlock;
+  // rows: warps = (Hp / 16) x (P / 32)
+  const long long wr = (long long)(L.Hp / 16) * (L.P / kTileLen);
+  const long long br = (wr + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  // columns: warps = (P / 16) x (Hp / 32)
+  const long long wc = (long long)(L.P / 16) * (L.Hp / kTileLen);
+  const long long bc = (wc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const long long sr_threads = (long long)L.Hp * nch, sc_threads = (long long)L.P * nch;
+  if (br > 0x7fffffffLL || bc > 0x7fffffffLL || sr_threads / 256 + 1 > 0x7fffffffLL ||
+      sc_threads / 256 + 1 > 0x7fffffffLL)
+    return BF_ERR_UNSUPPORTED;
+  if (gpa) rec_rows_carry<true><<<(int)br, threads, 0, s>>>(a);
+  else rec_rows_carry<false><<<(int)br, threads, 0, s>>>(a);
+  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(a, L.Hp, L.P / kTileLen);
+  if (gpa) rec_rows_apply<true><<<(int)br, threads, 0, s>>>(a);
+  else rec_rows_apply<false><<<(int)br, threads, 0, s>>>(a);
+  rec_cols_carry<<<(int)bc, threads, 0, s>>>(a);
+  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(a, L.P, L.Hp / kTileLen);
+  if (gpa) rec_cols_apply<true><<<(int)bc, threads, 0, s>>>(a);
+  else rec_cols_apply<false><<<(int)bc, threads, 0, s>>>(a);
+  return bfi::check_launch();
+}
+
+bf_status resolve_recursive(const bf_params *p, double *sigma_s) {
+  if (!p) return BF_ERR_INVALID_ARG;
+  if (p->kind != BF_SPATIAL_GAUSS_RECURSIVE) return BF_ERR_INVALID_ARG;
+  if (!(p->sigma_s >= (float)kMinSigmaS) || !std::isfinite(p->sigma_s)) return BF_ERR_INVALID_ARG;
+  if (!(p->sigma_r > 0.0f) || !std::isfinite(p->sigma_r) || !std::isfinite(p->t_c))
+    return BF_ERR_INVALID_ARG;
+  if (p->order_N < 1) return BF_ERR_INVALID_ARG;
+  if (p->order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
+  if ((double)p->t_c / (double)p->sigma_r > 13.0) return BF_ERR_UNSUPPORTED;
+  *sigma_s = p->sigma_s;
+  return BF_OK;
+}
+
+}  // namespace
+
+namespace bfi {
+double recursive_centre_weight(double sigma_s) {
+  const double h0 = deriche_modes(sigma_s).h0;
+  return h0 * h0;
+}
+}  // namespace bfi
+
+extern "C" {
+
+bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *bytes) {
+  if (!bytes || height < 1 || width < 1 || order_N < 0) return BF_ERR_INVALID_ARG;
+  if (order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
+  *bytes = layout(height, width, order_N + 1).total;
+  return BF_OK;
+}
+
+bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int width, int pitch,
+                             float sigma_s, void *d_ws, size_t ws_bytes, void *stream) {
+  return run(d_in, d_out, nullptr, height, width, pitch, sigma_s, false, 0, 0.f, 1.f, d_ws,
+             ws_bytes, stream);
+}
+
+bf_status bf_recursive_forward(const float *d_in, float *d_out, float *d_qaux, int height,
+                               int width, int pitch, const bf_params *p, void *d_ws,
+                               size_t ws_bytes, void *stream) {
+  double sigma_s = 0.0;
+  const bf_status st = resolve_recursive(p, &sigma_s);
+  if (st != BF_OK) return st;
+  if (d_qaux && (d_qaux == d_in || d_qaux == d_out)) return BF_ERR_INVALID_ARG;
+  return run(d_in, d_out, d_qaux, height, width, pitch, sigma_s, true, p->order_N, p->t_c,
+             p->sigma_r, d_ws, ws_bytes, stream);
+}
+
+}  // extern "C"

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -117,6 +118,44 @@ def test_argument_validation_without_gpu():
     assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big, fake, too_small, None) == 5
     assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big,
                                   ctypes.c_void_p(0x1004), 64 * 33 * 200 * 4, None) == 1
+
+
+def test_recursive_host_side():
+    """The recursive Gaussian's centre weight and order agree with the checker
+    (an independent derivation: closed-form geometric series on the library
+    side, a direct sum over the integers in the checker); workspace size and
+    argument checks need no GPU."""
+    from oracle import order
+    from oracle import recursive as rec
+    from paper_1603_08109_gb300 import api
+    L = _lib()
+    lib = L.lib()
+    for s in (0.5, 1.25, 3.0, 20.0, 64.0):
+        assert api.centre_weight(L.GAUSS_RECURSIVE, 0, s) == pytest.approx(
+            rec.centre_weight_recursive(float(np.float32(s))), rel=1e-12)
+    for s, sr, delta in ((20.0, 40.0, 0.5), (3.0, 30.0, 1.0), (10.0, 15.0, 0.1)):
+        w0 = rec.centre_weight_recursive(s)
+        N, _ = order.chernoff_order_lambertw((128.0 / sr) ** 2, order.eps_from_delta(w0, delta))
+        assert api.order_from_delta(L.GAUSS_RECURSIVE, 0, s, sr, delta) == N
+    sz = ctypes.c_size_t()
+    assert lib.bf_recursive_workspace(100, 70, 9, ctypes.byref(sz)) == 0
+    planes = 10 * 128 * 96 * 4
+    assert sz.value == planes + planes // 4
+    assert lib.bf_recursive_workspace(100, 70, -1, ctypes.byref(sz)) == 1
+    assert lib.bf_recursive_workspace(100, 70, 5000, ctypes.byref(sz)) == 3
+    fake = ctypes.c_void_p(0x1000)
+    good = L.make_params(L.GAUSS_RECURSIVE, 0, 3.0, 40.0, 9)
+    args = (fake, fake, None, 100, 70, 70)
+    assert lib.bf_recursive_forward(*args, ctypes.byref(good), None, 0, None) == 5
+    assert lib.bf_recursive_forward(*args, ctypes.byref(good), ctypes.c_void_p(0x1010),
+                                    sz.value, None) == 1  # workspace not 256-byte aligned
+    for bad in (L.make_params(L.GAUSS, 0, 3.0, 40.0, 9), L.make_params(L.GAUSS_RECURSIVE, 0, 0.4, 40.0, 9),
+                L.make_params(L.GAUSS_RECURSIVE, 0, 3.0, 40.0, 0)):
+        assert lib.bf_recursive_forward(*args, ctypes.byref(bad), fake, 1 << 30, None) == 1
+    assert lib.bf_recursive_gauss(fake, fake, 100, 70, 70, ctypes.c_float(0.3), fake, 1 << 30,
+                                  None) == 1
+    assert lib.bf_recursive_gauss(None, fake, 100, 70, 70, ctypes.c_float(3.0), fake, 1 << 30,
+                                  None) == 1
 
 
 def test_tuning_table_roundtrip():

@@ -1,0 +1,128 @@
+"""GPU parity of the recursive-Gaussian path (bf_recursive_gauss,
+bf_recursive_forward) against the checker's full-line Toeplitz-product
+evaluation (oracle.recursive), which is the zero-extended convolution with
+Deriche's fit written out.
+
+Sizes span several 32-pixel carry tiles in both directions with ragged last
+tiles, single-row / single-column / single-pixel images, pitched rows, the
+smallest accepted sigma_s and sigma_s far above the tile length (the carries
+then cross many tiles)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1603_08109_gb300 as bf
+from helpers import compare_forward, image, needs_gpu, scaled_q
+from oracle import recursive as rec
+from paper_1603_08109_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+# plain filter: FP32 recursions over values in [0, 255]; the complex one-pole
+# form keeps the error near 1e-6 of the largest value
+FILTER_RTOL = 1e-5
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (45, 1), (5, 7), (33, 65), (97, 301),
+                                   (256, 200)])
+@pytest.mark.parametrize("s", [0.5, 2.5, 9.0, 40.0])
+def test_recursive_filter(shape, s):
+    img = image(*shape, seed=shape[0] * 7 + shape[1], block=8)
+    out = bf.recursive_gauss(torch.from_numpy(img).cuda(), s).cpu().numpy().astype(np.float64)
+    ref = rec.recursive_filter(img, s)
+    scale = max(np.abs(ref).max(), 1e-30)
+    assert np.abs(out - ref).max() <= FILTER_RTOL * scale, (shape, s)
+
+
+def test_recursive_filter_impulse_and_pitch():
+    """A unit impulse gives the separable kernel h(j_y) h(j_x) itself; a
+    pitched (non-contiguous) view gives the same result as a packed copy."""
+    s = 6.0
+    H, W = 81, 95
+    img = np.zeros((H, W), np.float32)
+    img[40, 47] = 1.0
+    out = bf.recursive_gauss(torch.from_numpy(img).cuda(), s).cpu().numpy().astype(np.float64)
+    h = rec.deriche_impulse(s, 100)
+    ref = np.outer(h[np.abs(np.arange(H) - 40)], h[np.abs(np.arange(W) - 47)])
+    assert np.abs(out - ref).max() <= 1e-5 * ref.max()
+    base = torch.zeros((70, 131), device="cuda")
+    im2 = image(70, 120, seed=3)
+    base[:, :120] = torch.from_numpy(im2).cuda()
+    o1 = bf.recursive_gauss(base[:, :120], 3.0)
+    o2 = bf.recursive_gauss(base[:, :120].contiguous(), 3.0)
+    torch.testing.assert_close(o1, o2, rtol=0, atol=0)
+
+
+CASES = [  # (sigma_s, sigma_r, shape)
+    (1.5, 30.0, (70, 130)),
+    (5.0, 60.0, (64, 64)),
+    (20.0, 40.0, (97, 211)),
+    (3.0, 25.0, (33, 1)),
+    (0.5, 50.0, (1, 90)),
+]
+
+
+@pytest.mark.parametrize("s,sr,shape", CASES)
+def test_recursive_forward(s, sr, shape):
+    img = image(*shape, seed=int(s * 10) + shape[1], block=6)
+    w0 = rec.centre_weight_recursive(s)
+    assert bf.centre_weight(bf.GAUSS_RECURSIVE, 0, s) == pytest.approx(w0, rel=1e-6)
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    out, q = bf.recursive_forward(torch.from_numpy(img).cuda(), sr, N, s, return_q=True)
+    ro, P, Q = rec.gpa_alg2_recursive(img, s, sr, N, return_parts=True)
+    compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr), w0,
+                    "recursive s=%g sr=%g N=%d %s" % (s, sr, N, shape), sigma_r=sr, N=N)
+
+
+def test_recursive_forward_small_orders_and_ws_reuse():
+    """Orders below the bound (N = 1, 2, 3) and a reused workspace tensor."""
+    img = image(50, 77, seed=9)
+    s = 4.0
+    w0 = rec.centre_weight_recursive(s)
+    x = torch.from_numpy(img).cuda()
+    ws = torch.empty(bf.recursive_workspace_bytes(50, 77, 3) // 4, device="cuda")
+    for sr, N in ((40.0, 1), (40.0, 2), (60.0, 3)):
+        out, q = bf.recursive_forward(x, sr, N, s, return_q=True, ws=ws)
+        ro, P, Q = rec.gpa_alg2_recursive(img, s, sr, N, return_parts=True)
+        compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr), w0,
+                        "recursive small N=%d" % N, sigma_r=sr, N=N)
+
+
+def test_recursive_full_size_sampled_rows():
+    """8192^2-style content at 2048^2 (the launch configuration of the
+    benchmark's recursive sweep): rows sampled across the image, including
+    the first and last, against the checker's rows."""
+    H = W = 2048
+    s, sr = 20.0, 40.0
+    img = synth.gradient_polygons_image(H, W, 64, 15.0, seed=2001)
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 0.5)
+    out, q = bf.recursive_forward(torch.from_numpy(img).cuda(), sr, N, s, return_q=True)
+    rows = [0, 1, 31, 32, 777, 1024, 2016, 2047]
+    ro, P, Q = rec.gpa_alg2_recursive(img, s, sr, N, rows=rows, return_parts=True)
+    w0 = rec.centre_weight_recursive(s)
+    compare_forward(out.cpu().numpy()[rows], q.cpu().numpy()[rows], ro,
+                    scaled_q(img[rows], Q, sr), w0, "recursive 2048^2 rows", sigma_r=sr, N=N)
+
+
+def test_recursive_errors():
+    x = torch.from_numpy(image(20, 30, seed=1)).cuda()
+    with pytest.raises(bf._lib.BFError) as e:
+        bf.recursive_gauss(x, 0.4)
+    assert e.value.status == 1
+    with pytest.raises(bf._lib.BFError) as e:
+        bf.recursive_forward(x, 5.0, 10, 3.0)  # t_c / sigma_r > 13
+    assert e.value.status == 3
+    # the fused entry points reject the recursive kind
+    with pytest.raises(bf._lib.BFError) as e:
+        bf.gpa_forward(x, bf.GAUSS_RECURSIVE, 40.0, 10, sigma_s=3.0)
+    assert e.value.status == 1
+    # too small a workspace
+    p = bf._lib.make_params(bf.GAUSS_RECURSIVE, 0, 3.0, 40.0, 10)
+    o = torch.empty_like(x)
+    need = bf.recursive_workspace_bytes(20, 30, 10)
+    ws = torch.empty(need // 4, device="cuda")
+    import ctypes
+    st = bf._lib.lib().bf_recursive_forward(
+        ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(o.data_ptr()), None, 20, 30, 30,
+        ctypes.byref(p), ctypes.c_void_p(ws.data_ptr()), need - 256, None)
+    assert st == 5
