@@ -74,30 +74,70 @@ struct RecArgs {
   float e2c;        // -log2(e) / 2: a_0 = 2^(e2c H^2)
 };
 
-struct Cx {
-  float r, i;
+// The two modes side by side in packed two-lane FP32 (.x = mode 0,
+// .y = mode 1): one __ffma2_rn advances both.
+struct Pair {
+  float2 r, i;  // complex states of the two modes
 };
 
-// s <- x + r s for one mode.
-__device__ __forceinline__ Cx step(Cx s, float x, float pr, float pi) {
-  Cx o;
-  o.r = fmaf(pr, s.r, fmaf(-pi, s.i, x));
-  o.i = fmaf(pr, s.i, pi * s.r);
+struct PK {
+  float2 pr, pi, npi;  // poles and -Im
+  float2 ar, nai;      // A_j and -Im A_j
+  float2 p16r, p16i, np16i, p32r, p32i, np32i;
+};
+
+__device__ __forceinline__ PK packed(const RecConsts &K) {
+  PK k;
+  k.pr = make_float2(K.pr[0], K.pr[1]);
+  k.pi = make_float2(K.pi[0], K.pi[1]);
+  k.npi = make_float2(-K.pi[0], -K.pi[1]);
+  k.ar = make_float2(K.ar[0], K.ar[1]);
+  k.nai = make_float2(-K.ai[0], -K.ai[1]);
+  k.p16r = make_float2(K.p16r[0], K.p16r[1]);
+  k.p16i = make_float2(K.p16i[0], K.p16i[1]);
+  k.np16i = make_float2(-K.p16i[0], -K.p16i[1]);
+  k.p32r = make_float2(K.p32r[0], K.p32r[1]);
+  k.p32i = make_float2(K.p32i[0], K.p32i[1]);
+  k.np32i = make_float2(-K.p32i[0], -K.p32i[1]);
+  return k;
+}
+
+// s <- x + r s for both modes.
+__device__ __forceinline__ Pair step(Pair s, float x, const PK &k) {
+  Pair o;
+  o.r = __ffma2_rn(k.pr, s.r, __ffma2_rn(k.npi, s.i, make_float2(x, x)));
+  o.i = __ffma2_rn(k.pr, s.i, __fmul2_rn(k.pi, s.r));
   return o;
 }
 
-__device__ __forceinline__ Cx cmul(Cx a, float br, float bi) {
-  Cx o;
-  o.r = fmaf(a.r, br, -a.i * bi);
-  o.i = fmaf(a.r, bi, a.i * br);
+// c + sum_j Re(A_j s_j).
+__device__ __forceinline__ float contrib(Pair s, const PK &k, float c) {
+  const float2 t = __ffma2_rn(k.ar, s.r, __ffma2_rn(k.nai, s.i, make_float2(c, 0.f)));
+  return t.x + t.y;
+}
+
+// a * b per mode (b given as re, im, -im).
+__device__ __forceinline__ Pair cmul(Pair a, float2 br, float2 bi, float2 nbi) {
+  Pair o;
+  o.r = __ffma2_rn(a.r, br, __fmul2_rn(a.i, nbi));
+  o.i = __ffma2_rn(a.r, bi, __fmul2_rn(a.i, br));
   return o;
 }
 
-__device__ __forceinline__ Cx cadd(Cx a, Cx b) { return Cx{a.r + b.r, a.i + b.i}; }
-
-__device__ __forceinline__ Cx shfl16(Cx a) {
-  return Cx{__shfl_xor_sync(0xffffffffu, a.r, 16), __shfl_xor_sync(0xffffffffu, a.i, 16)};
+__device__ __forceinline__ Pair cadd(Pair a, Pair b) {
+  return Pair{__fadd2_rn(a.r, b.r), __fadd2_rn(a.i, b.i)};
 }
+
+__device__ __forceinline__ float2 shfl16(float2 a) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, 16), __shfl_xor_sync(0xffffffffu, a.y, 16));
+}
+__device__ __forceinline__ Pair shfl16(Pair a) { return Pair{shfl16(a.r), shfl16(a.i)}; }
+
+// Carry slot contents: float4 (r.x, r.y, i.x, i.y) per side.
+__device__ __forceinline__ Pair unpack(float4 v) {
+  return Pair{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ float4 pack(Pair p) { return make_float4(p.r.x, p.r.y, p.i.x, p.i.y); }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
@@ -111,73 +151,49 @@ __device__ __forceinline__ void cp_wait() {
 
 // Zero-state final states of one lane's 16 inputs walked in register order
 // (fw) and in reverse register order (bw).
-__device__ __forceinline__ void zero_state_finals(const RecConsts &K, const float (&x)[kHalf],
-                                                  Cx (&fw)[2], Cx (&bw)[2]) {
+__device__ __forceinline__ void zero_state_finals(const PK &K, const float (&x)[kHalf], Pair &fw,
+                                                  Pair &bw) {
+  const float2 z = make_float2(0.f, 0.f);
+  Pair s{z, z}, q{z, z};
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    Cx s{0.f, 0.f}, q{0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < kHalf; ++k) {
-      s = step(s, x[k], K.pr[j], K.pi[j]);
-      q = step(q, x[kHalf - 1 - k], K.pr[j], K.pi[j]);
-    }
-    fw[j] = s;
-    bw[j] = q;
+  for (int k = 0; k < kHalf; ++k) {
+    s = step(s, x[k], K);
+    q = step(q, x[kHalf - 1 - k], K);
   }
+  fw = s;
+  bw = q;
 }
 
 // Tile carries from the two lanes' zero-state finals: written by the first
 // lane of the pair.  First lane: fw = causal final at pixel 15, bw =
 // anticausal final at pixel 0.  Second lane (reversed): fw = anticausal final
 // at pixel 16, bw = causal final at pixel 31.
-__device__ __forceinline__ void write_carry(const RecConsts &K, const Cx (&fw)[2], const Cx (&bw)[2],
-                                            bool first, float *dst) {
-  float v[8];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const Cx pf = shfl16(fw[j]), pb = shfl16(bw[j]);
-    const Cx e = cadd(cmul(fw[j], K.p16r[j], K.p16i[j]), pb);  // causal at pixel 31
-    const Cx g = cadd(bw[j], cmul(pf, K.p16r[j], K.p16i[j]));  // anticausal at pixel 0
-    v[2 * j] = e.r;
-    v[2 * j + 1] = e.i;
-    v[4 + 2 * j] = g.r;
-    v[4 + 2 * j + 1] = g.i;
-  }
+__device__ __forceinline__ void write_carry(const PK &K, Pair fw, Pair bw, bool first, float *dst) {
+  const Pair pf = shfl16(fw), pb = shfl16(bw);
+  const Pair e = cadd(cmul(fw, K.p16r, K.p16i, K.np16i), pb);  // causal at pixel 31
+  const Pair g = cadd(bw, cmul(pf, K.p16r, K.p16i, K.np16i));  // anticausal at pixel 0
   if (first) {
-    reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-    reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    reinterpret_cast<float4 *>(dst)[0] = pack(e);
+    reinterpret_cast<float4 *>(dst)[1] = pack(g);
   }
 }
 
 // Both recursions over one tile from its incoming states; y = the filtered
 // values in the lane's register order.
-__device__ __forceinline__ void apply_tile(const RecConsts &K, const float (&x)[kHalf], float4 c0,
+__device__ __forceinline__ void apply_tile(const PK &K, float h0, const float (&x)[kHalf], float4 c0,
                                            float4 c1, bool first, float (&y)[kHalf]) {
   // c0: causal incoming state S_in, c1: anticausal incoming state Q_in
-  Cx st[2];
-  st[0] = first ? Cx{c0.x, c0.y} : Cx{c1.x, c1.y};
-  st[1] = first ? Cx{c0.z, c0.w} : Cx{c1.z, c1.w};
+  Pair st = unpack(first ? c0 : c1);
 #pragma unroll
   for (int k = 0; k < kHalf; ++k) {
-    float c = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      st[j] = step(st[j], x[k], K.pr[j], K.pi[j]);
-      c = fmaf(K.ar[j], st[j].r, fmaf(-K.ai[j], st[j].i, c));
-    }
-    y[k] = c;
+    st = step(st, x[k], K);
+    y[k] = contrib(st, K, 0.f);
   }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) st[j] = shfl16(st[j]);
+  st = shfl16(st);
 #pragma unroll
   for (int k = kHalf - 1; k >= 0; --k) {
-    float c = fmaf(-K.h0, x[k], y[k]);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      st[j] = step(st[j], x[k], K.pr[j], K.pi[j]);
-      c = fmaf(K.ar[j], st[j].r, fmaf(-K.ai[j], st[j].i, c));
-    }
-    y[k] = c;
+    st = step(st, x[k], K);
+    y[k] = contrib(st, K, fmaf(-h0, x[k], y[k]));
   }
 }
 
@@ -188,6 +204,11 @@ __device__ __forceinline__ float *carry_at(const RecArgs &a, int ch, int tile, i
 }
 
 // ------------------------------------------------------------ rows (first)
+// Per-warp 16 x 32 tile in shared memory, rows kRowPitch floats apart: the
+// tile of f on entry, then each channel's output tile on its way to the
+// plane.  A pitch of 36 keeps rows 16-byte aligned, and the 16-byte stores of
+// 8 lanes to 8 different rows fall in 8 different bank quads.
+constexpr int kRowPitch = 36;
 // Warp w: rows 16 ry .. 16 ry + 15, tile tx (columns 32 tx .. 32 tx + 31).
 // Loads the tile's centred intensities H (sentinel outside the image) into
 // the lane's registers: first lane of a pair pixels 0..15 of row 16ry + l,
@@ -210,14 +231,14 @@ __device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, flo
     } else if (!GPA) {
       v = 0.f;
     }
-    sm[r * 33 + lane] = v;
+    sm[r * kRowPitch + lane] = v;
   }
   __syncwarp();
   first = lane < 16;
   const int r = lane & 15;
   y = y0 + r;
 #pragma unroll
-  for (int k = 0; k < kHalf; ++k) Hv[k] = sm[r * 33 + (first ? k : kTileLen - 1 - k)];
+  for (int k = 0; k < kHalf; ++k) Hv[k] = sm[r * kRowPitch + (first ? k : kTileLen - 1 - k)];
   return true;
 }
 
@@ -228,12 +249,13 @@ __device__ __forceinline__ void a0_from_H(const RecArgs &a, const float (&Hv)[kH
 
 template <bool GPA>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __grid_constant__ RecArgs a) {
-  __shared__ float smem[kWarpsPerBlock][16 * 33];
+  __shared__ __align__(16) float smem[kWarpsPerBlock][16 * kRowPitch];
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   float Hv[kHalf];
   int y, x0;
   bool first;
   if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
+  const PK K = packed(a.K);
   const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
   float x[kHalf];
   if (GPA) a0_from_H(a, Hv, x);
@@ -246,20 +268,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __gr
 #pragma unroll
       for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
     }
-    Cx fw[2], bw[2];
-    zero_state_finals(a.K, x, fw, bw);
-    write_carry(a.K, fw, bw, first, carry_at(a, n, tx, ntx, a.Hp, y));
+    Pair fw, bw;
+    zero_state_finals(K, x, fw, bw);
+    write_carry(K, fw, bw, first, carry_at(a, n, tx, ntx, a.Hp, y));
   }
 }
 
 template <bool GPA>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __grid_constant__ RecArgs a) {
-  __shared__ float smem[kWarpsPerBlock][16 * 33];
+  __shared__ __align__(16) float smem[kWarpsPerBlock][16 * kRowPitch];
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   float Hv[kHalf];
   int y, x0;
   bool first;
-  if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
+  float *sm = smem[threadIdx.x >> 5];
+  if (!row_tile<GPA>(a, w, sm, Hv, y, x0, first)) return;
+  const PK K = packed(a.K);
   const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
   float x[kHalf];
   if (GPA) a0_from_H(a, Hv, x);
@@ -267,24 +291,31 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
 #pragma unroll
     for (int k = 0; k < kHalf; ++k) x[k] = Hv[k];
   const size_t plane = (size_t)a.Hp * a.P;
-  const float4 *cp = reinterpret_cast<const float4 *>(carry_at(a, 0, tx, ntx, a.Hp, y));
-  float4 c0 = cp[0], c1 = cp[1];
+  // incoming states of channels n and n + 1 in registers; channel n + 2's
+  // are loaded while channel n computes
+  const float4 *cbase = reinterpret_cast<const float4 *>(carry_at(a, 0, tx, ntx, a.Hp, y));
+  const size_t cstride = (size_t)ntx * a.Hp * 2;  // float4s from one channel to the next
+  const int last = a.nch - 1;
+  float4 c0 = cbase[0], c1 = cbase[1];
+  float4 d0 = cbase[min(1, last) * cstride], d1 = cbase[min(1, last) * cstride + 1];
   for (int n = 0; n < a.nch; ++n) {
     if (GPA && n > 0) {
       const float is = 1.0f / sqrtf((float)n);
 #pragma unroll
       for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
     }
-    // the next channel's incoming states, loaded while this one computes
-    const float4 *cn = reinterpret_cast<const float4 *>(
-        carry_at(a, min(n + 1, a.nch - 1), tx, ntx, a.Hp, y));
+    const float4 *cn = cbase + min(n + 2, last) * cstride;
     const float4 n0 = cn[0], n1 = cn[1];
     float yv[kHalf];
-    apply_tile(a.K, x, c0, c1, first, yv);
-    c0 = n0;
-    c1 = n1;
-    // first lane: columns x0 + k; second lane: columns x0 + 31 - k
-    float *dst = a.planes + n * plane + (size_t)y * a.P + x0 + (first ? 0 : kHalf);
+    apply_tile(K, a.K.h0, x, c0, c1, first, yv);
+    c0 = d0;
+    c1 = d1;
+    d0 = n0;
+    d1 = n1;
+    // through shared memory (first lane: columns k; second lane: columns
+    // 31 - k), then 4 rows of 128 bytes per store instruction
+    float *row = sm + (threadIdx.x & 15) * kRowPitch + (first ? 0 : kHalf);
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       float4 v;
@@ -292,7 +323,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
       v.y = first ? yv[4 * m + 1] : yv[14 - 4 * m];
       v.z = first ? yv[4 * m + 2] : yv[13 - 4 * m];
       v.w = first ? yv[4 * m + 3] : yv[12 - 4 * m];
-      reinterpret_cast<float4 *>(dst)[m] = v;
+      reinterpret_cast<float4 *>(row)[m] = v;
+    }
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    float *dst = a.planes + n * plane + (size_t)(y - (lane & 15)) * a.P + x0 + (lane & 7) * 4;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int r = 4 * m + (lane >> 3);
+      *reinterpret_cast<float4 *>(dst + (size_t)r * a.P) =
+          *reinterpret_cast<const float4 *>(sm + r * kRowPitch + (lane & 7) * 4);
     }
   }
 }
@@ -301,7 +341,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
 // One thread per (line, channel): zero-state tile finals -> incoming states.
 // The loads of kScanChunk tiles are issued together before their sequential
 // updates, so a line costs ntiles / kScanChunk memory latencies per side.
-constexpr int kScanChunk = 8;
+constexpr int kScanChunk = 16;
 
 __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, int nlines, int ntiles) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,7 +349,9 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
   const int line = (int)(i % nlines), ch = (int)(i / nlines);
   const size_t step = (size_t)nlines * 2;  // float4 stride between consecutive tiles
   float4 *base = reinterpret_cast<float4 *>(carry_at(a, ch, 0, ntiles, nlines, line));
-  Cx S[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const PK K = packed(a.K);
+  const float2 z = make_float2(0.f, 0.f);
+  Pair S{z, z};
   for (int t0 = 0; t0 < ntiles; t0 += kScanChunk) {
     float4 e[kScanChunk];
 #pragma unroll
@@ -318,13 +360,12 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u) {
       if (t0 + u < ntiles) {
-        base[(t0 + u) * step] = make_float4(S[0].r, S[0].i, S[1].r, S[1].i);
-        S[0] = cadd(cmul(S[0], a.K.p32r[0], a.K.p32i[0]), Cx{e[u].x, e[u].y});
-        S[1] = cadd(cmul(S[1], a.K.p32r[1], a.K.p32i[1]), Cx{e[u].z, e[u].w});
+        base[(t0 + u) * step] = pack(S);
+        S = cadd(cmul(S, K.p32r, K.p32i, K.np32i), unpack(e[u]));
       }
     }
   }
-  Cx Q[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  Pair Q{z, z};
   for (int t0 = ntiles - 1; t0 >= 0; t0 -= kScanChunk) {
     float4 g[kScanChunk];
 #pragma unroll
@@ -333,9 +374,8 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u) {
       if (t0 - u >= 0) {
-        base[(t0 - u) * step + 1] = make_float4(Q[0].r, Q[0].i, Q[1].r, Q[1].i);
-        Q[0] = cadd(cmul(Q[0], a.K.p32r[0], a.K.p32i[0]), Cx{g[u].x, g[u].y});
-        Q[1] = cadd(cmul(Q[1], a.K.p32r[1], a.K.p32i[1]), Cx{g[u].z, g[u].w});
+        base[(t0 - u) * step + 1] = pack(Q);
+        Q = cadd(cmul(Q, K.p32r, K.p32i, K.np32i), unpack(g[u]));
       }
     }
   }
@@ -415,15 +455,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_cols_carry(const __gr
   int x, y0;
   bool first;
   if (!col_tile(a, w, x, y0, first)) return;
+  const PK K = packed(a.K);
   const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
   col_prologue(a, R, xb, y0, ty, nty, false);
   for (int n = 0; n < a.nch; ++n) {
     col_advance(a, R, n, xb, y0, ty, nty, false);
     float v[kHalf];
     col_read(R, n, first, v);
-    Cx fw[2], bw[2];
-    zero_state_finals(a.K, v, fw, bw);
-    write_carry(a.K, fw, bw, first, carry_at(a, n, ty, nty, a.P, x));
+    Pair fw, bw;
+    zero_state_finals(K, v, fw, bw);
+    write_carry(K, fw, bw, first, carry_at(a, n, ty, nty, a.P, x));
   }
   cp_wait<0>();
 }
@@ -431,13 +472,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_cols_carry(const __gr
 // Column pass.  Plain filter: the filtered plane is the output.  Algorithm 2:
 // A_n = w * a_n, accumulated into P' and Q' over the channel loop.
 template <bool GPA>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) rec_cols_apply(const __grid_constant__ RecArgs a) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const __grid_constant__ RecArgs a) {
   __shared__ ColRing ring[kWarpsPerBlock];
   ColRing &R = ring[threadIdx.x >> 5];
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   int x, y0;
   bool first;
   if (!col_tile(a, w, x, y0, first)) return;
+  const PK K = packed(a.K);
   const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
   const bool xin = x < a.W;
   const int cs = (threadIdx.x & 15) * 8;  // this column's carry slot in the ring
@@ -448,7 +490,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) rec_cols_apply(const _
     col_read(R, 0, first, v);
     const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
     const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][cs + 4]);
-    apply_tile(a.K, v, c0, c1, first, yv);
+    apply_tile(K, a.K.h0, v, c0, c1, first, yv);
 #pragma unroll
     for (int k = 0; k < kHalf; ++k) {
       const int yy = col_row(y0, first, k);
@@ -473,7 +515,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) rec_cols_apply(const _
       const int slot = n % kColDepth;
       const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs]);
       const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs + 4]);
-      apply_tile(a.K, v, c0, c1, first, An);
+      apply_tile(K, a.K.h0, v, c0, c1, first, An);
       if (n > 0) {  // P' += sqrt(n) a_{n-1} A_n, then a_n = a_{n-1} H / sqrt(n)
         const float sq = sqrtf((float)n), is = 1.0f / sq;
 #pragma unroll
