@@ -160,11 +160,10 @@ def rec_ops_per_pixel(N: int) -> float:
 
 def rec_bytes_per_pixel(N: int) -> float:
     """DRAM bytes per pixel the recursive forward's decomposition moves: per
-    channel the row pass's plane (4 written) and the column pass's two reads of
-    it (8), and the 32-pixel tile carries (1 B/px per channel, written, scanned
-    in place, read: 4 per direction); per pixel f read by three kernels (12)
-    and out written (4)."""
-    return (N + 1) * 20 + 16
+    channel the row pass's plane (4 written, 4 read by the column pass) and the
+    32-pixel tile carries (1 B/px per channel, written, scanned in place, read:
+    4 per direction); per pixel f read by three kernels (12) and out written (4)."""
+    return (N + 1) * 16 + 16
 
 
 def bwd_ops_per_pixel(kind: int, R: int, N: int) -> float:

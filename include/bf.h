@@ -374,8 +374,9 @@ bf_status bf_tuning_set(int kind, int radius_bucket, int order_bucket, int varia
  *
  * bf_recursive_workspace: bytes of the caller-owned device workspace for an
  *   image of height x width and order N (N = 0: the plain filter):
- *   1.25 (N + 1) 4 Hp P bytes (Hp, P = height, width rounded up to 32),
- *   rounded to 256-byte blocks.
+ *   1.5 (N + 1) 4 Hp P bytes (Hp, P = height, width rounded up to 32;
+ *   N + 1 planes and two carry arrays of a quarter plane each), rounded to
+ *   256-byte blocks.
  * bf_recursive_gauss: d_out = w * d_in (the plain filter, one image), for
  *   tests and as a building block.  sigma_s >= 0.5.
  * bf_recursive_forward: Algorithm 2 (f_GPA, optional Q') with w the

@@ -14,14 +14,17 @@
 // sigma_s = 20), so FP32 holds the 1e-3 parity bar at any sigma_s.
 //
 // Line parallelism.  A line is cut into tiles of 32 pixels, each handled by
-// two lanes of one warp (pixels 0-15 and 16-31).  Three kernels per
-// direction make every tile exact without halos:
+// two lanes of one warp (pixels 0-15 and 16-31).  Three steps per direction
+// make every tile exact without halos:
 //   carry  : each tile's zero-state final states (causal at its last pixel,
 //            anticausal at its first), per mode and channel;
 //   scan   : one thread per (line, channel) walks the tiles and turns them
 //            into the true incoming states (S_in(t+1) = r^32 S_in(t) + e(t),
 //            and mirrored for the anticausal side);
 //   apply  : each tile re-runs both recursions from its incoming states.
+// Five launches: rows carry, scan, rows apply (which also computes the
+// column tiles' carries from its 32 x 32 output blocks in shared memory),
+// scan, columns apply.
 // In `apply` both lanes of a tile run the same instruction stream: the second
 // lane holds its 16 pixels in reverse order, so phase 1 is the first lane's
 // causal pass and the second lane's anticausal pass; the two swap their final
@@ -57,6 +60,7 @@ struct RecConsts {
   float h0;                // h(0)
   float p16r[2], p16i[2];  // r_j^16
   float p32r[2], p32i[2];  // r_j^32
+  float wr[2][16], wi[2][16];  // r_j^k, k = 0..15: zero-state finals as dot products
 };
 
 struct RecArgs {
@@ -65,7 +69,8 @@ struct RecArgs {
   float *out;       // result (pitch)
   float *qaux;      // Q' (pitch) or null
   float *planes;    // (nch) planes of Hp x P floats
-  float *carry;     // nch * (lines of the direction) * tiles * 8 floats
+  float *carry_r;   // row tiles: nch * (P / 32) * Hp slots of 8 floats
+  float *carry_c;   // column tiles: nch * (Hp / 32) * P slots of 8 floats
   int H, W, pitch;
   int Hp, P;        // rows and pitch of a plane (multiples of 32)
   int nch;          // channels: N + 1 (GPA) or 1 (plain filter)
@@ -150,18 +155,26 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 // Zero-state final states of one lane's 16 inputs walked in register order
-// (fw) and in reverse register order (bw).
-__device__ __forceinline__ void zero_state_finals(const PK &K, const float (&x)[kHalf], Pair &fw,
-                                                  Pair &bw) {
-  const float2 z = make_float2(0.f, 0.f);
-  Pair s{z, z}, q{z, z};
+// (fw = sum_k r^(15-k) x[k]) and in reverse register order (bw = sum_k r^k
+// x[k]), as dot products with the constant powers r^k (two FMAs per mode and
+// sample, operands from the constant bank).
+__device__ __forceinline__ void zero_state_finals(const RecConsts &C, const float (&x)[kHalf],
+                                                  Pair &fw, Pair &bw) {
+  float fr0 = 0.f, fi0 = 0.f, fr1 = 0.f, fi1 = 0.f, br0 = 0.f, bi0 = 0.f, br1 = 0.f, bi1 = 0.f;
 #pragma unroll
   for (int k = 0; k < kHalf; ++k) {
-    s = step(s, x[k], K);
-    q = step(q, x[kHalf - 1 - k], K);
+    const float v = x[k];
+    fr0 = fmaf(C.wr[0][kHalf - 1 - k], v, fr0);
+    fi0 = fmaf(C.wi[0][kHalf - 1 - k], v, fi0);
+    fr1 = fmaf(C.wr[1][kHalf - 1 - k], v, fr1);
+    fi1 = fmaf(C.wi[1][kHalf - 1 - k], v, fi1);
+    br0 = fmaf(C.wr[0][k], v, br0);
+    bi0 = fmaf(C.wi[0][k], v, bi0);
+    br1 = fmaf(C.wr[1][k], v, br1);
+    bi1 = fmaf(C.wi[1][k], v, bi1);
   }
-  fw = s;
-  bw = q;
+  fw = Pair{make_float2(fr0, fr1), make_float2(fi0, fi1)};
+  bw = Pair{make_float2(br0, br1), make_float2(bi0, bi1)};
 }
 
 // Tile carries from the two lanes' zero-state finals: written by the first
@@ -198,9 +211,9 @@ __device__ __forceinline__ void apply_tile(const PK &K, float h0, const float (&
 }
 
 // Carry slot of (channel, tile, line).
-__device__ __forceinline__ float *carry_at(const RecArgs &a, int ch, int tile, int ntiles, int nlines,
+__device__ __forceinline__ float *carry_at(float *carry, int ch, int tile, int ntiles, int nlines,
                                            int line) {
-  return a.carry + (((size_t)ch * ntiles + tile) * nlines + line) * 8;
+  return carry + (((size_t)ch * ntiles + tile) * nlines + line) * 8;
 }
 
 // ------------------------------------------------------------ rows (first)
@@ -269,22 +282,31 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __gr
       for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
     }
     Pair fw, bw;
-    zero_state_finals(K, x, fw, bw);
-    write_carry(K, fw, bw, first, carry_at(a, n, tx, ntx, a.Hp, y));
+    zero_state_finals(a.K, x, fw, bw);
+    write_carry(K, fw, bw, first, carry_at(a.carry_r, n, tx, ntx, a.Hp, y));
   }
 }
 
+// Row pass with the column carries.  A CTA of two warps owns a 32 x 32 block
+// (warp 0 rows 0-15, warp 1 rows 16-31).  Per channel the block's filtered
+// rows go through shared memory: from there each warp stores its 16 rows to
+// the plane in full 128-byte lines, and computes the zero-state column finals
+// of 16 of the block's columns (the first column tile's carries), so the
+// column pass needs no separate carry sweep over the planes.
+constexpr int kRowApplyWarps = 2;
+
 template <bool GPA>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __grid_constant__ RecArgs a) {
-  __shared__ __align__(16) float smem[kWarpsPerBlock][16 * kRowPitch];
-  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __grid_constant__ RecArgs a) {
+  __shared__ __align__(16) float smem[kRowApplyWarps * 16 * kRowPitch];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntx = a.P / kTileLen, nty = a.Hp / kTileLen;
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;  // grid = ntx * nty exactly
+  float *sm = smem + wi * 16 * kRowPitch;
   float Hv[kHalf];
   int y, x0;
   bool first;
-  float *sm = smem[threadIdx.x >> 5];
-  if (!row_tile<GPA>(a, w, sm, Hv, y, x0, first)) return;
+  row_tile<GPA>(a, (2 * ty + wi) * ntx + tx, sm, Hv, y, x0, first);
   const PK K = packed(a.K);
-  const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
   float x[kHalf];
   if (GPA) a0_from_H(a, Hv, x);
   else
@@ -293,11 +315,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
   const size_t plane = (size_t)a.Hp * a.P;
   // incoming states of channels n and n + 1 in registers; channel n + 2's
   // are loaded while channel n computes
-  const float4 *cbase = reinterpret_cast<const float4 *>(carry_at(a, 0, tx, ntx, a.Hp, y));
+  const float4 *cbase = reinterpret_cast<const float4 *>(carry_at(a.carry_r, 0, tx, ntx, a.Hp, y));
   const size_t cstride = (size_t)ntx * a.Hp * 2;  // float4s from one channel to the next
   const int last = a.nch - 1;
   float4 c0 = cbase[0], c1 = cbase[1];
   float4 d0 = cbase[min(1, last) * cstride], d1 = cbase[min(1, last) * cstride + 1];
+  // this lane's column of the block for the column finals
+  const int cc = 16 * wi + (lane & 15);
   for (int n = 0; n < a.nch; ++n) {
     if (GPA && n > 0) {
       const float is = 1.0f / sqrtf((float)n);
@@ -312,10 +336,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
     c1 = d1;
     d0 = n0;
     d1 = n1;
-    // through shared memory (first lane: columns k; second lane: columns
-    // 31 - k), then 4 rows of 128 bytes per store instruction
-    float *row = sm + (threadIdx.x & 15) * kRowPitch + (first ? 0 : kHalf);
-    __syncwarp();
+    // first lane: columns k; second lane: columns 31 - k
+    float *row = sm + (lane & 15) * kRowPitch + (first ? 0 : kHalf);
+    __syncthreads();  // the previous channel's block is fully read
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       float4 v;
@@ -325,8 +348,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
       v.w = first ? yv[4 * m + 3] : yv[12 - 4 * m];
       reinterpret_cast<float4 *>(row)[m] = v;
     }
-    __syncwarp();
-    const int lane = threadIdx.x & 31;
+    __syncthreads();
     float *dst = a.planes + n * plane + (size_t)(y - (lane & 15)) * a.P + x0 + (lane & 7) * 4;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -334,6 +356,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
       *reinterpret_cast<float4 *>(dst + (size_t)r * a.P) =
           *reinterpret_cast<const float4 *>(sm + r * kRowPitch + (lane & 7) * 4);
     }
+    // column finals: first lane rows 0..15 of column cc, second lane rows 31..16
+    float v[kHalf];
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) v[k] = smem[(first ? k : kTileLen - 1 - k) * kRowPitch + cc];
+    Pair fw, bw;
+    zero_state_finals(a.K, v, fw, bw);
+    write_carry(K, fw, bw, first, carry_at(a.carry_c, n, ty, nty, a.P, x0 + cc));
   }
 }
 
@@ -343,12 +372,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_apply(const __gr
 // updates, so a line costs ntiles / kScanChunk memory latencies per side.
 constexpr int kScanChunk = 16;
 
-__global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, int nlines, int ntiles) {
+__global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, float *carry, int nlines,
+                                                int ntiles) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)nlines * a.nch) return;
   const int line = (int)(i % nlines), ch = (int)(i / nlines);
   const size_t step = (size_t)nlines * 2;  // float4 stride between consecutive tiles
-  float4 *base = reinterpret_cast<float4 *>(carry_at(a, ch, 0, ntiles, nlines, line));
+  float4 *base = reinterpret_cast<float4 *>(carry_at(carry, ch, 0, ntiles, nlines, line));
   const PK K = packed(a.K);
   const float2 z = make_float2(0.f, 0.f);
   Pair S{z, z};
@@ -418,7 +448,8 @@ __device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, i
     const int c = lane + 32 * j, row = c >> 2, col = (c & 3) * 4;
     cp_async16(&R.tile[slot][row * 16 + col], src + (size_t)row * a.P + col);
   }
-  if (with_carry) cp_async16(&R.carry[slot][lane * 4], carry_at(a, n, ty, nty, a.P, xb) + lane * 4);
+  if (with_carry)
+    cp_async16(&R.carry[slot][lane * 4], carry_at(a.carry_c, n, ty, nty, a.P, xb) + lane * 4);
 }
 
 // The lane's 16 inputs of channel n from the ring (call after col_wait).
@@ -446,27 +477,6 @@ __device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing &R, int x
     if (q < a.nch) col_issue(a, R, q, xb, y0, ty, nty, with_carry);
     cp_commit();
   }
-}
-
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_cols_carry(const __grid_constant__ RecArgs a) {
-  __shared__ ColRing ring[kWarpsPerBlock];
-  ColRing &R = ring[threadIdx.x >> 5];
-  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  int x, y0;
-  bool first;
-  if (!col_tile(a, w, x, y0, first)) return;
-  const PK K = packed(a.K);
-  const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
-  col_prologue(a, R, xb, y0, ty, nty, false);
-  for (int n = 0; n < a.nch; ++n) {
-    col_advance(a, R, n, xb, y0, ty, nty, false);
-    float v[kHalf];
-    col_read(R, n, first, v);
-    Pair fw, bw;
-    zero_state_finals(K, v, fw, bw);
-    write_carry(K, fw, bw, first, carry_at(a, n, ty, nty, a.P, x));
-  }
-  cp_wait<0>();
 }
 
 // Column pass.  Plain filter: the filtered plane is the output.  Algorithm 2:
@@ -595,6 +605,11 @@ RecConsts make_consts(double sigma_s) {
     K.ar[j] = (float)(2.0 * m.alpha[j].r);
     K.ai[j] = (float)(2.0 * m.alpha[j].i);
     const Cd p16 = cd_pow(m.r[j], 16), p32 = cd_pow(m.r[j], 32);
+    for (int k = 0; k < 16; ++k) {
+      const Cd w = cd_pow(m.r[j], k);
+      K.wr[j][k] = (float)w.r;
+      K.wi[j][k] = (float)w.i;
+    }
     K.p16r[j] = (float)p16.r;
     K.p16i[j] = (float)p16.i;
     K.p32r[j] = (float)p32.r;
@@ -617,11 +632,11 @@ Layout layout(int height, int width, int nch) {
   L.P = (int)round_up((size_t)width, kTileLen);
   L.plane_floats = (size_t)L.Hp * L.P;
   L.planes_bytes = round_up(L.plane_floats * nch * sizeof(float), 256);
-  // one carry slot (8 floats) per 32 pixels of a line per channel; rows and
-  // columns need the same count, and the row carries are dead once the row
-  // pass has run, so the column pass reuses them
+  // one carry slot (8 floats) per 32 pixels of a line per channel, for the
+  // row tiles and for the column tiles (the row pass reads the first while it
+  // writes the second)
   L.carry_bytes = round_up(L.plane_floats / kTileLen * 8 * nch * sizeof(float), 256);
-  L.total = L.planes_bytes + L.carry_bytes;
+  L.total = L.planes_bytes + 2 * L.carry_bytes;
   return L;
 }
 
@@ -643,7 +658,8 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
   a.out = out;
   a.qaux = qaux;
   a.planes = static_cast<float *>(ws);
-  a.carry = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes);
+  a.carry_r = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes);
+  a.carry_c = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes + L.carry_bytes);
   a.H = height;
   a.W = width;
   a.pitch = pitch;
@@ -657,23 +673,24 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
   a.e2c = (float)(-1.4426950408889634 / 2.0);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int threads = 32 * kWarpsPerBlock;
-  // rows: warps = (Hp / 16) x (P / 32)
+  // rows: warps = (Hp / 16) x (P / 32); the row pass's two-warp CTAs own
+  // one 32 x 32 block each
   const long long wr = (long long)(L.Hp / 16) * (L.P / kTileLen);
   const long long br = (wr + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const long long ba = (long long)(L.Hp / kTileLen) * (L.P / kTileLen);
   // columns: warps = (P / 16) x (Hp / 32)
   const long long wc = (long long)(L.P / 16) * (L.Hp / kTileLen);
   const long long bc = (wc + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const long long sr_threads = (long long)L.Hp * nch, sc_threads = (long long)L.P * nch;
-  if (br > 0x7fffffffLL || bc > 0x7fffffffLL || sr_threads / 256 + 1 > 0x7fffffffLL ||
+  if (br > 0x7fffffffLL || bc > 0x7fffffffLL || ba > 0x7fffffffLL || sr_threads / 256 + 1 > 0x7fffffffLL ||
       sc_threads / 256 + 1 > 0x7fffffffLL)
     return BF_ERR_UNSUPPORTED;
   if (gpa) rec_rows_carry<true><<<(int)br, threads, 0, s>>>(a);
   else rec_rows_carry<false><<<(int)br, threads, 0, s>>>(a);
-  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(a, L.Hp, L.P / kTileLen);
-  if (gpa) rec_rows_apply<true><<<(int)br, threads, 0, s>>>(a);
-  else rec_rows_apply<false><<<(int)br, threads, 0, s>>>(a);
-  rec_cols_carry<<<(int)bc, threads, 0, s>>>(a);
-  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(a, L.P, L.Hp / kTileLen);
+  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(a, a.carry_r, L.Hp, L.P / kTileLen);
+  if (gpa) rec_rows_apply<true><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
+  else rec_rows_apply<false><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
+  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(a, a.carry_c, L.P, L.Hp / kTileLen);
   if (gpa) rec_cols_apply<true><<<(int)bc, threads, 0, s>>>(a);
   else rec_cols_apply<false><<<(int)bc, threads, 0, s>>>(a);
   return bfi::check_launch();
