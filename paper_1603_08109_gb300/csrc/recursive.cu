@@ -69,8 +69,8 @@ struct RecArgs {
   float *out;       // result (pitch)
   float *qaux;      // Q' (pitch) or null
   float *planes;    // (nch) planes of Hp x P floats
-  float *carry_r;   // row tiles: nch * (P / 32) * Hp slots of 8 floats
-  float *carry_c;   // column tiles: nch * (Hp / 32) * P slots of 8 floats
+  float4 *carry_r;  // row tiles: 2 sides x nch x (P / 32) x Hp states (float4 each)
+  float4 *carry_c;  // column tiles: 2 sides x nch x (Hp / 32) x P states
   int H, W, pitch;
   int Hp, P;        // rows and pitch of a plane (multiples of 32)
   int nch;          // channels: N + 1 (GPA) or 1 (plain filter)
@@ -181,13 +181,14 @@ __device__ __forceinline__ void zero_state_finals(const RecConsts &C, const floa
 // lane of the pair.  First lane: fw = causal final at pixel 15, bw =
 // anticausal final at pixel 0.  Second lane (reversed): fw = anticausal final
 // at pixel 16, bw = causal final at pixel 31.
-__device__ __forceinline__ void write_carry(const PK &K, Pair fw, Pair bw, bool first, float *dst) {
+__device__ __forceinline__ void write_carry(const PK &K, Pair fw, Pair bw, bool first, float4 *dst,
+                                            size_t side) {
   const Pair pf = shfl16(fw), pb = shfl16(bw);
   const Pair e = cadd(cmul(fw, K.p16r, K.p16i, K.np16i), pb);  // causal at pixel 31
   const Pair g = cadd(bw, cmul(pf, K.p16r, K.p16i, K.np16i));  // anticausal at pixel 0
   if (first) {
-    reinterpret_cast<float4 *>(dst)[0] = pack(e);
-    reinterpret_cast<float4 *>(dst)[1] = pack(g);
+    dst[0] = pack(e);
+    dst[side] = pack(g);
   }
 }
 
@@ -210,10 +211,24 @@ __device__ __forceinline__ void apply_tile(const PK &K, float h0, const float (&
   }
 }
 
-// Carry slot of (channel, tile, line).
-__device__ __forceinline__ float *carry_at(float *carry, int ch, int tile, int ntiles, int nlines,
-                                           int line) {
-  return carry + (((size_t)ch * ntiles + tile) * nlines + line) * 8;
+// Tile states of one direction: the causal side (tile finals e, then the
+// incoming states S_in) and, `side` float4s further, the anticausal side
+// (g, then Q_in); lines fastest, so a warp's 16 or 32 lines are contiguous
+// and each scan pass streams whole sectors of its own side.
+struct CarryMap {
+  float4 *p;
+  int nch, ntiles, nlines;
+  __device__ __forceinline__ size_t side() const { return (size_t)nch * ntiles * nlines; }
+  __device__ __forceinline__ float4 *at(int ch, int tile, int line) const {
+    return p + ((size_t)ch * ntiles + tile) * nlines + line;
+  }
+};
+
+__device__ __forceinline__ CarryMap row_carries(const RecArgs &a) {
+  return CarryMap{a.carry_r, a.nch, a.P / kTileLen, a.Hp};
+}
+__device__ __forceinline__ CarryMap col_carries(const RecArgs &a) {
+  return CarryMap{a.carry_c, a.nch, a.Hp / kTileLen, a.P};
 }
 
 // ------------------------------------------------------------ rows (first)
@@ -269,7 +284,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __gr
   bool first;
   if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
   const PK K = packed(a.K);
-  const int ntx = a.P / kTileLen, tx = x0 / kTileLen;
+  const CarryMap cm = row_carries(a);
+  const int tx = x0 / kTileLen;
   float x[kHalf];
   if (GPA) a0_from_H(a, Hv, x);
   else
@@ -283,7 +299,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __gr
     }
     Pair fw, bw;
     zero_state_finals(a.K, x, fw, bw);
-    write_carry(K, fw, bw, first, carry_at(a.carry_r, n, tx, ntx, a.Hp, y));
+    write_carry(K, fw, bw, first, cm.at(n, tx, y), cm.side());
   }
 }
 
@@ -299,8 +315,8 @@ template <bool GPA>
 __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __grid_constant__ RecArgs a) {
   __shared__ __align__(16) float smem[kRowApplyWarps * 16 * kRowPitch];
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntx = a.P / kTileLen, nty = a.Hp / kTileLen;
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;  // grid = ntx * nty exactly
+  const int ntx = a.P / kTileLen;
+  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;  // grid = ntx * (Hp / 32) exactly
   float *sm = smem + wi * 16 * kRowPitch;
   float Hv[kHalf];
   int y, x0;
@@ -315,11 +331,12 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
   const size_t plane = (size_t)a.Hp * a.P;
   // incoming states of channels n and n + 1 in registers; channel n + 2's
   // are loaded while channel n computes
-  const float4 *cbase = reinterpret_cast<const float4 *>(carry_at(a.carry_r, 0, tx, ntx, a.Hp, y));
-  const size_t cstride = (size_t)ntx * a.Hp * 2;  // float4s from one channel to the next
+  const CarryMap rm = row_carries(a), cm = col_carries(a);
+  const float4 *cbase = rm.at(0, tx, y);
+  const size_t cstride = (size_t)ntx * a.Hp, cside = rm.side();  // channel step, side offset
   const int last = a.nch - 1;
-  float4 c0 = cbase[0], c1 = cbase[1];
-  float4 d0 = cbase[min(1, last) * cstride], d1 = cbase[min(1, last) * cstride + 1];
+  float4 c0 = cbase[0], c1 = cbase[cside];
+  float4 d0 = cbase[min(1, last) * cstride], d1 = cbase[min(1, last) * cstride + cside];
   // this lane's column of the block for the column finals
   const int cc = 16 * wi + (lane & 15);
   for (int n = 0; n < a.nch; ++n) {
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
       for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
     }
     const float4 *cn = cbase + min(n + 2, last) * cstride;
-    const float4 n0 = cn[0], n1 = cn[1];
+    const float4 n0 = cn[0], n1 = cn[cside];
     float yv[kHalf];
     apply_tile(K, a.K.h0, x, c0, c1, first, yv);
     c0 = d0;
@@ -362,23 +379,28 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
     for (int k = 0; k < kHalf; ++k) v[k] = smem[(first ? k : kTileLen - 1 - k) * kRowPitch + cc];
     Pair fw, bw;
     zero_state_finals(a.K, v, fw, bw);
-    write_carry(K, fw, bw, first, carry_at(a.carry_c, n, ty, nty, a.P, x0 + cc));
+    write_carry(K, fw, bw, first, cm.at(n, ty, x0 + cc), cm.side());
   }
 }
 
 // ----------------------------------------------------------------- scan
-// One thread per (line, channel): zero-state tile finals -> incoming states.
+// One thread per (line, channel, side): zero-state tile finals -> incoming
+// states, causal side walking the tiles forward, anticausal side backward.
 // The loads of kScanChunk tiles are issued together before their sequential
-// updates, so a line costs ntiles / kScanChunk memory latencies per side.
+// updates, so a line costs ntiles / kScanChunk memory latencies.
 constexpr int kScanChunk = 16;
 
-__global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, float *carry, int nlines,
-                                                int ntiles) {
+__global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, CarryMap cm) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)nlines * a.nch) return;
-  const int line = (int)(i % nlines), ch = (int)(i / nlines);
-  const size_t step = (size_t)nlines * 2;  // float4 stride between consecutive tiles
-  float4 *base = reinterpret_cast<float4 *>(carry_at(carry, ch, 0, ntiles, nlines, line));
+  if (i >= 2LL * cm.nlines * cm.nch) return;
+  const int line = (int)(i % cm.nlines);
+  const long long r = i / cm.nlines;
+  const int ch = (int)(r % cm.nch), sd = (int)(r / cm.nch);
+  const int ntiles = cm.ntiles;
+  const size_t step = (size_t)cm.nlines;  // float4 stride between consecutive tiles
+  // walk position u: tile u (causal) or ntiles - 1 - u (anticausal)
+  float4 *base = cm.at(ch, sd ? ntiles - 1 : 0, line) + (sd ? cm.side() : 0);
+  const ptrdiff_t dir = sd ? -(ptrdiff_t)step : (ptrdiff_t)step;
   const PK K = packed(a.K);
   const float2 z = make_float2(0.f, 0.f);
   Pair S{z, z};
@@ -386,26 +408,12 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
     float4 e[kScanChunk];
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u)
-      if (t0 + u < ntiles) e[u] = base[(t0 + u) * step];
+      if (t0 + u < ntiles) e[u] = base[(t0 + u) * dir];
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u) {
       if (t0 + u < ntiles) {
-        base[(t0 + u) * step] = pack(S);
+        base[(t0 + u) * dir] = pack(S);
         S = cadd(cmul(S, K.p32r, K.p32i, K.np32i), unpack(e[u]));
-      }
-    }
-  }
-  Pair Q{z, z};
-  for (int t0 = ntiles - 1; t0 >= 0; t0 -= kScanChunk) {
-    float4 g[kScanChunk];
-#pragma unroll
-    for (int u = 0; u < kScanChunk; ++u)
-      if (t0 - u >= 0) g[u] = base[(t0 - u) * step + 1];
-#pragma unroll
-    for (int u = 0; u < kScanChunk; ++u) {
-      if (t0 - u >= 0) {
-        base[(t0 - u) * step + 1] = pack(Q);
-        Q = cadd(cmul(Q, K.p32r, K.p32i, K.np32i), unpack(g[u]));
       }
     }
   }
@@ -435,7 +443,7 @@ __device__ __forceinline__ int col_row(int y0, bool first, int k) {
 constexpr int kColDepth = 3;
 struct ColRing {
   float tile[kColDepth][kTileLen * 16];  // row-major, 16 floats per row
-  float carry[kColDepth][16 * 8];
+  float carry[kColDepth][2 * 16 * 4];  // 16 causal states, then 16 anticausal
 };
 
 __device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, int xb, int y0,
@@ -448,8 +456,10 @@ __device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, i
     const int c = lane + 32 * j, row = c >> 2, col = (c & 3) * 4;
     cp_async16(&R.tile[slot][row * 16 + col], src + (size_t)row * a.P + col);
   }
-  if (with_carry)
-    cp_async16(&R.carry[slot][lane * 4], carry_at(a.carry_c, n, ty, nty, a.P, xb) + lane * 4);
+  if (with_carry) {
+    const CarryMap cm = col_carries(a);
+    cp_async16(&R.carry[slot][lane * 4], cm.at(n, ty, xb + (lane & 15)) + (lane < 16 ? 0 : cm.side()));
+  }
 }
 
 // The lane's 16 inputs of channel n from the ring (call after col_wait).
@@ -492,14 +502,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
   const PK K = packed(a.K);
   const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
   const bool xin = x < a.W;
-  const int cs = (threadIdx.x & 15) * 8;  // this column's carry slot in the ring
+  const int cs = (threadIdx.x & 15) * 4;  // this column's states in the ring's carry slots
   col_prologue(a, R, xb, y0, ty, nty, true);
   if constexpr (!GPA) {
     col_advance(a, R, 0, xb, y0, ty, nty, true);
     float v[kHalf], yv[kHalf];
     col_read(R, 0, first, v);
     const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
-    const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][cs + 4]);
+    const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][64 + cs]);
     apply_tile(K, a.K.h0, v, c0, c1, first, yv);
 #pragma unroll
     for (int k = 0; k < kHalf; ++k) {
@@ -524,7 +534,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
       col_read(R, n, first, v);
       const int slot = n % kColDepth;
       const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs]);
-      const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs + 4]);
+      const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][64 + cs]);
       apply_tile(K, a.K.h0, v, c0, c1, first, An);
       if (n > 0) {  // P' += sqrt(n) a_{n-1} A_n, then a_n = a_{n-1} H / sqrt(n)
         const float sq = sqrtf((float)n), is = 1.0f / sq;
@@ -658,8 +668,8 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
   a.out = out;
   a.qaux = qaux;
   a.planes = static_cast<float *>(ws);
-  a.carry_r = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes);
-  a.carry_c = reinterpret_cast<float *>(static_cast<char *>(ws) + L.planes_bytes + L.carry_bytes);
+  a.carry_r = reinterpret_cast<float4 *>(static_cast<char *>(ws) + L.planes_bytes);
+  a.carry_c = reinterpret_cast<float4 *>(static_cast<char *>(ws) + L.planes_bytes + L.carry_bytes);
   a.H = height;
   a.W = width;
   a.pitch = pitch;
@@ -681,16 +691,18 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
   // columns: warps = (P / 16) x (Hp / 32)
   const long long wc = (long long)(L.P / 16) * (L.Hp / kTileLen);
   const long long bc = (wc + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const long long sr_threads = (long long)L.Hp * nch, sc_threads = (long long)L.P * nch;
+  const long long sr_threads = 2LL * L.Hp * nch, sc_threads = 2LL * L.P * nch;
   if (br > 0x7fffffffLL || bc > 0x7fffffffLL || ba > 0x7fffffffLL || sr_threads / 256 + 1 > 0x7fffffffLL ||
       sc_threads / 256 + 1 > 0x7fffffffLL)
     return BF_ERR_UNSUPPORTED;
   if (gpa) rec_rows_carry<true><<<(int)br, threads, 0, s>>>(a);
   else rec_rows_carry<false><<<(int)br, threads, 0, s>>>(a);
-  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(a, a.carry_r, L.Hp, L.P / kTileLen);
+  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(
+      a, CarryMap{a.carry_r, nch, L.P / kTileLen, L.Hp});
   if (gpa) rec_rows_apply<true><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
   else rec_rows_apply<false><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
-  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(a, a.carry_c, L.P, L.Hp / kTileLen);
+  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(
+      a, CarryMap{a.carry_c, nch, L.Hp / kTileLen, L.P});
   if (gpa) rec_cols_apply<true><<<(int)bc, threads, 0, s>>>(a);
   else rec_cols_apply<false><<<(int)bc, threads, 0, s>>>(a);
   return bfi::check_launch();
