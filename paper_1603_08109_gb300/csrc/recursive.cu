@@ -386,9 +386,9 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
 // ----------------------------------------------------------------- scan
 // One thread per (line, channel, side): zero-state tile finals -> incoming
 // states, causal side walking the tiles forward, anticausal side backward.
-// The loads of kScanChunk tiles are issued together before their sequential
-// updates, so a line costs ntiles / kScanChunk memory latencies.
-constexpr int kScanChunk = 16;
+// Software-pipelined: the next kScanChunk tiles are loaded before the current
+// chunk's sequential updates and stores, so loads never wait behind stores.
+constexpr int kScanChunk = 8;
 
 __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs a, CarryMap cm) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -397,18 +397,21 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
   const long long r = i / cm.nlines;
   const int ch = (int)(r % cm.nch), sd = (int)(r / cm.nch);
   const int ntiles = cm.ntiles;
-  const size_t step = (size_t)cm.nlines;  // float4 stride between consecutive tiles
   // walk position u: tile u (causal) or ntiles - 1 - u (anticausal)
   float4 *base = cm.at(ch, sd ? ntiles - 1 : 0, line) + (sd ? cm.side() : 0);
-  const ptrdiff_t dir = sd ? -(ptrdiff_t)step : (ptrdiff_t)step;
+  const ptrdiff_t dir = sd ? -(ptrdiff_t)cm.nlines : (ptrdiff_t)cm.nlines;
   const PK K = packed(a.K);
   const float2 z = make_float2(0.f, 0.f);
   Pair S{z, z};
+  float4 e[kScanChunk];
+#pragma unroll
+  for (int u = 0; u < kScanChunk; ++u)
+    if (u < ntiles) e[u] = base[u * dir];
   for (int t0 = 0; t0 < ntiles; t0 += kScanChunk) {
-    float4 e[kScanChunk];
+    float4 en[kScanChunk];
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u)
-      if (t0 + u < ntiles) e[u] = base[(t0 + u) * dir];
+      if (t0 + kScanChunk + u < ntiles) en[u] = base[(t0 + kScanChunk + u) * dir];
 #pragma unroll
     for (int u = 0; u < kScanChunk; ++u) {
       if (t0 + u < ntiles) {
@@ -416,6 +419,8 @@ __global__ void __launch_bounds__(256) rec_scan(const __grid_constant__ RecArgs 
         S = cadd(cmul(S, K.p32r, K.p32i, K.np32i), unpack(e[u]));
       }
     }
+#pragma unroll
+    for (int u = 0; u < kScanChunk; ++u) e[u] = en[u];
   }
 }
 
