@@ -80,24 +80,17 @@ struct RecArgs {
 };
 
 // The two modes side by side in packed two-lane FP32 (.x = mode 0,
-// .y = mode 1): one __ffma2_rn advances both.
+// .y = mode 1) for the tile-state arithmetic (carries and scans).
 struct Pair {
   float2 r, i;  // complex states of the two modes
 };
 
 struct PK {
-  float2 pr, pi, npi;  // poles and -Im
-  float2 ar, nai;      // A_j and -Im A_j
-  float2 p16r, p16i, np16i, p32r, p32i, np32i;
+  float2 p16r, p16i, np16i, p32r, p32i, np32i;  // r^16, r^32 and their -Im
 };
 
 __device__ __forceinline__ PK packed(const RecConsts &K) {
   PK k;
-  k.pr = make_float2(K.pr[0], K.pr[1]);
-  k.pi = make_float2(K.pi[0], K.pi[1]);
-  k.npi = make_float2(-K.pi[0], -K.pi[1]);
-  k.ar = make_float2(K.ar[0], K.ar[1]);
-  k.nai = make_float2(-K.ai[0], -K.ai[1]);
   k.p16r = make_float2(K.p16r[0], K.p16r[1]);
   k.p16i = make_float2(K.p16i[0], K.p16i[1]);
   k.np16i = make_float2(-K.p16i[0], -K.p16i[1]);
@@ -105,20 +98,6 @@ __device__ __forceinline__ PK packed(const RecConsts &K) {
   k.p32i = make_float2(K.p32i[0], K.p32i[1]);
   k.np32i = make_float2(-K.p32i[0], -K.p32i[1]);
   return k;
-}
-
-// s <- x + r s for both modes.
-__device__ __forceinline__ Pair step(Pair s, float x, const PK &k) {
-  Pair o;
-  o.r = __ffma2_rn(k.pr, s.r, __ffma2_rn(k.npi, s.i, make_float2(x, x)));
-  o.i = __ffma2_rn(k.pr, s.i, __fmul2_rn(k.pi, s.r));
-  return o;
-}
-
-// c + sum_j Re(A_j s_j).
-__device__ __forceinline__ float contrib(Pair s, const PK &k, float c) {
-  const float2 t = __ffma2_rn(k.ar, s.r, __ffma2_rn(k.nai, s.i, make_float2(c, 0.f)));
-  return t.x + t.y;
 }
 
 // a * b per mode (b given as re, im, -im).
@@ -193,21 +172,38 @@ __device__ __forceinline__ void write_carry(const PK &K, Pair fw, Pair bw, bool 
 }
 
 // Both recursions over one tile from its incoming states; y = the filtered
-// values in the lane's register order.
-__device__ __forceinline__ void apply_tile(const PK &K, float h0, const float (&x)[kHalf], float4 c0,
+// values in the lane's register order.  Scalar FP32 with the constants as
+// constant-bank operands: these loops are bound by the FMA pipe, where the
+// packed form saves issue slots but no pipe cycles, and scalar constants take
+// no registers.
+__device__ __forceinline__ void apply_tile(const RecConsts &C, const float (&x)[kHalf], float4 c0,
                                            float4 c1, bool first, float (&y)[kHalf]) {
   // c0: causal incoming state S_in, c1: anticausal incoming state Q_in
-  Pair st = unpack(first ? c0 : c1);
+  // (r.x, r.y, i.x, i.y) = (mode 0 re, mode 1 re, mode 0 im, mode 1 im)
+  const float4 c = first ? c0 : c1;
+  float s0r = c.x, s1r = c.y, s0i = c.z, s1i = c.w;
 #pragma unroll
   for (int k = 0; k < kHalf; ++k) {
-    st = step(st, x[k], K);
-    y[k] = contrib(st, K, 0.f);
+    const float n0r = fmaf(C.pr[0], s0r, fmaf(-C.pi[0], s0i, x[k]));
+    const float n0i = fmaf(C.pr[0], s0i, C.pi[0] * s0r);
+    const float n1r = fmaf(C.pr[1], s1r, fmaf(-C.pi[1], s1i, x[k]));
+    const float n1i = fmaf(C.pr[1], s1i, C.pi[1] * s1r);
+    s0r = n0r; s0i = n0i; s1r = n1r; s1i = n1i;
+    y[k] = fmaf(C.ar[0], s0r, fmaf(-C.ai[0], s0i, fmaf(C.ar[1], s1r, -C.ai[1] * s1i)));
   }
-  st = shfl16(st);
+  s0r = __shfl_xor_sync(0xffffffffu, s0r, 16);
+  s0i = __shfl_xor_sync(0xffffffffu, s0i, 16);
+  s1r = __shfl_xor_sync(0xffffffffu, s1r, 16);
+  s1i = __shfl_xor_sync(0xffffffffu, s1i, 16);
 #pragma unroll
   for (int k = kHalf - 1; k >= 0; --k) {
-    st = step(st, x[k], K);
-    y[k] = contrib(st, K, fmaf(-h0, x[k], y[k]));
+    const float n0r = fmaf(C.pr[0], s0r, fmaf(-C.pi[0], s0i, x[k]));
+    const float n0i = fmaf(C.pr[0], s0i, C.pi[0] * s0r);
+    const float n1r = fmaf(C.pr[1], s1r, fmaf(-C.pi[1], s1i, x[k]));
+    const float n1i = fmaf(C.pr[1], s1i, C.pi[1] * s1r);
+    s0r = n0r; s0i = n0i; s1r = n1r; s1i = n1i;
+    y[k] = fmaf(C.ar[0], s0r, fmaf(-C.ai[0], s0i,
+                fmaf(C.ar[1], s1r, fmaf(-C.ai[1], s1i, fmaf(-C.h0, x[k], y[k])))));
   }
 }
 
@@ -348,7 +344,7 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
     const float4 *cn = cbase + min(n + 2, last) * cstride;
     const float4 n0 = cn[0], n1 = cn[cside];
     float yv[kHalf];
-    apply_tile(K, a.K.h0, x, c0, c1, first, yv);
+    apply_tile(a.K, x, c0, c1, first, yv);
     c0 = d0;
     c1 = d1;
     d0 = n0;
@@ -515,7 +511,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
     col_read(R, 0, first, v);
     const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
     const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][64 + cs]);
-    apply_tile(K, a.K.h0, v, c0, c1, first, yv);
+    apply_tile(a.K, v, c0, c1, first, yv);
 #pragma unroll
     for (int k = 0; k < kHalf; ++k) {
       const int yy = col_row(y0, first, k);
@@ -540,7 +536,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
       const int slot = n % kColDepth;
       const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs]);
       const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][64 + cs]);
-      apply_tile(K, a.K.h0, v, c0, c1, first, An);
+      apply_tile(a.K, v, c0, c1, first, An);
       if (n > 0) {  // P' += sqrt(n) a_{n-1} A_n, then a_n = a_{n-1} H / sqrt(n)
         const float sq = sqrtf((float)n), is = 1.0f / sq;
 #pragma unroll
