@@ -60,3 +60,26 @@ def test_random_forward_and_backward(seed):
     scale = max(np.abs(rgin).max(), 1e-30)
     assert np.abs(gin - rgin).max() <= 2e-3 * scale, where
     assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_recursive_forward(seed):
+    """The recursive-Gaussian route (reading of Sec. III-A's O(1) filter) at
+    random sigma_s in [0.5, 60], shapes, row pitches and orders, against the
+    checker's full-line evaluation."""
+    from oracle import recursive as rec
+    rng = np.random.default_rng(7000 + seed)
+    ss = float(np.exp(rng.uniform(np.log(0.5), np.log(60.0))))
+    sr = float(rng.uniform(25.0, 80.0))
+    H = int(rng.integers(1, 140))
+    W = int(rng.integers(1, 230))
+    pad = int(rng.integers(0, 5))
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, ss, sr, 1.0) if seed % 3 else int(rng.integers(1, 8))
+    img = image(H, W, seed=seed + 101, block=int(rng.integers(2, 20)))
+    base = torch.zeros((H, W + pad), dtype=torch.float32, device="cuda")
+    base[:, :W] = torch.from_numpy(img).cuda()
+    where = "seed %d sigma_s %.2f sr %.1f N %d %dx%d pitch %d" % (seed, ss, sr, N, H, W, W + pad)
+    out, q = bf.recursive_forward(base[:, :W], sr, N, ss, return_q=True)
+    ro, P, Q = rec.gpa_alg2_recursive(img, ss, sr, N, return_parts=True)
+    compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr),
+                    rec.centre_weight_recursive(ss), where, sigma_r=sr, N=N)
