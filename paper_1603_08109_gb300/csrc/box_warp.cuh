@@ -1,5 +1,5 @@
 // Warp-strip streaming forward for the box spatial kernel at small order
-// (N <= 5) and small radius (W <= 8): the memory-bound regime of Algorithm 2.
+// (N <= 8) and small radius (W <= 8): the memory-bound regime of Algorithm 2.
 //
 // Each warp owns a strip of 32 C region columns, C = 8 or 4 consecutive
 // columns per lane (the ceil(W / C) lanes at each end carry the W-column
@@ -16,7 +16,7 @@
 //   * per column and channel n the running vertical window sum
 //     V_n = sum of u_n over the 2W + 1 rows of the window stays in registers,
 //     u_n = e^{-H^2/2} H^n being the power image F_n of Algorithm 2 (unscaled:
-//     |u_n| <= (n/e)^{n/2} <= 4.6 for n <= 5).  A row leaving the window is
+//     |u_n| <= (n/e)^{n/2} <= 75 for n <= 8).  A row leaving the window is
 //     regenerated from its ring entry by the same instructions that produced
 //     it on entry, so what is subtracted is bitwise what was added;
 //   * horizontal window sums S_n take the W halo columns from the lanes one
@@ -45,7 +45,7 @@ struct WarpStripArgs {
   float hs, hs0;    // H = f hs + hs0 = (f - t_c) / sigma_r
   float qscale;     // w(0) = 1 / (2W + 1)^2: normalised Q'
   float sentinel;   // intensity with u_n = 0 exactly (t_c + 1e4 sigma_r)
-  float inv_n[8];   // 1 / n (entry 0 unused)
+  float inv_n[12];  // 1 / n (entry 0 unused)
   int band;         // output rows per warp (even)
   int nstrips, nbands;
   int vec_in;       // input rows 16-byte aligned: 16-byte copies
@@ -328,7 +328,7 @@ __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip
   using G = WarpStripGeom<R, DP, C>;
   constexpr int SW = G::SW, RS = G::RS;
   static_assert(R >= 1 && R <= 8 && G::HL <= 2, "the halo comes from at most two lanes");
-  static_assert(NN >= 2 && NN <= 6, "order range of the warp-strip kernel");
+  static_assert(NN >= 2 && NN <= 9, "order range of the warp-strip kernel");
   const TileIO &io = A.io;
   const int lane = threadIdx.x & 31;
   const int x0 = strip * G::TW - G::HL * C + C * lane;  // first region column of this lane

@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
 // columns, output rows per tile).  Variant 5: the compile-time-radius kernel
 // for the radii in kFixedRadii (forward without stored planes only).
-// Variants 6 and 7: the warp-strip streaming box kernel (box, W in {3, 5},
-// N <= 5) with 8 and 4 columns per lane.
+// Variants 6 and 7: the warp-strip streaming box kernel (box, W in {3, 5})
+// with 8 columns per lane (N <= 5) and 4 columns per lane (N <= 8; fewer
+// registers per channel).
 struct Variant {
   int NT, TH;
 };
@@ -63,8 +64,8 @@ constexpr int kStream4Variant = kNumGeneric + 2;
 constexpr int kNumVariants = kNumGeneric + 3;
 
 bool fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
-bool stream_fits(const bfi::FilterConsts &fc) {
-  return fc.kind == BF_SPATIAL_BOX && (fc.R == 3 || fc.R == 5) && fc.N >= 1 && fc.N <= 5;
+bool stream_fits(const bfi::FilterConsts &fc, int max_n) {
+  return fc.kind == BF_SPATIAL_BOX && (fc.R == 3 || fc.R == 5) && fc.N >= 1 && fc.N <= max_n;
 }
 
 int max_smem_optin() {
@@ -82,7 +83,8 @@ int max_smem_optin() {
 
 bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
   if (v == kFixedVariant) return !store && fixed_radius(fc.R);
-  if (v == kStreamVariant || v == kStream4Variant) return !store && stream_fits(fc);
+  if (v == kStreamVariant) return !store && stream_fits(fc, 5);
+  if (v == kStream4Variant) return !store && stream_fits(fc, 8);
   const Variant &var = kVariants[v];
   const int TW = var.NT - 2 * fc.R;
   if (TW < var.TH) return false;
@@ -92,9 +94,10 @@ bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
 // Measured at 2048^2, 4096^2 and 8192^2: 4 columns per lane is faster for
 // W = 3 at every N <= 5 and for W = 5 at N <= 3; at W = 5, N in {4, 5} the
 // extra halo shuffles and halo lanes of 4 columns per lane cost more than
-// the added resident warps gain.
+// the added resident warps gain.  N in 6..8 runs with 4 columns per lane only.
 int default_variant(const bfi::FilterConsts &fc, bool store) {
-  if (!store && stream_fits(fc)) return fc.R == 3 || fc.N <= 3 ? kStream4Variant : kStreamVariant;
+  if (!store && stream_fits(fc, 5)) return fc.R == 3 || fc.N <= 3 ? kStream4Variant : kStreamVariant;
+  if (!store && stream_fits(fc, 8)) return kStream4Variant;
   static const int order[] = {kFixedVariant, 0, 2, 4, 3, 1};
   for (int v : order)
     if (variant_fits(v, fc, store)) return v;
@@ -149,7 +152,7 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   A.hs0 = (float)(-tc / sr);
   A.qscale = a.fc.qscale;
   A.sentinel = (float)(tc + 1e4 * sr);
-  for (int n = 0; n < 8; ++n) A.inv_n[n] = n > 0 ? (float)(1.0 / n) : 0.f;
+  for (int n = 0; n < 12; ++n) A.inv_n[n] = n > 0 ? (float)(1.0 / n) : 0.f;
   const bool in_al = (reinterpret_cast<uintptr_t>(a.io.in) & 15u) == 0;
   const bool out_al = (reinterpret_cast<uintptr_t>(a.io.out) & 15u) == 0;
   const bool q_al = !a.io.qaux || (reinterpret_cast<uintptr_t>(a.io.qaux) & 15u) == 0;
@@ -177,8 +180,17 @@ bf_status launch_warp_r(const FwdArgs &a, cudaStream_t s) {
     case 4: return launch_warp_rn<R, 4, C>(a, s);
     case 5: return launch_warp_rn<R, 5, C>(a, s);
     case 6: return launch_warp_rn<R, 6, C>(a, s);
-    default: return BF_ERR_UNSUPPORTED;
+    default: break;
   }
+  if constexpr (C == 4) {
+    switch (a.fc.N + 1) {
+      case 7: return launch_warp_rn<R, 7, C>(a, s);
+      case 8: return launch_warp_rn<R, 8, C>(a, s);
+      case 9: return launch_warp_rn<R, 9, C>(a, s);
+      default: break;
+    }
+  }
+  return BF_ERR_UNSUPPORTED;
 }
 
 template <int C>

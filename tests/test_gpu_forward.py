@@ -68,14 +68,18 @@ def test_every_tile_variant(variant):
 @pytest.mark.parametrize("variant", [6, 7])
 @pytest.mark.parametrize("r", [3, 5])
 def test_streaming_box_kernel(r, variant):
-    """Variants 6 and 7 (warp-strip streaming box, N <= 5, 8 and 4 columns per
-    lane, halos from one or two lanes away): several strips and bands with
+    """Variants 6 and 7 (warp-strip streaming box, 8 columns per lane for
+    N <= 5, 4 columns per lane for N <= 8, halos from one or two lanes away):
+    several strips and bands with
     ragged tails, every supported N, aligned (vector copies and stores) and
     odd-pitch (scalar) rows, widths that end inside a 4-column chunk, and
     images smaller than one strip or band."""
     H, W = 150, 500
     img = image(H, W, seed=40 + r)
-    for sr, N in ((40.0, 1), (40.0, 2), (60.0, 3), (80.0, 5), (30.0, 4)):
+    orders = ((40.0, 1), (40.0, 2), (60.0, 3), (80.0, 5), (30.0, 4))
+    if variant == 7:
+        orders += ((50.0, 6), (35.0, 7), (70.0, 8))
+    for sr, N in orders:
         ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, sr, N)
         out, q = _run(img, bf.BOX, r, 0.0, sr, N, variant=variant)
         compare_forward(out, q, ro, rq, w0, "stream v%d r=%d N=%d" % (variant, r, N), sigma_r=sr, N=N)
@@ -90,7 +94,8 @@ def test_streaming_box_kernel(r, variant):
         out, q = _run(im, bf.BOX, r, 0.0, 70.0, 4, variant=variant)
         compare_forward(out, q, ro, rq, w0, "stream v%d shape %s" % (variant, shape), sigma_r=70.0, N=4)
     with pytest.raises(bf._lib.BFError):
-        bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6, radius=r, variant=variant)
+        bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6 if variant == 6 else 9,
+                       radius=r, variant=variant)
 
 
 @pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 12, 4.0), (bf.GAUSS, 20, 20 / 3.0),
