@@ -151,11 +151,12 @@ def fwd_ops_per_pixel(kind: int, R: int, N: int) -> float:
 
 
 def rec_ops_per_pixel(N: int) -> float:
-    """The recursive-Gaussian forward: per channel, rows 18 (zero-state finals
-    of both directions, advance a_n) + 27 (both recursions with their outputs,
-    advance a_n), columns 16 + 29 (with the recombination), the two tile scans
-    ~2; plus ~20 per pixel (centre, exp, ratio)."""
-    return (N + 1) * 92 + 20
+    """The recursive-Gaussian forward: per channel, rows carry 10 (the
+    zero-state tile finals of both directions as dot products, advance a_n),
+    rows apply 35 (both recursions with their outputs, the column tiles'
+    finals, advance a_n), columns apply 32 (both recursions, recombination,
+    advance a_n), the two tile scans ~2; plus ~20 per pixel."""
+    return (N + 1) * 79 + 20
 
 
 def rec_bytes_per_pixel(N: int) -> float:
