@@ -9,9 +9,10 @@
 // convolution of a line x[0..L) with h is
 //      y[i] = sum_j Re(A_j (s_j[i] + q_j[i])) - h(0) x[i],   A_j = 2 alpha_j,
 // since s_j + q_j counts the centre twice.  Each mode is a complex one-pole
-// recursion (four FP32 operations per step): unlike a fourth-order direct
-// form its rounding noise is amplified only by 1/|1 - r_j| (about 10 at
-// sigma_s = 20), so FP32 holds the 1e-3 parity bar at any sigma_s.
+// recursion (four FP32 operations per step, two more for its share of y):
+// unlike a fourth-order direct form its rounding noise is amplified only by
+// 1/|1 - r_j| (about 10 at sigma_s = 20), so FP32 holds the 1e-3 parity bar at
+// any sigma_s.
 //
 // Line parallelism.  A line is cut into tiles of 32 pixels, each handled by
 // two lanes of one warp (pixels 0-15 and 16-31).  Three steps per direction
@@ -448,7 +449,7 @@ struct ColRing {
 };
 
 __device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, int xb, int y0,
-                                          int ty, int nty, bool with_carry) {
+                                          int ty, bool with_carry) {
   const int lane = threadIdx.x & 31;
   const int slot = n % kColDepth;
   const float *src = a.planes + (size_t)n * a.Hp * a.P + (size_t)y0 * a.P + xb;
@@ -473,19 +474,19 @@ __device__ __forceinline__ void col_read(const ColRing &R, int n, bool first, fl
 // Before channel n: queue channel n + kColDepth - 1 (into the slot channel
 // n - 1 used; every lane finished reading it), then wait for channel n.
 __device__ __forceinline__ void col_advance(const RecArgs &a, ColRing &R, int n, int xb, int y0,
-                                            int ty, int nty, bool with_carry) {
+                                            int ty, bool with_carry) {
   __syncwarp();
-  if (n + kColDepth - 1 < a.nch) col_issue(a, R, n + kColDepth - 1, xb, y0, ty, nty, with_carry);
+  if (n + kColDepth - 1 < a.nch) col_issue(a, R, n + kColDepth - 1, xb, y0, ty, with_carry);
   cp_commit();
   cp_wait<kColDepth - 1>();
   __syncwarp();
 }
 
 __device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing &R, int xb, int y0, int ty,
-                                             int nty, bool with_carry) {
+                                             bool with_carry) {
 #pragma unroll
   for (int q = 0; q < kColDepth - 1; ++q) {
-    if (q < a.nch) col_issue(a, R, q, xb, y0, ty, nty, with_carry);
+    if (q < a.nch) col_issue(a, R, q, xb, y0, ty, with_carry);
     cp_commit();
   }
 }
@@ -500,13 +501,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
   int x, y0;
   bool first;
   if (!col_tile(a, w, x, y0, first)) return;
-  const PK K = packed(a.K);
-  const int nty = a.Hp / kTileLen, ty = y0 / kTileLen, xb = x & ~15;
+  const int ty = y0 / kTileLen, xb = x & ~15;
   const bool xin = x < a.W;
   const int cs = (threadIdx.x & 15) * 4;  // this column's states in the ring's carry slots
-  col_prologue(a, R, xb, y0, ty, nty, true);
+  col_prologue(a, R, xb, y0, ty, true);
   if constexpr (!GPA) {
-    col_advance(a, R, 0, xb, y0, ty, nty, true);
+    col_advance(a, R, 0, xb, y0, ty, true);
     float v[kHalf], yv[kHalf];
     col_read(R, 0, first, v);
     const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
       Qa[k] = 0.f;
     }
     for (int n = 0; n <= a.N; ++n) {
-      col_advance(a, R, n, xb, y0, ty, nty, true);
+      col_advance(a, R, n, xb, y0, ty, true);
       float v[kHalf], An[kHalf];
       col_read(R, n, first, v);
       const int slot = n % kColDepth;
