@@ -22,7 +22,9 @@ once along rows, as products with the Toeplitz matrices T[i, k] = h(|i - k|).
 The zero extension is the same reading of the finite image domain (Sec. I) as
 for the truncated kernels: only neighbours inside the image contribute.
 
-Algorithm 2 then runs step by step in FP64 with this operator as F * w.
+Algorithm 2 then runs step by step in FP64 with this operator as F * w;
+its gradient (image and sigma_r, N fixed) is taken by FP64 reverse-mode
+differentiation of those same steps.
 
 Readings (also listed in the design notes):
 * The spatial support is the whole image (the recursion has an infinite
@@ -39,7 +41,8 @@ import math
 import numpy as np
 
 __all__ = ["DERICHE4", "deriche_raw", "deriche_impulse", "toeplitz_line",
-           "recursive_filter", "gpa_alg2_recursive", "centre_weight_recursive"]
+           "recursive_filter", "gpa_alg2_recursive", "gpa_grad_recursive",
+           "centre_weight_recursive"]
 
 # Deriche's fourth-order fit of the Gaussian (two damped cosine/sine pairs).
 DERICHE4 = {"a0": 1.680, "a1": 3.735, "b0": 1.783, "w0": 0.6318,
@@ -129,3 +132,36 @@ def gpa_alg2_recursive(img, sigma_s: float, sigma_r: float, N: int, T: float = 1
     if return_parts:
         return out, sigma_r * P, Q
     return out
+
+
+def gpa_grad_recursive(img, sigma_s: float, sigma_r: float, N: int, gout, T: float = 128.0):
+    """(d loss / d image, d loss / d sigma_r) of gpa_alg2_recursive for
+    loss = sum(gout * out), N held fixed: reverse-mode differentiation in
+    FP64 (plain PyTorch CPU autograd) through the same Algorithm 2 steps with
+    the same Toeplitz-product filter."""
+    import torch
+    f = torch.tensor(np.asarray(img, dtype=np.float64), requires_grad=True)
+    sr = torch.tensor(float(sigma_r), dtype=torch.float64, requires_grad=True)
+    Hh, Ww = f.shape
+    TH = torch.from_numpy(toeplitz_line(sigma_s, Hh))
+    TW = torch.from_numpy(toeplitz_line(sigma_s, Ww))
+
+    def filt(F):
+        return TH @ F @ TW.T
+
+    h = f - T
+    F = torch.exp(-h * h / (2.0 * sr * sr))
+    Hs = h / sr
+    G = torch.ones_like(f)
+    P = torch.zeros_like(f)
+    Q = torch.zeros_like(f)
+    Fbar = filt(F)
+    for n in range(1, N + 1):
+        Q = Q + G * Fbar
+        F = Hs * F
+        Fbar = filt(F)
+        P = P + G * Fbar
+        G = Hs * G / n
+    out = sr * (P / Q) + T
+    (out * torch.from_numpy(np.asarray(gout, dtype=np.float64))).sum().backward()
+    return f.grad.numpy(), float(sr.grad)

@@ -142,3 +142,35 @@ def test_gpa_accuracy_against_direct_filter(s, sr):
         assert err <= delta
         errs.append(err)
     assert errs[0] > errs[1] > errs[2]
+
+
+@pytest.mark.parametrize("s,sr,N,Hh,Ww", [(1.5, 30.0, 6, 9, 13), (3.0, 45.0, 10, 12, 8)])
+def test_gradient_matches_bruteforce_chain_rule(s, sr, N, Hh, Ww):
+    """The autograd gradient of the recursive Algorithm 2 equals the C
+    checker's brute-force chain rule on eq. GPA (a different route: the
+    ratio's derivative per neighbour) with the explicit kernel h(j_y) h(j_x)."""
+    img = synth.blocks_image(Hh, Ww, 3, 25.0, seed=Hh * Ww).astype(np.float64)
+    g = np.random.default_rng(5).standard_normal((Hh, Ww))
+    gin, gs = rec.gpa_grad_recursive(img, s, sr, N, g)
+    rgin, rgs = oracle.gpa_grad(img, _explicit_kernel(s, Hh, Ww), sr, N, g)
+    assert np.abs(gin - rgin).max() <= 1e-9 * max(np.abs(rgin).max(), 1.0)
+    assert gs == pytest.approx(rgs, rel=1e-9, abs=1e-12)
+
+
+def test_gradient_matches_finite_differences():
+    """Central differences of gpa_alg2_recursive along a random direction and
+    in sigma_r (step 1e-3 / 1e-4, FP64)."""
+    s, sr, N = 2.0, 35.0, 12
+    img = synth.blocks_image(14, 19, 4, 20.0, seed=21).astype(np.float64)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal(img.shape)
+    d = rng.standard_normal(img.shape)
+    gin, gs = rec.gpa_grad_recursive(img, s, sr, N, g)
+    e = 1e-3
+    fd = (np.sum(g * rec.gpa_alg2_recursive(img + e * d, s, sr, N))
+          - np.sum(g * rec.gpa_alg2_recursive(img - e * d, s, sr, N))) / (2 * e)
+    assert np.sum(gin * d) == pytest.approx(fd, rel=1e-6)
+    e = 1e-4
+    fds = (np.sum(g * rec.gpa_alg2_recursive(img, s, sr + e, N))
+           - np.sum(g * rec.gpa_alg2_recursive(img, s, sr - e, N))) / (2 * e)
+    assert gs == pytest.approx(fds, rel=1e-6)
