@@ -439,6 +439,34 @@ def run_sweeps(args):
                                     "max_abs_fir_vs_direct": float((o2 - d).abs().max())})
                         del d
                 emit(row)
+            # forward + backward (image and sigma_r gradients) at sigma_s = 20
+            ss = 20.0
+            N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, ss, 40.0, 0.5)
+            q = torch.empty_like(x)
+            g = torch.from_numpy(synth.random_like((size, size), seed=2002)).to(dev)
+            ws = torch.empty(bf.recursive_workspace_bytes(size, size, N) // 4, device=dev)
+            o, q = bf.recursive_forward(x, 40.0, N, ss, return_q=True, ws=ws)
+            del ws
+            bms = _time_ms(lambda: bf.recursive_backward(x, o, q, g, 40.0, N, ss), 3, stream, flush)
+            fms = _time_ms(lambda: bf.recursive_forward(x, 40.0, N, ss, out=o2), 3, stream, flush)
+            row = {"sweep": "recursive", "size": size, "sigma_s": ss, "sigma_r": 40.0, "N": N,
+                   "rec_fwd_ms": fms, "rec_bwd_ms": bms,
+                   "rec_fwd_bwd_mpx_s": px / (fms + bms) / 1e3}
+            if size == 2048:
+                R = 60
+                Nf = bf.order_from_delta(bf.GAUSS, R, ss, 40.0, 0.5)
+                of, qf = bf.gpa_forward(x, bf.GAUSS, 40.0, Nf, radius=R, sigma_s=ss, return_q=True)
+                ffms = _time_ms(lambda: bf.gpa_forward(x, bf.GAUSS, 40.0, Nf, radius=R, sigma_s=ss,
+                                                       out=o2), 3, stream, flush)
+                fbms = _time_ms(lambda: bf.gpa_backward(x, of, qf, g, bf.GAUSS, 40.0, Nf, radius=R,
+                                                        sigma_s=ss), 3, stream, flush)
+                row.update({"fir_fwd_ms": ffms, "fir_bwd_ms": fbms,
+                            "fir_fwd_bwd_mpx_s": px / (ffms + fbms) / 1e3,
+                            "speedup_vs_fir_fwd_bwd": (ffms + fbms) / (fms + bms)})
+                del of, qf
+            emit(row)
+            del g, q
+            torch.cuda.empty_cache()
             # the spatial operator alone, and its kernel against the sampled Gaussian
             ws = torch.empty(bf.recursive_workspace_bytes(size, size, 0) // 4, device=dev)
             for ss in (3.0, 40.0):

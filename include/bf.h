@@ -384,9 +384,26 @@ bf_status bf_tuning_set(int kind, int radius_bucket, int order_bucket, int varia
  *   p->sigma_s >= 0.5, p->radius is ignored; otherwise as bf_fast_forward
  *   (the same sigma_r limit).  Choose N with bf_order_from_delta (kind 2:
  *   w(0) = h(0)^2).
+ * bf_recursive_backward_workspace / bf_recursive_backward: the exact adjoint
+ *   of bf_recursive_forward (the paper has none; the same derivation as
+ *   bf_fast_backward): with qbar = -g (out - t_c) / Q', pbar = g sigma_r / Q',
+ *   the seeds c_n = qbar a_n [n<N] + pbar sqrt(n) a_{n-1} [n>=1] and the power
+ *   images a_n are both filtered (the zero-extended recursive filter is
+ *   self-adjoint), Hbar = sum_n abar_n (sqrt(n) a_{n-1} - H a_n), d in =
+ *   Hbar / sigma_r, d sigma_r = sum_i (g (out - t_c) - Hbar H) / sigma_r (N
+ *   held fixed).  d_out and d_qaux are the forward's out and Q' (order N,
+ *   same image and parameters); d_gout the cotangent of out; d_gin receives
+ *   d loss / d in; d_gsigma_r (device double, may be NULL) receives the sigma_r
+ *   gradient, summed in a fixed order (deterministic).  Workspace:
+ *   2.75 (N + 1) 4 Hp P bytes plus 8 bytes per 16 x 32 column tile.
  * Workspace: 256-byte aligned, at least the queried size, else
  * BF_ERR_WORKSPACE / BF_ERR_INVALID_ARG.  Asynchronous on `stream`. */
 bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *bytes);
+bf_status bf_recursive_backward_workspace(int height, int width, int order_N, size_t *bytes);
+bf_status bf_recursive_backward(const float *d_in, const float *d_out, const float *d_qaux,
+                                const float *d_gout, float *d_gin, double *d_gsigma_r, int height,
+                                int width, int pitch, const bf_params *p, void *d_ws,
+                                size_t ws_bytes, void *stream);
 bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int width, int pitch,
                              float sigma_s, void *d_ws, size_t ws_bytes, void *stream);
 bf_status bf_recursive_forward(const float *d_in, float *d_out, float *d_qaux, int height,

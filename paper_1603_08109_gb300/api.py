@@ -22,6 +22,7 @@ __all__ = [
     "variant_count", "forward_workspace_bytes", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
+    "recursive_backward", "RecursiveBilateral", "recursive_bilateral",
 ]
 
 
@@ -216,6 +217,37 @@ def recursive_forward(img: torch.Tensor, sigma_r: float, N: int, sigma_s: float,
         o = o.cpu()
         q = q.cpu() if q is not None else None
     return (o, q) if return_q else o
+
+
+def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float,
+                       t_c: float = 128.0, need_sigma: bool = True,
+                       ws: Optional[torch.Tensor] = None):
+    """(dL/d img, dL/d sigma_r or None) of recursive_forward, given gout."""
+    x, _ = _as_device_image(img)
+    tensors = []
+    for t in (out, q, gout):
+        if t.shape != x.shape or t.device != x.device or t.dtype != torch.float32:
+            raise ValueError("out, q, gout must match the image")
+        tensors.append(t)
+    if any(t.stride() != x.stride() for t in tensors):
+        x = x.contiguous()
+        tensors = [t.contiguous() for t in tensors]
+    o, qq, g = tensors
+    H, W = x.shape
+    gin = _like(x)
+    gs = torch.zeros(1, dtype=torch.float64, device=x.device) if need_sigma else None
+    n = ctypes.c_size_t(0)
+    check(lib().bf_recursive_backward_workspace(H, W, int(N), ctypes.byref(n)),
+          "bf_recursive_backward_workspace")
+    nbytes = int(n.value)
+    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != x.device:
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+    p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_recursive_backward(_ptr(x), _ptr(o), _ptr(qq), _ptr(g), _ptr(gin), _ptr(gs), H, W,
+                                      x.stride(0), ctypes.byref(p), _ptr(ws),
+                                      ws.numel() * ws.element_size(), _stream(x.device)),
+          "bf_recursive_backward")
+    return gin, gs
 
 
 def gpa_forward_stored(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
@@ -418,6 +450,38 @@ class DirectBilateral(torch.autograd.Function):
         gin, gs = direct_backward(img, gout.contiguous(), kind, sr, radius, sigma_s, t_c, need_s)
         gsig = gs.reshape(()).to(torch.float32) if need_s else None
         return gin, gsig, None, None, None, None
+
+
+class RecursiveBilateral(torch.autograd.Function):
+    """Autograd wrapper of the recursive-Gaussian route: forward =
+    bf_recursive_forward, backward = bf_recursive_backward."""
+
+    @staticmethod
+    def forward(ctx, img, sigma_r, N, sigma_s, t_c):
+        sr = _sigma_value(sigma_r)
+        out, q = recursive_forward(img, sr, N, sigma_s, t_c, return_q=True)
+        ctx.cfg = (sr, N, sigma_s, t_c)
+        ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
+        ctx.save_for_backward(img, out, q)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        img, out, q = ctx.saved_tensors
+        sr, N, sigma_s, t_c = ctx.cfg
+        need_s = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
+        gin, gs = recursive_backward(img, out, q, gout.contiguous(), sr, N, sigma_s, t_c,
+                                     need_sigma=need_s)
+        gsig = gs.reshape(()).to(torch.float32) if need_s else None
+        return gin, gsig, None, None, None
+
+
+def recursive_bilateral(img, sigma_r, sigma_s, N=None, t_c=128.0, delta=1.0):
+    """Differentiable fast bilateral filter with the recursive Gaussian;
+    N from delta (w(0) = h(0)^2) when not given."""
+    if N is None:
+        N = order_from_delta(GAUSS_RECURSIVE, 0, sigma_s, _sigma_value(sigma_r), delta, t_c)
+    return RecursiveBilateral.apply(img, sigma_r, int(N), float(sigma_s), float(t_c))
 
 
 def gpa_bilateral(img, sigma_r, kind=GAUSS, N=None, radius=0, sigma_s=0.0, t_c=128.0,

@@ -69,6 +69,13 @@ struct RecArgs {
   const float *in;  // image (pitch elements per row)
   float *out;       // result (pitch)
   float *qaux;      // Q' (pitch) or null
+  // backward: the forward's out and Q', the output cotangent; d in; per-CTA
+  // sigma_r partials; the second channel family's planes and column tiles
+  const float *f_out, *f_q, *gout;
+  float *gin;
+  double *partials;
+  float *planes2;
+  float4 *carry_c2;
   float *planes;    // (nch) planes of Hp x P floats
   float4 *carry_r;  // row tiles: 2 sides x nch x (P / 32) x Hp states (float4 each)
   float4 *carry_c;  // column tiles: 2 sides x nch x (Hp / 32) x P states
@@ -234,12 +241,64 @@ __device__ __forceinline__ CarryMap col_carries(const RecArgs &a) {
 // plane.  A pitch of 36 keeps rows 16-byte aligned, and the 16-byte stores of
 // 8 lanes to 8 different rows fall in 8 different bank quads.
 constexpr int kRowPitch = 36;
+__device__ __forceinline__ void a0_from_H(const RecArgs &a, const float (&Hv)[kHalf], float (&x)[kHalf]) {
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) x[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
+}
+
+// What the row pass filters, channel by channel:
+//   kFilter: the image itself (one channel);
+//   kPower : a_n = e^{-H^2/2} H^n / sqrt(n!), n = 0..N (Algorithm 2's F_n,
+//            rescaled), by a_n = a_{n-1} H / sqrt(n);
+//   kSeed  : the adjoint seeds c_n = qbar a_n [n < N] + pbar sqrt(n) a_{n-1}
+//            [n >= 1] of the backward (qbar = -g (out - t_c) / Q',
+//            pbar = g sigma_r / Q' at the pixel).
+enum { kFilter = 0, kPower = 1, kSeed = 2 };
+
+template <int MODE>
+struct RowSource {
+  float H[kHalf], a[kHalf], qb[kHalf], pb[kHalf];
+  // channel 0's values into x
+  __device__ __forceinline__ void first_channel(const RecArgs &A, float (&x)[kHalf]) {
+    if constexpr (MODE == kFilter) {
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) x[k] = H[k];
+    } else {
+      a0_from_H(A, H, a);
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) x[k] = MODE == kPower ? a[k] : qb[k] * a[k];
+    }
+  }
+  // channel n >= 1's values into x
+  __device__ __forceinline__ void next_channel(const RecArgs &A, int n, float (&x)[kHalf]) {
+    const float sq = sqrtf((float)n), is = 1.0f / sq;
+    const bool q_on = n < A.N;
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      const float prev = a[k];
+      a[k] = prev * (H[k] * is);
+      if constexpr (MODE == kPower) x[k] = a[k];
+      else x[k] = fmaf(pb[k] * sq, prev, q_on ? qb[k] * a[k] : 0.f);
+    }
+  }
+};
+
 // Warp w: rows 16 ry .. 16 ry + 15, tile tx (columns 32 tx .. 32 tx + 31).
-// Loads the tile's centred intensities H (sentinel outside the image) into
-// the lane's registers: first lane of a pair pixels 0..15 of row 16ry + l,
-// second lane pixels 31..16 of row 16ry + l - 16.
-template <bool GPA>
-__device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, float (&Hv)[kHalf],
+// Loads the tile's centred intensities H (sentinel outside the image; the
+// image values themselves for kFilter) into the lane's registers: first lane
+// of a pair pixels 0..15 of row 16ry + l, second lane pixels 31..16 of row
+// 16ry + l - 16.  kSeed also loads qbar and pbar (0 outside the image).
+template <int MODE>
+__device__ __forceinline__ void tile_to_lanes(float *sm, bool first, float (&v)[kHalf]) {
+  __syncwarp();
+  const int r = threadIdx.x & 15;
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) v[k] = sm[r * kRowPitch + (first ? k : kTileLen - 1 - k)];
+  __syncwarp();
+}
+
+template <int MODE>
+__device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, RowSource<MODE> &src,
                                          int &y, int &x0, bool &first) {
   const int ntx = a.P / kTileLen;
   const int tx = w % ntx, ry = w / ntx;
@@ -247,53 +306,52 @@ __device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, flo
   const int lane = threadIdx.x & 31;
   x0 = tx * kTileLen;
   const int y0 = ry * 16;
+  first = lane < 16;
+  y = y0 + (lane & 15);
+  const int xx = x0 + lane;
   for (int r = 0; r < 16; ++r) {
-    const int yy = y0 + r, xx = x0 + lane;
-    float v = kSentinelH;
+    const int yy = y0 + r;
+    float v = MODE == kFilter ? 0.f : kSentinelH;
     if (yy < a.H && xx < a.W) {
       const float f = __ldg(a.in + (size_t)yy * a.pitch + xx);
-      v = GPA ? (f - a.tc) * a.inv_sr : f;
-    } else if (!GPA) {
-      v = 0.f;
+      v = MODE == kFilter ? f : (f - a.tc) * a.inv_sr;
     }
     sm[r * kRowPitch + lane] = v;
   }
-  __syncwarp();
-  first = lane < 16;
-  const int r = lane & 15;
-  y = y0 + r;
-#pragma unroll
-  for (int k = 0; k < kHalf; ++k) Hv[k] = sm[r * kRowPitch + (first ? k : kTileLen - 1 - k)];
+  tile_to_lanes<MODE>(sm, first, src.H);
+  if constexpr (MODE == kSeed) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int r = 0; r < 16; ++r) {
+        const int yy = y0 + r;
+        float v = 0.f;
+        if (yy < a.H && xx < a.W) {
+          const size_t i = (size_t)yy * a.pitch + xx;
+          const float g = __ldg(a.gout + i), q = __ldg(a.f_q + i);
+          v = pass == 0 ? -g * (__ldg(a.f_out + i) - a.tc) / q : g * a.sr / q;
+        }
+        sm[r * kRowPitch + lane] = v;
+      }
+      tile_to_lanes<MODE>(sm, first, pass == 0 ? src.qb : src.pb);
+    }
+  }
   return true;
 }
 
-__device__ __forceinline__ void a0_from_H(const RecArgs &a, const float (&Hv)[kHalf], float (&x)[kHalf]) {
-#pragma unroll
-  for (int k = 0; k < kHalf; ++k) x[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
-}
-
-template <bool GPA>
+template <int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __grid_constant__ RecArgs a) {
   __shared__ __align__(16) float smem[kWarpsPerBlock][16 * kRowPitch];
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  float Hv[kHalf];
+  RowSource<MODE> src;
   int y, x0;
   bool first;
-  if (!row_tile<GPA>(a, w, smem[threadIdx.x >> 5], Hv, y, x0, first)) return;
+  if (!row_tile<MODE>(a, w, smem[threadIdx.x >> 5], src, y, x0, first)) return;
   const PK K = packed(a.K);
   const CarryMap cm = row_carries(a);
   const int tx = x0 / kTileLen;
   float x[kHalf];
-  if (GPA) a0_from_H(a, Hv, x);
-  else
-#pragma unroll
-    for (int k = 0; k < kHalf; ++k) x[k] = Hv[k];
+  src.first_channel(a, x);
   for (int n = 0; n < a.nch; ++n) {
-    if (GPA && n > 0) {
-      const float is = 1.0f / sqrtf((float)n);
-#pragma unroll
-      for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
-    }
+    if (n > 0) src.next_channel(a, n, x);
     Pair fw, bw;
     zero_state_finals(a.K, x, fw, bw);
     write_carry(K, fw, bw, first, cm.at(n, tx, y), cm.side());
@@ -308,23 +366,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) rec_rows_carry(const __gr
 // column pass needs no separate carry sweep over the planes.
 constexpr int kRowApplyWarps = 2;
 
-template <bool GPA>
+template <int MODE>
 __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __grid_constant__ RecArgs a) {
   __shared__ __align__(16) float smem[kRowApplyWarps * 16 * kRowPitch];
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntx = a.P / kTileLen;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;  // grid = ntx * (Hp / 32) exactly
   float *sm = smem + wi * 16 * kRowPitch;
-  float Hv[kHalf];
+  RowSource<MODE> src;
   int y, x0;
   bool first;
-  row_tile<GPA>(a, (2 * ty + wi) * ntx + tx, sm, Hv, y, x0, first);
+  row_tile<MODE>(a, (2 * ty + wi) * ntx + tx, sm, src, y, x0, first);
   const PK K = packed(a.K);
   float x[kHalf];
-  if (GPA) a0_from_H(a, Hv, x);
-  else
-#pragma unroll
-    for (int k = 0; k < kHalf; ++k) x[k] = Hv[k];
+  src.first_channel(a, x);
   const size_t plane = (size_t)a.Hp * a.P;
   // incoming states of channels n and n + 1 in registers; channel n + 2's
   // are loaded while channel n computes
@@ -337,11 +392,7 @@ __global__ void __launch_bounds__(32 * kRowApplyWarps) rec_rows_apply(const __gr
   // this lane's column of the block for the column finals
   const int cc = 16 * wi + (lane & 15);
   for (int n = 0; n < a.nch; ++n) {
-    if (GPA && n > 0) {
-      const float is = 1.0f / sqrtf((float)n);
-#pragma unroll
-      for (int k = 0; k < kHalf; ++k) x[k] *= Hv[k] * is;
-    }
+    if (n > 0) src.next_channel(a, n, x);
     const float4 *cn = cbase + min(n + 2, last) * cstride;
     const float4 n0 = cn[0], n1 = cn[cside];
     float yv[kHalf];
@@ -439,54 +490,64 @@ __device__ __forceinline__ int col_row(int y0, bool first, int k) {
   return y0 + (first ? k : kTileLen - 1 - k);
 }
 
-// Per-warp ring of kColDepth channels in shared memory: the 32 x 16 plane
-// tile of a channel and (apply pass) the 16 columns' incoming states, copied
-// with cp.async kColDepth - 1 channels ahead of use.
+// Per-warp ring of kColDepth channels in shared memory: per channel family
+// (one for the forward, the power images and the adjoint seeds for the
+// backward) the 32 x 16 plane tile and the 16 columns' incoming states,
+// copied with cp.async kColDepth - 1 channels ahead of use.
 constexpr int kColDepth = 3;
+template <int F>
 struct ColRing {
-  float tile[kColDepth][kTileLen * 16];  // row-major, 16 floats per row
-  float carry[kColDepth][2 * 16 * 4];  // 16 causal states, then 16 anticausal
+  float tile[kColDepth][F][kTileLen * 16];  // row-major, 16 floats per row
+  float carry[kColDepth][F][2 * 16 * 4];    // 16 causal states, then 16 anticausal
 };
 
-__device__ __forceinline__ void col_issue(const RecArgs &a, ColRing &R, int n, int xb, int y0,
-                                          int ty, bool with_carry) {
+template <int F>
+__device__ __forceinline__ void col_issue(const RecArgs &a, ColRing<F> &R, int n, int xb, int y0,
+                                          int ty) {
   const int lane = threadIdx.x & 31;
   const int slot = n % kColDepth;
-  const float *src = a.planes + (size_t)n * a.Hp * a.P + (size_t)y0 * a.P + xb;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {  // 128 chunks of 16 bytes
-    const int c = lane + 32 * j, row = c >> 2, col = (c & 3) * 4;
-    cp_async16(&R.tile[slot][row * 16 + col], src + (size_t)row * a.P + col);
-  }
-  if (with_carry) {
-    const CarryMap cm = col_carries(a);
-    cp_async16(&R.carry[slot][lane * 4], cm.at(n, ty, xb + (lane & 15)) + (lane < 16 ? 0 : cm.side()));
+  for (int f = 0; f < F; ++f) {
+    const float *src = (f == 0 ? a.planes : a.planes2) + (size_t)n * a.Hp * a.P + (size_t)y0 * a.P + xb;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // 128 chunks of 16 bytes
+      const int c = lane + 32 * j, row = c >> 2, col = (c & 3) * 4;
+      cp_async16(&R.tile[slot][f][row * 16 + col], src + (size_t)row * a.P + col);
+    }
+    CarryMap cm = col_carries(a);
+    if (f == 1) cm.p = a.carry_c2;
+    cp_async16(&R.carry[slot][f][lane * 4], cm.at(n, ty, xb + (lane & 15)) + (lane < 16 ? 0 : cm.side()));
   }
 }
 
-// The lane's 16 inputs of channel n from the ring (call after col_wait).
-__device__ __forceinline__ void col_read(const ColRing &R, int n, bool first, float (&v)[kHalf]) {
+// The lane's 16 inputs of channel n, family f, from the ring (after col_advance).
+template <int F>
+__device__ __forceinline__ void col_read(const ColRing<F> &R, int n, int f, bool first,
+                                         float (&v)[kHalf], float4 &c0, float4 &c1) {
   const int c = threadIdx.x & 15, slot = n % kColDepth;
 #pragma unroll
-  for (int k = 0; k < kHalf; ++k) v[k] = R.tile[slot][(first ? k : kTileLen - 1 - k) * 16 + c];
+  for (int k = 0; k < kHalf; ++k) v[k] = R.tile[slot][f][(first ? k : kTileLen - 1 - k) * 16 + c];
+  c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][f][c * 4]);
+  c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][f][64 + c * 4]);
 }
 
 // Before channel n: queue channel n + kColDepth - 1 (into the slot channel
 // n - 1 used; every lane finished reading it), then wait for channel n.
-__device__ __forceinline__ void col_advance(const RecArgs &a, ColRing &R, int n, int xb, int y0,
-                                            int ty, bool with_carry) {
+template <int F>
+__device__ __forceinline__ void col_advance(const RecArgs &a, ColRing<F> &R, int n, int xb, int y0,
+                                            int ty) {
   __syncwarp();
-  if (n + kColDepth - 1 < a.nch) col_issue(a, R, n + kColDepth - 1, xb, y0, ty, with_carry);
+  if (n + kColDepth - 1 < a.nch) col_issue<F>(a, R, n + kColDepth - 1, xb, y0, ty);
   cp_commit();
   cp_wait<kColDepth - 1>();
   __syncwarp();
 }
 
-__device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing &R, int xb, int y0, int ty,
-                                             bool with_carry) {
+template <int F>
+__device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing<F> &R, int xb, int y0, int ty) {
 #pragma unroll
   for (int q = 0; q < kColDepth - 1; ++q) {
-    if (q < a.nch) col_issue(a, R, q, xb, y0, ty, with_carry);
+    if (q < a.nch) col_issue<F>(a, R, q, xb, y0, ty);
     cp_commit();
   }
 }
@@ -495,22 +556,20 @@ __device__ __forceinline__ void col_prologue(const RecArgs &a, ColRing &R, int x
 // A_n = w * a_n, accumulated into P' and Q' over the channel loop.
 template <bool GPA>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const __grid_constant__ RecArgs a) {
-  __shared__ ColRing ring[kWarpsPerBlock];
-  ColRing &R = ring[threadIdx.x >> 5];
+  __shared__ ColRing<1> ring[kWarpsPerBlock];
+  ColRing<1> &R = ring[threadIdx.x >> 5];
   const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   int x, y0;
   bool first;
   if (!col_tile(a, w, x, y0, first)) return;
   const int ty = y0 / kTileLen, xb = x & ~15;
   const bool xin = x < a.W;
-  const int cs = (threadIdx.x & 15) * 4;  // this column's states in the ring's carry slots
-  col_prologue(a, R, xb, y0, ty, true);
+  col_prologue<1>(a, R, xb, y0, ty);
   if constexpr (!GPA) {
-    col_advance(a, R, 0, xb, y0, ty, true);
+    col_advance<1>(a, R, 0, xb, y0, ty);
     float v[kHalf], yv[kHalf];
-    col_read(R, 0, first, v);
-    const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[0][cs]);
-    const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[0][64 + cs]);
+    float4 c0, c1;
+    col_read<1>(R, 0, 0, first, v, c0, c1);
     apply_tile(a.K, v, c0, c1, first, yv);
 #pragma unroll
     for (int k = 0; k < kHalf; ++k) {
@@ -530,12 +589,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
       Qa[k] = 0.f;
     }
     for (int n = 0; n <= a.N; ++n) {
-      col_advance(a, R, n, xb, y0, ty, true);
+      col_advance<1>(a, R, n, xb, y0, ty);
       float v[kHalf], An[kHalf];
-      col_read(R, n, first, v);
-      const int slot = n % kColDepth;
-      const float4 c0 = *reinterpret_cast<const float4 *>(&R.carry[slot][cs]);
-      const float4 c1 = *reinterpret_cast<const float4 *>(&R.carry[slot][64 + cs]);
+      float4 c0, c1;
+      col_read<1>(R, n, 0, first, v, c0, c1);
       apply_tile(a.K, v, c0, c1, first, An);
       if (n > 0) {  // P' += sqrt(n) a_{n-1} A_n, then a_n = a_{n-1} H / sqrt(n)
         const float sq = sqrtf((float)n), is = 1.0f / sq;
@@ -560,6 +617,104 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) rec_cols_apply(const _
     }
   }
   cp_wait<0>();
+}
+
+// Column pass of the backward.  With A_n = w * a_n and C_n = w * c_n (the
+// zero-extended recursive filter is self-adjoint: h is symmetric) and
+// D_n = d a_n / d H = sqrt(n) a_{n-1} - H a_n, the adjoint gather
+//   Hbar = sum_n abar_n D_n,  abar_n = qbar A_n [n<N] + pbar sqrt(n+1) A_{n+1} [n<N] + C_n
+// is re-associated into three running sums over the channel loop,
+//   X = sum_{n<N} A_n D_n,  Y = sum_n C_n D_n,  Z = sum_{m>=1} sqrt(m) A_m D_{m-1},
+// Hbar = qbar X + Y + pbar Z; then d in = Hbar / sigma_r and the sigma_r
+// gradient's per-pixel terms g (out - t_c) / sigma_r - Hbar H / sigma_r, summed
+// per warp in double into one partial per warp (reduced in a fixed order).
+constexpr int kGradWarps = 2;
+
+__global__ void __launch_bounds__(32 * kGradWarps, 4) rec_cols_grad(const __grid_constant__ RecArgs a) {
+  __shared__ ColRing<2> ring[kGradWarps];
+  ColRing<2> &R = ring[threadIdx.x >> 5];
+  const int w = blockIdx.x * kGradWarps + (threadIdx.x >> 5);
+  int x, y0;
+  bool first;
+  if (!col_tile(a, w, x, y0, first)) {  // past the last tile: an empty partial
+    if (a.partials && (threadIdx.x & 31) == 0) a.partials[w] = 0.0;
+    return;
+  }
+  const int ty = y0 / kTileLen, xb = x & ~15;
+  const bool xin = x < a.W;
+  float Hv[kHalf], av[kHalf], Dp[kHalf], X[kHalf], Y[kHalf], Z[kHalf];
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) {
+    const int yy = col_row(y0, first, k);
+    Hv[k] = (xin && yy < a.H) ? (__ldg(a.in + (size_t)yy * a.pitch + x) - a.tc) * a.inv_sr
+                              : kSentinelH;
+    av[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
+    Dp[k] = X[k] = Y[k] = Z[k] = 0.f;
+  }
+  col_prologue<2>(a, R, xb, y0, ty);
+  for (int n = 0; n <= a.N; ++n) {
+    col_advance<2>(a, R, n, xb, y0, ty);
+    const float sq = sqrtf((float)n), is = n > 0 ? 1.0f / sq : 0.f;
+    float D[kHalf];
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {  // a_n and D_n = sqrt(n) a_{n-1} - H a_n
+      if (n == 0) {
+        D[k] = -Hv[k] * av[k];
+      } else {
+        const float prev = av[k];
+        av[k] = prev * (Hv[k] * is);
+        D[k] = fmaf(sq, prev, -Hv[k] * av[k]);
+      }
+    }
+    float v[kHalf], t[kHalf];
+    float4 c0, c1;
+    col_read<2>(R, n, 0, first, v, c0, c1);
+    apply_tile(a.K, v, c0, c1, first, t);  // A_n
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      if (n < a.N) X[k] = fmaf(t[k], D[k], X[k]);
+      if (n > 0) Z[k] = fmaf(sq * t[k], Dp[k], Z[k]);
+    }
+    col_read<2>(R, n, 1, first, v, c0, c1);
+    apply_tile(a.K, v, c0, c1, first, t);  // C_n
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) {
+      Y[k] = fmaf(t[k], D[k], Y[k]);
+      Dp[k] = D[k];
+    }
+  }
+  cp_wait<0>();
+  double gs = 0.0;
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) {
+    const int yy = col_row(y0, first, k);
+    if (xin && yy < a.H) {
+      const size_t i = (size_t)yy * a.pitch + x;
+      const float g = __ldg(a.gout + i), o = __ldg(a.f_out + i) - a.tc, q = __ldg(a.f_q + i);
+      const float qbar = -g * o / q, pbar = g * a.sr / q;
+      const float hb = fmaf(qbar, X[k], fmaf(pbar, Z[k], Y[k]));
+      a.gin[i] = hb * a.inv_sr;
+      gs += (double)((g * o - hb * Hv[k]) * a.inv_sr);
+    }
+  }
+  if (a.partials) {
+    for (int o = 16; o > 0; o >>= 1) gs += __shfl_down_sync(0xffffffffu, gs, o);
+    if ((threadIdx.x & 31) == 0) a.partials[w] = gs;
+  }
+}
+
+// Sum of the per-warp sigma_r partials in a fixed order (one CTA).
+__global__ void __launch_bounds__(256) rec_reduce(const double *p, long long n, double *out) {
+  __shared__ double red[256];
+  double t = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) t += p[i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // ------------------------------------------------------------------ host
@@ -634,43 +789,59 @@ size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 struct Layout {
   int Hp, P;
-  size_t plane_floats, planes_bytes, carry_bytes, total;
+  size_t plane_floats, planes_bytes, carry_bytes, partial_bytes, total;
+  size_t off_planes2, off_carry_r, off_carry_c, off_carry_c2, off_partials;
 };
 
-Layout layout(int height, int width, int nch) {
+// Grid sizes: rows warps (Hp / 16) x (P / 32) in 4-warp CTAs; the row apply's
+// two-warp CTAs own one 32 x 32 block each; columns warps (P / 16) x (Hp / 32).
+long long row_ctas(const Layout &L) {
+  return ((long long)(L.Hp / 16) * (L.P / kTileLen) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+}
+long long block_ctas(const Layout &L) { return (long long)(L.Hp / kTileLen) * (L.P / kTileLen); }
+long long col_warps(const Layout &L) { return (long long)(L.P / 16) * (L.Hp / kTileLen); }
+
+// Forward: nch planes, the row tiles' and the column tiles' states.
+// Backward: two families (a_n and c_n) of nch planes and column-tile states,
+// one row-tile state array reused by the two row passes, one sigma_r partial
+// per column-pass warp.  One carry slot is 8 floats per 32 pixels of a line
+// per channel.
+Layout layout(int height, int width, int nch, bool backward) {
   Layout L;
   L.Hp = (int)round_up((size_t)height, kTileLen);
   L.P = (int)round_up((size_t)width, kTileLen);
   L.plane_floats = (size_t)L.Hp * L.P;
   L.planes_bytes = round_up(L.plane_floats * nch * sizeof(float), 256);
-  // one carry slot (8 floats) per 32 pixels of a line per channel, for the
-  // row tiles and for the column tiles (the row pass reads the first while it
-  // writes the second)
   L.carry_bytes = round_up(L.plane_floats / kTileLen * 8 * nch * sizeof(float), 256);
-  L.total = L.planes_bytes + 2 * L.carry_bytes;
+  const long long cw = col_warps(L);
+  L.partial_bytes = backward ? round_up((size_t)((cw + kGradWarps - 1) / kGradWarps * kGradWarps) *
+                                            sizeof(double), 256)
+                             : 0;
+  size_t o = L.planes_bytes;
+  L.off_planes2 = backward ? o : 0;
+  if (backward) o += L.planes_bytes;
+  L.off_carry_r = o;
+  o += L.carry_bytes;
+  L.off_carry_c = o;
+  o += L.carry_bytes;
+  L.off_carry_c2 = backward ? o : 0;
+  if (backward) o += L.carry_bytes;
+  L.off_partials = o;
+  L.total = o + L.partial_bytes;
   return L;
 }
 
 constexpr double kMinSigmaS = 0.5;
 
-bf_status run(const float *in, float *out, float *qaux, int height, int width, int pitch,
-              double sigma_s, bool gpa, int N, float tc, float sr, void *ws, size_t ws_bytes,
-              void *stream) {
-  bf_status st = bfi::check_image(in, out, height, width, pitch);
-  if (st != BF_OK) return st;
-  if (!(sigma_s >= kMinSigmaS) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
-  const int nch = gpa ? N + 1 : 1;
-  const Layout L = layout(height, width, nch);
-  if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
-  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
-  RecArgs a;
+RecArgs base_args(const float *in, int height, int width, int pitch, double sigma_s, int nch, int N,
+                  float tc, float sr, const Layout &L, void *ws) {
+  RecArgs a = {};
   a.K = make_consts(sigma_s);
   a.in = in;
-  a.out = out;
-  a.qaux = qaux;
-  a.planes = static_cast<float *>(ws);
-  a.carry_r = reinterpret_cast<float4 *>(static_cast<char *>(ws) + L.planes_bytes);
-  a.carry_c = reinterpret_cast<float4 *>(static_cast<char *>(ws) + L.planes_bytes + L.carry_bytes);
+  char *base = static_cast<char *>(ws);
+  a.planes = reinterpret_cast<float *>(base);
+  a.carry_r = reinterpret_cast<float4 *>(base + L.off_carry_r);
+  a.carry_c = reinterpret_cast<float4 *>(base + L.off_carry_c);
   a.H = height;
   a.W = width;
   a.pitch = pitch;
@@ -682,30 +853,90 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
   a.sr = sr;
   a.inv_sr = (float)(1.0 / (double)sr);
   a.e2c = (float)(-1.4426950408889634 / 2.0);
+  return a;
+}
+
+bool grid_fits(const Layout &L, int nch) {
+  const long long lim = 0x7fffffffLL;
+  return row_ctas(L) <= lim && block_ctas(L) <= lim && col_warps(L) / 2 + 1 <= lim &&
+         2LL * L.Hp * nch / 256 + 1 <= lim && 2LL * L.P * nch / 256 + 1 <= lim;
+}
+
+// The row passes of one channel family: carry, scan, apply (which also
+// writes the column tiles' zero-state finals into a.carry_c).
+template <int MODE>
+void row_passes(const RecArgs &a, const Layout &L, cudaStream_t s) {
+  rec_rows_carry<MODE><<<(int)row_ctas(L), 32 * kWarpsPerBlock, 0, s>>>(a);
+  rec_scan<<<(int)((2LL * L.Hp * a.nch + 255) / 256), 256, 0, s>>>(
+      a, CarryMap{a.carry_r, a.nch, L.P / kTileLen, L.Hp});
+  rec_rows_apply<MODE><<<(int)block_ctas(L), 32 * kRowApplyWarps, 0, s>>>(a);
+}
+
+void col_scan(const RecArgs &a, float4 *carry, const Layout &L, cudaStream_t s) {
+  rec_scan<<<(int)((2LL * L.P * a.nch + 255) / 256), 256, 0, s>>>(
+      a, CarryMap{carry, a.nch, L.Hp / kTileLen, L.P});
+}
+
+bf_status run(const float *in, float *out, float *qaux, int height, int width, int pitch,
+              double sigma_s, bool gpa, int N, float tc, float sr, void *ws, size_t ws_bytes,
+              void *stream) {
+  bf_status st = bfi::check_image(in, out, height, width, pitch);
+  if (st != BF_OK) return st;
+  if (!(sigma_s >= kMinSigmaS) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
+  const int nch = gpa ? N + 1 : 1;
+  const Layout L = layout(height, width, nch, false);
+  if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
+  if (!grid_fits(L, nch)) return BF_ERR_UNSUPPORTED;
+  RecArgs a = base_args(in, height, width, pitch, sigma_s, nch, N, tc, sr, L, ws);
+  a.out = out;
+  a.qaux = qaux;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int threads = 32 * kWarpsPerBlock;
-  // rows: warps = (Hp / 16) x (P / 32); the row pass's two-warp CTAs own
-  // one 32 x 32 block each
-  const long long wr = (long long)(L.Hp / 16) * (L.P / kTileLen);
-  const long long br = (wr + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const long long ba = (long long)(L.Hp / kTileLen) * (L.P / kTileLen);
-  // columns: warps = (P / 16) x (Hp / 32)
-  const long long wc = (long long)(L.P / 16) * (L.Hp / kTileLen);
-  const long long bc = (wc + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const long long sr_threads = 2LL * L.Hp * nch, sc_threads = 2LL * L.P * nch;
-  if (br > 0x7fffffffLL || bc > 0x7fffffffLL || ba > 0x7fffffffLL || sr_threads / 256 + 1 > 0x7fffffffLL ||
-      sc_threads / 256 + 1 > 0x7fffffffLL)
-    return BF_ERR_UNSUPPORTED;
-  if (gpa) rec_rows_carry<true><<<(int)br, threads, 0, s>>>(a);
-  else rec_rows_carry<false><<<(int)br, threads, 0, s>>>(a);
-  rec_scan<<<(int)((sr_threads + 255) / 256), 256, 0, s>>>(
-      a, CarryMap{a.carry_r, nch, L.P / kTileLen, L.Hp});
-  if (gpa) rec_rows_apply<true><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
-  else rec_rows_apply<false><<<(int)ba, 32 * kRowApplyWarps, 0, s>>>(a);
-  rec_scan<<<(int)((sc_threads + 255) / 256), 256, 0, s>>>(
-      a, CarryMap{a.carry_c, nch, L.Hp / kTileLen, L.P});
-  if (gpa) rec_cols_apply<true><<<(int)bc, threads, 0, s>>>(a);
-  else rec_cols_apply<false><<<(int)bc, threads, 0, s>>>(a);
+  const int bc = (int)((col_warps(L) + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  if (gpa) row_passes<kPower>(a, L, s);
+  else row_passes<kFilter>(a, L, s);
+  col_scan(a, a.carry_c, L, s);
+  if (gpa) rec_cols_apply<true><<<bc, 32 * kWarpsPerBlock, 0, s>>>(a);
+  else rec_cols_apply<false><<<bc, 32 * kWarpsPerBlock, 0, s>>>(a);
+  return bfi::check_launch();
+}
+
+// Backward: the power images and the adjoint seeds through the row passes
+// (two families of N + 1 planes), then one column pass over both that forms
+// d in and the sigma_r partials, then their fixed-order sum.
+bf_status run_backward(const float *in, const float *f_out, const float *f_q, const float *gout,
+                       float *gin, double *gsigma, int height, int width, int pitch,
+                       double sigma_s, int N, float tc, float sr, void *ws, size_t ws_bytes,
+                       void *stream) {
+  bf_status st = bfi::check_image(in, gin, height, width, pitch);
+  if (st != BF_OK) return st;
+  if (!f_out || !f_q || !gout) return BF_ERR_INVALID_ARG;
+  if (gin == f_out || gin == f_q || gin == gout) return BF_ERR_INVALID_ARG;
+  const int nch = N + 1;
+  const Layout L = layout(height, width, nch, true);
+  if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
+  if (!grid_fits(L, nch)) return BF_ERR_UNSUPPORTED;
+  char *base = static_cast<char *>(ws);
+  RecArgs a = base_args(in, height, width, pitch, sigma_s, nch, N, tc, sr, L, ws);
+  a.f_out = f_out;
+  a.f_q = f_q;
+  a.gout = gout;
+  a.gin = gin;
+  a.planes2 = reinterpret_cast<float *>(base + L.off_planes2);
+  a.carry_c2 = reinterpret_cast<float4 *>(base + L.off_carry_c2);
+  a.partials = gsigma ? reinterpret_cast<double *>(base + L.off_partials) : nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RecArgs seeds = a;  // the c_n family writes the second planes and column tiles
+  seeds.planes = a.planes2;
+  seeds.carry_c = a.carry_c2;
+  row_passes<kPower>(a, L, s);
+  row_passes<kSeed>(seeds, L, s);
+  col_scan(a, a.carry_c, L, s);
+  col_scan(a, a.carry_c2, L, s);
+  const long long warps = col_warps(L), ctas = (warps + kGradWarps - 1) / kGradWarps;
+  rec_cols_grad<<<(int)ctas, 32 * kGradWarps, 0, s>>>(a);
+  if (gsigma) rec_reduce<<<1, 256, 0, s>>>(a.partials, ctas * kGradWarps, gsigma);
   return bfi::check_launch();
 }
 
@@ -736,8 +967,26 @@ extern "C" {
 bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *bytes) {
   if (!bytes || height < 1 || width < 1 || order_N < 0) return BF_ERR_INVALID_ARG;
   if (order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
-  *bytes = layout(height, width, order_N + 1).total;
+  *bytes = layout(height, width, order_N + 1, false).total;
   return BF_OK;
+}
+
+bf_status bf_recursive_backward_workspace(int height, int width, int order_N, size_t *bytes) {
+  if (!bytes || height < 1 || width < 1 || order_N < 1) return BF_ERR_INVALID_ARG;
+  if (order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
+  *bytes = layout(height, width, order_N + 1, true).total;
+  return BF_OK;
+}
+
+bf_status bf_recursive_backward(const float *d_in, const float *d_out, const float *d_qaux,
+                                const float *d_gout, float *d_gin, double *d_gsigma_r, int height,
+                                int width, int pitch, const bf_params *p, void *d_ws,
+                                size_t ws_bytes, void *stream) {
+  double sigma_s = 0.0;
+  const bf_status st = resolve_recursive(p, &sigma_s);
+  if (st != BF_OK) return st;
+  return run_backward(d_in, d_out, d_qaux, d_gout, d_gin, d_gsigma_r, height, width, pitch,
+                      sigma_s, p->order_N, p->t_c, p->sigma_r, d_ws, ws_bytes, stream);
 }
 
 bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int width, int pitch,

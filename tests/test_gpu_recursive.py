@@ -1,7 +1,8 @@
 """GPU parity of the recursive-Gaussian path (bf_recursive_gauss,
-bf_recursive_forward) against the checker's full-line Toeplitz-product
-evaluation (oracle.recursive), which is the zero-extended convolution with
-Deriche's fit written out.
+bf_recursive_forward, bf_recursive_backward) against the checker's full-line
+Toeplitz-product evaluation (oracle.recursive), which is the zero-extended
+convolution with Deriche's fit written out, and its FP64 reverse-mode
+gradient.
 
 Sizes span several 32-pixel carry tiles in both directions with ragged last
 tiles, single-row / single-column / single-pixel images, pitched rows, the
@@ -125,4 +126,64 @@ def test_recursive_errors():
     st = bf._lib.lib().bf_recursive_forward(
         ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(o.data_ptr()), None, 20, 30, 30,
         ctypes.byref(p), ctypes.c_void_p(ws.data_ptr()), need - 256, None)
+    assert st == 5
+
+
+GRAD_CASES = [  # (sigma_s, sigma_r, shape)
+    (1.5, 30.0, (40, 70)),
+    (5.0, 60.0, (64, 64)),
+    (20.0, 40.0, (50, 97)),
+    (3.0, 25.0, (33, 1)),
+    (0.5, 50.0, (1, 90)),
+]
+
+
+@pytest.mark.parametrize("s,sr,shape", GRAD_CASES)
+def test_recursive_backward(s, sr, shape):
+    """bf_recursive_backward against the checker's FP64 reverse-mode gradient
+    of the same Algorithm 2 (image: 2e-3 of the largest entry; sigma_r: 1e-3
+    relative), through the autograd wrapper as well."""
+    img = image(*shape, seed=int(s * 7) + shape[0], block=5)
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    g = synth.random_like(shape, seed=shape[1] + 3)
+    rgin, rgs = rec.gpa_grad_recursive(img, s, sr, N, g.astype(np.float64))
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.recursive_forward(x, sr, N, s, return_q=True)
+    gin, gs = bf.recursive_backward(x, out, q, torch.from_numpy(g).cuda(), sr, N, s)
+    torch.cuda.synchronize()
+    scale = max(np.abs(rgin).max(), 1e-30)
+    where = "s=%g sr=%g N=%d %s" % (s, sr, N, shape)
+    assert np.abs(gin.cpu().numpy() - rgin).max() <= 2e-3 * scale, where
+    assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+    # the autograd wrapper
+    xin = x.clone().requires_grad_(True)
+    sig = torch.tensor(sr, dtype=torch.float32, device="cuda", requires_grad=True)
+    (bf.recursive_bilateral(xin, sig, s, N=N) * torch.from_numpy(g).cuda()).sum().backward()
+    assert np.abs(xin.grad.cpu().numpy() - rgin).max() <= 2e-3 * scale, where
+    assert abs(float(sig.grad) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+
+
+def test_recursive_backward_pitched_and_errors():
+    """A pitched image gives the same gradient as its packed copy (the wrapper
+    packs mismatched layouts); too small a workspace is rejected."""
+    import ctypes
+    H, W, s, sr = 45, 80, 4.0, 40.0
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    base = torch.zeros((H, W + 3), device="cuda")
+    base[:, :W] = torch.from_numpy(image(H, W, seed=4)).cuda()
+    x = base[:, :W]
+    out, q = bf.recursive_forward(x, sr, N, s, return_q=True)
+    g = torch.from_numpy(synth.random_like((H, W), seed=6)).cuda()
+    gin, gs = bf.recursive_backward(x, out, q, g, sr, N, s)
+    gin2, gs2 = bf.recursive_backward(x.contiguous(), out, q, g, sr, N, s)
+    torch.testing.assert_close(gin, gin2, rtol=0, atol=0)
+    assert float(gs.item()) == float(gs2.item())
+    n = ctypes.c_size_t(0)
+    assert bf._lib.lib().bf_recursive_backward_workspace(H, W, N, ctypes.byref(n)) == 0
+    p = bf._lib.make_params(bf.GAUSS_RECURSIVE, 0, s, sr, N)
+    xc = x.contiguous()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    ws = torch.empty(n.value // 4, device="cuda")
+    st = bf._lib.lib().bf_recursive_backward(ptr(xc), ptr(out), ptr(q), ptr(g), ptr(gin), None, H, W,
+                                             W, ctypes.byref(p), ptr(ws), n.value - 256, None)
     assert st == 5
