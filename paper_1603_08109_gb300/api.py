@@ -22,7 +22,8 @@ __all__ = [
     "variant_count", "forward_workspace_bytes", "tuning_get", "tuning_set", "radius_bucket", "order_bucket",
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
-    "recursive_backward", "RecursiveBilateral", "recursive_bilateral",
+    "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
+    "recursive_bilateral",
 ]
 
 
@@ -219,6 +220,14 @@ def recursive_forward(img: torch.Tensor, sigma_r: float, N: int, sigma_s: float,
     return (o, q) if return_q else o
 
 
+def recursive_backward_workspace_bytes(H: int, W: int, N: int) -> int:
+    """Workspace of bf_recursive_backward (it also covers the forward's)."""
+    n = ctypes.c_size_t(0)
+    check(lib().bf_recursive_backward_workspace(int(H), int(W), int(N), ctypes.byref(n)),
+          "bf_recursive_backward_workspace")
+    return int(n.value)
+
+
 def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float,
                        t_c: float = 128.0, need_sigma: bool = True,
                        ws: Optional[torch.Tensor] = None):
@@ -236,10 +245,7 @@ def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float
     H, W = x.shape
     gin = _like(x)
     gs = torch.zeros(1, dtype=torch.float64, device=x.device) if need_sigma else None
-    n = ctypes.c_size_t(0)
-    check(lib().bf_recursive_backward_workspace(H, W, int(N), ctypes.byref(n)),
-          "bf_recursive_backward_workspace")
-    nbytes = int(n.value)
+    nbytes = recursive_backward_workspace_bytes(H, W, N)
     if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != x.device:
         ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
     p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)

@@ -187,3 +187,36 @@ def test_recursive_backward_pitched_and_errors():
     st = bf._lib.lib().bf_recursive_backward(ptr(xc), ptr(out), ptr(q), ptr(g), ptr(gin), None, H, W,
                                              W, ctypes.byref(p), ptr(ws), n.value - 256, None)
     assert st == 5
+
+
+def test_recursive_graph_capture():
+    """The forward and the backward enqueue only kernels (no allocation, no
+    synchronisation inside the library), so both capture into a CUDA graph;
+    replays on new image contents match eager calls bitwise."""
+    H, W, s, sr = 70, 90, 6.0, 40.0
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    x = torch.from_numpy(image(H, W, seed=31)).cuda()
+    g = torch.from_numpy(synth.random_like((H, W), seed=32)).cuda()
+    out = torch.empty_like(x)
+    q = torch.empty_like(x)
+    ws = torch.empty(bf.recursive_backward_workspace_bytes(H, W, N) // 4, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up (module loading) outside the capture
+        bf.recursive_forward(x, sr, N, s, return_q=False, out=out, ws=ws)
+        o0, q0 = bf.recursive_forward(x, sr, N, s, return_q=True, ws=ws)
+        bf.recursive_backward(x, o0, q0, g, sr, N, s, ws=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        o, qq = bf.recursive_forward(x, sr, N, s, return_q=True, ws=ws)
+        gin, gs = bf.recursive_backward(x, o, qq, g, sr, N, s, ws=ws)
+    for seed in (33, 34):
+        x.copy_(torch.from_numpy(image(H, W, seed=seed)).cuda())
+        graph.replay()
+        torch.cuda.synchronize()
+        eo, eq = bf.recursive_forward(x, sr, N, s, return_q=True)
+        egin, egs = bf.recursive_backward(x, eo, eq, g, sr, N, s)
+        torch.testing.assert_close(o, eo, rtol=0, atol=0)
+        torch.testing.assert_close(gin, egin, rtol=0, atol=0)
+        assert float(gs.item()) == float(egs.item())
