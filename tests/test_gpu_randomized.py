@@ -83,3 +83,30 @@ def test_random_recursive_forward(seed):
     ro, P, Q = rec.gpa_alg2_recursive(img, ss, sr, N, return_parts=True)
     compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr),
                     rec.centre_weight_recursive(ss), where, sigma_r=sr, N=N)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_recursive_backward(seed):
+    """The recursive route's adjoint at random sigma_s, shapes, pitches and
+    orders against the checker's FP64 reverse-mode gradient."""
+    from oracle import recursive as rec
+    rng = np.random.default_rng(7500 + seed)
+    ss = float(np.exp(rng.uniform(np.log(0.5), np.log(40.0))))
+    sr = float(rng.uniform(25.0, 80.0))
+    H = int(rng.integers(1, 90))
+    W = int(rng.integers(1, 140))
+    pad = int(rng.integers(0, 5))
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, ss, sr, 1.0)
+    img = image(H, W, seed=seed + 201, block=int(rng.integers(2, 20)))
+    base = torch.zeros((H, W + pad), dtype=torch.float32, device="cuda")
+    base[:, :W] = torch.from_numpy(img).cuda()
+    x = base[:, :W]
+    g = synth.random_like((H, W), seed=seed + 301)
+    out, q = bf.recursive_forward(x, sr, N, ss, return_q=True)
+    gin, gs = bf.recursive_backward(x, out, q, torch.from_numpy(g).cuda(), sr, N, ss)
+    torch.cuda.synchronize()
+    rgin, rgs = rec.gpa_grad_recursive(img, ss, sr, N, g.astype(np.float64))
+    where = "seed %d sigma_s %.2f sr %.1f N %d %dx%d" % (seed, ss, sr, N, H, W)
+    scale = max(np.abs(rgin).max(), 1e-30)
+    assert np.abs(gin.cpu().numpy().astype(np.float64) - rgin).max() <= 2e-3 * scale, where
+    assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
