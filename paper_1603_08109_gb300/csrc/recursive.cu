@@ -19,13 +19,15 @@
 // make every tile exact without halos:
 //   carry  : each tile's zero-state final states (causal at its last pixel,
 //            anticausal at its first), per mode and channel;
-//   scan   : one thread per (line, channel) walks the tiles and turns them
-//            into the true incoming states (S_in(t+1) = r^32 S_in(t) + e(t),
-//            and mirrored for the anticausal side);
+//   scan   : one thread per (line, channel, side) walks the tiles and turns
+//            them into the true incoming states (S_in(t+1) = r^32 S_in(t) +
+//            e(t), and mirrored for the anticausal side);
 //   apply  : each tile re-runs both recursions from its incoming states.
-// Five launches: rows carry, scan, rows apply (which also computes the
-// column tiles' carries from its 32 x 32 output blocks in shared memory),
-// scan, columns apply.
+// Forward, five launches: rows carry, scan, rows apply (which also computes
+// the column tiles' carries from its 32 x 32 output blocks in shared
+// memory), scan, columns apply.  Backward: the row launches for the power
+// images and again for the adjoint seeds, two column scans, one column
+// gather, one fixed-order sum of the sigma_r partials.
 // In `apply` both lanes of a tile run the same instruction stream: the second
 // lane holds its 16 pixels in reverse order, so phase 1 is the first lane's
 // causal pass and the second lane's anticausal pass; the two swap their final
@@ -69,8 +71,9 @@ struct RecArgs {
   const float *in;  // image (pitch elements per row)
   float *out;       // result (pitch)
   float *qaux;      // Q' (pitch) or null
-  // backward: the forward's out and Q', the output cotangent; d in; per-CTA
-  // sigma_r partials; the second channel family's planes and column tiles
+  // backward: the forward's out and Q', the output cotangent; d in; one
+  // sigma_r partial per column-pass warp; the second channel family's planes
+  // and column tiles
   const float *f_out, *f_q, *gout;
   float *gin;
   double *partials;
@@ -81,7 +84,7 @@ struct RecArgs {
   float4 *carry_c;  // column tiles: 2 sides x nch x (Hp / 32) x P states
   int H, W, pitch;
   int Hp, P;        // rows and pitch of a plane (multiples of 32)
-  int nch;          // channels: N + 1 (GPA) or 1 (plain filter)
+  int nch;          // channels per family: N + 1 (Algorithm 2) or 1 (plain filter)
   int N;
   float tc, sr, inv_sr;
   float e2c;        // -log2(e) / 2: a_0 = 2^(e2c H^2)
