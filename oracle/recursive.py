@@ -24,7 +24,8 @@ for the truncated kernels: only neighbours inside the image contribute.
 
 Algorithm 2 then runs step by step in FP64 with this operator as F * w;
 its gradient (image and sigma_r, N fixed) is taken by FP64 reverse-mode
-differentiation of those same steps.
+differentiation of those same steps.  The cross (joint) filter with the same
+operator is written out as its 2N filterings.
 
 Readings (also listed in the design notes):
 * The spatial support is the whole image (the recursion has an infinite
@@ -42,7 +43,7 @@ import numpy as np
 
 __all__ = ["DERICHE4", "deriche_raw", "deriche_impulse", "toeplitz_line",
            "recursive_filter", "gpa_alg2_recursive", "gpa_grad_recursive",
-           "centre_weight_recursive"]
+           "joint_gpa_recursive", "centre_weight_recursive"]
 
 # Deriche's fourth-order fit of the Gaussian (two damped cosine/sine pairs).
 DERICHE4 = {"a0": 1.680, "a1": 3.735, "b0": 1.783, "w0": 0.6318,
@@ -165,3 +166,38 @@ def gpa_grad_recursive(img, sigma_s: float, sigma_r: float, N: int, gout, T: flo
     out = sr * (P / Q) + T
     (out * torch.from_numpy(np.asarray(gout, dtype=np.float64))).sum().backward()
     return f.grad.numpy(), float(sr.grad)
+
+
+def joint_gpa_recursive(img, guide, sigma_s: float, sigma_r: float, N: int, T: float = 128.0,
+                        return_parts: bool = False):
+    """Cross (joint) bilateral filter (Sec. I, Sec. V) with phi_N on centred
+    guide values and the recursive Gaussian as w, written as its N + N
+    filterings: with B_n = e^{-G^2/2} G^n / n!-weighted guide power images
+    (G = (guide - T) / sigma_r), out = T + U / Q where
+    Q = sum_{n<N} (G^n / n!) e^{-G^2/2} (w * (e^{-G^2/2} G^n)) and
+    U = sum_{n<N} (G^n / n!) e^{-G^2/2} (w * (e^{-G^2/2} G^n (img - T))),
+    in FP64 with the Toeplitz-product filter.  Parts are U and Q."""
+    f = np.asarray(img, dtype=np.float64)
+    e = np.asarray(guide, dtype=np.float64)
+    Hh, Ww = f.shape
+    TH = toeplitz_line(sigma_s, Hh)
+    TW = toeplitz_line(sigma_s, Ww)
+
+    def filt(F):
+        return TH @ F @ TW.T
+
+    g = e - T
+    E = np.exp(-g * g / (2.0 * sigma_r * sigma_r))
+    Gs = g / sigma_r
+    F = E.copy()         # e^{-G^2/2} G^n
+    C = E.copy()         # e^{-G^2/2} G^n / n!  (the centre's factor)
+    U = np.zeros_like(f)
+    Q = np.zeros_like(f)
+    for n in range(N):
+        if n > 0:
+            F = Gs * F
+            C = Gs * C / n
+        Q = Q + C * filt(F)
+        U = U + C * filt(F * (f - T))
+    out = U / Q + T
+    return (out, U, Q) if return_parts else out

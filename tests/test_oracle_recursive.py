@@ -174,3 +174,20 @@ def test_gradient_matches_finite_differences():
     fds = (np.sum(g * rec.gpa_alg2_recursive(img, s, sr + e, N))
            - np.sum(g * rec.gpa_alg2_recursive(img, s, sr - e, N))) / (2 * e)
     assert gs == pytest.approx(fds, rel=1e-6)
+
+
+@pytest.mark.parametrize("s,sr,N,Hh,Ww", [(1.5, 30.0, 6, 9, 13), (4.0, 50.0, 9, 12, 8)])
+def test_joint_matches_bruteforce(s, sr, N, Hh, Ww):
+    """The joint filter with the recursive kernel equals the C checker's
+    brute-force cross filter with phi_N and the explicit kernel h(j_y) h(j_x)
+    (outputs and both sums), and with guide = image it is Algorithm 2."""
+    img = synth.blocks_image(Hh, Ww, 3, 25.0, seed=Hh + 2 * Ww).astype(np.float64)
+    guide = synth.blocks_image(Hh, Ww, 4, 15.0, seed=Hh * Ww).astype(np.float64)
+    w = _explicit_kernel(s, Hh, Ww)
+    o, U, Q = rec.joint_gpa_recursive(img, guide, s, sr, N, return_parts=True)
+    ro, rU, rQ = oracle.joint_gpa(img, guide, w, sr, N, return_parts=True)
+    assert np.abs(o - ro).max() < 1e-9
+    assert np.abs(Q - rQ).max() <= 1e-11 * np.abs(rQ).max()
+    assert np.abs(U - rU).max() <= 1e-11 * max(np.abs(rU).max(), 1e-300)
+    same = rec.joint_gpa_recursive(img, img, s, sr, N)
+    assert np.abs(same - rec.gpa_alg2_recursive(img, s, sr, N)).max() < 1e-9
