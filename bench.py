@@ -561,6 +561,22 @@ def run_sweeps(args):
                   "direct_fwd_ms": dms, "direct_fwd_mpx_s": 4.194304 / dms * 1e3,
                   "speedup_vs_direct": dms / fms,
                   "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max())})
+        # the recursive Gaussian (the same cost for any sigma_s) against the banded
+        # truncated-Gaussian joint filter at sigma_s = 10 and 20
+        for ss in (10.0, 20.0):
+            N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, ss, 30.0, 1.0)
+            ws = torch.empty(bf.recursive_backward_workspace_bytes(2048, 2048, N) // 4, device=dev)
+            rms = _time_ms(lambda: bf.recursive_joint_forward(x, e, 30.0, N, ss, out=o, ws=ws), 5,
+                           stream, flush)
+            R = int(math.ceil(3.0 * ss - 1e-9))
+            Nf = bf.order_from_delta(bf.GAUSS, R, ss, 30.0, 1.0)
+            fms = _time_ms(lambda: bf.joint_forward(x, e, bf.GAUSS, 30.0, Nf, radius=R, sigma_s=ss,
+                                                    out=d), 3, stream, flush)
+            emit({"sweep": "joint2048", "kind": "gaussian_recursive", "sigma_s": ss,
+                  "sigma_r": 30.0, "N": N, "rec_fwd_ms": rms, "rec_fwd_mpx_s": 4.194304 / rms * 1e3,
+                  "fir_radius": R, "fir_N": Nf, "fir_fwd_ms": fms, "speedup_vs_fir": fms / rms,
+                  "max_abs_rec_vs_fir": float((o.double() - d.double()).abs().max())})
+            del ws
     if "grad512" in names:
         # 32 x 512^2, Gaussian sigma_s=5 (W=15), sigma_r=25, N from delta=1: fwd+bwd
         N = bf.order_from_delta(bf.GAUSS, 15, 5.0, 25.0, 1.0)

@@ -399,6 +399,17 @@ bf_status bf_tuning_set(int kind, int radius_bucket, int order_bucket, int varia
  * Workspace: 256-byte aligned, at least the queried size, else
  * BF_ERR_WORKSPACE / BF_ERR_INVALID_ARG.  Asynchronous on `stream`. */
 bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *bytes);
+/* bf_recursive_joint_workspace / bf_recursive_joint_forward: the cross (joint)
+ *   filter of bf_joint_forward (guide d_guide, averaged image d_in, same
+ *   layout) with the recursive Gaussian as w: the guide's power images b_n
+ *   and the products b_n (f - t_c), n < N, through the same row and column
+ *   passes (2N filterings), out = t_c + U'/Q' and optionally Q' (d_qaux).
+ *   Workspace: (2.75 N) 4 Hp P bytes plus 8 bytes per 16 x 32 column tile. */
+bf_status bf_recursive_joint_workspace(int height, int width, int order_N, size_t *bytes);
+bf_status bf_recursive_joint_forward(const float *d_in, const float *d_guide, float *d_out,
+                                     float *d_qaux, int height, int width, int pitch,
+                                     const bf_params *p, void *d_ws, size_t ws_bytes,
+                                     void *stream);
 bf_status bf_recursive_backward_workspace(int height, int width, int order_N, size_t *bytes);
 bf_status bf_recursive_backward(const float *d_in, const float *d_out, const float *d_qaux,
                                 const float *d_gout, float *d_gin, double *d_gsigma_r, int height,

@@ -14,7 +14,7 @@ from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABi
                   gpa_forward_stored, joint_direct,
                   joint_forward, kernel_error_max, order_bucket, order_estimates, order_from_delta,
                   radius_bucket, RecursiveBilateral, recursive_backward,
-                  recursive_backward_workspace_bytes, recursive_bilateral,
+                  recursive_backward_workspace_bytes, recursive_bilateral, recursive_joint_forward,
                   recursive_forward, recursive_gauss, recursive_workspace_bytes,
                   resolve_radius, tuning_get, tuning_set, variant_count)
 

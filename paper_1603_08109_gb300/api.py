@@ -23,7 +23,7 @@ __all__ = [
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
     "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
-    "recursive_bilateral",
+    "recursive_bilateral", "recursive_joint_forward",
 ]
 
 
@@ -214,6 +214,36 @@ def recursive_forward(img: torch.Tensor, sigma_r: float, N: int, sigma_s: float,
     p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
     check(lib().bf_recursive_forward(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0), ctypes.byref(p),
                                      _ptr(ws), nbytes, _stream(x.device)), "bf_recursive_forward")
+    if on_cpu:
+        o = o.cpu()
+        q = q.cpu() if q is not None else None
+    return (o, q) if return_q else o
+
+
+def recursive_joint_forward(img: torch.Tensor, guide: torch.Tensor, sigma_r: float, N: int,
+                            sigma_s: float, t_c: float = 128.0, return_q: bool = False,
+                            out: Optional[torch.Tensor] = None,
+                            ws: Optional[torch.Tensor] = None):
+    """Cross (joint) filter with the recursive Gaussian: range kernel on the
+    guide, average of img.  Returns out, or (out, Q')."""
+    x, on_cpu = _as_device_image(img)
+    gd, _ = _as_device_image(guide)
+    if gd.shape != x.shape or gd.stride() != x.stride():
+        x = x.contiguous()
+        gd = gd.contiguous()
+    o = _image_like(x, out if not on_cpu else None)
+    q = _like(x) if return_q else None
+    H, W = x.shape
+    n = ctypes.c_size_t(0)
+    check(lib().bf_recursive_joint_workspace(H, W, int(N), ctypes.byref(n)),
+          "bf_recursive_joint_workspace")
+    nbytes = int(n.value)
+    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != x.device:
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+    p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_recursive_joint_forward(_ptr(x), _ptr(gd), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                           ctypes.byref(p), _ptr(ws), ws.numel() * ws.element_size(),
+                                           _stream(x.device)), "bf_recursive_joint_forward")
     if on_cpu:
         o = o.cpu()
         q = q.cpu() if q is not None else None

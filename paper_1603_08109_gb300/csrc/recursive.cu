@@ -75,6 +75,7 @@ struct RecArgs {
   // sigma_r partial per column-pass warp; the second channel family's planes
   // and column tiles
   const float *f_out, *f_q, *gout;
+  const float *data;  // cross filter: the averaged image (in is then the guide)
   float *gin;
   double *partials;
   float *planes2;
@@ -255,8 +256,10 @@ __device__ __forceinline__ void a0_from_H(const RecArgs &a, const float (&Hv)[kH
 //            rescaled), by a_n = a_{n-1} H / sqrt(n);
 //   kSeed  : the adjoint seeds c_n = qbar a_n [n < N] + pbar sqrt(n) a_{n-1}
 //            [n >= 1] of the backward (qbar = -g (out - t_c) / Q',
-//            pbar = g sigma_r / Q' at the pixel).
-enum { kFilter = 0, kPower = 1, kSeed = 2 };
+//            pbar = g sigma_r / Q' at the pixel);
+//   kData  : the cross filter's b_n (f - t_c), b_n the guide's power images
+//            (a.in is the guide, a.data the averaged image).
+enum { kFilter = 0, kPower = 1, kSeed = 2, kData = 3 };
 
 template <int MODE>
 struct RowSource {
@@ -269,7 +272,7 @@ struct RowSource {
     } else {
       a0_from_H(A, H, a);
 #pragma unroll
-      for (int k = 0; k < kHalf; ++k) x[k] = MODE == kPower ? a[k] : qb[k] * a[k];
+      for (int k = 0; k < kHalf; ++k) x[k] = MODE == kPower ? a[k] : qb[k] * a[k];  // kData: qb = f - t_c
     }
   }
   // channel n >= 1's values into x
@@ -281,6 +284,7 @@ struct RowSource {
       const float prev = a[k];
       a[k] = prev * (H[k] * is);
       if constexpr (MODE == kPower) x[k] = a[k];
+      else if constexpr (MODE == kData) x[k] = qb[k] * a[k];
       else x[k] = fmaf(pb[k] * sq, prev, q_on ? qb[k] * a[k] : 0.f);
     }
   }
@@ -322,6 +326,14 @@ __device__ __forceinline__ bool row_tile(const RecArgs &a, int w, float *sm, Row
     sm[r * kRowPitch + lane] = v;
   }
   tile_to_lanes<MODE>(sm, first, src.H);
+  if constexpr (MODE == kData) {  // f - t_c of the averaged image (0 outside)
+    for (int r = 0; r < 16; ++r) {
+      const int yy = y0 + r;
+      sm[r * kRowPitch + lane] =
+          (yy < a.H && xx < a.W) ? __ldg(a.data + (size_t)yy * a.pitch + xx) - a.tc : 0.f;
+    }
+    tile_to_lanes<MODE>(sm, first, src.qb);
+  }
   if constexpr (MODE == kSeed) {
     for (int pass = 0; pass < 2; ++pass) {
       for (int r = 0; r < 16; ++r) {
@@ -706,6 +718,60 @@ __global__ void __launch_bounds__(32 * kGradWarps, 4) rec_cols_grad(const __grid
   }
 }
 
+// Column pass of the cross filter: per channel n < N, B_n = w * b_n and
+// U_n = w * (b_n (f - t_c)) from the two plane families; with the guide's
+// b_n at the pixel, Q' = sum b_n B_n and U' = sum b_n U_n accumulate in
+// registers; out = t_c + U'/Q' (and Q').
+constexpr int kJointWarps = 2;
+
+__global__ void __launch_bounds__(32 * kJointWarps) rec_cols_joint(const __grid_constant__ RecArgs a) {
+  __shared__ ColRing<2> ring[kJointWarps];
+  ColRing<2> &R = ring[threadIdx.x >> 5];
+  const int w = blockIdx.x * kJointWarps + (threadIdx.x >> 5);
+  int x, y0;
+  bool first;
+  if (!col_tile(a, w, x, y0, first)) return;
+  const int ty = y0 / kTileLen, xb = x & ~15;
+  const bool xin = x < a.W;
+  float Hv[kHalf], bv[kHalf], Qa[kHalf], Ua[kHalf];
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) {  // the guide's centred values (sentinel outside)
+    const int yy = col_row(y0, first, k);
+    Hv[k] = (xin && yy < a.H) ? (__ldg(a.in + (size_t)yy * a.pitch + x) - a.tc) * a.inv_sr
+                              : kSentinelH;
+    bv[k] = exp2f(a.e2c * Hv[k] * Hv[k]);
+    Qa[k] = Ua[k] = 0.f;
+  }
+  col_prologue<2>(a, R, xb, y0, ty);
+  for (int n = 0; n < a.nch; ++n) {
+    col_advance<2>(a, R, n, xb, y0, ty);
+    if (n > 0) {
+      const float is = 1.0f / sqrtf((float)n);
+#pragma unroll
+      for (int k = 0; k < kHalf; ++k) bv[k] *= Hv[k] * is;
+    }
+    float v[kHalf], t[kHalf];
+    float4 c0, c1;
+    col_read<2>(R, n, 0, first, v, c0, c1);
+    apply_tile(a.K, v, c0, c1, first, t);  // B_n
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) Qa[k] = fmaf(bv[k], t[k], Qa[k]);
+    col_read<2>(R, n, 1, first, v, c0, c1);
+    apply_tile(a.K, v, c0, c1, first, t);  // U_n
+#pragma unroll
+    for (int k = 0; k < kHalf; ++k) Ua[k] = fmaf(bv[k], t[k], Ua[k]);
+  }
+  cp_wait<0>();
+#pragma unroll
+  for (int k = 0; k < kHalf; ++k) {
+    const int yy = col_row(y0, first, k);
+    if (xin && yy < a.H) {
+      a.out[(size_t)yy * a.pitch + x] = __fdividef(Ua[k], Qa[k]) + a.tc;
+      if (a.qaux) a.qaux[(size_t)yy * a.pitch + x] = Qa[k];
+    }
+  }
+}
+
 // Sum of the per-warp sigma_r partials in a fixed order (one CTA).
 __global__ void __launch_bounds__(256) rec_reduce(const double *p, long long n, double *out) {
   __shared__ double red[256];
@@ -943,6 +1009,39 @@ bf_status run_backward(const float *in, const float *f_out, const float *f_q, co
   return bfi::check_launch();
 }
 
+// Cross filter: the guide's power images b_n and the products b_n (f - t_c)
+// through the row passes (two families of N planes), then one column pass.
+bf_status run_joint(const float *in, const float *guide, float *out, float *qaux, int height,
+                    int width, int pitch, double sigma_s, int N, float tc, float sr, void *ws,
+                    size_t ws_bytes, void *stream) {
+  bf_status st = bfi::check_image(in, out, height, width, pitch);
+  if (st != BF_OK) return st;
+  if (!guide || guide == out || (qaux && (qaux == in || qaux == out || qaux == guide)))
+    return BF_ERR_INVALID_ARG;
+  const Layout L = layout(height, width, N, true);
+  if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
+  if (!grid_fits(L, N)) return BF_ERR_UNSUPPORTED;
+  char *base = static_cast<char *>(ws);
+  RecArgs a = base_args(guide, height, width, pitch, sigma_s, N, N, tc, sr, L, ws);
+  a.data = in;
+  a.out = out;
+  a.qaux = qaux;
+  a.planes2 = reinterpret_cast<float *>(base + L.off_planes2);
+  a.carry_c2 = reinterpret_cast<float4 *>(base + L.off_carry_c2);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RecArgs data = a;  // the b_n (f - t_c) family writes the second planes and column tiles
+  data.planes = a.planes2;
+  data.carry_c = a.carry_c2;
+  row_passes<kPower>(a, L, s);
+  row_passes<kData>(data, L, s);
+  col_scan(a, a.carry_c, L, s);
+  col_scan(a, a.carry_c2, L, s);
+  const long long ctas = (col_warps(L) + kJointWarps - 1) / kJointWarps;
+  rec_cols_joint<<<(int)ctas, 32 * kJointWarps, 0, s>>>(a);
+  return bfi::check_launch();
+}
+
 bf_status resolve_recursive(const bf_params *p, double *sigma_s) {
   if (!p) return BF_ERR_INVALID_ARG;
   if (p->kind != BF_SPATIAL_GAUSS_RECURSIVE) return BF_ERR_INVALID_ARG;
@@ -972,6 +1071,24 @@ bf_status bf_recursive_workspace(int height, int width, int order_N, size_t *byt
   if (order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
   *bytes = layout(height, width, order_N + 1, false).total;
   return BF_OK;
+}
+
+bf_status bf_recursive_joint_workspace(int height, int width, int order_N, size_t *bytes) {
+  if (!bytes || height < 1 || width < 1 || order_N < 1) return BF_ERR_INVALID_ARG;
+  if (order_N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
+  *bytes = layout(height, width, order_N, true).total;
+  return BF_OK;
+}
+
+bf_status bf_recursive_joint_forward(const float *d_in, const float *d_guide, float *d_out,
+                                     float *d_qaux, int height, int width, int pitch,
+                                     const bf_params *p, void *d_ws, size_t ws_bytes,
+                                     void *stream) {
+  double sigma_s = 0.0;
+  const bf_status st = resolve_recursive(p, &sigma_s);
+  if (st != BF_OK) return st;
+  return run_joint(d_in, d_guide, d_out, d_qaux, height, width, pitch, sigma_s, p->order_N,
+                   p->t_c, p->sigma_r, d_ws, ws_bytes, stream);
 }
 
 bf_status bf_recursive_backward_workspace(int height, int width, int order_N, size_t *bytes) {

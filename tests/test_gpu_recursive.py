@@ -220,3 +220,22 @@ def test_recursive_graph_capture():
         torch.testing.assert_close(o, eo, rtol=0, atol=0)
         torch.testing.assert_close(gin, egin, rtol=0, atol=0)
         assert float(gs.item()) == float(egs.item())
+
+
+@pytest.mark.parametrize("s,sr,shape", [(2.0, 30.0, (60, 110)), (15.0, 45.0, (97, 64)),
+                                        (0.5, 60.0, (1, 77))])
+def test_recursive_joint(s, sr, shape):
+    """The cross filter with the recursive Gaussian against the checker's 2N
+    filterings (Q' is the checker's Q as is: the guide's factors are already
+    rescaled); with guide = image it equals the Algorithm 2 route."""
+    img = image(*shape, seed=shape[0] + 5, block=6)
+    guide = synth.gradient_polygons_image(*shape, 8, 10.0, seed=shape[1] + 9)
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.recursive_joint_forward(x, torch.from_numpy(guide).cuda(), sr, N, s, return_q=True)
+    ro, U, Q = rec.joint_gpa_recursive(img, guide, s, sr, N, return_parts=True)
+    compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, Q, rec.centre_weight_recursive(s),
+                    "joint s=%g sr=%g N=%d %s" % (s, sr, N, shape), sigma_r=sr, N=N)
+    same = bf.recursive_joint_forward(x, x, sr, N, s)
+    gpa = bf.recursive_forward(x, sr, N, s)
+    assert float((same - gpa).abs().max()) <= 1e-3
