@@ -239,3 +239,23 @@ def test_recursive_joint(s, sr, shape):
     same = bf.recursive_joint_forward(x, x, sr, N, s)
     gpa = bf.recursive_forward(x, sr, N, s)
     assert float((same - gpa).abs().max()) <= 1e-3
+
+
+def test_recursive_large_order():
+    """sigma_r = 10.5 (the bound asks N ~ 230): hundreds of channels through
+    the carries and the ring, forward and backward."""
+    H, W, s, sr = 37, 70, 3.0, 10.5
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    assert N > 150
+    img = image(H, W, seed=77, block=5)
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.recursive_forward(x, sr, N, s, return_q=True)
+    ro, P, Q = rec.gpa_alg2_recursive(img, s, sr, N, return_parts=True)
+    compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr),
+                    rec.centre_weight_recursive(s), "recursive N=%d" % N, sigma_r=sr, N=N)
+    g = synth.random_like((H, W), seed=78)
+    gin, gs = bf.recursive_backward(x, out, q, torch.from_numpy(g).cuda(), sr, N, s)
+    rgin, rgs = rec.gpa_grad_recursive(img, s, sr, N, g.astype(np.float64))
+    scale = max(np.abs(rgin).max(), 1e-30)
+    assert np.abs(gin.cpu().numpy() - rgin).max() <= 2e-3 * scale
+    assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4)
