@@ -386,6 +386,44 @@ def run_sweeps(args):
                       "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src,
                       "alu_ops_frac": fwd_ops_per_pixel(kind, R, N) * px / (fms * 1e-3) /
                       fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+        # back-to-back launches over 8 rotating image/output pairs (1 GB in all, so every
+        # launch reads inputs and writes outputs that are not in L2): the per-launch time
+        # without an isolated launch's latency and ramp, for the copy and the small-N box
+        K = 8
+        xs = [torch.from_numpy(synth.gradient_polygons_image(4096, 4096, 64, 15.0,
+                                                             seed=2000 + k)).to(dev) for k in range(K)]
+        os_ = [torch.empty_like(xs[0]) for _ in range(K)]
+
+        def stream_ms(body, rounds=5):
+            for k in range(K):
+                body(xs[k], os_[k])
+            torch.cuda.synchronize()
+            best = []
+            for _ in range(rounds):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for k in range(K):
+                    body(xs[k], os_[k])
+                e1.record(stream)
+                e1.synchronize()
+                best.append(e0.elapsed_time(e1) / K)
+            return statistics.median(best)
+
+        cms = stream_ms(lambda a, b: b.copy_(a))
+        emit({"sweep": "roofline4096", "timing": "back-to-back, 8 rotating pairs",
+              "kernel": "torch copy (reference)", "ms": cms, "gbs": 8 * px / cms / 1e6,
+              "frac_of_measured_hbm": 8 * px / cms / 1e6 / hbm_peak})
+        for R in (3, 5):
+            for N in (1, 2, 3):
+                fms = stream_ms(lambda a, b: bf.gpa_forward(a, bf.BOX, 40.0, N, radius=R, out=b))
+                gbs = 8 * px / fms / 1e6
+                emit({"sweep": "roofline4096", "timing": "back-to-back, 8 rotating pairs",
+                      "kind": "box", "radius": R, "sigma_r": 40.0, "N": N, "fwd_ms": fms,
+                      "fwd_mpx_s": px / fms / 1e3, "algorithmic_gbs": gbs,
+                      "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src})
+        del xs, os_
+        torch.cuda.empty_cache()
         # the same generator at 8192^2: the small-N box forward past the launch ramp and tail
         x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)
         o = torch.empty_like(x)
