@@ -18,4 +18,4 @@ from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABi
                   recursive_forward, recursive_gauss, recursive_workspace_bytes,
                   resolve_radius, tuning_get, tuning_set, variant_count)
 
-__version__ = "1.0.0"
+__version__ = "1.1.0"
