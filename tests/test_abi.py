@@ -156,6 +156,27 @@ def test_recursive_host_side():
                                   None) == 1
     assert lib.bf_recursive_gauss(None, fake, 100, 70, 70, ctypes.c_float(3.0), fake, 1 << 30,
                                   None) == 1
+    # backward and cross filter: workspace queries and checks made before any launch
+    bsz, jsz = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.bf_recursive_backward_workspace(100, 70, 9, ctypes.byref(bsz)) == 0
+    assert lib.bf_recursive_joint_workspace(100, 70, 9, ctypes.byref(jsz)) == 0
+    assert bsz.value > sz.value and jsz.value > sz.value
+    assert lib.bf_recursive_backward_workspace(100, 70, 0, ctypes.byref(bsz)) == 1
+    assert lib.bf_recursive_joint_workspace(100, 70, 0, ctypes.byref(jsz)) == 1
+    g = ctypes.c_void_p(0x2000)
+    bargs = (fake, g, g, g, ctypes.c_void_p(0x3000), None, 100, 70, 70)
+    assert lib.bf_recursive_backward(*bargs, ctypes.byref(good), fake, 0, None) == 5
+    assert lib.bf_recursive_backward(fake, None, g, g, ctypes.c_void_p(0x3000), None, 100, 70, 70,
+                                     ctypes.byref(good), fake, 1 << 30, None) == 1
+    assert lib.bf_recursive_backward(fake, g, g, g, g, None, 100, 70, 70,  # d_gin aliases d_out
+                                     ctypes.byref(good), fake, 1 << 30, None) == 1
+    jargs = (fake, g, ctypes.c_void_p(0x3000), None, 100, 70, 70)
+    assert lib.bf_recursive_joint_forward(*jargs, ctypes.byref(good), fake, 0, None) == 5
+    assert lib.bf_recursive_joint_forward(fake, None, ctypes.c_void_p(0x3000), None, 100, 70, 70,
+                                          ctypes.byref(good), fake, 1 << 30, None) == 1
+    assert lib.bf_recursive_joint_forward(*jargs, ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 40.0,
+                                                                             9)),
+                                          fake, 1 << 30, None) == 1
 
 
 def test_tuning_table_roundtrip():
