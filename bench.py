@@ -506,9 +506,19 @@ def run_sweeps(args):
             del ws
             bms = _time_ms(lambda: bf.recursive_backward(x, o, q, g, 40.0, N, ss), 3, stream, flush)
             fms = _time_ms(lambda: bf.recursive_forward(x, 40.0, N, ss, out=o2), 3, stream, flush)
+            # the stored pair: the forward keeps the power images' row-pass planes
+            wsb = torch.empty(bf.recursive_backward_workspace_bytes(size, size, N) // 4, device=dev)
+            so, sq, _ = bf.recursive_forward_stored(x, 40.0, N, ss, ws=wsb)
+            sbms = _time_ms(lambda: bf.recursive_backward_stored(x, so, sq, g, 40.0, N, ss, wsb), 3,
+                            stream, flush)
+            sfms = _time_ms(lambda: bf.recursive_forward_stored(x, 40.0, N, ss, out=so, ws=wsb), 3,
+                            stream, flush)
+            del wsb, sq
             row = {"sweep": "recursive", "size": size, "sigma_s": ss, "sigma_r": 40.0, "N": N,
                    "rec_fwd_ms": fms, "rec_bwd_ms": bms,
-                   "rec_fwd_bwd_mpx_s": px / (fms + bms) / 1e3}
+                   "rec_fwd_bwd_mpx_s": px / (fms + bms) / 1e3,
+                   "stored_fwd_ms": sfms, "stored_bwd_ms": sbms,
+                   "stored_fwd_bwd_mpx_s": px / (sfms + sbms) / 1e3}
             if size == 2048:
                 R = 60
                 Nf = bf.order_from_delta(bf.GAUSS, R, ss, 40.0, 0.5)

@@ -420,6 +420,29 @@ bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int wi
 bf_status bf_recursive_forward(const float *d_in, float *d_out, float *d_qaux, int height,
                                int width, int pitch, const bf_params *p, void *d_ws,
                                size_t ws_bytes, void *stream);
+/* bf_recursive_forward_stored / bf_recursive_backward_stored: the same
+ *   forward and gradient, with the power images' row-pass planes kept between
+ *   them instead of recomputed (the paper has no backward; this trades memory
+ *   for the backward's repeat of those row passes).  The forward takes a
+ *   workspace of the backward's size (bf_recursive_backward_workspace, same
+ *   height, width and N) and writes the same out and Q' as
+ *   bf_recursive_forward; afterwards the workspace holds the N + 1 row-filtered
+ *   power planes and their scanned column-tile states.  The backward then
+ *   runs only the adjoint seeds' passes and the gather, and returns the same
+ *   bits as bf_recursive_backward.  Contract (not checkable on the host): the
+ *   backward gets the workspace the stored forward wrote, unmodified, with the
+ *   same d_in contents, height, width, pitch and parameters; anything else
+ *   gives wrong gradients (never an out-of-bounds access: every index comes
+ *   from the sizes).  The backward overwrites only the seeds' part, so one
+ *   stored forward serves several backwards (e.g. several cotangents). */
+bf_status bf_recursive_forward_stored(const float *d_in, float *d_out, float *d_qaux,
+                                      int height, int width, int pitch, const bf_params *p,
+                                      void *d_ws, size_t ws_bytes, void *stream);
+bf_status bf_recursive_backward_stored(const float *d_in, const float *d_out,
+                                       const float *d_qaux, const float *d_gout, float *d_gin,
+                                       double *d_gsigma_r, int height, int width, int pitch,
+                                       const bf_params *p, void *d_ws, size_t ws_bytes,
+                                       void *stream);
 
 #ifdef __cplusplus
 }

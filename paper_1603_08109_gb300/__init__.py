@@ -16,6 +16,7 @@ from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABi
                   radius_bucket, RecursiveBilateral, recursive_backward,
                   recursive_backward_workspace_bytes, recursive_bilateral, recursive_joint_forward,
                   recursive_forward, recursive_gauss, recursive_workspace_bytes,
+                  recursive_forward_stored, recursive_backward_stored,
                   resolve_radius, tuning_get, tuning_set, variant_count)
 
-__version__ = "1.1.0"
+__version__ = "1.2.0"

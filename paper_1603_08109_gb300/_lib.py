@@ -67,6 +67,9 @@ SIGNATURES = {
     "bf_recursive_joint_workspace": (_i, [_i, _i, _i, ctypes.POINTER(_sz)]),
     "bf_recursive_joint_forward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_recursive_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
+    "bf_recursive_forward_stored": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
+    "bf_recursive_backward_stored": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz,
+                                          _vp]),
     "bf_fast_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_fast_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_backward_stored": (_i, [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _i, _pp,

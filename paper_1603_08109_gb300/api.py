@@ -23,7 +23,8 @@ __all__ = [
     "joint_forward", "joint_direct", "order_estimates", "kernel_error_max", "exhaustive_order",
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
     "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
-    "recursive_bilateral", "recursive_joint_forward",
+    "recursive_bilateral", "recursive_joint_forward", "recursive_forward_stored",
+    "recursive_backward_stored",
 ]
 
 
@@ -258,11 +259,51 @@ def recursive_backward_workspace_bytes(H: int, W: int, N: int) -> int:
     return int(n.value)
 
 
+def _backward_ws(H, W, N, dev, ws):
+    nbytes = recursive_backward_workspace_bytes(H, W, N)
+    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != dev:
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=dev)
+    return ws
+
+
+def recursive_forward_stored(img: torch.Tensor, sigma_r: float, N: int, sigma_s: float,
+                             t_c: float = 128.0, out: Optional[torch.Tensor] = None,
+                             ws: Optional[torch.Tensor] = None):
+    """recursive_forward that keeps the power images' row-pass planes for
+    recursive_backward_stored: returns (out, Q', ws).  Pass the returned
+    workspace, unmodified, with the same image and parameters to the
+    backward."""
+    x, on_cpu = _as_device_image(img)
+    if on_cpu:
+        raise ValueError("the stored forward keeps device state: pass a CUDA image")
+    x = x.contiguous()
+    o = _image_like(x, out)
+    q = _like(x)
+    H, W = x.shape
+    ws = _backward_ws(H, W, N, x.device, ws)
+    p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_recursive_forward_stored(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                            ctypes.byref(p), _ptr(ws),
+                                            ws.numel() * ws.element_size(), _stream(x.device)),
+          "bf_recursive_forward_stored")
+    return o, q, ws
+
+
+def recursive_backward_stored(img, out, q, gout, sigma_r: float, N: int, sigma_s: float,
+                              ws: torch.Tensor, t_c: float = 128.0, need_sigma: bool = True):
+    """(dL/d img, dL/d sigma_r or None) from the workspace that
+    recursive_forward_stored returned (same image and parameters)."""
+    return recursive_backward(img, out, q, gout, sigma_r, N, sigma_s, t_c, need_sigma, ws,
+                              stored=True)
+
+
 def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float,
                        t_c: float = 128.0, need_sigma: bool = True,
-                       ws: Optional[torch.Tensor] = None):
+                       ws: Optional[torch.Tensor] = None, stored: bool = False):
     """(dL/d img, dL/d sigma_r or None) of recursive_forward, given gout."""
     x, _ = _as_device_image(img)
+    if stored and (x.stride(-1) != 1 or x.stride(0) != x.shape[1]):
+        raise ValueError("the stored backward takes the contiguous image of the stored forward")
     tensors = []
     for t in (out, q, gout):
         if t.shape != x.shape or t.device != x.device or t.dtype != torch.float32:
@@ -276,13 +317,16 @@ def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float
     gin = _like(x)
     gs = torch.zeros(1, dtype=torch.float64, device=x.device) if need_sigma else None
     nbytes = recursive_backward_workspace_bytes(H, W, N)
-    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != x.device:
-        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+    if stored:
+        if ws is None or ws.device != x.device or ws.numel() * ws.element_size() < nbytes:
+            raise ValueError("the stored backward needs the stored forward's workspace")
+    else:
+        ws = _backward_ws(H, W, N, x.device, ws)
     p = _params(GAUSS_RECURSIVE, 0, sigma_s, sigma_r, N, t_c)
-    check(lib().bf_recursive_backward(_ptr(x), _ptr(o), _ptr(qq), _ptr(g), _ptr(gin), _ptr(gs), H, W,
-                                      x.stride(0), ctypes.byref(p), _ptr(ws),
-                                      ws.numel() * ws.element_size(), _stream(x.device)),
-          "bf_recursive_backward")
+    fn = lib().bf_recursive_backward_stored if stored else lib().bf_recursive_backward
+    check(fn(_ptr(x), _ptr(o), _ptr(qq), _ptr(g), _ptr(gin), _ptr(gs), H, W, x.stride(0),
+             ctypes.byref(p), _ptr(ws), ws.numel() * ws.element_size(), _stream(x.device)),
+          "bf_recursive_backward_stored" if stored else "bf_recursive_backward")
     return gin, gs
 
 
@@ -490,15 +534,23 @@ class DirectBilateral(torch.autograd.Function):
 
 class RecursiveBilateral(torch.autograd.Function):
     """Autograd wrapper of the recursive-Gaussian route: forward =
-    bf_recursive_forward, backward = bf_recursive_backward."""
+    bf_recursive_forward, backward = bf_recursive_backward; with store, the
+    stored pair (the workspace with the power images' row-pass planes is held
+    from forward to backward)."""
 
     @staticmethod
-    def forward(ctx, img, sigma_r, N, sigma_s, t_c):
+    def forward(ctx, img, sigma_r, N, sigma_s, t_c, store):
         sr = _sigma_value(sigma_r)
-        out, q = recursive_forward(img, sr, N, sigma_s, t_c, return_q=True)
+        if store:
+            x = img.contiguous()
+            out, q, ctx.ws = recursive_forward_stored(x, sr, N, sigma_s, t_c)
+        else:
+            x = img
+            out, q = recursive_forward(x, sr, N, sigma_s, t_c, return_q=True)
+            ctx.ws = None
         ctx.cfg = (sr, N, sigma_s, t_c)
         ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
-        ctx.save_for_backward(img, out, q)
+        ctx.save_for_backward(x, out, q)
         return out
 
     @staticmethod
@@ -507,17 +559,19 @@ class RecursiveBilateral(torch.autograd.Function):
         sr, N, sigma_s, t_c = ctx.cfg
         need_s = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
         gin, gs = recursive_backward(img, out, q, gout.contiguous(), sr, N, sigma_s, t_c,
-                                     need_sigma=need_s)
+                                     need_sigma=need_s, ws=ctx.ws, stored=ctx.ws is not None)
         gsig = gs.reshape(()).to(torch.float32) if need_s else None
-        return gin, gsig, None, None, None
+        return gin, gsig, None, None, None, None
 
 
-def recursive_bilateral(img, sigma_r, sigma_s, N=None, t_c=128.0, delta=1.0):
+def recursive_bilateral(img, sigma_r, sigma_s, N=None, t_c=128.0, delta=1.0, store=False):
     """Differentiable fast bilateral filter with the recursive Gaussian;
-    N from delta (w(0) = h(0)^2) when not given."""
+    N from delta (w(0) = h(0)^2) when not given.  store: keep the power
+    images' row-pass planes from forward to backward (backward workspace
+    held between them; the backward skips those row passes)."""
     if N is None:
         N = order_from_delta(GAUSS_RECURSIVE, 0, sigma_s, _sigma_value(sigma_r), delta, t_c)
-    return RecursiveBilateral.apply(img, sigma_r, int(N), float(sigma_s), float(t_c))
+    return RecursiveBilateral.apply(img, sigma_r, int(N), float(sigma_s), float(t_c), bool(store))
 
 
 def gpa_bilateral(img, sigma_r, kind=GAUSS, N=None, radius=0, sigma_s=0.0, t_c=128.0,

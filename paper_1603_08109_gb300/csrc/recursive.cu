@@ -946,14 +946,16 @@ void col_scan(const RecArgs &a, float4 *carry, const Layout &L, cudaStream_t s) 
       a, CarryMap{carry, a.nch, L.Hp / kTileLen, L.P});
 }
 
+// keep: the workspace has the backward's layout, and the row-filtered power
+// planes and the scanned column-tile states stay there for run_backward.
 bf_status run(const float *in, float *out, float *qaux, int height, int width, int pitch,
               double sigma_s, bool gpa, int N, float tc, float sr, void *ws, size_t ws_bytes,
-              void *stream) {
+              void *stream, bool keep = false) {
   bf_status st = bfi::check_image(in, out, height, width, pitch);
   if (st != BF_OK) return st;
   if (!(sigma_s >= kMinSigmaS) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
   const int nch = gpa ? N + 1 : 1;
-  const Layout L = layout(height, width, nch, false);
+  const Layout L = layout(height, width, nch, keep);
   if (!ws || ws_bytes < L.total) return BF_ERR_WORKSPACE;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return BF_ERR_INVALID_ARG;
   if (!grid_fits(L, nch)) return BF_ERR_UNSUPPORTED;
@@ -972,11 +974,13 @@ bf_status run(const float *in, float *out, float *qaux, int height, int width, i
 
 // Backward: the power images and the adjoint seeds through the row passes
 // (two families of N + 1 planes), then one column pass over both that forms
-// d in and the sigma_r partials, then their fixed-order sum.
+// d in and the sigma_r partials, then their fixed-order sum.  stored: the
+// power images' planes and scanned column-tile states are already in the
+// workspace (a forward run with keep), so only the seeds' passes run.
 bf_status run_backward(const float *in, const float *f_out, const float *f_q, const float *gout,
                        float *gin, double *gsigma, int height, int width, int pitch,
                        double sigma_s, int N, float tc, float sr, void *ws, size_t ws_bytes,
-                       void *stream) {
+                       void *stream, bool stored = false) {
   bf_status st = bfi::check_image(in, gin, height, width, pitch);
   if (st != BF_OK) return st;
   if (!f_out || !f_q || !gout) return BF_ERR_INVALID_ARG;
@@ -999,9 +1003,9 @@ bf_status run_backward(const float *in, const float *f_out, const float *f_q, co
   RecArgs seeds = a;  // the c_n family writes the second planes and column tiles
   seeds.planes = a.planes2;
   seeds.carry_c = a.carry_c2;
-  row_passes<kPower>(a, L, s);
+  if (!stored) row_passes<kPower>(a, L, s);
   row_passes<kSeed>(seeds, L, s);
-  col_scan(a, a.carry_c, L, s);
+  if (!stored) col_scan(a, a.carry_c, L, s);
   col_scan(a, a.carry_c2, L, s);
   const long long warps = col_warps(L), ctas = (warps + kGradWarps - 1) / kGradWarps;
   rec_cols_grad<<<(int)ctas, 32 * kGradWarps, 0, s>>>(a);
@@ -1109,6 +1113,18 @@ bf_status bf_recursive_backward(const float *d_in, const float *d_out, const flo
                       sigma_s, p->order_N, p->t_c, p->sigma_r, d_ws, ws_bytes, stream);
 }
 
+bf_status bf_recursive_backward_stored(const float *d_in, const float *d_out,
+                                       const float *d_qaux, const float *d_gout, float *d_gin,
+                                       double *d_gsigma_r, int height, int width, int pitch,
+                                       const bf_params *p, void *d_ws, size_t ws_bytes,
+                                       void *stream) {
+  double sigma_s = 0.0;
+  const bf_status st = resolve_recursive(p, &sigma_s);
+  if (st != BF_OK) return st;
+  return run_backward(d_in, d_out, d_qaux, d_gout, d_gin, d_gsigma_r, height, width, pitch,
+                      sigma_s, p->order_N, p->t_c, p->sigma_r, d_ws, ws_bytes, stream, true);
+}
+
 bf_status bf_recursive_gauss(const float *d_in, float *d_out, int height, int width, int pitch,
                              float sigma_s, void *d_ws, size_t ws_bytes, void *stream) {
   return run(d_in, d_out, nullptr, height, width, pitch, sigma_s, false, 0, 0.f, 1.f, d_ws,
@@ -1124,6 +1140,17 @@ bf_status bf_recursive_forward(const float *d_in, float *d_out, float *d_qaux, i
   if (d_qaux && (d_qaux == d_in || d_qaux == d_out)) return BF_ERR_INVALID_ARG;
   return run(d_in, d_out, d_qaux, height, width, pitch, sigma_s, true, p->order_N, p->t_c,
              p->sigma_r, d_ws, ws_bytes, stream);
+}
+
+bf_status bf_recursive_forward_stored(const float *d_in, float *d_out, float *d_qaux,
+                                      int height, int width, int pitch, const bf_params *p,
+                                      void *d_ws, size_t ws_bytes, void *stream) {
+  double sigma_s = 0.0;
+  const bf_status st = resolve_recursive(p, &sigma_s);
+  if (st != BF_OK) return st;
+  if (d_qaux && (d_qaux == d_in || d_qaux == d_out)) return BF_ERR_INVALID_ARG;
+  return run(d_in, d_out, d_qaux, height, width, pitch, sigma_s, true, p->order_N, p->t_c,
+             p->sigma_r, d_ws, ws_bytes, stream, true);
 }
 
 }  // extern "C"

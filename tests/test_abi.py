@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 def test_version_and_status_strings():
     L = _lib()
-    assert L.lib().bf_version() == 10100
+    assert L.lib().bf_version() == 10200
     for code, text in L.STATUS.items():
         assert L.lib().bf_status_string(code).decode() == text
 
@@ -170,6 +170,17 @@ def test_recursive_host_side():
                                      ctypes.byref(good), fake, 1 << 30, None) == 1
     assert lib.bf_recursive_backward(fake, g, g, g, g, None, 100, 70, 70,  # d_gin aliases d_out
                                      ctypes.byref(good), fake, 1 << 30, None) == 1
+    # the stored pair: the forward wants the backward's workspace size
+    ws = ctypes.c_void_p(0x100000)
+    assert lib.bf_recursive_forward_stored(*args, ctypes.byref(good), ws, sz.value, None) == 5
+    assert lib.bf_recursive_forward_stored(*args, ctypes.byref(good), None, bsz.value, None) == 5
+    assert lib.bf_recursive_forward_stored(fake, fake, fake, 100, 70, 70,  # Q' aliases the input
+                                           ctypes.byref(good), ws, bsz.value, None) == 1
+    assert lib.bf_recursive_forward_stored(*args, ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 40.0, 9)),
+                                           ws, bsz.value, None) == 1
+    assert lib.bf_recursive_backward_stored(*bargs, ctypes.byref(good), ws, sz.value, None) == 5
+    assert lib.bf_recursive_backward_stored(fake, g, g, g, g, None, 100, 70, 70,
+                                            ctypes.byref(good), ws, bsz.value, None) == 1
     jargs = (fake, g, ctypes.c_void_p(0x3000), None, 100, 70, 70)
     assert lib.bf_recursive_joint_forward(*jargs, ctypes.byref(good), fake, 0, None) == 5
     assert lib.bf_recursive_joint_forward(fake, None, ctypes.c_void_p(0x3000), None, 100, 70, 70,

@@ -189,6 +189,46 @@ def test_recursive_backward_pitched_and_errors():
     assert st == 5
 
 
+@pytest.mark.parametrize("s,sr,shape", [(3.0, 30.0, (97, 130)), (15.0, 45.0, (64, 33)),
+                                        (0.5, 60.0, (1, 70))])
+def test_recursive_stored_pair(s, sr, shape):
+    """The stored pair keeps the power images' row-pass planes from the
+    forward for the backward: out, Q' and both gradients equal the recompute
+    pair's bitwise (the same kernels on the same data), for two cotangents
+    from one stored forward, through the autograd wrapper as well; and the
+    gradient matches the checker's FP64 reverse-mode gradient."""
+    img = image(*shape, seed=int(s * 11) + shape[1], block=5)
+    N = bf.order_from_delta(bf.GAUSS_RECURSIVE, 0, s, sr, 1.0)
+    x = torch.from_numpy(img).cuda()
+    out, q = bf.recursive_forward(x, sr, N, s, return_q=True)
+    so, sq, ws = bf.recursive_forward_stored(x, sr, N, s)
+    torch.cuda.synchronize()
+    where = "s=%g sr=%g N=%d %s" % (s, sr, N, shape)
+    torch.testing.assert_close(so, out, rtol=0, atol=0, msg=where)
+    torch.testing.assert_close(sq, q, rtol=0, atol=0, msg=where)
+    for seed in (41, 42):
+        g = torch.from_numpy(synth.random_like(shape, seed=seed)).cuda()
+        gin, gs = bf.recursive_backward(x, out, q, g, sr, N, s)
+        sgin, sgs = bf.recursive_backward_stored(x, so, sq, g, sr, N, s, ws)
+        torch.cuda.synchronize()
+        torch.testing.assert_close(sgin, gin, rtol=0, atol=0, msg=where)
+        assert float(sgs.item()) == float(gs.item()), where
+    rgin, rgs = rec.gpa_grad_recursive(img, s, sr, N, g.cpu().numpy().astype(np.float64))
+    scale = max(np.abs(rgin).max(), 1e-30)
+    assert np.abs(sgin.cpu().numpy() - rgin).max() <= 2e-3 * scale, where
+    assert abs(float(sgs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+    grads = []
+    for store in (False, True):
+        xin = x.clone().requires_grad_(True)
+        sig = torch.tensor(sr, dtype=torch.float32, device="cuda", requires_grad=True)
+        (bf.recursive_bilateral(xin, sig, s, N=N, store=store) * g).sum().backward()
+        grads.append((xin.grad, sig.grad))
+    torch.testing.assert_close(grads[1][0], grads[0][0], rtol=0, atol=0, msg=where)
+    assert float(grads[1][1]) == float(grads[0][1]), where
+    with pytest.raises(ValueError):  # the stored backward needs the stored forward's workspace
+        bf.recursive_backward_stored(x, so, sq, g, sr, N, s, ws[:16])
+
+
 def test_recursive_graph_capture():
     """The forward and the backward enqueue only kernels (no allocation, no
     synchronisation inside the library), so both capture into a CUDA graph;
