@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "bf_internal.h"
+#include "gpa_fixed.cuh"  // cp.async helpers
 #include "gpa_tile.cuh"
 
 namespace {
@@ -340,25 +341,43 @@ struct BwdFixedGeom {
   static constexpr int VP = TH >= 16 ? NT + 25 : NT + 33;
   static_assert(VP % 16 == (TH >= 16 ? 9 : 1), "phase-H row pitch");
   static_assert(VP >= NT + KH - 1, "phase-H window reads stay inside the row");
-  static constexpr size_t smem_bytes() {
-    return ((size_t)TH * VP + (size_t)RH * NT) * sizeof(float2) +
-           ((size_t)TH * VP + (size_t)RH * NT) * sizeof(float);
+  // Floats of the vertical-pass rows: (a_n, c_n) pairs, or c_n alone when
+  // w*a_n comes from stored planes (kept even so that sQP stays 8-byte aligned).
+  __host__ __device__ static constexpr size_t sv_floats(bool stored) {
+    return stored ? ((size_t)TH * VP + 1) / 2 * 2 : (size_t)2 * TH * VP;
+  }
+  // STORED: one TH x PP tile of the current channel's plane; PP = 1 (mod 32)
+  // keeps the phase-H reads conflict-free, PP >= TW + KH covers their columns.
+  static constexpr int PP = TW + KH <= 129 ? 129 : 161;
+  static_assert(PP >= TW + KH, "plane tile pitch");
+  static constexpr size_t smem_bytes(bool stored) {
+    return (sv_floats(stored) + (size_t)RH * NT * 2 + (size_t)TH * VP + (size_t)RH * NT +
+            (stored ? (size_t)TH * PP : 0)) *
+           sizeof(float);
   }
 };
 
-template <int KIND, int R, int NT, int TH>
+// STORED: w*a_n is read from the planes of the stored-plane forward
+// (normalised, plane n at abar + n * plane_stride) instead of filtered here;
+// only c_n goes through the two passes.  The tile's TH x TW block of plane n
+// is copied (cp.async, consecutive threads on consecutive columns) into a
+// shared tile at the start of channel n, while phase V computes.
+template <int KIND, int R, int NT, int TH, bool STORED>
 __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant__ BwdArgs A) {
   using G = BwdFixedGeom<R, NT, TH>;
   constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L, VP = G::VP;
+  constexpr int PP = G::PP;
   static_assert(TH % KH == 0 && NT % TH == 0 && TW >= KH, "tile geometry");
   extern __shared__ __align__(16) float smem[];
   const bfi::FilterConsts &fc = A.fc;
   const int N = fc.N;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (a_n, c_n)
-  float2 *sQP = sV + TH * VP;                     // RH x NT: (qbar, pbar)
+  float *sVc = smem;                              // TH x VP: vertical pass of c_n (STORED)
+  float2 *sQP = reinterpret_cast<float2 *>(smem + G::sv_floats(STORED));  // RH x NT: (qbar, pbar)
   float *sD = reinterpret_cast<float *>(sQP + RH * NT);  // TH x VP: D_n of the centre rows
   float *sH = sD + TH * VP;                       // RH x NT: H
+  float *sP = sH + RH * NT;                       // TH x PP: plane tile (STORED)
   const int c = threadIdx.x;
 
   // Region inputs, in groups of rows whose loads are all issued before any
@@ -417,11 +436,22 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
 
   // One channel n.  FIRST (n = 0): a_0 as loaded, no p-bar term; LAST (n = N):
   // no q-bar term (the sums of Q' stop at N - 1).
+  const float inv_qscale = 1.0f / fc.qscale;  // plane units -> kernel-sum units
   auto channel = [&](int n, auto first_tag, auto last_tag) {
     constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
     const float rs = FIRST ? 0.f : __frsqrt_rn((float)n);
     const float sq = __fsqrt_rn((float)n);
     __syncthreads();
+    if (STORED) {  // plane n's block (clamped at the image edges); the tile's
+                   // last reader was phase H of channel n - 1
+      const float *src = A.abar + (long long)n * A.plane_stride;
+      for (int e = c; e < TH * TW; e += NT) {
+        const int y = e / TW, j = e - y * TW;
+        bfk::cp_async4(sP + y * PP + j, src + (long long)min(ty0 + y, A.H - 1) * A.pitch +
+                                            min(tx0 + j, A.W - 1));
+      }
+      bfk::cp_async_commit();
+    }
 
     // ---------------- phase V: advance, seeds c_n, D_n of centre rows, vertical pass of (a_n, c_n)
     float2 acc[TH];
@@ -449,14 +479,27 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
         for (int y = 0; y < TH; ++y) {
           if (r - y >= 0 && r - y < L) {
             const float w = fc.taps[r - y];
-            acc[y] = __ffma2_rn(make_float2(w, w), ac, acc[y]);
+            if (STORED) acc[y].y = fmaf(w, ac.y, acc[y].y);  // the c_n lane alone
+            else acc[y] = __ffma2_rn(make_float2(w, w), ac, acc[y]);
           }
         }
       } else {
         cbox[KIND == BF_SPATIAL_BOX ? r : 0] = ac;
       }
     }
-    if (KIND == BF_SPATIAL_BOX) {
+    if (KIND == BF_SPATIAL_BOX && STORED) {
+      float s1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < L; ++r) s1 += cbox[KIND == BF_SPATIAL_BOX ? r : 0].y;
+      acc[0].y = s1;
+#pragma unroll
+      for (int y = 1; y < TH; ++y) {
+        const float in = cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0].y;
+        const float out = cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0].y;
+        s1 += in + -out;
+        acc[y].y = s1;
+      }
+    } else if (KIND == BF_SPATIAL_BOX) {
       float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = 0; r < L; ++r) s2 = __fadd2_rn(s2, cbox[KIND == BF_SPATIAL_BOX ? r : 0]);
@@ -470,7 +513,11 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
       }
     }
 #pragma unroll
-    for (int y = 0; y < TH; ++y) sV[y * VP + c] = acc[y];
+    for (int y = 0; y < TH; ++y) {
+      if (STORED) sVc[y * VP + c] = acc[y].y;
+      else sV[y * VP + c] = acc[y];
+    }
+    if (STORED) bfk::cp_async_wait<0>();  // this thread's copies of plane n have landed
     __syncthreads();
 
     // ---------------- phase H: horizontal pass of (a_n, c_n) + running sums
@@ -481,7 +528,42 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
       if (hx0 >= TW) continue;
       const float2 *rv = sV + hy * VP + hx0;
       float2 AC[KH];
-      if (KIND == BF_SPATIAL_GAUSS) {
+      if (STORED) {
+        const float *rc = sVc + hy * VP + hx0;
+        float Cc[KH];
+        if (KIND == BF_SPATIAL_GAUSS) {
+          float win[KH];
+#pragma unroll
+          for (int i = 0; i < KH; ++i) {
+            Cc[i] = 0.f;
+            win[i] = rc[i];
+          }
+#pragma unroll
+          for (int t = 0; t < L; ++t) {
+            const float w = fc.taps[t];
+#pragma unroll
+            for (int i = 0; i < KH; ++i) Cc[i] = fmaf(w, win[(t + i) % KH], Cc[i]);
+            win[t % KH] = rc[t + KH];
+          }
+        } else {
+          float v[KH + 2 * R];
+#pragma unroll
+          for (int i = 0; i < KH + 2 * R; ++i) v[i] = rc[i];
+          float s1 = 0.f;
+#pragma unroll
+          for (int i = 0; i < L; ++i) s1 += v[i];
+          Cc[0] = s1;
+#pragma unroll
+          for (int j = 1; j < KH; ++j) {
+            s1 += v[j + 2 * R] + -v[j - 1];
+            Cc[j] = s1;
+          }
+        }
+#pragma unroll
+        const float *pr = sP + hy * PP + hx0;
+#pragma unroll
+        for (int k = 0; k < KH; ++k) AC[k] = make_float2(pr[k] * inv_qscale, Cc[k]);
+      } else if (KIND == BF_SPATIAL_GAUSS) {
         float2 win[KH];
 #pragma unroll
         for (int i = 0; i < KH; ++i) {
@@ -565,24 +647,25 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
 constexpr int kBwdFixedNT = 128, kBwdFixedTH = 8;
 bool bwd_fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 
-template <int KIND, int R>
+template <int KIND, int R, bool STORED>
 bf_status launch_bwd_fixed_r(const BwdArgs &A, cudaStream_t s) {
   using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
-  auto kern = gpa_bwd_fixed_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH>;
-  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), G::smem_bytes());
+  constexpr size_t smem = G::smem_bytes(STORED);
+  auto kern = gpa_bwd_fixed_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH, STORED>;
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
   if (st != BF_OK) return st;
   dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
-  kern<<<grid, kBwdFixedNT, G::smem_bytes(), s>>>(A);
+  kern<<<grid, kBwdFixedNT, smem, s>>>(A);
   return bfi::check_launch();
 }
 
-template <int KIND>
+template <int KIND, bool STORED>
 bf_status launch_bwd_fixed(const BwdArgs &A, cudaStream_t s) {
   switch (A.fc.R) {
-    case 3: return launch_bwd_fixed_r<KIND, 3>(A, s);
-    case 5: return launch_bwd_fixed_r<KIND, 5>(A, s);
-    case 9: return launch_bwd_fixed_r<KIND, 9>(A, s);
-    case 15: return launch_bwd_fixed_r<KIND, 15>(A, s);
+    case 3: return launch_bwd_fixed_r<KIND, 3, STORED>(A, s);
+    case 5: return launch_bwd_fixed_r<KIND, 5, STORED>(A, s);
+    case 9: return launch_bwd_fixed_r<KIND, 9, STORED>(A, s);
+    case 15: return launch_bwd_fixed_r<KIND, 15, STORED>(A, s);
     default: return BF_ERR_UNSUPPORTED;
   }
 }
@@ -703,8 +786,10 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // The reduction sums exactly the partials of the grid that was launched.
   int ctas = 0;
-  if (!abar && bwd_fixed_radius(A.fc.R)) {
-    st = A.fc.kind == BF_SPATIAL_GAUSS ? launch_bwd_fixed<1>(A, s) : launch_bwd_fixed<0>(A, s);
+  if (bwd_fixed_radius(A.fc.R)) {
+    const bool g = A.fc.kind == BF_SPATIAL_GAUSS;
+    if (abar) st = g ? launch_bwd_fixed<1, true>(A, s) : launch_bwd_fixed<0, true>(A, s);
+    else st = g ? launch_bwd_fixed<1, false>(A, s) : launch_bwd_fixed<0, false>(A, s);
     const int TWf = kBwdFixedNT - 2 * A.fc.R;
     ctas = ((width + TWf - 1) / TWf) * ((height + kBwdFixedTH - 1) / kBwdFixedTH);
   } else {

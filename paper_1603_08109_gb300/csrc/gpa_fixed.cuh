@@ -10,7 +10,11 @@
 //    kernel's parameter block), with no shared-memory loads;
 //  - the shared rows are padded so that no index needs clamping.
 // Phase V also copies the TH centre rows of a_n to shared memory (sC) for the
-// recombination in phase H.
+// recombination in phase H.  With STORE, each channel's w * a_n (normalised)
+// also goes to plane n of io.abar for the stored-plane backward: staged in sV
+// once phase H is done reading it, then written row by row so that a warp
+// stores 32 consecutive floats (a thread's own KH columns would scatter one
+// store instruction over 32 rows and segments).
 //
 // The kernel is persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...
 // and copies the next tile's region (f) into a second shared buffer with
@@ -70,7 +74,7 @@ __device__ __forceinline__ void prefetch_region(const TileIO &io, int ty0, int t
   }
 }
 
-template <int KIND, int R, int NT, int TH>
+template <int KIND, int R, int NT, int TH, bool STORE>
 __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::FilterConsts &fc,
                                                    int ty0, int tx0, float *sH, float *sV,
                                                    float *sC, const float2 *sRS) {
@@ -141,8 +145,8 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
     __syncthreads();
 
     // ---------------- phase H: horizontal pass + recombination
+    float Ab[KH];
     if (hact) {
-      float Ab[KH];
       if (KIND == BF_SPATIAL_GAUSS) {
         float win[KH];
 #pragma unroll
@@ -180,6 +184,20 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
         ap[k] = av;
       }
     }
+    if (STORE) {
+      __syncthreads();  // every thread is done reading sV for this channel
+      if (hact) {
+#pragma unroll
+        for (int k = 0; k < KH; ++k) sV[hy * VP + hx0 + k] = Ab[k] * fc.qscale;
+      }
+      __syncthreads();
+      if (c < min(TW, io.W - tx0)) {
+        float *dst = io.abar + (long long)n * io.plane_stride + tx0 + c;
+#pragma unroll
+        for (int y = 0; y < TH; ++y)
+          if (ty0 + y < io.H) dst[(long long)(ty0 + y) * io.pitch] = sV[y * VP + c];
+      }
+    }
   }
 
   // ---- epilogue: f_GPA = t_c + sigma_r P'/Q', staged in sV / sC, stored row-wise
@@ -206,7 +224,7 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
 
 // Persistent driver: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // (row-major over the tile grid), double-buffered region copies.
-template <int KIND, int R, int NT, int TH>
+template <int KIND, int R, int NT, int TH, bool STORE>
 __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
                                                          const bfi::FilterConsts &fc, float *smem) {
   using G = FixedGeom<R, NT, TH>;
@@ -237,7 +255,7 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
     } else {
       cp_async_wait<0>();
     }
-    gpa_fwd_tile_fixed<KIND, R, NT, TH>(io, fc, (t / ntx) * TH, (t % ntx) * G::TW, cur, sV, sC,
+    gpa_fwd_tile_fixed<KIND, R, NT, TH, STORE>(io, fc, (t / ntx) * TH, (t % ntx) * G::TW, cur, sV, sC,
                                         sRS);
     buf ^= 1;
   }

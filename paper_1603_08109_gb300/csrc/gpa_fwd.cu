@@ -27,10 +27,10 @@ __global__ void __launch_bounds__(NT) gpa_fwd_kernel(const __grid_constant__ Fwd
 
 // Compile-time-radius kernel (gpa_fixed.cuh): persistent, 256 threads,
 // 16-row tiles, double-buffered region copies.
-template <int KIND, int R>
+template <int KIND, int R, bool STORE>
 __global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constant__ FwdArgs args) {
   extern __shared__ __align__(16) float smem[];
-  bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16>(args.io, args.fc, smem);
+  bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16, STORE>(args.io, args.fc, smem);
 }
 
 // Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid
 
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
 // columns, output rows per tile).  Variant 5: the compile-time-radius kernel
-// for the radii in kFixedRadii (forward without stored planes only).
+// for the radii in kFixedRadii (with or without stored planes).
 // Variants 6 and 7: the warp-strip streaming box kernel (box, W in {3, 5})
 // with 8 columns per lane (N <= 5) and 4 columns per lane (N <= 8; fewer
 // registers per channel).
@@ -82,7 +82,7 @@ int max_smem_optin() {
 }
 
 bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
-  if (v == kFixedVariant) return !store && fixed_radius(fc.R);
+  if (v == kFixedVariant) return fixed_radius(fc.R);
   if (v == kStreamVariant) return !store && stream_fits(fc, 5);
   if (v == kStream4Variant) return !store && stream_fits(fc, 8);
   const Variant &var = kVariants[v];
@@ -104,11 +104,11 @@ int default_variant(const bfi::FilterConsts &fc, bool store) {
   return -1;
 }
 
-template <int KIND, int R>
+template <int KIND, int R, bool STORE>
 bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   using G = bfk::FixedGeom<R, 256, 16>;
   const size_t smem = G::smem_bytes(args.fc.N);
-  auto kern = gpa_fwd_fixed_kernel<KIND, R>;
+  auto kern = gpa_fwd_fixed_kernel<KIND, R, STORE>;
   const void *fn = reinterpret_cast<const void *>(kern);
   bf_status st = bfi::ensure_smem(fn, G::smem_bytes(BF_MAX_ORDER));
   int resident = 0;  // resident CTAs (SMs x CTAs per SM) at this shared-memory size
@@ -200,13 +200,13 @@ bf_status launch_warp(const FwdArgs &a, cudaStream_t s) {
   return BF_ERR_UNSUPPORTED;
 }
 
-template <int KIND>
+template <int KIND, bool STORE>
 bf_status launch_fixed(const FwdArgs &a, cudaStream_t s) {
   switch (a.fc.R) {
-    case 3: return launch_fixed_r<KIND, 3>(a, s);
-    case 5: return launch_fixed_r<KIND, 5>(a, s);
-    case 9: return launch_fixed_r<KIND, 9>(a, s);
-    case 15: return launch_fixed_r<KIND, 15>(a, s);
+    case 3: return launch_fixed_r<KIND, 3, STORE>(a, s);
+    case 5: return launch_fixed_r<KIND, 5, STORE>(a, s);
+    case 9: return launch_fixed_r<KIND, 9, STORE>(a, s);
+    case 15: return launch_fixed_r<KIND, 15, STORE>(a, s);
     default: return BF_ERR_UNSUPPORTED;
   }
 }
@@ -226,10 +226,7 @@ bf_status launch_fwd(const FwdArgs &args, cudaStream_t s) {
 template <bool STORE>
 bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
   const bool g = a.fc.kind == BF_SPATIAL_GAUSS;
-  if (v == kFixedVariant) {
-    if (STORE) return BF_ERR_UNSUPPORTED;
-    return g ? launch_fixed<1>(a, s) : launch_fixed<0>(a, s);
-  }
+  if (v == kFixedVariant) return g ? launch_fixed<1, STORE>(a, s) : launch_fixed<0, STORE>(a, s);
   if (v == kStreamVariant || v == kStream4Variant) {
     if (STORE) return BF_ERR_UNSUPPORTED;
     return v == kStreamVariant ? launch_warp<8>(a, s) : launch_warp<4>(a, s);

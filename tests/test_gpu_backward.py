@@ -49,11 +49,40 @@ def test_fast_backward_matches_exact_derivatives(case):
     rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
     assert _rel(gin, rgin) <= GIN_RTOL
     assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs)
-    # stored planes (runtime-radius kernel) vs recompute (possibly the
-    # compile-time-radius kernel with re-associated sums): same math, float32
+    # stored planes vs recompute: same math, float32 (for radii 3, 5, 9, 15 both
+    # run the compile-time-radius kernels; otherwise the stored planes go
+    # through the runtime-radius kernel and the sums are associated differently)
     gin2, gs2 = _fast_grads(img, g, kind, r, ss, sr, N, store=True)
     assert _rel(gin2, gin) <= 1e-4
     assert abs(gs2 - gs) <= 1e-4 * abs(gs)
+    assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
+
+
+@pytest.mark.parametrize("case", [
+    (bf.GAUSS, 3, 1.0, 30.0, 37, (70, 301)),
+    (bf.GAUSS, 5, 5 / 3.0, 40.0, 25, (33, 250)),
+    (bf.GAUSS, 9, 3.0, 30.0, 40, (17, 229)),
+    (bf.GAUSS, 15, 5.0, 25.0, 54, (41, 200)),
+    (bf.BOX, 3, 0.0, 30.0, 41, (26, 127)),
+    (bf.BOX, 15, 0.0, 50.0, 22, (9, 333)),
+], ids=lambda c: "k%d_r%d" % (c[0], c[1]))
+def test_stored_fixed_radius_backward(case):
+    """The stored-plane pair at the compile-time radii: the forward stages each
+    plane through shared memory and writes whole rows, the backward copies
+    each channel's plane block into shared memory and filters only the
+    adjoint seeds.  Images several tiles wide (238 and 110 output columns per
+    tile) and tall with ragged edges; gradients against recompute (the same
+    arithmetic: bitwise for the Gaussian, within the plane normalisation's
+    rounding for the box) and against the checker's exact derivatives."""
+    kind, r, ss, sr, N, (H, W) = case
+    img = image(H, W, seed=H * 13 + W)
+    g = synth.random_like((H, W), seed=H * W)
+    gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+    gin2, gs2 = _fast_grads(img, g, kind, r, ss, sr, N, store=True)
+    assert _rel(gin2, gin) <= 1e-5
+    assert abs(gs2 - gs) <= 1e-5 * abs(gs)
+    rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
+    assert _rel(gin2, rgin) <= GIN_RTOL
     assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
 
 

@@ -159,11 +159,16 @@ def test_pitched_input_and_cpu_tensor_roundtrip():
     assert torch.equal(out_cpu, out.cpu())
 
 
-def test_stored_planes_match_filtered_images():
+@pytest.mark.parametrize("kind,r,ss,shape", [(bf.GAUSS, 6, 2.0, (40, 280)),
+                                              (bf.GAUSS, 9, 3.0, (37, 500)),
+                                              (bf.BOX, 5, 0.0, (19, 250))])
+def test_stored_planes_match_filtered_images(kind, r, ss, shape):
     """bf_fast_forward_stored plane n = Fbar_n / sqrt(n!) (the rescaled
-    filtered image of Algorithm 2), and out is bitwise the plain forward's."""
-    img = image(40, 280, seed=31)
-    kind, r, ss, sr, N = bf.GAUSS, 6, 2.0, 30.0, 30
+    filtered image of Algorithm 2), and out is bitwise the plain forward's:
+    the runtime-radius kernel (radius 6) and the compile-time-radius kernel
+    with its row-wise staged plane stores (radii 9 and 5, several tiles)."""
+    img = image(*shape, seed=31 + r)
+    sr, N = 30.0, 30
     w = spatial(kind, r, ss)
     _, _, _, planes = oracle.gpa_alg2(img, w, sr, N, return_parts=True, return_planes=True)
     x = torch.from_numpy(img).cuda()
