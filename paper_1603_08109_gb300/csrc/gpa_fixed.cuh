@@ -27,6 +27,10 @@
 
 namespace bfk {
 
+// Gaussian tap pairs for the vertical pass over pairs of output rows:
+// tap2[k] = (w[k], w[k - 1]), w[-1] = w[L] = 0, k = 0 .. L (L <= 31).
+constexpr int kTap2 = 32;
+
 template <int R, int NT, int TH>
 struct FixedGeom {
   static constexpr int RH = TH + 2 * R;
@@ -76,8 +80,8 @@ __device__ __forceinline__ void prefetch_region(const TileIO &io, int ty0, int t
 
 template <int KIND, int R, int NT, int TH, bool STORE>
 __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::FilterConsts &fc,
-                                                   int ty0, int tx0, float *sH, float *sV,
-                                                   float *sC, const float2 *sRS) {
+                                                   const float2 *tap2, int ty0, int tx0, float *sH,
+                                                   float *sV, float *sC, const float2 *sRS) {
   using G = FixedGeom<R, NT, TH>;
   constexpr int RH = G::RH, TW = G::TW, KH = G::KH, L = G::L, VP = G::VP;
   static_assert(TW >= KH, "tile too narrow for this radius");
@@ -124,12 +128,26 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
 #pragma unroll
     for (int y = 0; y < TH; ++y) sC[y * VP + c] = a[y + R];
     if (KIND == BF_SPATIAL_GAUSS) {
+      // rows (y, y + 1) as one packed pair: (acc_y, acc_y+1) += (w[r-y], w[r-y-1]) a_r,
+      // taps in ascending order per row as in the scalar sum (the extra terms
+      // have weight 0 and leave each sum unchanged)
+      static_assert(TH % 2 == 0 && L + 1 <= kTap2, "row pairs");
+      float2 acc[TH / 2];
 #pragma unroll
-      for (int y = 0; y < TH; ++y) {
-        float acc = 0.f;
+      for (int p = 0; p < TH / 2; ++p) acc[p] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int t = 0; t < L; ++t) acc = fmaf(fc.taps[t], a[y + t], acc);
-        sV[y * VP + c] = acc;
+      for (int r = 0; r < RH; ++r) {
+        const float2 ar = make_float2(a[r], a[r]);
+#pragma unroll
+        for (int p = 0; p < TH / 2; ++p) {
+          const int t = r - 2 * p;
+          if (t >= 0 && t <= L) acc[p] = __ffma2_rn(tap2[t >= 0 && t <= L ? t : 0], ar, acc[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < TH / 2; ++p) {
+        sV[2 * p * VP + c] = acc[p].x;
+        sV[(2 * p + 1) * VP + c] = acc[p].y;
       }
     } else {
       float s = 0.f;
@@ -148,18 +166,27 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
     float Ab[KH];
     if (hact) {
       if (KIND == BF_SPATIAL_GAUSS) {
-        float win[KH];
+        // columns (i, i + 1) as one packed pair, element by element of the
+        // window: (Ab_i, Ab_i+1) += (w[e-i], w[e-i-1]) v_e, each sum in
+        // ascending tap order as in the scalar form
+        static_assert(KH % 2 == 0, "column pairs");
+        float2 ab[KH / 2];
 #pragma unroll
-        for (int i = 0; i < KH; ++i) {
-          Ab[i] = 0.f;
-          win[i] = vrow[i];
+        for (int p = 0; p < KH / 2; ++p) ab[p] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < KH + 2 * R; ++e) {
+          const float v = vrow[e];
+          const float2 vv = make_float2(v, v);
+#pragma unroll
+          for (int p = 0; p < KH / 2; ++p) {
+            const int t = e - 2 * p;
+            if (t >= 0 && t <= L) ab[p] = __ffma2_rn(tap2[t >= 0 && t <= L ? t : 0], vv, ab[p]);
+          }
         }
 #pragma unroll
-        for (int t = 0; t < L; ++t) {
-          const float w = fc.taps[t];
-#pragma unroll
-          for (int i = 0; i < KH; ++i) Ab[i] = fmaf(w, win[(t + i) % KH], Ab[i]);
-          win[t % KH] = vrow[t + KH];
+        for (int p = 0; p < KH / 2; ++p) {
+          Ab[2 * p] = ab[p].x;
+          Ab[2 * p + 1] = ab[p].y;
         }
       } else {
         float v[KH + 2 * R];
@@ -226,7 +253,8 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
 // (row-major over the tile grid), double-buffered region copies.
 template <int KIND, int R, int NT, int TH, bool STORE>
 __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
-                                                         const bfi::FilterConsts &fc, float *smem) {
+                                                         const bfi::FilterConsts &fc,
+                                                         const float2 *tap2, float *smem) {
   using G = FixedGeom<R, NT, TH>;
   float *sV = smem;
   float *sC = sV + TH * G::VP;
@@ -255,8 +283,8 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
     } else {
       cp_async_wait<0>();
     }
-    gpa_fwd_tile_fixed<KIND, R, NT, TH, STORE>(io, fc, (t / ntx) * TH, (t % ntx) * G::TW, cur, sV, sC,
-                                        sRS);
+    gpa_fwd_tile_fixed<KIND, R, NT, TH, STORE>(io, fc, tap2, (t / ntx) * TH, (t % ntx) * G::TW, cur,
+                                               sV, sC, sRS);
     buf ^= 1;
   }
 }

@@ -15,6 +15,7 @@ namespace {
 struct FwdArgs {
   bfk::TileIO io;
   bfi::FilterConsts fc;
+  float2 tap2[bfk::kTap2];  // compile-time-radius Gaussian: (w[k], w[k - 1]) pairs
 };
 
 template <int KIND, int NT, int TH, bool STORE>
@@ -28,9 +29,9 @@ __global__ void __launch_bounds__(NT) gpa_fwd_kernel(const __grid_constant__ Fwd
 // Compile-time-radius kernel (gpa_fixed.cuh): persistent, 256 threads,
 // 16-row tiles, double-buffered region copies.
 template <int KIND, int R, bool STORE>
-__global__ void __launch_bounds__(256) gpa_fwd_fixed_kernel(const __grid_constant__ FwdArgs args) {
+__global__ void __launch_bounds__(256, 2) gpa_fwd_fixed_kernel(const __grid_constant__ FwdArgs args) {
   extern __shared__ __align__(16) float smem[];
-  bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16, STORE>(args.io, args.fc, smem);
+  bfk::gpa_fwd_fixed_persistent<KIND, R, 256, 16, STORE>(args.io, args.fc, args.tap2, smem);
 }
 
 // Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of
@@ -118,7 +119,11 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   const long long tiles = (long long)((args.io.W + G::TW - 1) / G::TW) * ((args.io.H + 15) / 16);
   if (tiles > 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
   const int grid = (int)std::min<long long>(tiles, resident);
-  kern<<<grid, 256, smem, s>>>(args);
+  FwdArgs a = args;
+  constexpr int L = 2 * R + 1;
+  for (int k = 0; k < bfk::kTap2; ++k)
+    a.tap2[k] = make_float2(k < L ? args.fc.taps[k] : 0.f, k >= 1 && k <= L ? args.fc.taps[k - 1] : 0.f);
+  kern<<<grid, 256, smem, s>>>(a);
   return bfi::check_launch();
 }
 
