@@ -38,6 +38,16 @@ UNIT = "Mpixel/s"
 WORKLOAD = ("2048x2048 blocks(64)+N(0,10^2) image; Gaussian spatial sigma_s=3 (W=9), "
             "sigma_r=30, N=40 (bound for delta=1); step = fused forward + fused backward "
             "(image and sigma_r gradients)")
+
+
+def workload(S, kind, R, ss, sr, N, only):
+    """The workload text of a run (the default run's is WORKLOAD)."""
+    spatial = ("Gaussian spatial sigma_s=%g (W=%d)" % (ss, R) if kind == 1
+               else "box spatial W=%d" % R)
+    step = {"all": "fused forward + fused backward (image and sigma_r gradients)",
+            "fwd": "fused forward", "bwd": "fused backward (image and sigma_r gradients)"}[only]
+    return "%dx%d blocks(64)+N(0,10^2) image; %s, sigma_r=%g, N=%d; step = %s" % (
+        S, S, spatial, sr, N, step)
 L2_NOTE = "L2 flushed between timed steps (512 MB write, outside the per-step events)"
 FIXED_RADII = (3, 5, 9, 15)  # radii with compile-time-specialised kernels
 
@@ -981,7 +991,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "image": "%dx%d" % (S, S),
+            "config": {"workload": (WORKLOAD if (S, kind, R, ss, sr, N, args.only) ==
+                                    (2048, 1, 9, 3.0, 30.0, 40, "all")
+                                    else workload(S, kind, R, ss, sr, N, args.only)),
+                       "image": "%dx%d" % (S, S),
                        "kind": "gaussian" if kind == 1 else "box", "radius": R, "sigma_s": ss,
                        "sigma_r": sr, "N": N, "only": args.only, "l2": L2_NOTE,
                        "parallelism": "dp%d (one image per rank)" % world},
