@@ -224,12 +224,17 @@ __global__ void __launch_bounds__(NT) joint_kernel(const __grid_constant__ Joint
 // tiles; each column thread keeps its RH = 8 + 2W guide power images b_n in
 // registers, (E, f~) of the region stay in shared memory, Gaussian taps are
 // constant-bank FMA operands; phase V writes the centre rows of b_n for the
-// recombination.
+// recombination.  The two filterings of a channel (b_n and b_n f~ share
+// every tap) run as one filtering of the pair with the packed two-lane FP32
+// instructions (each lane rounded exactly as the scalar operation), and the
+// recombination updates (Q', U') as a pair.
 template <int R>
 struct JointFixedGeom {
   static constexpr int NT = 128, TH = 8, KH = 8;
   static constexpr int RH = TH + 2 * R, TW = NT - 2 * R, L = 2 * R + 1;
-  static constexpr int VP = NT + 33;  // 1 (mod 32): the 4 x 8 phase-H lanes of a warp use 32 banks
+  // 1 (mod 32): the 4 x 8 phase-H lanes read distinct bank pairs of the
+  // (b, c) rows (per half-warp) and distinct banks of the b_n centre rows
+  static constexpr int VP = NT + 33;
   static constexpr size_t smem_bytes() {
     return (size_t)3 * TH * VP * sizeof(float) + (size_t)RH * NT * sizeof(float2);
   }
@@ -244,7 +249,8 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
   const bfi::FilterConsts &fc = A.fc;
   const int N = fc.N;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-  float *sVb = smem, *sVc = sVb + TH * VP, *sCb = sVc + TH * VP;
+  float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (b_n, b_n f~)
+  float *sCb = smem + 2 * TH * VP;                // TH x VP: b_n of the centre rows
   float2 *sEF = reinterpret_cast<float2 *>(sCb + TH * VP);  // (E, f - t_c)
   const int c = threadIdx.x;
   float b[RH];
@@ -267,18 +273,18 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
   }
   const int hy = c % TH, hx0 = (c / TH) * KH;
   const bool hact = hx0 < TW;
-  float Q[KH], U[KH];
+  float2 QU[KH];  // (Q', U')
 #pragma unroll
-  for (int k = 0; k < KH; ++k) Q[k] = U[k] = 0.f;
-  const float *rb = sVb + hy * VP + hx0, *rc = sVc + hy * VP + hx0;
+  for (int k = 0; k < KH; ++k) QU[k] = make_float2(0.f, 0.f);
+  const float2 *rv = sV + hy * VP + hx0;
   const float *cb = sCb + hy * VP + R + hx0;
 
   for (int n = 0; n < N; ++n) {
     const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
     __syncthreads();
-    float ab[TH], ac[TH];
+    float2 acc[TH];  // (b_n, b_n f~) of the TH output rows
 #pragma unroll
-    for (int y = 0; y < TH; ++y) ab[y] = ac[y] = 0.f;
+    for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
     float cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
@@ -287,11 +293,12 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
       const float cn = b[r] * ef.y;
       if (r >= R && r < R + TH) sCb[(r - R) * VP + c] = b[r];
       if (KIND == BF_SPATIAL_GAUSS) {
+        const float2 bc = make_float2(b[r], cn);
 #pragma unroll
         for (int y = 0; y < TH; ++y) {
           if (r - y >= 0 && r - y < L) {
-            ab[y] = fmaf(fc.taps[r - y], b[r], ab[y]);
-            ac[y] = fmaf(fc.taps[r - y], cn, ac[y]);
+            const float w = fc.taps[r - y];
+            acc[y] = __ffma2_rn(make_float2(w, w), bc, acc[y]);
           }
         }
       } else {
@@ -305,49 +312,39 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
         sb += b[r];
         sc += cbox[KIND == BF_SPATIAL_BOX ? r : 0];
       }
-      ab[0] = sb;
-      ac[0] = sc;
+      acc[0] = make_float2(sb, sc);
 #pragma unroll
       for (int y = 1; y < TH; ++y) {
         sb += b[y + 2 * R] - b[y - 1];
         sc += cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0] - cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
-        ab[y] = sb;
-        ac[y] = sc;
+        acc[y] = make_float2(sb, sc);
       }
     }
 #pragma unroll
-    for (int y = 0; y < TH; ++y) {
-      sVb[y * VP + c] = ab[y];
-      sVc[y * VP + c] = ac[y];
-    }
+    for (int y = 0; y < TH; ++y) sV[y * VP + c] = acc[y];
     __syncthreads();
     if (hact) {
-      float Bb[KH], Cb[KH];
+      float2 BC[KH];  // (w * b_n, w * (b_n f~)) of the item's KH columns
       if (KIND == BF_SPATIAL_GAUSS) {
-        float wb[KH], wc[KH];
+        float2 win[KH];
 #pragma unroll
         for (int i = 0; i < KH; ++i) {
-          Bb[i] = Cb[i] = 0.f;
-          wb[i] = rb[i];
-          wc[i] = rc[i];
+          BC[i] = make_float2(0.f, 0.f);
+          win[i] = rv[i];
         }
 #pragma unroll
         for (int t = 0; t < L; ++t) {
           const float w = fc.taps[t];
 #pragma unroll
-          for (int i = 0; i < KH; ++i) {
-            Bb[i] = fmaf(w, wb[(t + i) % KH], Bb[i]);
-            Cb[i] = fmaf(w, wc[(t + i) % KH], Cb[i]);
-          }
-          wb[t % KH] = rb[t + KH];
-          wc[t % KH] = rc[t + KH];
+          for (int i = 0; i < KH; ++i) BC[i] = __ffma2_rn(make_float2(w, w), win[(t + i) % KH], BC[i]);
+          win[t % KH] = rv[t + KH];
         }
       } else {
         float vb[KH + 2 * R], vc[KH + 2 * R];
 #pragma unroll
         for (int i = 0; i < KH + 2 * R; ++i) {
-          vb[i] = rb[i];
-          vc[i] = rc[i];
+          vb[i] = rv[i].x;
+          vc[i] = rv[i].y;
         }
         float sb = 0.f, sc = 0.f;
 #pragma unroll
@@ -355,21 +352,18 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
           sb += vb[i];
           sc += vc[i];
         }
-        Bb[0] = sb;
-        Cb[0] = sc;
+        BC[0] = make_float2(sb, sc);
 #pragma unroll
         for (int j = 1; j < KH; ++j) {
           sb += vb[j + 2 * R] - vb[j - 1];
           sc += vc[j + 2 * R] - vc[j - 1];
-          Bb[j] = sb;
-          Cb[j] = sc;
+          BC[j] = make_float2(sb, sc);
         }
       }
 #pragma unroll
       for (int k = 0; k < KH; ++k) {
-        const float bc = cb[k];
-        Q[k] = fmaf(bc, Bb[k], Q[k]);
-        U[k] = fmaf(bc, Cb[k], U[k]);
+        const float bk = cb[k];
+        QU[k] = __ffma2_rn(make_float2(bk, bk), BC[k], QU[k]);
       }
     }
   }
@@ -380,8 +374,8 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
       for (int k = 0; k < KH; ++k) {
         const int gx = tx0 + hx0 + k;
         if (hx0 + k < TW && gx < A.W) {
-          A.out[(long long)gy * A.pitch + gx] = fc.tc + U[k] / Q[k];
-          if (A.qaux) A.qaux[(long long)gy * A.pitch + gx] = Q[k] * fc.qscale;
+          A.out[(long long)gy * A.pitch + gx] = fc.tc + QU[k].y / QU[k].x;
+          if (A.qaux) A.qaux[(long long)gy * A.pitch + gx] = QU[k].x * fc.qscale;
         }
       }
     }
