@@ -432,7 +432,25 @@ def run_sweeps(args):
                       "kind": "box", "radius": R, "sigma_r": 40.0, "N": N, "fwd_ms": fms,
                       "fwd_mpx_s": px / fms / 1e3, "algorithmic_gbs": gbs,
                       "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src})
+        # the same 8 images as one batch (bf_fast_forward_many): one launch of the
+        # warp-strip kernel for all of them; per-image time = batch time / 8
+        xb = torch.stack(xs)
+        ob = torch.empty_like(xb)
         del xs, os_
+        cms = _time_ms(lambda: ob.copy_(xb), 5, stream, flush) / K
+        emit({"sweep": "roofline4096", "timing": "one call for a batch of 8", "kernel":
+              "torch copy (reference)", "ms": cms, "gbs": 8 * px / cms / 1e6,
+              "frac_of_measured_hbm": 8 * px / cms / 1e6 / hbm_peak})
+        for R in (3, 5):
+            for N in (1, 2, 3):
+                fms = _time_ms(lambda: bf.gpa_forward_many(xb, bf.BOX, 40.0, N, radius=R, out=ob),
+                               5, stream, flush) / K
+                gbs = 8 * px / fms / 1e6
+                emit({"sweep": "roofline4096", "timing": "one call for a batch of 8",
+                      "kind": "box", "radius": R, "sigma_r": 40.0, "N": N, "fwd_ms": fms,
+                      "fwd_mpx_s": px / fms / 1e3, "algorithmic_gbs": gbs,
+                      "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src})
+        del xb, ob
         torch.cuda.empty_cache()
         # the same generator at 8192^2: the small-N box forward past the launch ramp and tail
         x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)

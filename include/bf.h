@@ -164,6 +164,20 @@ bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux,
                              int height, int width, int pitch, const bf_params *p,
                              void *d_workspace, size_t ws_bytes, void *stream);
 
+/* bf_fast_forward for `count` images of the same height, width, pitch and
+ * parameters (e.g. the frames of a video): image k is read from
+ * d_in + k * image_stride and written to d_out (and d_qaux, if not NULL)
+ * + k * image_stride; image_stride >= height * pitch (elements), and the
+ * input and output blocks must not overlap.  Each image is filtered on its
+ * own (zero extension at its edges), with the same results as bf_fast_forward
+ * image by image.  The warp-strip box kernel (box, W in {3, 5}, N <= 8) takes
+ * the whole batch in one launch, which amortises its ramp-up and tail over
+ * the batch; the other kernels run one launch per image.
+ * BF_ERR_INVALID_ARG for count < 1 or a smaller image_stride. */
+bf_status bf_fast_forward_many(const float *d_in, float *d_out, float *d_qaux, int count,
+                               size_t image_stride, int height, int width, int pitch,
+                               const bf_params *p, void *stream);
+
 /* Same as bf_fast_forward, and also stores the N+1 filtered power images
  * w * a_n (normalised kernel) to d_abar: plane n at d_abar + n * plane_stride,
  * each plane height x width with row pitch `pitch`; plane_stride >=

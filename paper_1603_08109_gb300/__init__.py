@@ -11,7 +11,7 @@ signatures), ``build`` (nvcc), ``synth`` (seeded synthetic inputs).
 from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
                   centre_weight, direct, direct_backward, direct_bilateral, gpa_backward,
                   exhaustive_order, forward_workspace_bytes, gpa_bilateral, gpa_forward,
-                  gpa_forward_stored, joint_direct,
+                  gpa_forward_many, gpa_forward_stored, joint_direct,
                   joint_forward, kernel_error_max, order_bucket, order_estimates, order_from_delta,
                   radius_bucket, RecursiveBilateral, recursive_backward,
                   recursive_backward_workspace_bytes, recursive_bilateral, recursive_joint_forward,
@@ -19,4 +19,4 @@ from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABi
                   recursive_forward_stored, recursive_backward_stored,
                   resolve_radius, tuning_get, tuning_set, variant_count)
 
-__version__ = "1.2.0"
+__version__ = "1.3.0"

@@ -24,7 +24,7 @@ __all__ = [
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
     "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
     "recursive_bilateral", "recursive_joint_forward", "recursive_forward_stored",
-    "recursive_backward_stored",
+    "recursive_backward_stored", "gpa_forward_many",
 ]
 
 
@@ -328,6 +328,29 @@ def recursive_backward(img, out, q, gout, sigma_r: float, N: int, sigma_s: float
              ctypes.byref(p), _ptr(ws), ws.numel() * ws.element_size(), _stream(x.device)),
           "bf_recursive_backward_stored" if stored else "bf_recursive_backward")
     return gin, gs
+
+
+def gpa_forward_many(imgs: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
+                     sigma_s: float = 0.0, t_c: float = 128.0, return_q: bool = False,
+                     out: Optional[torch.Tensor] = None):
+    """f_GPA of each image of a (B, H, W) CUDA tensor (same parameters, e.g.
+    video frames) through bf_fast_forward_many: one launch for the whole batch
+    on the warp-strip box kernel, one per image otherwise.  Returns out, or
+    (out, Q')."""
+    if imgs.dim() != 3 or imgs.device.type != "cuda":
+        raise ValueError("imgs must be a (B, H, W) CUDA tensor")
+    x = imgs.to(torch.float32)
+    if x.stride(2) != 1 or x.stride(0) < x.shape[1] * x.stride(1):
+        x = x.contiguous()
+    B, H, W = x.shape
+    if out is None or out.shape != x.shape or out.stride() != x.stride() or out.dtype != torch.float32:
+        out = torch.empty_strided(x.shape, x.stride(), dtype=torch.float32, device=x.device)
+    q = torch.empty_strided(x.shape, x.stride(), dtype=torch.float32, device=x.device) if return_q else None
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_fast_forward_many(_ptr(x), _ptr(out), _ptr(q), B, ctypes.c_size_t(x.stride(0)), H, W,
+                                     x.stride(1), ctypes.byref(p), _stream(x.device)),
+          "bf_fast_forward_many")
+    return (out, q) if return_q else out
 
 
 def gpa_forward_stored(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,

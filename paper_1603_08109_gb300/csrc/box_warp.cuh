@@ -48,6 +48,8 @@ struct WarpStripArgs {
   float inv_n[12];  // 1 / n (entry 0 unused)
   int band;         // output rows per warp (even)
   int nstrips, nbands;
+  int nimg;               // images of the same size and parameters
+  long long img_stride;   // elements from one image (in, out, Q') to the next
   int vec_in;       // input rows 16-byte aligned: 16-byte copies
   int vec_out;      // out (and Q') rows 16-byte aligned: 16-byte stores
 };
@@ -175,7 +177,7 @@ template <int R, int NN, int C, bool FULL>
 __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst &K,
                                            const float2 (&V)[NN][C / 2],
                                            const float2 (&fc)[C / 2], int yo, int x0,
-                                           bool store) {
+                                           bool store, long long off) {
   constexpr int N = NN - 1, NP = C / 2;
   float2 H[NP], Pa[NP], Qa[NP];
 #pragma unroll
@@ -204,7 +206,7 @@ __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst
     const float2 r = __fmul2_rn(Pa[p], make_float2(ws_rcp(Qa[p].x), ws_rcp(Qa[p].y)));
     o[p] = __ffma2_rn(f2(A.sr), r, f2(A.tc));
   }
-  float *orow = io.out + (long long)yo * io.pitch + x0;
+  float *orow = io.out + off + (long long)yo * io.pitch + x0;
   const bool full = FULL || (A.vec_out && x0 + C <= io.W);
   if (full) {
 #pragma unroll
@@ -220,7 +222,7 @@ __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst
     float2 q[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) q[p] = __fmul2_rn(__fmul2_rn(ws_u0(K, fc[p]), Qa[p]), f2(A.qscale));
-    float *qrow = io.qaux + (long long)yo * io.pitch + x0;
+    float *qrow = io.qaux + off + (long long)yo * io.pitch + x0;
     if (full) {
 #pragma unroll
       for (int j = 0; j < C / 4; ++j)
@@ -238,14 +240,15 @@ __device__ __forceinline__ void ws_row_out(const WarpStripArgs &A, const WsConst
 // every lane's C columns are inside the image with 16-byte aligned rows.
 template <int R, int NN, int DP, int C, bool FAST>
 __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K, float *my,
-                                        int x0, int yo0, int yo1, int cnt0, int cnt1) {
+                                        int x0, int yo0, int yo1, int cnt0, int cnt1,
+                                        long long off) {
   using G = WarpStripGeom<R, DP, C>;
   constexpr int SW = G::SW, L = G::L, RS = G::RS, NP = C / 2, HL = G::HL;
   const TileIO &io = A.io;
   const bool vec0 = FAST || (A.vec_in && cnt0 == 4), vec1 = FAST || (A.vec_in && cnt1 == 4);
   auto issue = [&](int y, int slot) {
     if (FAST || (y >= 0 && y < io.H)) {
-      const float *src = io.in + (long long)y * io.pitch + x0;
+      const float *src = io.in + off + (long long)y * io.pitch + x0;
       float *dst = my + slot * SW;
       if (vec0) {
         cp_async16(dst, src);
@@ -309,22 +312,23 @@ __device__ __forceinline__ void ws_band(const WarpStripArgs &A, const WsConst &K
       // when rho >= L)
       if (FAST || y < io.H) ws_update<NN, NP, true>(K, V, fe0);
       if (rho >= L && (FAST || y - L >= 0)) ws_update<NN, NP, false>(K, V, fl0);
-      ws_row_out<R, NN, C, FAST>(A, K, V, fc0, yo, x0, writer);
+      ws_row_out<R, NN, C, FAST>(A, K, V, fc0, yo, x0, writer, off);
       if (FAST || y + 1 < io.H) ws_update<NN, NP, true>(K, V, fe1);
       if (FAST || y + 1 - L >= 0) ws_update<NN, NP, false>(K, V, fl1);
-      ws_row_out<R, NN, C, FAST>(A, K, V, fc1, yo + 1, x0, writer && yo + 1 < yo1);
+      ws_row_out<R, NN, C, FAST>(A, K, V, fc1, yo + 1, x0, writer && yo + 1 < yo1, off);
     }
     s0 = wrap(s0 + 2);
   }
   cp_async_wait<0>();
 }
 
-// One warp: strip `strip` (TW output columns), band `band` (A.band output rows).
-// The warp's ring holds RS rows of SW floats, lane l's chunk j of a row at
-// offset 128 j + 4 l.
+// One warp: strip `strip` (TW output columns), band `band` (A.band output rows)
+// of the image whose in, out and Q' start `off` elements after io's.  The
+// warp's ring holds RS rows of SW floats, lane l's chunk j of a row at offset
+// 128 j + 4 l.
 template <int R, int NN, int DP = 1, int C = 8>
 __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip, int band,
-                                               float *ring) {
+                                               long long off, float *ring) {
   using G = WarpStripGeom<R, DP, C>;
   constexpr int SW = G::SW, RS = G::RS;
   static_assert(R >= 1 && R <= 8 && G::HL <= 2, "the halo comes from at most two lanes");
@@ -354,9 +358,9 @@ __device__ __forceinline__ void box_warp_strip(const WarpStripArgs &A, int strip
   const bool fast = __all_sync(0xffffffffu, rows_in && A.vec_in && A.vec_out && cnt0 == 4 &&
                                                 cnt1 == 4);
   if (fast)
-    ws_band<R, NN, DP, C, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, C, true>(A, K, my, x0, yo0, yo1, cnt0, cnt1, off);
   else
-    ws_band<R, NN, DP, C, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1);
+    ws_band<R, NN, DP, C, false>(A, K, my, x0, yo0, yo1, cnt0, cnt1, off);
 }
 
 }  // namespace bfk

@@ -16,6 +16,8 @@ struct FwdArgs {
   bfk::TileIO io;
   bfi::FilterConsts fc;
   float2 tap2[bfk::kTap2];  // compile-time-radius Gaussian: (w[k], w[k - 1]) pairs
+  int count = 1;            // images (same size and parameters), image_stride apart
+  long long image_stride = 0;
 };
 
 template <int KIND, int NT, int TH, bool STORE>
@@ -43,9 +45,11 @@ __global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid
   using G = bfk::WarpStripGeom<R, 1, C>;
   const int w = threadIdx.x >> 5;
   const int wid = blockIdx.x * kWarpWPB + w;
-  const int strip = wid % A.nstrips, band = wid / A.nstrips;
-  if (band >= A.nbands) return;
-  bfk::box_warp_strip<R, NN, 1, C>(A, strip, band, smem + w * G::warp_floats);
+  const int strip = wid % A.nstrips, rest = wid / A.nstrips;
+  const int band = rest % A.nbands, img = rest / A.nbands;
+  if (img >= A.nimg) return;
+  bfk::box_warp_strip<R, NN, 1, C>(A, strip, band, (long long)img * A.img_stride,
+                                   smem + w * G::warp_floats);
 }
 
 // Tile variants 0..4: runtime-radius kernel, (threads per CTA = region
@@ -132,7 +136,8 @@ bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
 // N in {1, 3}): with 8 columns per lane (14-16 resident warps per SM) about
 // one wave of warps, or half a wave for N <= 2, is fastest; with 4 columns
 // per lane (20-28 resident warps per SM) short bands filling two or more
-// waves are fastest, the warm-up rows being mostly L2 hits.
+// waves are fastest, the warm-up rows being mostly L2 hits.  A batch of
+// images counts the rows of all of them (longer bands, fewer warm-up rows).
 template <int R, int NN, int C>
 bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   using G = bfk::WarpStripGeom<R, 1, C>;
@@ -161,16 +166,20 @@ bf_status launch_warp_rn(const FwdArgs &a, cudaStream_t s) {
   const bool in_al = (reinterpret_cast<uintptr_t>(a.io.in) & 15u) == 0;
   const bool out_al = (reinterpret_cast<uintptr_t>(a.io.out) & 15u) == 0;
   const bool q_al = !a.io.qaux || (reinterpret_cast<uintptr_t>(a.io.qaux) & 15u) == 0;
-  A.vec_in = (in_al && a.io.pitch % 4 == 0) ? 1 : 0;
-  A.vec_out = (out_al && q_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  const bool st_al = a.count == 1 || a.image_stride % 4 == 0;  // every image's rows 16-byte aligned
+  A.vec_in = (in_al && st_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  A.vec_out = (out_al && q_al && st_al && a.io.pitch % 4 == 0) ? 1 : 0;
+  A.nimg = a.count;
+  A.img_stride = a.image_stride;
   A.nstrips = (a.io.W + G::TW - 1) / G::TW;
   const long long per_strip = std::max(1, resident_warps / A.nstrips);
-  const long long one_wave = (a.io.H + per_strip - 1) / per_strip;  // band rows for one wave
+  const long long all_rows = (long long)a.io.H * a.count;
+  const long long one_wave = (all_rows + per_strip - 1) / per_strip;  // band rows for one wave
   const long long rows = C == 4 ? (one_wave + 1) / 2 : (NN <= 3 ? 2 : 1) * one_wave;
   const int band = (int)std::min<long long>(64, std::max<long long>(16, rows));
   A.band = (band + 1) & ~1;
   A.nbands = (a.io.H + A.band - 1) / A.band;
-  const long long warps = (long long)A.nstrips * A.nbands;
+  const long long warps = (long long)A.nstrips * A.nbands * A.nimg;
   const long long ctas = (warps + kWarpWPB - 1) / kWarpWPB;
   if (ctas > 0x7fffffffLL) return BF_ERR_UNSUPPORTED;
   kern<<<(int)ctas, 32 * kWarpWPB, smem, s>>>(A);
@@ -246,11 +255,16 @@ bf_status dispatch(int v, const FwdArgs &a, cudaStream_t s) {
   }
 }
 
+// count > 1: images k = 0 .. count - 1 at in / out / qaux + k image_stride
+// (same size and parameters); the warp-strip kernels take them in one launch,
+// the tile kernels in one launch per image.
 bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, size_t plane_stride,
                        int height, int width, int pitch, const bf_params *p, int variant,
-                       void *stream) {
+                       void *stream, int count = 1, size_t image_stride = 0) {
   bf_status st = bfi::check_image(in, out, height, width, pitch);
   if (st != BF_OK) return st;
+  if (count < 1 || (count > 1 && (abar || image_stride < (size_t)height * (size_t)pitch)))
+    return BF_ERR_INVALID_ARG;
   FwdArgs a;
   st = bfi::resolve(p, true, &a.fc);
   if (st != BF_OK) return st;
@@ -268,7 +282,21 @@ bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, si
     if (!variant_fits(v, a.fc, store)) return BF_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return abar ? dispatch<true>(v, a, s) : dispatch<false>(v, a, s);
+  if (abar) return dispatch<true>(v, a, s);
+  if (count == 1 || v == kStreamVariant || v == kStream4Variant) {
+    a.count = count;
+    a.image_stride = (long long)image_stride;
+    return dispatch<false>(v, a, s);
+  }
+  for (int k = 0; k < count; ++k) {
+    const size_t o = (size_t)k * image_stride;
+    a.io.in = in + o;
+    a.io.out = out + o;
+    a.io.qaux = qaux ? qaux + o : nullptr;
+    st = dispatch<false>(v, a, s);
+    if (st != BF_OK) return st;
+  }
+  return BF_OK;
 }
 
 }  // namespace
@@ -289,6 +317,13 @@ bf_status bf_fast_forward_variant(const float *d_in, float *d_out, float *d_qaux
                                   int width, int pitch, const bf_params *p, int variant,
                                   void *stream) {
   return forward_impl(d_in, d_out, d_qaux, nullptr, 0, height, width, pitch, p, variant, stream);
+}
+
+bf_status bf_fast_forward_many(const float *d_in, float *d_out, float *d_qaux, int count,
+                               size_t image_stride, int height, int width, int pitch,
+                               const bf_params *p, void *stream) {
+  return forward_impl(d_in, d_out, d_qaux, nullptr, 0, height, width, pitch, p, -1, stream, count,
+                      image_stride);
 }
 
 bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux, float *d_abar,

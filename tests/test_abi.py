@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 def test_version_and_status_strings():
     L = _lib()
-    assert L.lib().bf_version() == 10200
+    assert L.lib().bf_version() == 10300
     for code, text in L.STATUS.items():
         assert L.lib().bf_status_string(code).decode() == text
 

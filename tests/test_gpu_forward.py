@@ -98,6 +98,42 @@ def test_streaming_box_kernel(r, variant):
                        radius=r, variant=variant)
 
 
+@pytest.mark.parametrize("kind,r,ss,sr,N", [(bf.BOX, 3, 0.0, 40.0, 1), (bf.BOX, 5, 0.0, 60.0, 3),
+                                             (bf.BOX, 3, 0.0, 35.0, 7), (bf.GAUSS, 9, 3.0, 30.0, 12)])
+def test_forward_many(kind, r, ss, sr, N):
+    """bf_fast_forward_many: a batch of images of one size in one call (one
+    launch on the warp-strip box kernel, one per image on the tile kernels);
+    each image is filtered on its own (zero extension at its edges), against
+    the checker image by image and against single-image calls, with ragged
+    strips and bands, odd image strides and padded rows (scalar copies)."""
+    B, H, W = 3, 61, 301
+    imgs = np.stack([image(H, W, seed=500 + 7 * k + r) for k in range(B)])
+    x = torch.from_numpy(imgs).cuda()
+    out, q = bf.gpa_forward_many(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True)
+    padded = torch.zeros((B, H, W + 3), device="cuda")
+    padded[:, :, :W] = x
+    out_p = bf.gpa_forward_many(padded[:, :, :W], kind, sr, N, radius=r, sigma_s=ss)
+    torch.cuda.synchronize()
+    for k in range(B):
+        ro, rq, w0 = _ref(imgs[k], kind, r, ss, sr, N)
+        where = "many k=%d kind %d r=%d N=%d" % (k, kind, r, N)
+        compare_forward(out[k].cpu().numpy(), q[k].cpu().numpy(), ro, rq, w0, where, sigma_r=sr, N=N)
+        compare_forward(out_p[k].cpu().numpy(), None, ro, rq, w0, where + " padded", sigma_r=sr, N=N)
+        one, _ = _run(imgs[k], kind, r, ss, sr, N)
+        assert np.abs(out[k].cpu().numpy() - one).max() <= 1e-3, where
+    # the last image alone past a batch of one: count 1 behaves as bf_fast_forward
+    o1 = bf.gpa_forward_many(x[2:], kind, sr, N, radius=r, sigma_s=ss)
+    one, _ = _run(imgs[2], kind, r, ss, sr, N)
+    assert np.abs(o1[0].cpu().numpy() - one).max() == 0.0
+    import ctypes
+    p = bf._lib.make_params(kind, r, ss, sr, N)
+    ptr = ctypes.c_void_p(x.data_ptr())
+    optr = ctypes.c_void_p(out.data_ptr())
+    lib = bf._lib.lib()
+    assert lib.bf_fast_forward_many(ptr, optr, None, 0, H * W, H, W, W, ctypes.byref(p), None) == 1
+    assert lib.bf_fast_forward_many(ptr, optr, None, 2, H * W - 1, H, W, W, ctypes.byref(p), None) == 1
+
+
 @pytest.mark.parametrize("kind,r,ss", [(bf.GAUSS, 12, 4.0), (bf.GAUSS, 20, 20 / 3.0),
                                        (bf.GAUSS, 60, 20.0), (bf.BOX, 20, 0.0), (bf.BOX, 50, 0.0)])
 def test_banded_two_pass(kind, r, ss):
