@@ -68,6 +68,8 @@ def parse():
                     help="restrict the timed step (profiling runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--no-hbm-study", action="store_true",
+                    help="skip the small-N 4096^2 batch HBM measurement of the JSON line")
     ap.add_argument("--sweep", default="",
                     help="comma list of extra studies, one JSON line per point: "
                          "grid2048, roofline4096, large8192, recursive, batch256, grad512, "
@@ -998,6 +1000,24 @@ def main():
         hbm = {"fwd_algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
                "peak_gbs": hbm_peak, "peak_src": pk_src}
 
+    # the small-N HBM study at 4096^2 (a batch of 8 same-sized images in one call:
+    # one launch of the warp-strip box kernel), live CUDA events, inputs > L2
+    hbm_4096 = None
+    if world == 1 and not args.no_hbm_study:
+        K4, S4 = 8, 4096
+        xb = torch.from_numpy(np.stack([synth.blocks_image(S4, S4, 64, 10.0, seed=3000 + k)
+                                        for k in range(K4)])).to(dev)
+        ob = torch.empty_like(xb)
+        ms4 = _time_ms(lambda: bf.gpa_forward_many(xb, bf.BOX, 40.0, 1, radius=3, out=ob), 5,
+                       stream, flush) / K4
+        gbs4 = 8.0 * S4 * S4 / (ms4 * 1e-3) / 1e9
+        hbm_4096 = {"workload": "8 x 4096x4096 blocks(64)+N(0,10^2); box W=3, sigma_r=40, N=1; "
+                                "one bf_fast_forward_many call (one launch)",
+                    "ms_per_image": ms4, "algorithmic_bytes_per_px": 8,
+                    "algorithmic_gbs": gbs4, "frac_of_measured_hbm": gbs4 / hbm_peak,
+                    "peak_gbs": hbm_peak, "peak_src": pk_src}
+        del xb, ob
+
     cpu = None
     if not args.no_cpu_baseline and world == 1 and args.only == "all":
         fwd()
@@ -1017,7 +1037,7 @@ def main():
                        "sigma_r": sr, "N": N, "only": args.only, "l2": L2_NOTE,
                        "parallelism": "dp%d (one image per rank)" % world},
             "fwd_mpx_s": fwd_mpx, "fwd_ms": mf, "bwd_ms": mb, "order_selection_ms": order_ms,
-            "direct": direct, "hbm": hbm, "clocks": clocks, "e2e": e2e,
+            "direct": direct, "hbm": hbm, "hbm_4096_batch": hbm_4096, "clocks": clocks, "e2e": e2e,
             "gpu_launches": launches_per * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "wall_s_timed_region": wall}
     print(json.dumps(line), flush=True)
