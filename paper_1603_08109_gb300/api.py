@@ -343,9 +343,8 @@ def gpa_forward_many(imgs: torch.Tensor, kind: int, sigma_r: float, N: int, radi
     if x.stride(2) != 1 or x.stride(0) < x.shape[1] * x.stride(1):
         x = x.contiguous()
     B, H, W = x.shape
-    if out is None or out.shape != x.shape or out.stride() != x.stride() or out.dtype != torch.float32:
-        out = torch.empty_strided(x.shape, x.stride(), dtype=torch.float32, device=x.device)
-    q = torch.empty_strided(x.shape, x.stride(), dtype=torch.float32, device=x.device) if return_q else None
+    out = _image_like(x, out)
+    q = _like(x) if return_q else None
     p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
     check(lib().bf_fast_forward_many(_ptr(x), _ptr(out), _ptr(q), B, ctypes.c_size_t(x.stride(0)), H, W,
                                      x.stride(1), ctypes.byref(p), _stream(x.device)),
