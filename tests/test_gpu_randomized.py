@@ -2,7 +2,11 @@
 random kind, radius (1..60, covering the fused runtime-radius tile, the
 compile-time-radius kernels, the warp-strip box kernel and the banded passes
 with their crossover radii), sigma_r, order, image shape and row pitch, against
-the checker's Algorithm 2 and exact gradient at the same N."""
+the checker's Algorithm 2 and exact gradient at the same N.
+
+BF_RANDOM_SCALE=k (environment) runs k times as many seeds of each test."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -16,6 +20,7 @@ pytestmark = [pytest.mark.gpu, needs_gpu]
 
 
 RADII = [1, 2, 3, 5, 6, 9, 11, 12, 14, 15, 16, 21, 33, 60]
+SCALE = max(1, int(os.environ.get("BF_RANDOM_SCALE", "1")))
 
 
 def _case(seed):
@@ -36,7 +41,7 @@ def _case(seed):
     return kind, r, ss, sr, N, H, W, pad, small_n
 
 
-@pytest.mark.parametrize("seed", range(2 * len(RADII)))
+@pytest.mark.parametrize("seed", range(2 * len(RADII) * SCALE))
 def test_random_forward_and_backward(seed):
     kind, r, ss, sr, N, H, W, pad, small_n = _case(seed)
     img = image(H, W, seed=seed + 11, block=int(np.random.default_rng(seed).integers(2, 20)))
@@ -60,9 +65,17 @@ def test_random_forward_and_backward(seed):
     scale = max(np.abs(rgin).max(), 1e-30)
     assert np.abs(gin - rgin).max() <= 2e-3 * scale, where
     assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+    if r <= 15:  # the stored-plane pair (packed rows of the image: the planes' layout)
+        xc = x.contiguous()
+        so, sq, abar = bf.gpa_forward_stored(xc, kind, sr, N, radius=r, sigma_s=ss)
+        sgin, sgs = bf.gpa_backward(xc, so, sq, torch.from_numpy(g).cuda(), kind, sr, N, radius=r,
+                                    sigma_s=ss, abar=abar)
+        torch.cuda.synchronize()
+        assert np.abs(sgin.cpu().numpy() - rgin).max() <= 2e-3 * scale, where + " stored"
+        assert abs(float(sgs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where + " stored"
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(12 * SCALE))
 def test_random_recursive_forward(seed):
     """The recursive-Gaussian route (reading of Sec. III-A's O(1) filter) at
     random sigma_s in [0.5, 60], shapes, row pitches and orders, against the
@@ -85,7 +98,7 @@ def test_random_recursive_forward(seed):
                     rec.centre_weight_recursive(ss), where, sigma_r=sr, N=N)
 
 
-@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("seed", range(8 * SCALE))
 def test_random_recursive_backward(seed):
     """The recursive route's adjoint at random sigma_s, shapes, pitches and
     orders against the checker's FP64 reverse-mode gradient."""
@@ -110,3 +123,11 @@ def test_random_recursive_backward(seed):
     scale = max(np.abs(rgin).max(), 1e-30)
     assert np.abs(gin.cpu().numpy().astype(np.float64) - rgin).max() <= 2e-3 * scale, where
     assert abs(float(gs.item()) - rgs) <= max(1e-3 * abs(rgs), 1e-4), where
+    # the stored pair: the same kernels on the same data, so the same bits
+    so, sq, ws = bf.recursive_forward_stored(x, sr, N, ss)
+    sgin, sgs = bf.recursive_backward_stored(x.contiguous(), so, sq, torch.from_numpy(g).cuda(), sr,
+                                             N, ss, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(so, out.contiguous()), where
+    assert torch.equal(sgin, gin.contiguous()), where
+    assert float(sgs.item()) == float(gs.item()), where
