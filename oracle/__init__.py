@@ -12,6 +12,8 @@ Provably Accurate Bilateral Filtering" (arXiv 1603.08109):
 * ``order``              -- order selection and kernel error (Sec. II).
 * ``recursive``          -- Algorithm 2 with the recursive (Deriche) Gaussian
                             as the spatial filter, the O(1) route of Sec. III-A.
+* ``volume``             -- eq. BF, eq. GPA and Algorithm 2 on volume / video
+                            data (a box of Z^3, separable kernel), Sec. I, Sec. V.
 
 Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
 this package. It shares no code with the GPU library. Parity status of each
