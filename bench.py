@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--sweep", default="",
                     help="comma list of extra studies, one JSON line per point: "
                          "grid2048, roofline4096, large8192, recursive, batch256, grad512, "
-                         "joint2048, tightness (or 'all')")
+                         "joint2048, tightness, volume (or 'all')")
     return ap.parse_args()
 
 
@@ -342,7 +342,7 @@ def run_sweeps(args):
     from paper_1603_08109_gb300 import synth
     names = set(args.sweep.split(",")) if args.sweep != "all" else {
         "grid2048", "roofline4096", "large8192", "recursive", "batch256", "grad512", "joint2048",
-        "tightness"}
+        "tightness", "volume"}
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -621,6 +621,29 @@ def run_sweeps(args):
                 emit({"sweep": "tightness", "eps": eps, "sigma_r": sr, "N_chebyshev": ch,
                       "N_chernoff": cn, "N_poisson": po, "N_exhaustive": ex,
                       "grid_error": errs, "s_per_grid_eval_gpu": gpu_s})
+    if "volume" in names:
+        # a 128 x 256 x 256 volume (video: 128 frames of blocks(16)+N(0,10^2));
+        # separable 3-D kernel, sigma_r=30, N from delta=1 with w(0) = w1(0)^3
+        D3, H3, W3 = 128, 256, 256
+        v = torch.from_numpy(np.stack([synth.blocks_image(H3, W3, 16, 10.0, seed=6000 + k)
+                                       for k in range(D3)])).to(dev)
+        o = torch.empty_like(v)
+        vox = float(D3 * H3 * W3)
+        for kind, R, ss in ((bf.GAUSS, 6, 2.0), (bf.BOX, 3, 0.0)):
+            N = bf.volume_order_from_delta(kind, R, ss, 30.0, 1.0)
+            ws = torch.empty(bf.volume_workspace_bytes(D3, H3, W3, kind, 30.0, N, R, ss) // 4,
+                             device=dev)
+            vms = _time_ms(lambda: bf.gpa_volume(v, kind, 30.0, N, radius=R, sigma_s=ss, out=o,
+                                                 ws=ws), 5, stream, flush)
+            # algorithmic FMAs per voxel and channel: the three 1-D filterings
+            ops = (N + 1) * (3 * (2 * R + 1) + 3) * vox
+            emit({"sweep": "volume", "shape": [D3, H3, W3], "kind": "box" if kind == 0 else "gaussian",
+                  "radius": R, "sigma_r": 30.0, "N": N, "ms": vms, "mvoxel_s": vox / vms / 1e3,
+                  "fp32_frac": ops / (vms * 1e-3) / fp32_peak_ops(152, 2070.0),
+                  "workspace_bytes": ws.numel() * 4})
+            del ws
+        del v, o
+        torch.cuda.empty_cache()
     if "joint2048" in names:
         # cross (joint) filter: 2048^2 blocks(64) image, gradient+polygons guide
         x = torch.from_numpy(synth.blocks_image(2048, 2048, 64, 10.0, seed=1000)).to(dev)

@@ -458,6 +458,30 @@ bf_status bf_recursive_backward_stored(const float *d_in, const float *d_out,
                                        const bf_params *p, void *d_ws, size_t ws_bytes,
                                        void *stream);
 
+/* ------------------------------------------------ volume / video (Sec. I, V)
+ * The paper notes that the filter extends directly to video and volume data.
+ * bf_volume_forward runs Algorithm 2 on a grayscale volume f of depth x
+ * height x width voxels (packed: x fastest, then y, then z; for video, z is
+ * time) with the same Gaussian range kernel and the separable spatial kernel
+ * w(j) = w1(j_z) w1(j_y) w1(j_x), w1 the normalised 1-D box (p->kind =
+ * BF_SPATIAL_BOX) or truncated Gaussian (BF_SPATIAL_GAUSS, radius = ceil(3
+ * sigma_s) if p->radius <= 0) of the planar filter, the same along every
+ * axis; neighbours outside the volume do not contribute.  Outputs f_GPA and
+ * optionally Q' (normalised), as bf_fast_forward per voxel.  Choose N from
+ * eq. eps with w(0) = w1(0)^3 (bf_order_estimates' Chernoff order for
+ * eps = w(0) delta / (2T + delta)).  Two passes: the z-filtering of the N + 1
+ * power images into the workspace, then per z-plane the y- and x-filterings
+ * and the ratio.  Workspace: bf_volume_workspace bytes = (N + 1) depth height
+ * width floats, device memory owned by the caller, 16-byte aligned.
+ * BF_ERR_UNSUPPORTED for radius > 31 or depth or height > 65535;
+ * BF_ERR_WORKSPACE for a missing or small workspace; BF_ERR_INVALID_ARG for
+ * other kinds, aliasing outputs or sizes < 1.  Asynchronous on `stream`. */
+bf_status bf_volume_workspace(int depth, int height, int width, const bf_params *p,
+                              size_t *bytes);
+bf_status bf_volume_forward(const float *d_in, float *d_out, float *d_qaux, int depth,
+                            int height, int width, const bf_params *p, void *d_ws,
+                            size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

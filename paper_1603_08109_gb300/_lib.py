@@ -69,6 +69,8 @@ SIGNATURES = {
     "bf_recursive_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_recursive_forward_stored": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_forward_many": (_i, [_vp, _vp, _vp, _i, _sz, _i, _i, _i, _pp, _vp]),
+    "bf_volume_workspace": (_i, [_i, _i, _i, _pp, ctypes.POINTER(_sz)]),
+    "bf_volume_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_recursive_backward_stored": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz,
                                           _vp]),
     "bf_fast_backward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),

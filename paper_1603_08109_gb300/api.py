@@ -24,7 +24,8 @@ __all__ = [
     "GAUSS_RECURSIVE", "recursive_workspace_bytes", "recursive_gauss", "recursive_forward",
     "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
     "recursive_bilateral", "recursive_joint_forward", "recursive_forward_stored",
-    "recursive_backward_stored", "gpa_forward_many",
+    "recursive_backward_stored", "gpa_forward_many", "gpa_volume", "volume_order_from_delta",
+    "volume_workspace_bytes",
 ]
 
 
@@ -350,6 +351,46 @@ def gpa_forward_many(imgs: torch.Tensor, kind: int, sigma_r: float, N: int, radi
                                      x.stride(1), ctypes.byref(p), _stream(x.device)),
           "bf_fast_forward_many")
     return (out, q) if return_q else out
+
+
+def volume_order_from_delta(kind: int, radius: int, sigma_s: float, sigma_r: float, delta: float,
+                            t_c: float = 128.0) -> int:
+    """N for a volume filter accuracy delta: eq. eps with the volume kernel's
+    w(0) = w1(0)^3 = (planar w(0))^(3/2), then the Chernoff order (eq. LambW)."""
+    r = resolve_radius(kind, radius, sigma_s)
+    w0 = centre_weight(kind, r, sigma_s) ** 1.5
+    eps = w0 * delta / (2.0 * t_c + delta)
+    return order_estimates(sigma_r, eps, t_c)[1]
+
+
+def volume_workspace_bytes(D: int, H: int, W: int, kind: int, sigma_r: float, N: int,
+                           radius: int = 0, sigma_s: float = 0.0, t_c: float = 128.0) -> int:
+    n = ctypes.c_size_t(0)
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_volume_workspace(int(D), int(H), int(W), ctypes.byref(p), ctypes.byref(n)),
+          "bf_volume_workspace")
+    return int(n.value)
+
+
+def gpa_volume(vol: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
+               sigma_s: float = 0.0, t_c: float = 128.0, return_q: bool = False,
+               out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None):
+    """f_GPA of a (D, H, W) grayscale volume or video (Algorithm 2 with the
+    separable 3-D kernel; bf_volume_forward).  Returns out, or (out, Q')."""
+    if vol.dim() != 3 or vol.device.type != "cuda":
+        raise ValueError("vol must be a (D, H, W) CUDA tensor")
+    x = vol.to(torch.float32).contiguous()
+    D, H, W = x.shape
+    o = _image_like(x, out)
+    q = _like(x) if return_q else None
+    nbytes = volume_workspace_bytes(D, H, W, kind, sigma_r, N, radius, sigma_s, t_c)
+    if ws is None or ws.numel() * ws.element_size() < nbytes or ws.device != x.device:
+        ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
+    p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
+    check(lib().bf_volume_forward(_ptr(x), _ptr(o), _ptr(q), D, H, W, ctypes.byref(p), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _stream(x.device)),
+          "bf_volume_forward")
+    return (o, q) if return_q else o
 
 
 def gpa_forward_stored(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,

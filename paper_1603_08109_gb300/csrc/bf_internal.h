@@ -7,7 +7,7 @@
 
 #include "../../include/bf.h"
 
-#define BF_VERSION 10300  // 1.3.0: batches of same-sized images (bf_fast_forward_many)
+#define BF_VERSION 10400  // 1.4.0: video / volume data (bf_volume_forward)
 
 // Gaussian taps are padded with zeros to a multiple of 16 (the register-window
 // unroll of the separable passes); 2 * BF_MAX_RADIUS + 1 = 193 -> 208 <= 224.

@@ -1,0 +1,218 @@
+// Algorithm 2 on volume (video) data: the straightforward extension of the
+// filter to a box of Z^3 that Sec. I and Sec. V mention.  f is a grayscale
+// volume (depth x height x width, packed: x fastest), the range kernel is the
+// Gaussian of the planar filter, and the spatial kernel is the separable
+// w(j) = w1(j_z) w1(j_y) w1(j_x) with the normalised 1-D box or Gaussian w1 of
+// the planar filter along every axis; neighbours outside the volume do not
+// contribute (zero extension).  With the rescaled power images
+// a_n = e^{-H^2/2} H^n / sqrt(n!), H = (f - t_c) / sigma_r,
+//   Q' = sum_{n<N} a_n (w * a_n),  P' = sum_{n=1..N} sqrt(n) a_{n-1} (w * a_n),
+//   f_GPA = t_c + sigma_r P'/Q',
+// exactly as for images; only the N + 1 filterings are 3-D.
+//
+// Two kernels:
+//   vol_zpass   one thread per (y, x) column and 16 output planes z0..z0+15:
+//               the column's f over the tile plus the W-plane halos is turned
+//               into a_0 and H in shared memory (each thread its own column,
+//               so no barriers), then channel by channel a_n is advanced in
+//               place and filtered along z into the workspace plane Z_n
+//               (N + 1 volumes of floats);
+//   vol_yxpass  one CTA per 32 x 32 output tile of one z-plane: per channel
+//               the Z_n region with the W-pixel halos is staged in shared
+//               memory, filtered along y, then along x, and the result
+//               (w * a_n at the tile's voxels) is recombined with a_n at the
+//               voxel itself (regenerated from f in registers) into Q', P'.
+#include <algorithm>
+#include <cmath>
+
+#include "bf_internal.h"
+
+namespace {
+
+constexpr int kVolMaxR = 31;   // radius limit of the volume path (taps <= 63)
+constexpr int kZT = 16;        // z-pass output planes per thread
+constexpr int kZNT = 128;      // z-pass threads per CTA (consecutive x)
+constexpr int kYT = 32;        // y/x-pass output tile side
+constexpr int kYNT = 256;      // y/x-pass threads per CTA (32 x 8)
+
+struct VolArgs {
+  const float *in;
+  float *out, *qaux, *ws;
+  long long plane;  // D * H * W: floats per workspace volume
+  int D, H, W, R, L, N;
+  float tc, sr, inv_sr, e2c;
+  float taps[2 * kVolMaxR + 1];  // normalised w1(k - R), k = 0 .. 2R
+};
+
+__global__ void __launch_bounds__(kZNT) vol_zpass(const __grid_constant__ VolArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  const int RZ = kZT + 2 * A.R;
+  float *sA = sm, *sH = sm + RZ * kZNT;  // [r][thread]
+  const int t = threadIdx.x;
+  const int x = blockIdx.x * kZNT + t, y = blockIdx.y, z0 = blockIdx.z * kZT;
+  if (x >= A.W) return;  // no barriers: every thread owns its column
+  const long long col = (long long)y * A.W + x, zs = (long long)A.H * A.W;
+  for (int r = 0; r < RZ; ++r) {
+    const int z = z0 - A.R + r;
+    float a = 0.f, h = 0.f;
+    if (z >= 0 && z < A.D) {
+      const float d = __ldg(A.in + z * zs + col) - A.tc;
+      h = d * A.inv_sr;
+      a = exp2f(d * d * A.e2c);  // exp(-H^2/2)
+    }
+    sA[r * kZNT + t] = a;
+    sH[r * kZNT + t] = h;
+  }
+  const int zn = min(kZT, A.D - z0);
+  for (int n = 0; n <= A.N; ++n) {
+    if (n > 0) {
+      const float rs = __frsqrt_rn((float)n);
+      for (int r = 0; r < RZ; ++r) sA[r * kZNT + t] *= sH[r * kZNT + t] * rs;
+    }
+    float *dst = A.ws + (long long)n * A.plane + z0 * zs + col;
+    for (int zo = 0; zo < zn; ++zo) {
+      float acc = 0.f;
+      for (int k = 0; k < A.L; ++k) acc = fmaf(A.taps[k], sA[(zo + k) * kZNT + t], acc);
+      dst[zo * zs] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolArgs A) {
+  extern __shared__ __align__(16) float sm[];
+  const int RC = kYT + 2 * A.R, RP = RC + 1;  // region side, row pitch
+  float *sR = sm, *sV = sm + RC * RP;        // region (RC x RP), vertical pass (32 x RP)
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int x0 = blockIdx.x * kYT, y0 = blockIdx.y * kYT, z = blockIdx.z;
+  const long long zs = (long long)A.H * A.W, zoff = z * zs;
+  constexpr int KR = kYT / (kYNT / 32);  // output rows per thread: ty, ty + 8, ...
+  float a[KR], H[KR], Q[KR], P[KR];
+  const int x = x0 + tx;
+  for (int k = 0; k < KR; ++k) {
+    const int y = y0 + ty + 8 * k;
+    float av = 0.f, h = 0.f;
+    if (x < A.W && y < A.H) {
+      const float d = __ldg(A.in + zoff + (long long)y * A.W + x) - A.tc;
+      h = d * A.inv_sr;
+      av = exp2f(d * d * A.e2c);
+    }
+    a[k] = av;
+    H[k] = h;
+    Q[k] = P[k] = 0.f;
+  }
+  for (int n = 0; n <= A.N; ++n) {
+    const float *src = A.ws + (long long)n * A.plane + zoff;
+    __syncthreads();  // the previous channel is done with sR and sV
+    for (int e = t; e < RC * RC; e += kYNT) {
+      const int rr = e / RC, cc = e - rr * RC;
+      const int gy = y0 - A.R + rr, gx = x0 - A.R + cc;
+      sR[rr * RP + cc] = (gy >= 0 && gy < A.H && gx >= 0 && gx < A.W)
+                             ? __ldg(src + (long long)gy * A.W + gx) : 0.f;
+    }
+    __syncthreads();
+    for (int e = t; e < kYT * RC; e += kYNT) {  // along y: 32 output rows, every region column
+      const int row = e / RC, cc = e - row * RC;
+      float acc = 0.f;
+      for (int k = 0; k < A.L; ++k) acc = fmaf(A.taps[k], sR[(row + k) * RP + cc], acc);
+      sV[row * RP + cc] = acc;
+    }
+    __syncthreads();
+    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+    const float sq = __fsqrt_rn((float)n);
+    for (int k = 0; k < KR; ++k) {  // along x, then the recursion and the sums
+      const float *vr = sV + (ty + 8 * k) * RP + tx;
+      float ab = 0.f;
+      for (int j = 0; j < A.L; ++j) ab = fmaf(A.taps[j], vr[j], ab);
+      const float aold = a[k];  // a_{n-1}
+      const float an = n > 0 ? aold * (H[k] * rs) : aold;
+      if (n < A.N) Q[k] = fmaf(an, ab, Q[k]);
+      if (n > 0) P[k] = fmaf(sq * aold, ab, P[k]);
+      a[k] = an;
+    }
+  }
+  if (x >= A.W) return;
+  for (int k = 0; k < KR; ++k) {
+    const int y = y0 + ty + 8 * k;
+    if (y >= A.H) break;
+    const long long o = zoff + (long long)y * A.W + x;
+    A.out[o] = fmaf(A.sr, __fdividef(P[k], Q[k]), A.tc);  // approximate division (2 ulp)
+    if (A.qaux) A.qaux[o] = Q[k];
+  }
+}
+
+size_t zpass_smem(int R) { return (size_t)2 * (kZT + 2 * R) * kZNT * sizeof(float); }
+size_t yxpass_smem(int R) {
+  const size_t RC = kYT + 2 * (size_t)R;
+  return (RC + kYT) * (RC + 1) * sizeof(float);
+}
+
+bf_status resolve_volume(const bf_params *p, bfi::FilterConsts *fc) {
+  bf_status st = bfi::resolve(p, true, fc);
+  if (st != BF_OK) return st;
+  if (fc->kind != BF_SPATIAL_BOX && fc->kind != BF_SPATIAL_GAUSS) return BF_ERR_INVALID_ARG;
+  if (fc->R > kVolMaxR) return BF_ERR_UNSUPPORTED;
+  return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_volume_workspace(int depth, int height, int width, const bf_params *p,
+                              size_t *bytes) {
+  if (!bytes || depth < 1 || height < 1 || width < 1) return BF_ERR_INVALID_ARG;
+  bfi::FilterConsts fc;
+  const bf_status st = resolve_volume(p, &fc);
+  if (st != BF_OK) return st;
+  *bytes = (size_t)(fc.N + 1) * (size_t)depth * (size_t)height * (size_t)width * sizeof(float);
+  return BF_OK;
+}
+
+bf_status bf_volume_forward(const float *d_in, float *d_out, float *d_qaux, int depth,
+                            int height, int width, const bf_params *p, void *d_ws,
+                            size_t ws_bytes, void *stream) {
+  if (!d_in || !d_out || d_in == d_out || depth < 1 || height < 1 || width < 1)
+    return BF_ERR_INVALID_ARG;
+  if (d_qaux && (d_qaux == d_in || d_qaux == d_out)) return BF_ERR_INVALID_ARG;
+  if (height > 65535 || depth > 65535) return BF_ERR_UNSUPPORTED;  // grid limits
+  bfi::FilterConsts fc;
+  bf_status st = resolve_volume(p, &fc);
+  if (st != BF_OK) return st;
+  const size_t need = (size_t)(fc.N + 1) * (size_t)depth * (size_t)height * (size_t)width *
+                      sizeof(float);
+  if (!d_ws || ws_bytes < need) return BF_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return BF_ERR_INVALID_ARG;
+  VolArgs A = {};
+  A.in = d_in;
+  A.out = d_out;
+  A.qaux = d_qaux;
+  A.ws = static_cast<float *>(d_ws);
+  A.plane = (long long)depth * height * width;
+  A.D = depth;
+  A.H = height;
+  A.W = width;
+  A.R = fc.R;
+  A.L = 2 * fc.R + 1;
+  A.N = fc.N;
+  A.tc = fc.tc;
+  A.sr = fc.sr;
+  A.inv_sr = fc.inv_sr;
+  A.e2c = fc.e2c;
+  for (int k = 0; k < A.L; ++k)
+    A.taps[k] = fc.kind == BF_SPATIAL_GAUSS ? fc.taps[k] : (float)(1.0 / (double)A.L);
+  const size_t zs = zpass_smem(fc.R), ys = yxpass_smem(fc.R);
+  st = bfi::ensure_smem(reinterpret_cast<const void *>(vol_zpass), zpass_smem(kVolMaxR));
+  if (st == BF_OK)
+    st = bfi::ensure_smem(reinterpret_cast<const void *>(vol_yxpass), yxpass_smem(kVolMaxR));
+  if (st != BF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dim3 gz((width + kZNT - 1) / kZNT, height, (depth + kZT - 1) / kZT);
+  vol_zpass<<<gz, kZNT, zs, s>>>(A);
+  st = bfi::check_launch();
+  if (st != BF_OK) return st;
+  dim3 gy((width + kYT - 1) / kYT, (height + kYT - 1) / kYT, depth);
+  vol_yxpass<<<gy, kYNT, ys, s>>>(A);
+  return bfi::check_launch();
+}
+
+}  // extern "C"

@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 def test_version_and_status_strings():
     L = _lib()
-    assert L.lib().bf_version() == 10300
+    assert L.lib().bf_version() == 10400
     for code, text in L.STATUS.items():
         assert L.lib().bf_status_string(code).decode() == text
 
@@ -188,6 +188,26 @@ def test_recursive_host_side():
     assert lib.bf_recursive_joint_forward(*jargs, ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 40.0,
                                                                              9)),
                                           fake, 1 << 30, None) == 1
+
+
+def test_volume_host_side():
+    """Workspace query and the argument checks made before any launch."""
+    L = _lib()
+    lib = L.lib()
+    n = ctypes.c_size_t()
+    p = L.make_params(L.BOX, 3, 0.0, 40.0, 7)
+    assert lib.bf_volume_workspace(5, 6, 7, ctypes.byref(p), ctypes.byref(n)) == 0
+    assert n.value == 8 * 5 * 6 * 7 * 4
+    assert lib.bf_volume_workspace(0, 6, 7, ctypes.byref(p), ctypes.byref(n)) == 1
+    big = L.make_params(L.BOX, 32, 0.0, 40.0, 7)
+    assert lib.bf_volume_workspace(5, 6, 7, ctypes.byref(big), ctypes.byref(n)) == 3
+    fake = ctypes.c_void_p(0x1000)
+    out = ctypes.c_void_p(0x2000)
+    assert lib.bf_volume_forward(fake, out, None, 5, 6, 7, ctypes.byref(p), None, 0, None) == 5
+    assert lib.bf_volume_forward(fake, fake, None, 5, 6, 7, ctypes.byref(p), fake, 1 << 20,
+                                 None) == 1
+    assert lib.bf_volume_forward(fake, out, None, 5, 70000, 7, ctypes.byref(p), fake, 1 << 40,
+                                 None) == 3
 
 
 def test_tuning_table_roundtrip():
