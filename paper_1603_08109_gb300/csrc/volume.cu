@@ -19,13 +19,15 @@
 //               (N + 1 volumes of floats);
 //   vol_yxpass  one CTA per 32 x 32 output tile of one z-plane: per channel
 //               the Z_n region with the W-pixel halos is staged in shared
-//               memory, filtered along y, then along x, and the result
+//               memory (cp.async, the next channel's region copied while the
+//               current one is filtered), filtered along y, then along x, and the result
 //               (w * a_n at the tile's voxels) is recombined with a_n at the
 //               voxel itself (regenerated from f in registers) into Q', P'.
 #include <algorithm>
 #include <cmath>
 
 #include "bf_internal.h"
+#include "gpa_fixed.cuh"  // cp.async helpers
 
 namespace {
 
@@ -81,7 +83,8 @@ __global__ void __launch_bounds__(kZNT) vol_zpass(const __grid_constant__ VolArg
 __global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolArgs A) {
   extern __shared__ __align__(16) float sm[];
   const int RC = kYT + 2 * A.R, RP = RC + 1;  // region side, row pitch
-  float *sR = sm, *sV = sm + RC * RP;        // region (RC x RP), vertical pass (32 x RP)
+  float *sR0 = sm, *sR1 = sm + RC * RP;       // two regions (RC x RP): channels n, n + 1
+  float *sV = sm + 2 * RC * RP;               // vertical pass (32 x RP)
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   const int x0 = blockIdx.x * kYT, y0 = blockIdx.y * kYT, z = blockIdx.z;
   const long long zs = (long long)A.H * A.W, zoff = z * zs;
@@ -100,16 +103,28 @@ __global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolAr
     H[k] = h;
     Q[k] = P[k] = 0.f;
   }
-  for (int n = 0; n <= A.N; ++n) {
+  // channel n's region into buffer b (zeros outside the plane)
+  auto issue = [&](int n, float *b) {
     const float *src = A.ws + (long long)n * A.plane + zoff;
-    __syncthreads();  // the previous channel is done with sR and sV
     for (int e = t; e < RC * RC; e += kYNT) {
       const int rr = e / RC, cc = e - rr * RC;
       const int gy = y0 - A.R + rr, gx = x0 - A.R + cc;
-      sR[rr * RP + cc] = (gy >= 0 && gy < A.H && gx >= 0 && gx < A.W)
-                             ? __ldg(src + (long long)gy * A.W + gx) : 0.f;
+      if (gy >= 0 && gy < A.H && gx >= 0 && gx < A.W)
+        bfk::cp_async4(b + rr * RP + cc, src + (long long)gy * A.W + gx);
+      else
+        b[rr * RP + cc] = 0.f;
     }
-    __syncthreads();
+  };
+  issue(0, sR0);
+  bfk::cp_async_commit();
+  for (int n = 0; n <= A.N; ++n) {
+    // the other buffer was last read by the previous channel's y pass, which
+    // every thread finished before the barrier that ended it
+    if (n + 1 <= A.N) issue(n + 1, (n & 1) ? sR0 : sR1);
+    bfk::cp_async_commit();
+    bfk::cp_async_wait<1>();  // this thread's copies of channel n have landed
+    __syncthreads();          // ... and every thread's; the x pass of n - 1 is done with sV
+    const float *sR = (n & 1) ? sR1 : sR0;
     for (int e = t; e < kYT * RC; e += kYNT) {  // along y: 32 output rows, every region column
       const int row = e / RC, cc = e - row * RC;
       float acc = 0.f;
@@ -143,7 +158,7 @@ __global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolAr
 size_t zpass_smem(int R) { return (size_t)2 * (kZT + 2 * R) * kZNT * sizeof(float); }
 size_t yxpass_smem(int R) {
   const size_t RC = kYT + 2 * (size_t)R;
-  return (RC + kYT) * (RC + 1) * sizeof(float);
+  return (2 * RC + kYT) * (RC + 1) * sizeof(float);
 }
 
 bf_status resolve_volume(const bf_params *p, bfi::FilterConsts *fc) {
