@@ -155,6 +155,170 @@ __global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolAr
   }
 }
 
+// Compile-time radius (W <= 8): the same two passes with every filter loop
+// unrolled, the taps as constant operands and register windows, so that a
+// shared-memory load serves several FMAs.  z-pass: the column's a_n and H in
+// registers.  y/x pass: the y filter per (region column, 8 output rows), the
+// x filter per (output row, 4 consecutive voxels), which are also the
+// thread's voxels for the recursion and the sums.
+constexpr int kVolFixedMaxR = 8;
+
+template <int R>
+__global__ void __launch_bounds__(kZNT) vol_zpass_r(const __grid_constant__ VolArgs A) {
+  constexpr int L = 2 * R + 1, RZ = kZT + 2 * R;
+  const int t = threadIdx.x;
+  const int x = blockIdx.x * kZNT + t, y = blockIdx.y, z0 = blockIdx.z * kZT;
+  if (x >= A.W) return;
+  const long long col = (long long)y * A.W + x, zs = (long long)A.H * A.W;
+  float a[RZ], h[RZ];
+#pragma unroll
+  for (int r = 0; r < RZ; ++r) {
+    const int z = z0 - R + r;
+    float av = 0.f, hv = 0.f;
+    if (z >= 0 && z < A.D) {
+      const float d = __ldg(A.in + z * zs + col) - A.tc;
+      hv = d * A.inv_sr;
+      av = exp2f(d * d * A.e2c);  // exp(-H^2/2)
+    }
+    a[r] = av;
+    h[r] = hv;
+  }
+  const int zn = min(kZT, A.D - z0);
+  for (int n = 0; n <= A.N; ++n) {
+    if (n > 0) {
+      const float rs = __frsqrt_rn((float)n);
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) a[r] *= h[r] * rs;
+    }
+    float *dst = A.ws + (long long)n * A.plane + z0 * zs + col;
+#pragma unroll
+    for (int zo = 0; zo < kZT; ++zo) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < L; ++k) acc = fmaf(A.taps[k], a[zo + k], acc);
+      if (zo < zn) dst[zo * zs] = acc;
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kYNT) vol_yxpass_r(const __grid_constant__ VolArgs A) {
+  constexpr int L = 2 * R + 1, RC = kYT + 2 * R, RP = RC + 1;  // RP odd
+  static_assert(4 * RC <= kYNT && kYT * kYT == 4 * kYNT, "thread mapping");
+  extern __shared__ __align__(16) float sm[];
+  float *sR0 = sm, *sR1 = sm + RC * RP, *sV = sm + 2 * RC * RP;
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * kYT, y0 = blockIdx.y * kYT, z = blockIdx.z;
+  const long long zs = (long long)A.H * A.W, zoff = z * zs;
+  const int orow = t >> 3, oc = 4 * (t & 7);  // the thread's voxels: row orow, columns oc..oc+3
+  const int y = y0 + orow;
+  const int vcc = t % RC, vch = t / RC;        // y filter item: region column, 8-row chunk
+  const bool vact = vch < 4;
+  float a[4], H[4], Q[4], P[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = x0 + oc + k;
+    float av = 0.f, h = 0.f;
+    if (x < A.W && y < A.H) {
+      const float d = __ldg(A.in + zoff + (long long)y * A.W + x) - A.tc;
+      h = d * A.inv_sr;
+      av = exp2f(d * d * A.e2c);
+    }
+    a[k] = av;
+    H[k] = h;
+    Q[k] = P[k] = 0.f;
+  }
+  auto issue = [&](int n, float *b) {  // channel n's region (zeros outside the plane)
+    const float *src = A.ws + (long long)n * A.plane + zoff;
+    for (int e = t; e < RC * RC; e += kYNT) {
+      const int rr = e / RC, cc = e - rr * RC;
+      const int gy = y0 - R + rr, gx = x0 - R + cc;
+      if (gy >= 0 && gy < A.H && gx >= 0 && gx < A.W)
+        bfk::cp_async4(b + rr * RP + cc, src + (long long)gy * A.W + gx);
+      else
+        b[rr * RP + cc] = 0.f;
+    }
+  };
+  issue(0, sR0);
+  bfk::cp_async_commit();
+  for (int n = 0; n <= A.N; ++n) {
+    if (n + 1 <= A.N) issue(n + 1, (n & 1) ? sR0 : sR1);  // last read by the y filter of n - 1
+    bfk::cp_async_commit();
+    bfk::cp_async_wait<1>();
+    __syncthreads();
+    const float *sR = (n & 1) ? sR1 : sR0;
+    if (vact) {
+      float w[8 + 2 * R];
+#pragma unroll
+      for (int i = 0; i < 8 + 2 * R; ++i) w[i] = sR[(8 * vch + i) * RP + vcc];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < L; ++k) acc = fmaf(A.taps[k], w[r + k], acc);
+        sV[(8 * vch + r) * RP + vcc] = acc;
+      }
+    }
+    __syncthreads();
+    float w[4 + 2 * R];
+#pragma unroll
+    for (int i = 0; i < 4 + 2 * R; ++i) w[i] = sV[orow * RP + oc + i];
+    const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
+    const float sq = __fsqrt_rn((float)n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float ab = 0.f;
+#pragma unroll
+      for (int j = 0; j < L; ++j) ab = fmaf(A.taps[j], w[k + j], ab);
+      const float aold = a[k];  // a_{n-1}
+      const float an = n > 0 ? aold * (H[k] * rs) : aold;
+      if (n < A.N) Q[k] = fmaf(an, ab, Q[k]);
+      if (n > 0) P[k] = fmaf(sq * aold, ab, P[k]);
+      a[k] = an;
+    }
+  }
+  if (y >= A.H) return;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = x0 + oc + k;
+    if (x < A.W) {
+      const long long o = zoff + (long long)y * A.W + x;
+      A.out[o] = fmaf(A.sr, __fdividef(P[k], Q[k]), A.tc);  // approximate division (2 ulp)
+      if (A.qaux) A.qaux[o] = Q[k];
+    }
+  }
+}
+
+template <int R>
+bf_status launch_volume_r(const VolArgs &A, cudaStream_t s) {
+  constexpr int RC = kYT + 2 * R;
+  constexpr size_t ys = (size_t)(2 * RC + kYT) * (RC + 1) * sizeof(float);
+  bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(vol_yxpass_r<R>), ys);
+  if (st != BF_OK) return st;
+  dim3 gz((A.W + kZNT - 1) / kZNT, A.H, (A.D + kZT - 1) / kZT);
+  vol_zpass_r<R><<<gz, kZNT, 0, s>>>(A);
+  st = bfi::check_launch();
+  if (st != BF_OK) return st;
+  dim3 gy((A.W + kYT - 1) / kYT, (A.H + kYT - 1) / kYT, A.D);
+  vol_yxpass_r<R><<<gy, kYNT, ys, s>>>(A);
+  return bfi::check_launch();
+}
+
+bf_status launch_volume_fixed(const VolArgs &A, cudaStream_t s) {
+  switch (A.R) {
+    case 0: return launch_volume_r<0>(A, s);
+    case 1: return launch_volume_r<1>(A, s);
+    case 2: return launch_volume_r<2>(A, s);
+    case 3: return launch_volume_r<3>(A, s);
+    case 4: return launch_volume_r<4>(A, s);
+    case 5: return launch_volume_r<5>(A, s);
+    case 6: return launch_volume_r<6>(A, s);
+    case 7: return launch_volume_r<7>(A, s);
+    case 8: return launch_volume_r<8>(A, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
+}
+
 size_t zpass_smem(int R) { return (size_t)2 * (kZT + 2 * R) * kZNT * sizeof(float); }
 size_t yxpass_smem(int R) {
   const size_t RC = kYT + 2 * (size_t)R;
@@ -215,12 +379,13 @@ bf_status bf_volume_forward(const float *d_in, float *d_out, float *d_qaux, int 
   A.e2c = fc.e2c;
   for (int k = 0; k < A.L; ++k)
     A.taps[k] = fc.kind == BF_SPATIAL_GAUSS ? fc.taps[k] : (float)(1.0 / (double)A.L);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fc.R <= kVolFixedMaxR) return launch_volume_fixed(A, s);
   const size_t zs = zpass_smem(fc.R), ys = yxpass_smem(fc.R);
   st = bfi::ensure_smem(reinterpret_cast<const void *>(vol_zpass), zpass_smem(kVolMaxR));
   if (st == BF_OK)
     st = bfi::ensure_smem(reinterpret_cast<const void *>(vol_yxpass), yxpass_smem(kVolMaxR));
   if (st != BF_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   dim3 gz((width + kZNT - 1) / kZNT, height, (depth + kZT - 1) / kZT);
   vol_zpass<<<gz, kZNT, zs, s>>>(A);
   st = bfi::check_launch();
