@@ -27,7 +27,9 @@
  *    The library never allocates device memory and never synchronises the
  *    stream: every GPU entry point only enqueues work on `stream` (a
  *    cudaStream_t passed as void*, NULL = legacy default stream).
- *  - float arrays must be 4-byte aligned; inputs and outputs may not alias.
+ *  - float arrays must be 4-byte aligned; inputs and outputs may not alias
+ *    (an output equal to the input is rejected with BF_ERR_INVALID_ARG;
+ *    partial overlaps are not detected).
  *  - Errors are returned, never raised: nothing traps or aborts.  A CUDA
  *    launch error is reported as BF_ERR_CUDA (the CUDA error string is
  *    available from bf_last_cuda_error()).

@@ -85,6 +85,8 @@ bf_status resident_ctas(const void *func, int threads, size_t smem, int *ctas) {
 
 bf_status check_image(const void *in, const void *out, int height, int width, int pitch) {
   if (!in || !out) return BF_ERR_INVALID_ARG;
+  // the tiles read neighbours' pixels that other CTAs write: no in-place filtering
+  if (in == out) return BF_ERR_INVALID_ARG;
   if (height < 1 || width < 1 || pitch < width) return BF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(in) & 3u) || (reinterpret_cast<uintptr_t>(out) & 3u))
     return BF_ERR_INVALID_ARG;

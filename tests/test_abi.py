@@ -86,16 +86,18 @@ def test_argument_validation_without_gpu():
     good = L.make_params(L.GAUSS, 9, 3.0, 30.0, 40)
     p = ctypes.byref(good)
     fake = ctypes.c_void_p(0x1000)
+    out = ctypes.c_void_p(0x9000)  # a distinct output (an output equal to the input is rejected)
     assert lib.bf_fast_forward(None, fake, None, 8, 8, 8, p, None) == 1
-    assert lib.bf_fast_forward(fake, fake, None, 0, 8, 8, p, None) == 1
-    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 4, p, None) == 1
+    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8, p, None) == 1
+    assert lib.bf_fast_forward(fake, out, None, 0, 8, 8, p, None) == 1
+    assert lib.bf_fast_forward(fake, out, None, 8, 8, 4, p, None) == 1
     for bad in (L.make_params(L.GAUSS, 9, 3.0, 0.0, 40), L.make_params(L.GAUSS, 9, 3.0, 30.0, 0),
                 L.make_params(7, 9, 3.0, 30.0, 40), L.make_params(L.GAUSS, 0, 0.0, 30.0, 4),
                 L.make_params(L.BOX, -1, 0.0, 30.0, 4)):
-        assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8, ctypes.byref(bad), None) == 1
-    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8,
+        assert lib.bf_fast_forward(fake, out, None, 8, 8, 8, ctypes.byref(bad), None) == 1
+    assert lib.bf_fast_forward(fake, out, None, 8, 8, 8,
                                ctypes.byref(L.make_params(L.BOX, 2, 0.0, 30.0, 5000)), None) == 3
-    assert lib.bf_fast_forward(fake, fake, None, 8, 8, 8,
+    assert lib.bf_fast_forward(fake, out, None, 8, 8, 8,
                                ctypes.byref(L.make_params(L.BOX, 2, 0.0, 5.0, 5)), None) == 3
     n = ctypes.c_int()
     assert lib.bf_order_from_delta(0, 2, 0.0, 30.0, 0.0, 128.0, ctypes.byref(n)) == 1
@@ -104,7 +106,7 @@ def test_argument_validation_without_gpu():
     assert lib.bf_fast_backward_workspace(64, 64, p, ctypes.byref(sz)) == 0 and sz.value > 0
     assert lib.bf_direct_backward_workspace(64, 64, p, ctypes.byref(sz)) == 0 and sz.value > 0
     # backward asking for the sigma_r gradient without a workspace
-    assert lib.bf_fast_backward(fake, fake, fake, fake, fake, fake, 8, 8, 8, p, None, 0,
+    assert lib.bf_fast_backward(fake, fake, fake, fake, out, fake, 8, 8, 8, p, None, 0,
                                 None) in (5, 3)
     assert lib.bf_batch_plan_create(None, 0, None) == 1
     # banded forward: no workspace for radius <= 15; for W = 60 a workspace of
@@ -113,10 +115,10 @@ def test_argument_validation_without_gpu():
     big = ctypes.byref(L.make_params(L.GAUSS, 60, 20.0, 40.0, 32))
     assert lib.bf_fast_forward_workspace(8192, 8192, big, ctypes.byref(sz)) == 0
     assert sz.value >= 64 * 33 * 8192 * 4 and sz.value % (33 * 8192 * 4) == 0
-    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big, None, 0, None) == 5
+    assert lib.bf_fast_forward_ws(fake, out, None, 300, 200, 200, big, None, 0, None) == 5
     too_small = 63 * 33 * 200 * 4
-    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big, fake, too_small, None) == 5
-    assert lib.bf_fast_forward_ws(fake, fake, None, 300, 200, 200, big,
+    assert lib.bf_fast_forward_ws(fake, out, None, 300, 200, 200, big, fake, too_small, None) == 5
+    assert lib.bf_fast_forward_ws(fake, out, None, 300, 200, 200, big,
                                   ctypes.c_void_p(0x1004), 64 * 33 * 200 * 4, None) == 1
 
 
@@ -145,14 +147,14 @@ def test_recursive_host_side():
     assert lib.bf_recursive_workspace(100, 70, 5000, ctypes.byref(sz)) == 3
     fake = ctypes.c_void_p(0x1000)
     good = L.make_params(L.GAUSS_RECURSIVE, 0, 3.0, 40.0, 9)
-    args = (fake, fake, None, 100, 70, 70)
+    args = (fake, ctypes.c_void_p(0x9000), None, 100, 70, 70)
     assert lib.bf_recursive_forward(*args, ctypes.byref(good), None, 0, None) == 5
     assert lib.bf_recursive_forward(*args, ctypes.byref(good), ctypes.c_void_p(0x1010),
                                     sz.value, None) == 1  # workspace not 256-byte aligned
     for bad in (L.make_params(L.GAUSS, 0, 3.0, 40.0, 9), L.make_params(L.GAUSS_RECURSIVE, 0, 0.4, 40.0, 9),
                 L.make_params(L.GAUSS_RECURSIVE, 0, 3.0, 40.0, 0)):
         assert lib.bf_recursive_forward(*args, ctypes.byref(bad), fake, 1 << 30, None) == 1
-    assert lib.bf_recursive_gauss(fake, fake, 100, 70, 70, ctypes.c_float(0.3), fake, 1 << 30,
+    assert lib.bf_recursive_gauss(fake, ctypes.c_void_p(0x9000), 100, 70, 70, ctypes.c_float(0.3), fake, 1 << 30,
                                   None) == 1
     assert lib.bf_recursive_gauss(None, fake, 100, 70, 70, ctypes.c_float(3.0), fake, 1 << 30,
                                   None) == 1
@@ -174,7 +176,7 @@ def test_recursive_host_side():
     ws = ctypes.c_void_p(0x100000)
     assert lib.bf_recursive_forward_stored(*args, ctypes.byref(good), ws, sz.value, None) == 5
     assert lib.bf_recursive_forward_stored(*args, ctypes.byref(good), None, bsz.value, None) == 5
-    assert lib.bf_recursive_forward_stored(fake, fake, fake, 100, 70, 70,  # Q' aliases the input
+    assert lib.bf_recursive_forward_stored(fake, ctypes.c_void_p(0x9000), fake, 100, 70, 70,  # Q' = in
                                            ctypes.byref(good), ws, bsz.value, None) == 1
     assert lib.bf_recursive_forward_stored(*args, ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 40.0, 9)),
                                            ws, bsz.value, None) == 1
@@ -188,6 +190,19 @@ def test_recursive_host_side():
     assert lib.bf_recursive_joint_forward(*jargs, ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 40.0,
                                                                              9)),
                                           fake, 1 << 30, None) == 1
+
+
+def test_forward_many_host_side():
+    """bf_fast_forward_many rejects a batch count below 1 and an image stride
+    smaller than one image before any launch."""
+    L = _lib()
+    lib = L.lib()
+    p = L.make_params(L.BOX, 3, 0.0, 40.0, 1)
+    a, b = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x900000)
+    assert lib.bf_fast_forward_many(a, b, None, 0, 64 * 64, 64, 64, 64, ctypes.byref(p), None) == 1
+    assert lib.bf_fast_forward_many(a, b, None, 3, 64 * 64 - 1, 64, 64, 64, ctypes.byref(p),
+                                    None) == 1
+    assert lib.bf_fast_forward_many(a, a, None, 3, 64 * 64, 64, 64, 64, ctypes.byref(p), None) == 1
 
 
 def test_volume_host_side():
