@@ -114,3 +114,19 @@ def test_accuracy_against_direct_filter(kind, r, ss, sr):
         assert err <= delta
         errs.append(err)
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_support_larger_than_the_volume():
+    """Depth 2 with a radius of 3 (whole z-offsets outside the volume): the
+    z-constant reduction and the agreement of Algorithm 2 with the brute-force
+    definition still hold."""
+    img = synth.blocks_image(6, 7, 2, 25.0, seed=77).astype(np.float64)
+    v = np.repeat(img[None], 2, axis=0)
+    w = oracle.spatial_kernel(oracle.BOX, 3, 0.0)
+    o3 = vol.gpa_alg2_volume(v, oracle.BOX, 3, 0.0, 40.0, 10)
+    o2 = oracle.gpa_alg2(img, w, 40.0, 10)
+    assert np.abs(o3 - o2[None]).max() < 1e-10
+    v2 = _volume(2, 4, 5, seed=91)
+    a2 = vol.gpa_alg2_volume(v2, oracle.GAUSS, 3, 1.0, 30.0, 8)
+    df = vol.gpa_definition_volume(v2, oracle.GAUSS, 3, 1.0, 30.0, 8)
+    assert np.abs(a2 - df).max() < 1e-9
