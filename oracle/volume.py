@@ -82,16 +82,21 @@ def gpa_alg2_volume(vol, kind: int, radius: int, sigma_s: float, sigma_r: float,
     return out
 
 
+def _span(n, d):
+    """Along an axis of length n: the indices i with i - d inside [0, n), and
+    the matching source indices i - d (both empty when |d| >= n)."""
+    lo = max(d, 0)
+    hi = max(n + min(d, 0), lo)
+    return slice(lo, hi), slice(lo - d, hi - d)
+
+
 def _shifted(f, dz, dy, dx):
     """(f(i - j), inside) for the offset j = (dz, dy, dx): the neighbour's
     value and whether it lies in the volume."""
     D, H, W = f.shape
     val = np.zeros_like(f)
     ins = np.zeros(f.shape, dtype=bool)
-    zs, ys, xs = slice(max(dz, 0), D + min(dz, 0)), slice(max(dy, 0), H + min(dy, 0)), \
-        slice(max(dx, 0), W + min(dx, 0))
-    zt, yt, xt = slice(max(-dz, 0), D + min(-dz, 0)), slice(max(-dy, 0), H + min(-dy, 0)), \
-        slice(max(-dx, 0), W + min(-dx, 0))
+    (zs, zt), (ys, yt), (xs, xt) = _span(D, dz), _span(H, dy), _span(W, dx)
     val[zs, ys, xs] = f[zt, yt, xt]
     ins[zs, ys, xs] = True
     return val, ins
