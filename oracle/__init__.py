@@ -7,6 +7,8 @@ Provably Accurate Bilateral Filtering" (arXiv 1603.08109):
 * ``gpa_definition``     -- eq. GPA with phi_N of eq. GaussPolynomial, brute force.
 * ``gpa_alg2``           -- Algorithm 2 (GPA) step by step over whole images.
 * ``gpa_alg2_at``        -- Algorithm 2 evaluated at sampled pixels.
+* ``gpa_term_magnitudes`` -- the sums of eq. GPA's terms in absolute value
+                            (the conditioning of its ratio).
 * ``*_grad``             -- exact derivatives of eq. BF / eq. GPA with respect
                             to the image and sigma_r (chain rule on the ratio).
 * ``order``              -- order selection and kernel error (Sec. II).
@@ -148,6 +150,19 @@ def gpa_definition(img, w, sigma_r, N, T=128.0, samples=None, return_parts=False
     brute force. Parts: num = P_2, den = Q_2 of App. C."""
     out, num, den = _range_filter(1, img, w, sigma_r, N, T, samples)
     return (out, num, den) if return_parts else out
+
+
+def gpa_term_magnitudes(img, w, sigma_r, N, T=128.0, samples=None):
+    """Magnitudes of the sums behind eq. GPA's ratio, term by term:
+    S_P = sum_j w(j) |t| sum_{n<N} |a_n(t) a_n(tau)| and
+    S_Q = sum_j w(j) sum_{n<N} |a_n(t) a_n(tau)| (t = f(i-j) - T, tau = f(i) - T,
+    the n-th term of phi_N in eq. GaussPolynomial taken in absolute value).
+    Same units as ``gpa_definition``'s (num, den).  A finite-precision
+    evaluation of eq. GPA in any summation order carries absolute errors of
+    order u * S_P and u * S_Q in its numerator and denominator; where the terms
+    cancel (S_Q >> |den|) the ratio is ill-conditioned."""
+    _, num, den = _range_filter(2, img, w, sigma_r, N, T, samples)
+    return num, den
 
 
 def _joint(kind, img, guide, w, sigma_r, N, T, samples):

@@ -64,6 +64,10 @@ int orc_spatial_kernel(int kind, int r, double sigma_s, double *w)
 /*           (eq. range_kernel inside eq. BF);                               */
 /*   kind 1: phi_{N,sigma_r}(t, tau) = exp(-(t^2 + tau^2) / (2 sigma_r^2))   */
 /*           * sum_{n=0}^{N-1} (tau t / sigma_r^2)^n / n!  (eq. GaussPolynomial). */
+/*   kind 2: the same N terms of phi_N taken in absolute value,              */
+/*           exp(-(t^2 + tau^2) / (2 sigma_r^2)) * sum_n |tau t / sigma_r^2|^n / n!, */
+/*           the magnitude of the sum a finite-precision evaluation of       */
+/*           eq. GPA accumulates (value only; d[1..3] are not set).          */
 /* d[0] = value, d[1] = d/dt, d[2] = d/dtau, d[3] = d/dsigma_r.              */
 /* ------------------------------------------------------------------------ */
 
@@ -88,6 +92,9 @@ static void range_kernel(int kind, double t, double tau, double sr, int N, doubl
         d[1] = -u / s2 * g;
         d[2] = u / s2 * g;
         d[3] = u * u / (s2 * sr) * g;
+    } else if (kind == 2) {
+        d[0] = exp(-(t * t + tau * tau) / (2.0 * s2)) * trunc_exp(fabs(t * tau / s2), N);
+        d[1] = d[2] = d[3] = 0.0;
     } else {
         double gauss = exp(-(t * t + tau * tau) / (2.0 * s2));
         double x = t * tau / s2;
@@ -103,7 +110,8 @@ static void range_kernel(int kind, double t, double tau, double sr, int N, doubl
 }
 
 /* Ratio of eq. BF (kind 0) or eq. GPA (kind 1) at pixel (y, x), on centred
- * values h: num = sum_j w(j) k(h(i-j), h(i)) h(i-j), den = sum_j w(j) k(...). */
+ * values h: num = sum_j w(j) k(h(i-j), h(i)) h(i-j), den = sum_j w(j) k(...).
+ * kind 2 sums the term magnitudes: num = sum_j w(j) k_2(...) |h(i-j)|. */
 static void ratio_at(int kind, const double *h, int H, int W, const double *w, int r,
                      double sr, int N, int y, int x, double *num, double *den)
 {
@@ -119,7 +127,7 @@ static void ratio_at(int kind, const double *h, int H, int W, const double *w, i
             double t = h[IDX(yy, xx, W)];
             range_kernel(kind, t, tau, sr, N, d);
             double wk = w[(dy + r) * S + (dx + r)];
-            nsum += wk * d[0] * t;
+            nsum += wk * d[0] * (kind == 2 ? fabs(t) : t);
             dsum += wk * d[0];
         }
     }
@@ -135,16 +143,17 @@ static double *centred_copy(const double *f, long n, double T)
     return h;
 }
 
-/* eq. BF (kind 0) or eq. GPA written out with phi_N (kind 1), brute force.
- * If iy == NULL every pixel is computed and out/num/den hold H*W values;
+/* eq. BF (kind 0) or eq. GPA written out with phi_N (kind 1), brute force;
+ * kind 2 gives the term magnitudes of eq. GPA in num/den (out is then not a
+ * filter output).  If iy == NULL every pixel is computed and out/num/den hold H*W values;
  * otherwise nsamp pixels (iy[k], ix[k]) are computed.  num/den may be NULL. */
 int orc_range_filter(int kind, const double *f, int H, int W, const double *w, int r,
                      double sr, int N, double T, const int *iy, const int *ix, long nsamp,
                      double *out, double *num, double *den)
 {
     if (!f || !w || !out || H < 1 || W < 1 || r < 0 || !(sr > 0.0)) return ORC_BAD_ARG;
-    if (kind != 0 && kind != 1) return ORC_BAD_ARG;
-    if (kind == 1 && N < 1) return ORC_BAD_ARG;
+    if (kind != 0 && kind != 1 && kind != 2) return ORC_BAD_ARG;
+    if (kind != 0 && N < 1) return ORC_BAD_ARG;
     long npix = (long)H * W;
     double *h = centred_copy(f, npix, T);
     if (!h) return ORC_BAD_ARG;

@@ -69,7 +69,8 @@ def test_batched_equals_single_image_kernel_and_graph_replays():
         w = spatial(sp["kind"], sp["radius"], sp["sigma_s"])
         ro, P, Q = oracle.gpa_alg2(host[k], w, sp["sigma_r"], sp["N"], return_parts=True)
         compare_forward(first[k].cpu().numpy(), None, ro, scaled_q(host[k], Q, sp["sigma_r"]),
-                        w[sp["radius"], sp["radius"]], "batched %d" % k)
+                        w[sp["radius"], sp["radius"]], "batched %d" % k, sigma_r=sp["sigma_r"],
+                        N=sp["N"], img=host[k], w=w)
     plan.close()
 
 
@@ -91,5 +92,6 @@ def test_batched_full_256_workload():
     ro, P, Q = oracle.gpa_alg2_at(host[k], w, sp["sigma_r"], sp["N"], (ys, xs), return_parts=True)
     compare_forward(outs[k].cpu().numpy()[ys, xs], None, ro,
                     scaled_q(host[k][ys, xs], Q, sp["sigma_r"]), w[sp["radius"], sp["radius"]],
-                    "batched max-N image")
+                    "batched max-N image", sigma_r=sp["sigma_r"], N=sp["N"], img=host[k], w=w,
+                    pixels=(ys, xs))
     plan.close()

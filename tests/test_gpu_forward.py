@@ -46,7 +46,7 @@ def test_forward_matches_algorithm2(case):
     img = image(H, W, seed=H * 1000 + W)
     out, q = _run(img, kind, r, ss, sr, N)
     ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
-    compare_forward(out, q, ro, rq, w0, str(case), sigma_r=sr, N=N)
+    compare_forward(out, q, ro, rq, w0, str(case), sigma_r=sr, N=N, img=img, w=spatial(kind, r, ss))
 
 
 @pytest.mark.parametrize("variant", range(6))
@@ -60,7 +60,8 @@ def test_every_tile_variant(variant):
         except bf._lib.BFError as e:  # the fixed-radius variant covers W in {3, 5, 9, 15} only
             assert e.status == 3 and variant == 5 and r == 7
             continue
-        compare_forward(out, q, ro, rq, w0, "variant %d kind %d" % (variant, kind))
+        compare_forward(out, q, ro, rq, w0, "variant %d kind %d" % (variant, kind), sigma_r=30.0,
+                        N=40, img=img, w=spatial(kind, r, ss))
         ran += 1
     assert ran >= 2
 
@@ -82,17 +83,20 @@ def test_streaming_box_kernel(r, variant):
     for sr, N in orders:
         ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, sr, N)
         out, q = _run(img, bf.BOX, r, 0.0, sr, N, variant=variant)
-        compare_forward(out, q, ro, rq, w0, "stream v%d r=%d N=%d" % (variant, r, N), sigma_r=sr, N=N)
+        compare_forward(out, q, ro, rq, w0, "stream v%d r=%d N=%d" % (variant, r, N), sigma_r=sr, N=N,
+                        img=img, w=spatial(bf.BOX, r, 0.0))
     base = torch.zeros((H, W + 1), dtype=torch.float32, device="cuda")
     base[:, :W] = torch.from_numpy(img).cuda()
     o = bf.gpa_forward(base[:, :W], bf.BOX, 60.0, 3, radius=r, variant=variant)
     ro, rq, w0 = _ref(img, bf.BOX, r, 0.0, 60.0, 3)
-    compare_forward(o.cpu().numpy(), None, ro, rq, w0, "stream odd pitch", sigma_r=60.0, N=3)
+    compare_forward(o.cpu().numpy(), None, ro, rq, w0, "stream odd pitch", sigma_r=60.0, N=3,
+                    img=img, w=spatial(bf.BOX, r, 0.0))
     for shape in ((70, 517), (37, 243), (9, 5), (1, 1), (300, 3)):
         im = image(*shape, seed=shape[0] + shape[1], block=4)
         ro, rq, w0 = _ref(im, bf.BOX, r, 0.0, 70.0, 4)
         out, q = _run(im, bf.BOX, r, 0.0, 70.0, 4, variant=variant)
-        compare_forward(out, q, ro, rq, w0, "stream v%d shape %s" % (variant, shape), sigma_r=70.0, N=4)
+        compare_forward(out, q, ro, rq, w0, "stream v%d shape %s" % (variant, shape), sigma_r=70.0, N=4,
+                        img=im, w=spatial(bf.BOX, r, 0.0))
     with pytest.raises(bf._lib.BFError):
         bf.gpa_forward(torch.from_numpy(img).cuda(), bf.BOX, 30.0, 6 if variant == 6 else 9,
                        radius=r, variant=variant)
@@ -117,8 +121,11 @@ def test_forward_many(kind, r, ss, sr, N):
     for k in range(B):
         ro, rq, w0 = _ref(imgs[k], kind, r, ss, sr, N)
         where = "many k=%d kind %d r=%d N=%d" % (k, kind, r, N)
-        compare_forward(out[k].cpu().numpy(), q[k].cpu().numpy(), ro, rq, w0, where, sigma_r=sr, N=N)
-        compare_forward(out_p[k].cpu().numpy(), None, ro, rq, w0, where + " padded", sigma_r=sr, N=N)
+        wk = spatial(kind, r, ss)
+        compare_forward(out[k].cpu().numpy(), q[k].cpu().numpy(), ro, rq, w0, where, sigma_r=sr, N=N,
+                        img=imgs[k], w=wk)
+        compare_forward(out_p[k].cpu().numpy(), None, ro, rq, w0, where + " padded", sigma_r=sr, N=N,
+                        img=imgs[k], w=wk)
         one, _ = _run(imgs[k], kind, r, ss, sr, N)
         assert np.abs(out[k].cpu().numpy() - one).max() <= 1e-3, where
     # the last image alone past a batch of one: count 1 behaves as bf_fast_forward
@@ -149,7 +156,8 @@ def test_banded_two_pass(kind, r, ss):
     for band in (64, 128, None):
         out, q = bf.gpa_forward(x, kind, sr, N, radius=r, sigma_s=ss, return_q=True, band_rows=band)
         compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, rq, w0,
-                        "banded kind %d r %d band %s" % (kind, r, band), sigma_r=sr, N=N)
+                        "banded kind %d r %d band %s" % (kind, r, band), sigma_r=sr, N=N,
+                        img=img, w=spatial(kind, r, ss))
 
 
 @pytest.mark.parametrize("r", [3, 5, 9, 15])
@@ -162,7 +170,7 @@ def test_fixed_radius_kernel(r):
             ro, rq, w0 = _ref(img, kind, r, ss, sr, N)
             out, q = _run(img, kind, r, ss, sr, N, variant=5)
             compare_forward(out, q, ro, rq, w0, "fixed r=%d kind %d N=%d" % (r, kind, N),
-                            sigma_r=sr, N=N)
+                            sigma_r=sr, N=N, img=img, w=spatial(kind, r, ss))
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 9), (9, 1), (5, 7), (3, 400), (300, 3)])
@@ -171,7 +179,8 @@ def test_tiny_and_thin_images_radius_beyond_image(shape):
     for kind, r, ss in ((bf.GAUSS, 9, 3.0), (bf.BOX, 12, 0.0)):
         ro, rq, w0 = _ref(img, kind, r, ss, 30.0, 40)
         out, q = _run(img, kind, r, ss, 30.0, 40)
-        compare_forward(out, q, ro, rq, w0, "shape %s kind %d" % (shape, kind))
+        compare_forward(out, q, ro, rq, w0, "shape %s kind %d" % (shape, kind), sigma_r=30.0, N=40,
+                        img=img, w=spatial(kind, r, ss))
 
 
 def test_constant_image_is_fixed_point():
@@ -189,7 +198,8 @@ def test_pitched_input_and_cpu_tensor_roundtrip():
     assert view.stride(0) == 160
     out = bf.gpa_forward(view, bf.GAUSS, 30.0, 40, radius=9, sigma_s=3.0)
     ro, rq, w0 = _ref(img, bf.GAUSS, 9, 3.0, 30.0, 40)
-    compare_forward(out.cpu().numpy(), None, ro, rq, w0, "pitched")
+    compare_forward(out.cpu().numpy(), None, ro, rq, w0, "pitched", sigma_r=30.0, N=40, img=img,
+                    w=spatial(bf.GAUSS, 9, 3.0))
     out_cpu = bf.gpa_forward(torch.from_numpy(img), bf.GAUSS, 30.0, 40, radius=9, sigma_s=3.0)
     assert out_cpu.device.type == "cpu"
     assert torch.equal(out_cpu, out.cpu())
@@ -231,7 +241,8 @@ def _sampled_case(H, W, gen, kind, r, ss, sr, N, nsamp, seed):
     rq = scaled_q(img[ys, xs], Q, sr)
     o = out[ys, xs].cpu().numpy()
     qq = q[ys, xs].cpu().numpy()
-    return compare_forward(o, qq, ro, rq, w[r, r], "sampled %dx%d" % (H, W))
+    return compare_forward(o, qq, ro, rq, w[r, r], "sampled %dx%d" % (H, W), sigma_r=sr, N=N,
+                           img=img, w=w, pixels=(ys, xs))
 
 
 def test_full_size_2048_sampled():

@@ -53,7 +53,7 @@ def test_random_forward_and_backward(seed):
     w = spatial(kind, r, ss)
     ro, P, Q = oracle.gpa_alg2(img, w, sr, N, return_parts=True)
     compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, sr), w[r, r], where,
-                    sigma_r=sr, N=N)
+                    sigma_r=sr, N=N, img=img, w=w)
     if small_n:  # orders below the bound: the ratio is ill-conditioned at some pixels
         return
     g = synth.random_like((H, W), seed=seed + 5)

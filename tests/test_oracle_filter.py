@@ -227,3 +227,73 @@ def test_gradient_sampled_equals_full():
     xs = np.array([20, 0, 10, 4])
     part, _ = oracle.gpa_grad(img, w, 25.0, 30, g, samples=(ys, xs))
     assert np.array_equal(part, full[ys, xs])
+
+
+# ------------------------------------------------ term magnitudes (conditioning)
+def test_term_magnitudes_order1_is_spatial_filter_of_positive_terms():
+    """N = 1: the single term e^{-(t^2+tau^2)/2 s^2} is positive, so S_Q = Q'
+    = e(i) (w * e)(i) and S_P = e(i) (w * |h| e)(i) (scipy convolution with an
+    asymmetric kernel on a non-square image)."""
+    img = synth.blocks_image(17, 27, 6, 20.0, seed=24).astype(np.float64)
+    w = _asym_kernel(3, seed=8)
+    sr = 35.0
+    h = img - T
+    e = np.exp(-h * h / (2 * sr * sr))
+    sp, sq = oracle.gpa_term_magnitudes(img, w, sr, 1)
+    ref_q = e * ndimage.convolve(e, w, mode="constant", cval=0.0)
+    ref_p = e * ndimage.convolve(np.abs(h) * e, w, mode="constant", cval=0.0)
+    assert np.abs(sq - ref_q).max() < 1e-13
+    assert np.abs(sp - ref_p).max() < 1e-11
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_term_magnitudes_equal_algorithm2_sums_on_one_sided_images(sign):
+    """Every intensity on one side of t_c: all terms t^n tau^n are >= 0, so the
+    magnitudes are Algorithm 2's own sums (Q' = e^{-H^2/2} Q and
+    P' = (out - t_c) Q'), evaluated by its recursion (an independent route);
+    for intensities below t_c the numerator is the negated P'."""
+    rng = np.random.default_rng(4)
+    img = T + sign * rng.uniform(0.0, 127.0, size=(19, 23))
+    w = _asym_kernel(2, seed=3)
+    sr, N = 30.0, 7
+    out, P, Q = oracle.gpa_alg2(img, w, sr, N, return_parts=True)
+    H = (img - T) / sr
+    qs = Q * np.exp(-H * H / 2)
+    sp, sq = oracle.gpa_term_magnitudes(img, w, sr, N)
+    assert np.abs(sq - qs).max() < 1e-12
+    assert np.abs(sp - sign * (out - T) * qs).max() < 1e-9
+
+
+def test_term_magnitudes_large_order_limit_brute_force():
+    """As N grows, sum_n |t tau|^n / (s^2n n!) -> e^{|t tau|/s^2}, so each term
+    sum tends to e^{-(|t| - |tau|)^2 / 2 s^2}: brute force over a tiny image."""
+    img = synth.blocks_image(9, 11, 3, 25.0, seed=6).astype(np.float64)
+    w = _asym_kernel(2, seed=12)
+    sr = 45.0
+    sp, sq = oracle.gpa_term_magnitudes(img, w, sr, 200)
+    h = np.abs(img - T)
+    r = 2
+    Hh, Ww = img.shape
+    for y in range(Hh):
+        for x in range(Ww):
+            rq = rp = 0.0
+            for dy in range(-r, r + 1):
+                for dx in range(-r, r + 1):
+                    yy, xx = y - dy, x - dx
+                    if 0 <= yy < Hh and 0 <= xx < Ww:
+                        g = np.exp(-(h[yy, xx] - h[y, x]) ** 2 / (2 * sr * sr))
+                        rq += w[dy + r, dx + r] * g
+                        rp += w[dy + r, dx + r] * g * h[yy, xx]
+            assert abs(sq[y, x] - rq) < 1e-12 and abs(sp[y, x] - rp) < 1e-10
+
+
+def test_term_magnitudes_bound_the_signed_sums():
+    """|num| <= S_P and |den| <= S_Q everywhere; at N = 2 with intensities on
+    both sides of t_c some terms cancel (strict inequality somewhere)."""
+    img = synth.blocks_image(20, 30, 5, 20.0, seed=9).astype(np.float64)
+    w = oracle.spatial_kernel(0, 3)
+    for N in (2, 3, 10):
+        sp, sq = oracle.gpa_term_magnitudes(img, w, 40.0, N)
+        _, num, den = oracle.gpa_definition(img, w, 40.0, N, return_parts=True)
+        assert (np.abs(den) <= sq * (1 + 1e-12)).all() and (np.abs(num) <= sp * (1 + 1e-12)).all()
+        assert (sq > np.abs(den) * 1.01).any()

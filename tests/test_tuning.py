@@ -39,4 +39,4 @@ def test_autotune_then_forward_meets_parity(tmp_path):
     w = spatial(bf.GAUSS, 12, 4.0)
     ro, P, Q = oracle.gpa_alg2(img, w, 30.0, 24, return_parts=True)
     compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, 30.0), w[12, 12],
-                    "tuned", sigma_r=30.0, N=24)
+                    "tuned", sigma_r=30.0, N=24, img=img, w=w)
