@@ -87,7 +87,8 @@ typedef struct {
 
 /* ------------------------------------------------------------------ misc */
 const char *bf_status_string(int status);
-/* Message of the last CUDA error seen by this library in this thread. */
+/* Message of the last CUDA error seen by this library in this thread, or the
+ * reason given with the last BF_ERR_UNSUPPORTED that carries one. */
 const char *bf_last_cuda_error(void);
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int bf_version(void);
@@ -143,8 +144,10 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
                           int height, int width, int pitch,
                           const bf_params *p, void *stream);
 
-/* Forward with a caller-provided workspace, for large radii (Gaussian W >= 12
- * except 15, box W > 15, where it is faster than the fused kernels).  The
+/* Forward with a caller-provided workspace, for large radii (by default
+ * Gaussian W >= 12 except 15, box W > 15, where it is faster than the fused
+ * kernels; the tuning table below can choose it, variant 8, for other radii
+ * and keep the fused kernels at some of these).  The
  * spatial filter is separable (eq. spatial_kernel1 on the square Omega), so
  * the image is processed in bands of rows, two kernels per band: the first
  * filters the columns of every power image a_0..a_N of the band (with the
@@ -153,18 +156,25 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
  * Results equal bf_fast_forward's up to float rounding.
  * bf_fast_forward_workspace: the workspace in bytes for bands tall enough
  *   to give each launch several waves of CTAs (at most 2 GiB unless 64 rows
- *   need more); 0 below those radii (bf_fast_forward_ws then runs
- *   bf_fast_forward).
+ *   need more); 0 when the banded path is not chosen (bf_fast_forward_ws
+ *   then runs the fused kernels, as bf_fast_forward).
  * bf_fast_forward_ws: d_workspace device memory, 16-byte aligned, owned by
  *   the caller, of ws_bytes >= 64 rows of N + 1 planes, i.e. 64 (N+1) Wp
  *   floats with Wp = width rounded up to a multiple of 4; a larger workspace
  *   gives taller bands.  Same arguments and outputs as bf_fast_forward.
- *   BF_ERR_WORKSPACE for a missing or too small workspace at those radii. */
+ *   BF_ERR_WORKSPACE for a missing or too small workspace when the banded
+ *   path is chosen.
+ * bf_fast_forward_ws_variant: the same with an explicit variant (see the
+ *   tuning section; -1 = the table / built-in choice, as bf_fast_forward_ws). */
 bf_status bf_fast_forward_workspace(int height, int width, const bf_params *p,
                                     size_t *bytes);
 bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux,
                              int height, int width, int pitch, const bf_params *p,
                              void *d_workspace, size_t ws_bytes, void *stream);
+bf_status bf_fast_forward_ws_variant(const float *d_in, float *d_out, float *d_qaux,
+                                     int height, int width, int pitch, const bf_params *p,
+                                     int variant, void *d_workspace, size_t ws_bytes,
+                                     void *stream);
 
 /* bf_fast_forward for `count` images of the same height, width, pitch and
  * parameters (e.g. the frames of a video): image k is read from
@@ -245,11 +255,20 @@ bf_status bf_fast_backward_stored(const float *d_in, const float *d_out, const f
  *  - All calls share the array and it keeps the last call's partial sums;
  *    each call writes every entry it reads, so nothing needs clearing, but
  *    calls that overlap on the GPU (e.g. on two streams) race on it.
- *  - An image that needs more than 65536 partial sums (one per CTA of the
- *    backward grid: roughly beyond 5.7e7 pixels at W = 9, e.g. above
- *    7500 x 7500) is rejected with BF_ERR_UNSUPPORTED before any
- *    GPU work.  Nothing here calls cudaMalloc, cudaFree or any allocating
- *    library routine. */
+ *  - With d_gsigma non-NULL, an image that needs more than 65536 partial
+ *    sums (one per CTA of the backward grid: roughly beyond 5.7e7 pixels at
+ *    W = 9, e.g. above 7500 x 7500) is rejected with BF_ERR_UNSUPPORTED
+ *    before any GPU work.  With d_gsigma NULL no scratch is used and any
+ *    image size is accepted.
+ *  - Radii are limited to those whose fused backward tile fits in shared
+ *    memory (227 KB per block): Gaussian W <= 50, box W <= 39.  Larger radii
+ *    return BF_ERR_UNSUPPORTED with that reason in bf_last_cuda_error();
+ *    bf_fast_backward takes them through its banded backward, which needs a
+ *    caller workspace.
+ *  - The cached address outlives a cudaDeviceReset, so a device that was
+ *    reset after the first call is not supported.
+ *  Nothing here calls cudaMalloc, cudaFree or any allocating library
+ *  routine. */
 bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_out, const float *d_qaux,
                                    const float *d_gout, float *d_gin, double *d_gsigma,
                                    int height, int width, int pitch, const bf_params *p,
@@ -303,20 +322,32 @@ bf_status bf_joint_direct(const float *d_in, const float *d_guide, float *d_out,
 
 /* --------------------------------------------------- batched forward
  * Many images of uneven sizes, each with its own spatial kind, W, sigma_s,
- * sigma_r and N.  Images below the banded radii (see bf_fast_forward_ws) are
- * filtered by ONE persistent launch:
- * CTAs take output tiles from a device work queue (longest work first) until
- * it is empty.  The others take the two-pass banded forward (see
- * bf_fast_forward_ws): one column-pass launch and one row-pass launch over
- * the tiles of a group of images, their planes in the plan's workspace
- * (groups keep the plane region at most 4 GiB, reused group after group).
- * Results equal the single-image paths bit for bit.
- * Usage: bf_batch_plan_create (host: validates, picks tile shapes, orders
+ * sigma_r and N.  Each image runs the variant that the tuning table (below)
+ * holds for its (kind, radius bucket, order bucket), or the built-in choice
+ * of bf_fast_forward_ws where the table has no entry or its entry does not
+ * fit the image's radius:
+ *  - runtime-radius tiles (variants 0..4): ONE persistent launch per tile
+ *    shape present, whose CTAs take output tiles from a device work queue
+ *    (longest work first) until it is empty;
+ *  - compile-time-radius and warp-strip kernels (variants 5..7): one launch
+ *    per image (their filter taps are constant-bank operands of a launch);
+ *  - the two-pass banded forward (variant 8): one column-pass launch and one
+ *    row-pass launch over the tiles of a group of images, their planes in the
+ *    plan's workspace (groups keep the plane region at most 4 GiB, reused
+ *    group after group).
+ * The three groups run on the caller's stream and two side streams of the
+ * plan, forked from and joined back into the caller's stream with events.
+ * Each image's result equals the single-image call with its variant bit for
+ * bit.  The table is read when the plan is created.
+ * Usage: bf_batch_plan_create (host: validates, picks the variants, orders
  * the work) -> bf_batch_workspace -> bf_batch_upload (enqueue the plan's
  * tables into the workspace; the plan must stay alive until that copy has
  * completed) -> bf_batch_forward, any number of times (graph-capturable: a
- * memset node, the persistent kernel and two kernels per banded group; no
- * allocation, no host synchronisation) -> bf_batch_plan_destroy. */
+ * memset node, the persistent kernels, the per-image kernels and two kernels
+ * per banded group as parallel branches; no allocation, no host
+ * synchronisation) -> bf_batch_plan_destroy.
+ * bf_batch_variants: the variant each image runs (count = the plan's image
+ * count). */
 typedef struct {
     const float *d_in;   /* device input image                    */
     float *d_out;        /* device output image                   */
@@ -329,8 +360,10 @@ typedef struct bf_batch_plan bf_batch_plan;
 
 bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_plan **plan);
 bf_status bf_batch_workspace(const bf_batch_plan *plan, size_t *bytes);
-/* Number of work items (tiles) and CTAs the plan launches. */
+/* Number of work items (tiles of the persistent and banded launches, plus
+ * one per whole-image launch) and CTAs of the persistent launches. */
 bf_status bf_batch_info(const bf_batch_plan *plan, int *items, int *ctas);
+bf_status bf_batch_variants(const bf_batch_plan *plan, int *variants, int count);
 bf_status bf_batch_upload(const bf_batch_plan *plan, void *d_workspace,
                           size_t workspace_bytes, void *stream);
 /* d_status (optional, device int): set to BF_ERR_INVALID_ARG by the kernel
@@ -350,13 +383,24 @@ bf_status bf_graph_launch(void *graph_exec, void *stream);
 void bf_graph_destroy(void *graph_exec);
 
 /* ---------------------------------------------------- tile autotuning
- * The fused kernels come in several tile shapes (variants).  The library
- * keeps a table variant[kind][radius bucket][order bucket]; the defaults
- * are compiled in, bf_autotune times every variant on caller-provided
- * device buffers (it synchronises `stream`) and records the fastest.
+ * The forward comes in several kernels and tile shapes (variants):
+ *   0..4  the runtime-radius fused tile with (threads, output rows) =
+ *         (256, 16), (512, 8), (256, 8), (128, 16), (192, 8);
+ *   5     the compile-time-radius fused tile (W in {3, 5, 9, 15});
+ *   6, 7  the warp-strip streaming box kernel, 8 / 4 columns per lane
+ *         (box, W in {3, 5}, N <= 5 / N <= 8);
+ *   8     the two-pass banded forward (needs the workspace of
+ *         bf_fast_forward_ws; the calls without one skip it).
+ * The library keeps a table variant[kind][radius bucket][order bucket]
+ * (-1 = the built-in choice); bf_autotune times every variant that fits on
+ * caller-provided device buffers (it synchronises `stream`) and records the
+ * fastest.  The single-image forwards and the batch plan read the table.
  *  bf_variant_count        number of variants for a kind (>= 1).
- *  bf_fast_forward_variant forward with an explicit variant (-1 = table).
- *  bf_autotune             time all variants for (kind, W, N) at this size;
+ *  bf_fast_forward_variant forward with an explicit variant (-1 = table);
+ *                          variant 8 returns BF_ERR_WORKSPACE here.
+ *  bf_autotune(_ws)        time all variants for (kind, W, N) at this size
+ *                          (with a workspace of at least 64 band rows, see
+ *                          bf_fast_forward_ws, the banded forward too);
  *                          writes the winner to *best and into the table.
  *  bf_tuning_get/set       read / write one table entry (for a JSON cache). */
 int bf_variant_count(int kind);
@@ -366,6 +410,9 @@ bf_status bf_fast_forward_variant(const float *d_in, float *d_out, float *d_qaux
 bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, int pitch,
                       const bf_params *p, int reps, void *stream, int *best,
                       float *best_ms);
+bf_status bf_autotune_ws(const float *d_in, float *d_out, int height, int width, int pitch,
+                         const bf_params *p, void *d_workspace, size_t workspace_bytes,
+                         int reps, void *stream, int *best, float *best_ms);
 int bf_tuning_radius_bucket(int radius);
 int bf_tuning_order_bucket(int order_N);
 bf_status bf_tuning_get(int kind, int radius_bucket, int order_bucket, int *variant);

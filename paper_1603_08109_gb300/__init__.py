@@ -8,7 +8,7 @@ behind the C ABI in include/bf.h.  This package is the thin Python layer:
 ``api`` (PyTorch tensors in, library calls out), ``_lib`` (ctypes
 signatures), ``build`` (nvcc), ``synth`` (seeded synthetic inputs).
 """
-from .api import (BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
+from .api import (BANDED_VARIANT, BOX, GAUSS, GAUSS_RECURSIVE, BatchPlan, DirectBilateral, GPABilateral, autotune,  # noqa: F401
                   centre_weight, direct, direct_backward, direct_bilateral, gpa_backward,
                   exhaustive_order, forward_workspace_bytes, gpa_bilateral, gpa_forward,
                   gpa_forward_many, gpa_forward_stored, gpa_volume, joint_direct,

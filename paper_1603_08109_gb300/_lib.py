@@ -60,6 +60,7 @@ SIGNATURES = {
     "bf_joint_forward_workspace": (_i, [_i, _i, _pp, ctypes.POINTER(_sz)]),
     "bf_joint_forward_ws": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
     "bf_fast_forward_ws": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
+    "bf_fast_forward_ws_variant": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _i, _vp, _sz, _vp]),
     "bf_recursive_workspace": (_i, [_i, _i, _i, ctypes.POINTER(_sz)]),
     "bf_recursive_gauss": (_i, [_vp, _vp, _i, _i, _i, ctypes.c_float, _vp, _sz, _vp]),
     "bf_recursive_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp, _sz, _vp]),
@@ -86,6 +87,7 @@ SIGNATURES = {
     "bf_batch_plan_create": (_i, [ctypes.POINTER(BfImageDesc), _i, ctypes.POINTER(_vp)]),
     "bf_batch_workspace": (_i, [_vp, ctypes.POINTER(_sz)]),
     "bf_batch_info": (_i, [_vp, _ip, _ip]),
+    "bf_batch_variants": (_i, [_vp, _ip, _i]),
     "bf_batch_upload": (_i, [_vp, _vp, _sz, _vp]),
     "bf_batch_forward": (_i, [_vp, _vp, _sz, _vp, _vp]),
     "bf_batch_plan_destroy": (None, [_vp]),
@@ -95,6 +97,7 @@ SIGNATURES = {
     "bf_variant_count": (_i, [_i]),
     "bf_fast_forward_variant": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _i, _vp]),
     "bf_autotune": (_i, [_vp, _vp, _i, _i, _i, _pp, _i, _vp, _ip, _fp]),
+    "bf_autotune_ws": (_i, [_vp, _vp, _i, _i, _i, _pp, _vp, _sz, _i, _vp, _ip, _fp]),
     "bf_tuning_radius_bucket": (_i, [_i]),
     "bf_tuning_order_bucket": (_i, [_i]),
     "bf_tuning_get": (_i, [_i, _i, _i, _ip]),

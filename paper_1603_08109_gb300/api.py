@@ -25,8 +25,10 @@ __all__ = [
     "recursive_backward", "recursive_backward_workspace_bytes", "RecursiveBilateral",
     "recursive_bilateral", "recursive_joint_forward", "recursive_forward_stored",
     "recursive_backward_stored", "gpa_forward_many", "gpa_volume", "volume_order_from_delta",
-    "volume_workspace_bytes",
+    "volume_workspace_bytes", "BANDED_VARIANT",
 ]
+
+BANDED_VARIANT = 8  # the two-pass banded forward in the variant numbering of bf.h
 
 
 def resolve_radius(kind: int, radius: int, sigma_s: float) -> int:
@@ -145,27 +147,33 @@ def gpa_forward(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: in
                 band_rows: Optional[int] = None):
     """f_GPA of eq. GPA (Algorithm 2).  Returns out, or (out, Q').
 
-    variant -1 picks the kernel: for radii above 15 the banded two-pass
-    forward with a workspace from torch's allocator (band_rows, a multiple of
-    64, overrides its band height); otherwise, or for an explicit variant,
-    the fused single-pass kernels."""
+    variant -1 picks the kernel from the tuning table or the built-in rule:
+    the banded two-pass forward (by default for radii above 15) with a
+    workspace from torch's allocator (band_rows, a multiple of 64, overrides
+    its band height), else the fused single-pass kernels.  An explicit
+    variant runs that kernel (BANDED_VARIANT: the banded forward)."""
     x, on_cpu = _as_device_image(img)
     o = _image_like(x, out if not on_cpu else None)
     q = _like(x) if return_q else None
     p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
     H, W = x.shape
     nbytes = 0
+    row_bytes = (int(N) + 1) * ((W + 3) // 4 * 4) * 4
     if variant < 0:
         n = ctypes.c_size_t(0)
         check(lib().bf_fast_forward_workspace(H, W, ctypes.byref(p), ctypes.byref(n)),
               "bf_fast_forward_workspace")
         nbytes = int(n.value)
+    elif variant == BANDED_VARIANT:  # the whole image as one band, up to 1 GiB of planes
+        rows = min((H + 63) // 64 * 64, max(64, (1 << 30) // row_bytes // 64 * 64))
+        nbytes = rows * row_bytes
     if nbytes > 0:
         if band_rows is not None:
-            nbytes = int(band_rows) * (int(N) + 1) * ((W + 3) // 4 * 4) * 4
+            nbytes = int(band_rows) * row_bytes
         ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device)
-        st = lib().bf_fast_forward_ws(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
-                                      ctypes.byref(p), _ptr(ws), nbytes, _stream(x.device))
+        st = lib().bf_fast_forward_ws_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
+                                              ctypes.byref(p), int(variant), _ptr(ws), nbytes,
+                                              _stream(x.device))
     else:
         st = lib().bf_fast_forward_variant(_ptr(x), _ptr(o), _ptr(q), H, W, x.stride(0),
                                            ctypes.byref(p), int(variant), _stream(x.device))
@@ -699,6 +707,14 @@ class BatchPlan:
               "bf_batch_info")
         return items.value, ctas.value
 
+    def variants(self):
+        """The forward variant each image runs (read from the tuning table when
+        the plan was created)."""
+        n = len(self.images)
+        v = (ctypes.c_int * n)()
+        check(lib().bf_batch_variants(self._plan, v, n), "bf_batch_variants")
+        return list(v)
+
     def run(self):
         check(lib().bf_batch_forward(self._plan, _ptr(self.ws), ctypes.c_size_t(self.ws_bytes),
                                      _ptr(self.status), _stream(self.device)), "bf_batch_forward")
@@ -758,13 +774,20 @@ def tuning_set(kind: int, rb: int, ob: int, variant: int) -> None:
 
 
 def autotune(img: torch.Tensor, kind: int, sigma_r: float, N: int, radius: int = 0,
-             sigma_s: float = 0.0, t_c: float = 128.0, reps: int = 5):
-    """Time every tile variant on this image; record and return (variant, ms)."""
+             sigma_s: float = 0.0, t_c: float = 128.0, reps: int = 5, banded: bool = True):
+    """Time every variant on this image (with banded=True also the two-pass
+    banded forward, in a workspace of 64 band rows from torch's allocator);
+    record the fastest in the tuning table and return (variant, ms)."""
     x, _ = _as_device_image(img)
     o = _like(x)
     p = _params(kind, radius, sigma_s, sigma_r, N, t_c)
     best, ms = ctypes.c_int(), ctypes.c_float()
-    check(lib().bf_autotune(_ptr(x), _ptr(o), x.shape[0], x.shape[1], x.stride(0),
-                            ctypes.byref(p), int(reps), _stream(x.device), ctypes.byref(best),
-                            ctypes.byref(ms)), "bf_autotune")
+    H, W = x.shape
+    row_bytes = (int(N) + 1) * ((W + 3) // 4 * 4) * 4
+    rows = min((H + 63) // 64 * 64, max(64, (1 << 30) // row_bytes // 64 * 64))
+    nbytes = rows * row_bytes if banded else 0
+    ws = torch.empty(max(nbytes // 4, 1), dtype=torch.float32, device=x.device) if banded else None
+    check(lib().bf_autotune_ws(_ptr(x), _ptr(o), H, W, x.stride(0), ctypes.byref(p), _ptr(ws),
+                               nbytes, int(reps), _stream(x.device), ctypes.byref(best),
+                               ctypes.byref(ms)), "bf_autotune_ws")
     return best.value, ms.value

@@ -1,24 +1,34 @@
 // Batched forward: many images of uneven sizes, each with its own spatial
 // kind, W, sigma_s, sigma_r and N.
 //
-// Images below the banded path's radii (Gaussian W < 12 or W = 15, box
-// W <= 15) go through ONE persistent launch: the host plan splits
-// them into output tiles (work items), estimates each item's cost from its
-// (N + 1) filterings and tile geometry, and sorts the items longest first.
-// The grid is sized to the device (SMs x resident CTAs).  Each CTA
-// repeatedly takes the next item index from a device counter (atomicAdd; no
-// CTA ever waits on another) and runs the same tile body as the single-image
-// kernel with that item's parameters.
+// Each image runs the forward variant that the tuning table names for its
+// (kind, radius bucket, order bucket), or the built-in choice where the table
+// has no entry (bfi::forward_variant, the same rule a single-image call with
+// a workspace follows), so every image's result equals the single-image call
+// with that variant bit for bit.  The variants fall into three groups:
 //
-// The other images take the two-pass banded forward (gpa_banded.cuh), one
-// launch per pass over the tiles of a group of images (longest first); each
-// image's N + 1 column-filtered planes live in the plan's workspace, groups
-// are formed so that one group's planes fit a 4 GiB region that the next
-// group reuses.
+//  * runtime-radius tiles (variants 0..4, one (threads, rows) shape each):
+//    ONE persistent launch per shape present.  The host plan splits the
+//    images into output tiles (work items), estimates each item's cost from
+//    its (N + 1) filterings and tile geometry and sorts the items longest
+//    first.  The grid is sized to the device (SMs x resident CTAs); each CTA
+//    repeatedly takes the next item index from the shape's device counter
+//    (atomicAdd; no CTA ever waits on another) and runs the single-image
+//    tile body with that item's parameters;
+//  * whole-image kernels (variant 5, compile-time radius, and variants 6 / 7,
+//    warp-strip box): these keep the image's filter taps as constant-bank
+//    operands of a launch, so each such image is its own launch;
+//  * the two-pass banded forward (variant 8, gpa_banded.cuh): one launch per
+//    pass over the tiles of a group of images (longest first); each image's
+//    N + 1 column-filtered planes live in the plan's workspace, groups are
+//    formed so that one group's planes fit a 4 GiB region that the next group
+//    reuses.
 //
-// A launch is a memset of the counter, the persistent kernel and the
-// per-group pass launches, so it can be captured in a CUDA graph and
-// replayed.
+// The persistent launches run on the caller's stream, the whole-image
+// launches and the banded groups on two side streams of the plan that fork
+// from and join back into it with events, so the three groups overlap and a
+// captured CUDA graph holds them as parallel branches.  A launch is a memset
+// of the counters plus these kernels, so it can be captured and replayed.
 #include <stdlib.h>
 #include <string.h>
 
@@ -33,13 +43,11 @@
 
 namespace {
 
-constexpr int BNT = 256;  // threads per CTA (= region columns)
+constexpr int kMaxTileGroups = 5;  // runtime-radius tile variants 0..4
 
 struct BatchDesc {
   bfk::TileIO io;
   bfi::FilterConsts fc;
-  int th;  // output rows per tile for this image (16 or 8)
-  int pad[3];
 };
 
 struct WorkItem {
@@ -48,13 +56,14 @@ struct WorkItem {
 
 struct BatchArgs {
   const BatchDesc *descs;
-  const WorkItem *items;
+  const WorkItem *items;  // this launch's items
   int *counter;
   int *status;
   int count, nitems;
 };
 
-__global__ void __launch_bounds__(BNT) gpa_batched_kernel(const __grid_constant__ BatchArgs A) {
+template <int NT, int TH>
+__global__ void __launch_bounds__(NT) gpa_batched_kernel(const __grid_constant__ BatchArgs A) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_item;
   for (;;) {
@@ -70,22 +79,38 @@ __global__ void __launch_bounds__(BNT) gpa_batched_kernel(const __grid_constant_
     }
     const BatchDesc &d = A.descs[w.desc];
     const bfi::FilterConsts &fc = d.fc;
-    if (fc.kind == BF_SPATIAL_GAUSS) {
-      if (d.th == 16)
-        bfk::gpa_fwd_tile<1, BNT, 16, 16, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
-      else
-        bfk::gpa_fwd_tile<1, BNT, 8, 8, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
-    } else {
-      if (d.th == 16)
-        bfk::gpa_fwd_tile<0, BNT, 16, 16, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
-      else
-        bfk::gpa_fwd_tile<0, BNT, 8, 8, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
-    }
+    if (fc.kind == BF_SPATIAL_GAUSS)
+      bfk::gpa_fwd_tile<1, NT, TH, TH, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
+    else
+      bfk::gpa_fwd_tile<0, NT, TH, TH, false>(d.io, fc, fc.taps, w.ty0, w.tx0, smem);
     __syncthreads();  // the next item's region load reuses shared memory
   }
 }
 
-// ---- banded items (the banded path's radii)
+// The persistent kernel of tile variant v (shapes as in gpa_fwd.cu).
+const void *tile_kernel(int v) {
+  switch (v) {
+    case 0: return reinterpret_cast<const void *>(gpa_batched_kernel<256, 16>);
+    case 1: return reinterpret_cast<const void *>(gpa_batched_kernel<512, 8>);
+    case 2: return reinterpret_cast<const void *>(gpa_batched_kernel<256, 8>);
+    case 3: return reinterpret_cast<const void *>(gpa_batched_kernel<128, 16>);
+    case 4: return reinterpret_cast<const void *>(gpa_batched_kernel<192, 8>);
+    default: return nullptr;
+  }
+}
+
+void launch_tile_kernel(int v, int ctas, size_t smem, cudaStream_t s, const BatchArgs &A) {
+  switch (v) {
+    case 0: gpa_batched_kernel<256, 16><<<ctas, 256, smem, s>>>(A); break;
+    case 1: gpa_batched_kernel<512, 8><<<ctas, 512, smem, s>>>(A); break;
+    case 2: gpa_batched_kernel<256, 8><<<ctas, 256, smem, s>>>(A); break;
+    case 3: gpa_batched_kernel<128, 16><<<ctas, 128, smem, s>>>(A); break;
+    case 4: gpa_batched_kernel<192, 8><<<ctas, 192, smem, s>>>(A); break;
+    default: break;
+  }
+}
+
+// ---- banded items
 struct BandItem {
   int desc, bx, by, pad;
 };
@@ -128,6 +153,18 @@ struct BandGroup {
   size_t vsmem, hsmem;
 };
 
+struct TileGroup {
+  int variant, NT, TH;
+  int item0, nitems;  // range in the plan's item table
+  size_t smem;
+  int ctas;
+};
+
+struct WholeImage {
+  bf_image_desc d;
+  int variant;
+};
+
 constexpr size_t kBatchPlaneCap = 4ull << 30;  // plane bytes per group
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -136,15 +173,25 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct bf_batch_plan {
   std::vector<BatchDesc> descs;
+  std::vector<int> variants;  // per image
   std::vector<WorkItem> items;
+  std::vector<TileGroup> tgroups;
+  std::vector<WholeImage> whole;
   std::vector<bfk::BandArgs> bdescs;
   std::vector<BandItem> bitems;
   std::vector<BandGroup> groups;
-  size_t smem = 0;
-  int ctas = 0;
+  cudaStream_t side[2] = {nullptr, nullptr};  // whole-image launches, banded groups
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   size_t off_descs = 0, off_items = 0, off_bdescs = 0, off_bitems = 0, off_planes = 0;
   size_t ws_bytes = 0;
   std::vector<unsigned char> staging;  // tables, laid out as in the workspace
+  ~bf_batch_plan() {
+    for (cudaStream_t s : side)
+      if (s) cudaStreamDestroy(s);
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 extern "C" {
@@ -154,59 +201,67 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
   *plan_out = nullptr;
   bf_batch_plan *plan = new (std::nothrow) bf_batch_plan();
   if (!plan) return BF_ERR_INVALID_ARG;
-  int smem_optin = 232448, dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
-          cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  auto fail = [&](bf_status st) {
     delete plan;
-    return bfi::check_launch();
-  }
+    return st;
+  };
   struct Cost {
     double c;
     WorkItem w;
   };
-  std::vector<Cost> costs;
+  std::vector<Cost> costs[kMaxTileGroups];
+  size_t gsmem[kMaxTileGroups] = {};
   std::vector<int> large;  // images for the banded path
   plan->descs.resize(count);
+  plan->variants.resize(count);
   for (int i = 0; i < count; ++i) {
     const bf_image_desc &d = descs[i];
     bf_status st = bfi::check_image(d.d_in, d.d_out, d.height, d.width, d.pitch);
     BatchDesc &bd = plan->descs[i];
     if (st == BF_OK) st = bfi::resolve(&d.params, true, &bd.fc);
-    if (st != BF_OK) {
-      delete plan;
-      return st;
-    }
+    if (st != BF_OK) return fail(st);
     bd.io = {d.d_in, d.d_out, d.d_qaux, nullptr, 0, d.height, d.width, d.pitch};
-    const int R = bd.fc.R;
-    if (bfk::banded_forward_preferred(bd.fc.kind, R)) {
-      bd.th = 0;
+    const int v = bfi::forward_variant(bd.fc, true);
+    if (v < 0) return fail(BF_ERR_UNSUPPORTED);
+    plan->variants[i] = v;
+    int NT = 0, TH = 0;
+    if (v == bfi::kFwdBandedVariant) {
       large.push_back(i);
       continue;
     }
-    int th = 16;
-    if (BNT - 2 * R < 16 || bfk::fwd_smem_bytes(BNT, 16, R, bd.fc.ntaps_pad) > (size_t)smem_optin)
-      th = 8;
-    if (BNT - 2 * R < 8 || bfk::fwd_smem_bytes(BNT, th, R, bd.fc.ntaps_pad) > (size_t)smem_optin) {
-      delete plan;
-      return BF_ERR_UNSUPPORTED;
+    if (!bfi::tile_variant_shape(v, &NT, &TH)) {  // a whole-image kernel
+      plan->whole.push_back({d, v});
+      continue;
     }
-    bd.th = th;
-    plan->smem = std::max(plan->smem, bfk::fwd_smem_bytes(BNT, th, R, bd.fc.ntaps_pad));
-    const int TW = BNT - 2 * R;
+    const int R = bd.fc.R, TW = NT - 2 * R;
+    gsmem[v] = std::max(gsmem[v], bfk::fwd_smem_bytes(NT, TH, R, bd.fc.ntaps_pad));
     // cost model per tile: (N+1) x (region generation + both filter passes)
     const double taps = bd.fc.kind == BF_SPATIAL_GAUSS ? (double)bd.fc.ntaps_pad : 4.0;
-    const double per_ch = (double)(th + 2 * R) * BNT * 3.0 + (double)th * BNT * taps +
-                          (double)th * TW * (taps + 4.0);
-    const double c = (bd.fc.N + 1.0) * per_ch + (double)(th + 2 * R) * BNT * 8.0;
-    for (int y = 0; y < d.height; y += th)
-      for (int x = 0; x < d.width; x += TW) costs.push_back({c, {i, y, x, 0}});
+    const double per_ch = (double)(TH + 2 * R) * NT * 3.0 + (double)TH * NT * taps +
+                          (double)TH * TW * (taps + 4.0);
+    const double c = (bd.fc.N + 1.0) * per_ch + (double)(TH + 2 * R) * NT * 8.0;
+    for (int y = 0; y < d.height; y += TH)
+      for (int x = 0; x < d.width; x += TW) costs[v].push_back({c, {i, y, x, 0}});
   }
-  std::stable_sort(costs.begin(), costs.end(),
-                   [](const Cost &a, const Cost &b) { return a.c > b.c; });
-  plan->items.reserve(costs.size());
-  for (const Cost &c : costs) plan->items.push_back(c.w);
+  for (int v = 0; v < kMaxTileGroups; ++v) {
+    if (costs[v].empty()) continue;
+    std::stable_sort(costs[v].begin(), costs[v].end(),
+                     [](const Cost &a, const Cost &b) { return a.c > b.c; });
+    TileGroup g{};
+    g.variant = v;
+    bfi::tile_variant_shape(v, &g.NT, &g.TH);
+    g.item0 = (int)plan->items.size();
+    g.nitems = (int)costs[v].size();
+    g.smem = gsmem[v];
+    for (const Cost &c : costs[v]) plan->items.push_back(c.w);
+    const void *fn = tile_kernel(v);
+    int resident = 0;
+    bf_status st = bfi::ensure_smem(fn, g.smem);
+    if (st == BF_OK) st = bfi::resident_ctas(fn, g.NT, g.smem, &resident);
+    if (st != BF_OK || resident < 1) return fail(st != BF_OK ? st : BF_ERR_UNSUPPORTED);
+    g.ctas = (int)std::min<long long>((long long)resident, (long long)g.nitems);
+    plan->tgroups.push_back(g);
+  }
 
   // banded images: descriptors, groups of planes, tile items (longest first)
   size_t planes_max = 0;
@@ -269,11 +324,8 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
     }
     close_group();
   }
-  if (plan->items.size() > 0x7fffffff || plan->bitems.size() > 0x7fffffff) {
-    delete plan;
-    return BF_ERR_UNSUPPORTED;
-  }
-  cudaError_t e = cudaSuccess;
+  if (plan->items.size() > 0x7fffffff || plan->bitems.size() > 0x7fffffff)
+    return fail(BF_ERR_UNSUPPORTED);
   if (!large.empty()) {
     const int ntp_max = (2 * BF_MAX_RADIUS + 1 + 15) / 16 * 16;
     const size_t vs = std::max(bfk::vpass_smem(BF_SPATIAL_GAUSS, BF_MAX_RADIUS, ntp_max),
@@ -283,28 +335,20 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
     bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_band_kernel<true>), vs);
     if (st == BF_OK)
       st = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_band_kernel<false>), hs);
-    if (st != BF_OK) {
-      delete plan;
-      return st;
+    if (st != BF_OK) return fail(st);
+  }
+  // side streams for the whole-image launches and the banded groups
+  const bool sides[2] = {!plan->whole.empty(), !plan->groups.empty()};
+  if (sides[0] || sides[1]) {
+    cudaError_t e = cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      if (!sides[k]) continue;
+      e = cudaStreamCreateWithFlags(&plan->side[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->join[k], cudaEventDisableTiming);
     }
+    if (e != cudaSuccess) return fail(bfi::cuda_status(e));
   }
-  // fused launch: every SM filled with as many CTAs as fit
-  if (e == cudaSuccess && !plan->items.empty()) {
-    const void *fn = reinterpret_cast<const void *>(gpa_batched_kernel);
-    int resident = 0;
-    bf_status st = bfi::ensure_smem(fn, plan->smem);
-    if (st == BF_OK) st = bfi::resident_ctas(fn, BNT, plan->smem, &resident);
-    if (st != BF_OK || resident < 1) {
-      delete plan;
-      return st != BF_OK ? st : BF_ERR_UNSUPPORTED;
-    }
-    plan->ctas = (int)std::min<long long>((long long)resident, (long long)plan->items.size());
-  }
-  if (e != cudaSuccess) {
-    delete plan;
-    return bfi::cuda_status(e);
-  }
-  plan->off_descs = 256;
+  plan->off_descs = 256;  // the first 256 bytes hold the tile groups' counters
   plan->off_items = align256(plan->off_descs + sizeof(BatchDesc) * plan->descs.size());
   plan->off_bdescs = align256(plan->off_items + sizeof(WorkItem) * plan->items.size());
   plan->off_bitems = align256(plan->off_bdescs + sizeof(bfk::BandArgs) * plan->bdescs.size());
@@ -328,8 +372,18 @@ bf_status bf_batch_workspace(const bf_batch_plan *plan, size_t *bytes) {
 
 bf_status bf_batch_info(const bf_batch_plan *plan, int *items, int *ctas) {
   if (!plan) return BF_ERR_INVALID_ARG;
-  if (items) *items = (int)(plan->items.size() + plan->bitems.size());
-  if (ctas) *ctas = plan->ctas;
+  if (items) *items = (int)(plan->items.size() + plan->bitems.size() + plan->whole.size());
+  if (ctas) {
+    int c = 0;
+    for (const TileGroup &g : plan->tgroups) c += g.ctas;
+    *ctas = c;
+  }
+  return BF_OK;
+}
+
+bf_status bf_batch_variants(const bf_batch_plan *plan, int *variants, int count) {
+  if (!plan || !variants || count != (int)plan->variants.size()) return BF_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) variants[i] = plan->variants[i];
   return BF_OK;
 }
 
@@ -351,35 +405,61 @@ bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_byte
     return BF_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_ws);
-  if (!plan->items.empty()) {
-    const bf_status sm = bfi::ensure_smem(reinterpret_cast<const void *>(gpa_batched_kernel),
-                                          plan->smem);
-    if (sm != BF_OK) return sm;
-    BatchArgs A;
-    A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
-    A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items);
-    A.counter = reinterpret_cast<int *>(base);
-    A.status = d_status;
-    A.count = (int)plan->descs.size();
-    A.nitems = (int)plan->items.size();
-    cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), s);
+  cudaError_t e = cudaSuccess;
+  // fork: the side streams start after everything already on s
+  if (plan->fork) {
+    e = cudaEventRecord(plan->fork, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      if (plan->side[k]) e = cudaStreamWaitEvent(plan->side[k], plan->fork, 0);
     if (e != cudaSuccess) return bfi::cuda_status(e);
-    gpa_batched_kernel<<<plan->ctas, BNT, plan->smem, s>>>(A);
-    bf_status st = bfi::check_launch();
+  }
+  // whole-image kernels, one launch per image (side stream 0)
+  for (const WholeImage &w : plan->whole) {
+    const bf_status st = bf_fast_forward_variant(w.d.d_in, w.d.d_out, w.d.d_qaux, w.d.height,
+                                                 w.d.width, w.d.pitch, &w.d.params, w.variant,
+                                                 plan->side[0]);
     if (st != BF_OK) return st;
   }
+  // banded groups (side stream 1)
   for (const BandGroup &g : plan->groups) {
     BandBatchArgs B;
     B.descs = reinterpret_cast<const bfk::BandArgs *>(base + plan->off_bdescs);
     B.planes = base + plan->off_planes;
     B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.v0;
-    gpa_batched_band_kernel<true><<<g.nv, bfk::kVNT, g.vsmem, s>>>(B);
+    gpa_batched_band_kernel<true><<<g.nv, bfk::kVNT, g.vsmem, plan->side[1]>>>(B);
     bf_status st = bfi::check_launch();
     if (st != BF_OK) return st;
     B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.h0;
-    gpa_batched_band_kernel<false><<<g.nh, bfk::kBandNT, g.hsmem, s>>>(B);
+    gpa_batched_band_kernel<false><<<g.nh, bfk::kBandNT, g.hsmem, plan->side[1]>>>(B);
     st = bfi::check_launch();
     if (st != BF_OK) return st;
+  }
+  // one persistent launch per runtime-radius tile shape (caller's stream)
+  if (!plan->tgroups.empty()) {
+    int *counters = reinterpret_cast<int *>(base);
+    e = cudaMemsetAsync(counters, 0, kMaxTileGroups * sizeof(int), s);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
+    for (const TileGroup &g : plan->tgroups) {
+      const bf_status sm = bfi::ensure_smem(tile_kernel(g.variant), g.smem);
+      if (sm != BF_OK) return sm;
+      BatchArgs A;
+      A.descs = reinterpret_cast<const BatchDesc *>(base + plan->off_descs);
+      A.items = reinterpret_cast<const WorkItem *>(base + plan->off_items) + g.item0;
+      A.counter = counters + g.variant;
+      A.status = d_status;
+      A.count = (int)plan->descs.size();
+      A.nitems = g.nitems;
+      launch_tile_kernel(g.variant, g.ctas, g.smem, s, A);
+      const bf_status st = bfi::check_launch();
+      if (st != BF_OK) return st;
+    }
+  }
+  // join
+  for (int k = 0; k < 2; ++k) {
+    if (!plan->side[k]) continue;
+    e = cudaEventRecord(plan->join[k], plan->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->join[k], 0);
+    if (e != cudaSuccess) return bfi::cuda_status(e);
   }
   return BF_OK;
 }

@@ -61,4 +61,18 @@ double recursive_centre_weight(double sigma_s);
 // Fastest compiled-in tile variant for (kind, R, N) from the tuning table.
 int tuned_variant(int kind, int R, int N);
 
+// Forward variants (gpa_fwd.cu): 0..4 runtime-radius tiles, 5 compile-time
+// radius, 6 / 7 warp-strip box, 8 the two-pass banded forward (workspace).
+constexpr int kFwdBandedVariant = 8;
+constexpr int kFwdNumVariants = 9;
+// Whether variant v can run these constants (without stored planes).
+bool forward_variant_fits(int v, const FilterConsts &fc);
+// The variant a forward runs: the tuning table's entry for (kind, radius
+// bucket, order bucket) when it fits, else the built-in rule (banded for
+// Gaussian W >= 12 except 15 and box W > 15 when allow_banded, then the
+// compile-time-radius, warp-strip and runtime-radius kernels).  -1: none fits.
+int forward_variant(const FilterConsts &fc, bool allow_banded);
+// (threads per CTA, output rows per tile) of a runtime-radius tile variant.
+bool tile_variant_shape(int v, int *NT, int *TH);
+
 }  // namespace bfi

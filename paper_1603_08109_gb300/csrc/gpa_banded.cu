@@ -1,6 +1,7 @@
-// Two-pass banded forward of Algorithm 2 for large radii (Gaussian W >= 12
-// except 15, box W > 15): single-image launches and the workspace entry
-// points (tile bodies in gpa_banded.cuh).
+// Two-pass banded forward of Algorithm 2 for large radii (by default
+// Gaussian W >= 12 except 15, box W > 15; the tuning table may choose it for
+// any radius): single-image launches and the workspace entry points (tile
+// bodies in gpa_banded.cuh).
 //
 // A fused 2-D tile needs a 2W halo in both directions: at W = 60 its region
 // is tens of times the tile, does not fit shared memory at a useful size, and
@@ -35,7 +36,11 @@ __global__ void __launch_bounds__(kBandNT) band_hpass(const __grid_constant__ Ba
   band_hpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm);
 }
 
-bool banded_fits(const bfi::FilterConsts &fc) { return banded_forward_preferred(fc.kind, fc.R); }
+// Whether a forward with a workspace takes the banded path: the tuning
+// table's choice, else the built-in radius rule.
+bool banded_route(const bfi::FilterConsts &fc) {
+  return bfi::forward_variant(fc, true) == bfi::kFwdBandedVariant;
+}
 
 int round_up4(int w) { return (w + 3) / 4 * 4; }
 
@@ -96,21 +101,25 @@ bf_status bf_fast_forward_workspace(int height, int width, const bf_params *p, s
   bf_status st = bfi::resolve(p, true, &fc);
   if (st != BF_OK) return st;
   *bytes = 0;
-  if (!banded_fits(fc)) return BF_OK;
+  if (!banded_route(fc)) return BF_OK;
   const size_t row_bytes = (size_t)(fc.N + 1) * (size_t)round_up4(width) * sizeof(float);
   *bytes = row_bytes * (size_t)preferred_band_rows(height, width, fc.N);
   return BF_OK;
 }
 
-bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux, int height, int width,
-                             int pitch, const bf_params *p, void *d_workspace, size_t ws_bytes,
-                             void *stream) {
+bf_status bf_fast_forward_ws_variant(const float *d_in, float *d_out, float *d_qaux, int height,
+                                     int width, int pitch, const bf_params *p, int variant,
+                                     void *d_workspace, size_t ws_bytes, void *stream) {
   bf_status st = bfi::check_image(d_in, d_out, height, width, pitch);
   if (st != BF_OK) return st;
   bfi::FilterConsts fc;
   st = bfi::resolve(p, true, &fc);
   if (st != BF_OK) return st;
-  if (!banded_fits(fc)) return bf_fast_forward(d_in, d_out, d_qaux, height, width, pitch, p, stream);
+  if (variant >= bfi::kFwdNumVariants) return BF_ERR_INVALID_ARG;
+  const int v = variant >= 0 ? variant : bfi::forward_variant(fc, true);
+  if (v < 0) return BF_ERR_UNSUPPORTED;
+  if (v != bfi::kFwdBandedVariant)
+    return bf_fast_forward_variant(d_in, d_out, d_qaux, height, width, pitch, p, v, stream);
   if (!d_workspace) return BF_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(d_workspace) & 15u) return BF_ERR_INVALID_ARG;
   const int rows = band_rows(height, width, fc.N, ws_bytes);
@@ -131,6 +140,13 @@ bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux, int
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return fc.kind == BF_SPATIAL_GAUSS ? launch_band<BF_SPATIAL_GAUSS>(A, s)
                                      : launch_band<BF_SPATIAL_BOX>(A, s);
+}
+
+bf_status bf_fast_forward_ws(const float *d_in, float *d_out, float *d_qaux, int height, int width,
+                             int pitch, const bf_params *p, void *d_workspace, size_t ws_bytes,
+                             void *stream) {
+  return bf_fast_forward_ws_variant(d_in, d_out, d_qaux, height, width, pitch, p, -1, d_workspace,
+                                    ws_bytes, stream);
 }
 
 }  // extern "C"

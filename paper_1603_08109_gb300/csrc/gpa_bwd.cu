@@ -860,7 +860,9 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 // Device address of g_noalloc_partials on the current device.  In host code
 // the symbol's name is only a host-side stand-in, so its address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached for the life of the
+// process; after a cudaDeviceReset the module may load elsewhere, so a reset
+// device is not supported by this entry point.
 static bf_status noalloc_partials(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -885,14 +887,23 @@ extern "C" bf_status bf_fast_backward_noalloc(const float *d_in, const float *d_
   size_t need = 0;
   bfi::FilterConsts fc;
   bf_status st = workspace_bytes(height, width, p, &need, nullptr, &fc);  // the fused kernels'
-  if (st != BF_OK) return st;
-  if (need > sizeof(double) * (size_t)kNoAllocPartials) {
-    bfi::set_error_text("image too large for the allocation-free backward: it needs more "
-                        "sigma_r partial sums than the 65536 of its static scratch");
-    return BF_ERR_UNSUPPORTED;
+  if (st == BF_ERR_UNSUPPORTED) {
+    // no fused tile holds this radius's region in shared memory; only the
+    // banded backward (which needs a caller workspace) takes it
+    bfi::set_error_text("radius too large for the allocation-free backward: its fused tiles "
+                        "hold Gaussian radii up to 50 and box radii up to 39 (227 KB of shared "
+                        "memory per block); bf_fast_backward with a workspace takes larger ones");
+    return st;
   }
+  if (st != BF_OK) return st;
   double *scratch = nullptr;
-  if (d_gsigma) {
+  if (d_gsigma) {  // the partial sums are the only scratch, and only with d_gsigma
+    if (need > sizeof(double) * (size_t)kNoAllocPartials) {
+      bfi::set_error_text("image too large for the allocation-free backward with a sigma_r "
+                          "gradient: it needs more partial sums than the 65536 of its static "
+                          "scratch");
+      return BF_ERR_UNSUPPORTED;
+    }
     st = noalloc_partials(&scratch);
     if (st != BF_OK) return st;
   }

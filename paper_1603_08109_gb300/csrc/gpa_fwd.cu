@@ -7,6 +7,7 @@
 
 #include "bf_internal.h"
 #include "box_warp.cuh"
+#include "gpa_banded.cuh"
 #include "gpa_fixed.cuh"
 #include "gpa_tile.cuh"
 
@@ -57,7 +58,9 @@ __global__ void __launch_bounds__(32 * kWarpWPB, 8) box_warp_kernel(const __grid
 // for the radii in kFixedRadii (with or without stored planes).
 // Variants 6 and 7: the warp-strip streaming box kernel (box, W in {3, 5})
 // with 8 columns per lane (N <= 5) and 4 columns per lane (N <= 8; fewer
-// registers per channel).
+// registers per channel).  Variant 8: the two-pass banded forward
+// (gpa_banded.cu), which needs a caller workspace: only the entry points
+// that take one run it.
 struct Variant {
   int NT, TH;
 };
@@ -66,7 +69,10 @@ constexpr int kNumGeneric = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kFixedVariant = kNumGeneric;
 constexpr int kStreamVariant = kNumGeneric + 1;
 constexpr int kStream4Variant = kNumGeneric + 2;
-constexpr int kNumVariants = kNumGeneric + 3;
+constexpr int kBandedVariant = kNumGeneric + 3;
+constexpr int kNumVariants = kNumGeneric + 4;
+static_assert(kBandedVariant == bfi::kFwdBandedVariant && kNumVariants == bfi::kFwdNumVariants,
+              "variant numbering shared with the banded forward and the batch plan");
 
 bool fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 bool stream_fits(const bfi::FilterConsts &fc, int max_n) {
@@ -87,6 +93,7 @@ int max_smem_optin() {
 }
 
 bool variant_fits(int v, const bfi::FilterConsts &fc, bool store = false) {
+  if (v == kBandedVariant) return !store;
   if (v == kFixedVariant) return fixed_radius(fc.R);
   if (v == kStreamVariant) return !store && stream_fits(fc, 5);
   if (v == kStream4Variant) return !store && stream_fits(fc, 8);
@@ -274,11 +281,13 @@ bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, si
   int v = variant;
   if (v < 0) {
     v = bfi::tuned_variant(a.fc.kind, a.fc.R, a.fc.N);
-    if (v >= 0 && !variant_fits(v, a.fc, store)) v = -1;
+    // the banded forward needs a workspace, which this path does not have
+    if (v == kBandedVariant || (v >= 0 && !variant_fits(v, a.fc, store))) v = -1;
     if (v < 0) v = default_variant(a.fc, store);
     if (v < 0) return BF_ERR_UNSUPPORTED;
   } else {
     if (v >= kNumVariants) return BF_ERR_INVALID_ARG;
+    if (v == kBandedVariant) return BF_ERR_WORKSPACE;
     if (!variant_fits(v, a.fc, store)) return BF_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -300,6 +309,30 @@ bf_status forward_impl(const float *in, float *out, float *qaux, float *abar, si
 }
 
 }  // namespace
+
+namespace bfi {
+
+bool forward_variant_fits(int v, const FilterConsts &fc) {
+  return v >= 0 && v < kNumVariants && variant_fits(v, fc, false);
+}
+
+int forward_variant(const FilterConsts &fc, bool allow_banded) {
+  int v = tuned_variant(fc.kind, fc.R, fc.N);
+  if (v == kBandedVariant && !allow_banded) v = -1;
+  if (v >= 0 && !variant_fits(v, fc, false)) v = -1;
+  if (v >= 0) return v;
+  if (allow_banded && bfk::banded_forward_preferred(fc.kind, fc.R)) return kBandedVariant;
+  return default_variant(fc, false);
+}
+
+bool tile_variant_shape(int v, int *NT, int *TH) {
+  if (v < 0 || v >= kNumGeneric) return false;
+  *NT = kVariants[v].NT;
+  *TH = kVariants[v].TH;
+  return true;
+}
+
+}  // namespace bfi
 
 extern "C" {
 
@@ -336,8 +369,11 @@ bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux,
 
 // Times every fitting variant (CUDA events on `stream`, after one warm-up
 // launch each) and records the fastest in the tuning table.  Synchronises.
-bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, int pitch,
-                      const bf_params *p, int reps, void *stream, int *best, float *best_ms) {
+// With a workspace that holds at least 64 band rows the two-pass banded
+// forward (variant 8) is timed too.
+bf_status bf_autotune_ws(const float *d_in, float *d_out, int height, int width, int pitch,
+                         const bf_params *p, void *d_workspace, size_t workspace_bytes, int reps,
+                         void *stream, int *best, float *best_ms) {
   if (!best || reps < 1) return BF_ERR_INVALID_ARG;
   bfi::FilterConsts fc;
   bf_status st = bfi::resolve(p, true, &fc);
@@ -351,13 +387,22 @@ bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, in
   }
   int bv = -1;
   float bms = 0.f;
+  auto run = [&](int v) {
+    if (v == kBandedVariant)
+      return bf_fast_forward_ws_variant(d_in, d_out, nullptr, height, width, pitch, p, v,
+                                        d_workspace, workspace_bytes, stream);
+    return bf_fast_forward_variant(d_in, d_out, nullptr, height, width, pitch, p, v, stream);
+  };
   for (int v = 0; v < kNumVariants; ++v) {
     if (!variant_fits(v, fc)) continue;
-    st = bf_fast_forward_variant(d_in, d_out, nullptr, height, width, pitch, p, v, stream);
+    st = run(v);
+    if (v == kBandedVariant && st == BF_ERR_WORKSPACE) {  // no room for it: not a candidate
+      st = BF_OK;
+      continue;
+    }
     if (st != BF_OK) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < reps; ++r)
-      bf_fast_forward_variant(d_in, d_out, nullptr, height, width, pitch, p, v, stream);
+    for (int r = 0; r < reps; ++r) run(v);
     cudaEventRecord(e1, s);
     cudaError_t ce = cudaEventSynchronize(e1);
     if (ce != cudaSuccess) {
@@ -379,6 +424,12 @@ bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, in
   *best = bv;
   if (best_ms) *best_ms = bms;
   return bf_tuning_set(fc.kind, bf_tuning_radius_bucket(fc.R), bf_tuning_order_bucket(fc.N), bv);
+}
+
+bf_status bf_autotune(const float *d_in, float *d_out, int height, int width, int pitch,
+                      const bf_params *p, int reps, void *stream, int *best, float *best_ms) {
+  return bf_autotune_ws(d_in, d_out, height, width, pitch, p, nullptr, 0, reps, stream, best,
+                        best_ms);
 }
 
 }  // extern "C"

@@ -26,9 +26,19 @@ def test_json_cache_roundtrip(tmp_path):
     assert tuning.load(str(tmp_path / "missing.json")) == 0
 
 
+@pytest.fixture
+def restored_table():
+    """The tuning table is process-wide: put back every entry a test changed."""
+    saved = {(k, rb, ob): bf.tuning_get(k, rb, ob)
+             for k in (bf.BOX, bf.GAUSS) for rb in range(8) for ob in range(6)}
+    yield
+    for key, v in saved.items():
+        bf.tuning_set(*key, v)
+
+
 @pytest.mark.gpu
 @needs_gpu
-def test_autotune_then_forward_meets_parity(tmp_path):
+def test_autotune_then_forward_meets_parity(tmp_path, restored_table):
     entries = tuning.autotune_grid(128, 300, kinds=(bf.GAUSS,), radii=(12,), orders=(24,), reps=2)
     assert len(entries) == 1 and 0 <= entries[0]["variant"] < bf.variant_count()
     tuning.save(entries, str(tmp_path / "t.json"))
@@ -40,3 +50,7 @@ def test_autotune_then_forward_meets_parity(tmp_path):
     ro, P, Q = oracle.gpa_alg2(img, w, 30.0, 24, return_parts=True)
     compare_forward(out.cpu().numpy(), q.cpu().numpy(), ro, scaled_q(img, Q, 30.0), w[12, 12],
                     "tuned", sigma_r=30.0, N=24, img=img, w=w)
+    # the table's winner is the kernel the default call ran
+    again = bf.gpa_forward(torch.from_numpy(img).cuda(), bf.GAUSS, 30.0, 24, radius=12,
+                           sigma_s=4.0, variant=entries[0]["variant"])
+    assert torch.equal(again, out)
