@@ -112,6 +112,14 @@ bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out);
 bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r,
                               float delta, float T, int *N_out);
 
+/* Order N for a volume (video) filter accuracy delta: as bf_order_from_delta
+ * with the centre weight of the separable 3-D kernel w1(j_z) w1(j_y) w1(j_x)
+ * of bf_volume_forward, w1(0)^3 = (planar w(0))^(3/2) in eq. eps (the Sec. I
+ * and Sec. V extension to video and volume data).  kind: BF_SPATIAL_BOX or
+ * BF_SPATIAL_GAUSS (radius <= 0: ceil(3 sigma_s)).  Same errors.  Host only. */
+bf_status bf_volume_order_from_delta(int kind, int radius, float sigma_s, float sigma_r,
+                                     float delta, float T, int *N_out);
+
 /* -------------------------------------------- kernel-error analysis (Sec. II)
  * bf_kernel_error_max: sup-norm of the kernel error (eq. Linf),
  *   max |g(t - tau) - phi_N(t, tau)|  (eq. error)

@@ -52,6 +52,7 @@ SIGNATURES = {
     "bf_version": (_i, []),
     "bf_centre_weight": (_i, [_i, _i, _f, ctypes.POINTER(_d)]),
     "bf_order_from_delta": (_i, [_i, _i, _f, _f, _f, _f, _ip]),
+    "bf_volume_order_from_delta": (_i, [_i, _i, _f, _f, _f, _f, _ip]),
     "bf_kernel_error_max": (_i, [_i, _d, _d, _i, _vp, _vp]),
     "bf_order_estimates": (_i, [_d, _d, _d, _ip, _ip, _ip]),
     "bf_fast_forward": (_i, [_vp, _vp, _vp, _i, _i, _i, _pp, _vp]),

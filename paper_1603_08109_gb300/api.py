@@ -363,12 +363,13 @@ def gpa_forward_many(imgs: torch.Tensor, kind: int, sigma_r: float, N: int, radi
 
 def volume_order_from_delta(kind: int, radius: int, sigma_s: float, sigma_r: float, delta: float,
                             t_c: float = 128.0) -> int:
-    """N for a volume filter accuracy delta: eq. eps with the volume kernel's
-    w(0) = w1(0)^3 = (planar w(0))^(3/2), then the Chernoff order (eq. LambW)."""
-    r = resolve_radius(kind, radius, sigma_s)
-    w0 = centre_weight(kind, r, sigma_s) ** 1.5
-    eps = w0 * delta / (2.0 * t_c + delta)
-    return order_estimates(sigma_r, eps, t_c)[1]
+    """N for a volume filter accuracy delta (bf_volume_order_from_delta: eq.
+    eps with the volume kernel's w(0) = w1(0)^3, then eq. LambW)."""
+    n = ctypes.c_int()
+    check(lib().bf_volume_order_from_delta(int(kind), int(radius), float(sigma_s), float(sigma_r),
+                                           float(delta), float(t_c), ctypes.byref(n)),
+          "bf_volume_order_from_delta")
+    return n.value
 
 
 def volume_workspace_bytes(D: int, H: int, W: int, kind: int, sigma_r: float, N: int,

@@ -193,22 +193,28 @@ bf_status bf_centre_weight(int kind, int radius, float sigma_s, double *w0_out) 
   return BF_OK;
 }
 
-// Order from the accuracy target (Sec. III-C and App. A).  nu(x) = x log x -
-// p x - q is strictly convex with its minimum at lambda, and nu(lambda) =
-// log(eps) < 0, so exactly one root theta > lambda exists; nu is increasing
-// there.  Bracket it by doubling, then take Newton steps (eq. Newton_method),
-// falling back to bisection whenever a step leaves the bracket.
-bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r, float delta,
-                              float T, int *N_out) {
-  if (!N_out || !(delta > 0.0f) || !(T > 0.0f) || !(sigma_r > 0.0f)) return BF_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// w(0) of the planar kernel of (kind, radius, sigma_s), the Gaussian radius
+// defaulting to ceil(3 sigma_s) (the recursive Gaussian has no radius).
+bf_status planar_centre_weight(int kind, int radius, float sigma_s, double *w0) {
   int R = kind == BF_SPATIAL_GAUSS_RECURSIVE ? 0 : radius;
   if (kind == BF_SPATIAL_GAUSS && R <= 0) {
     if (!(sigma_s > 0.0f)) return BF_ERR_INVALID_ARG;
     R = (int)ceil(3.0 * (double)sigma_s - 1e-9);
   }
-  double w0 = 0.0;
-  bf_status st = bf_centre_weight(kind, R, sigma_s, &w0);
-  if (st != BF_OK) return st;
+  return bf_centre_weight(kind, R, sigma_s, w0);
+}
+
+// Order from the accuracy target (Sec. III-C and App. A): eps from eq. eps,
+// then the root theta of nu.  nu(x) = x log x - p x - q is strictly convex
+// with its minimum at lambda, and nu(lambda) = log(eps) < 0, so exactly one
+// root theta > lambda exists; nu is increasing there.  Bracket it by
+// doubling, then take Newton steps (eq. Newton_method), falling back to
+// bisection whenever a step leaves the bracket.
+bf_status order_from_centre_weight(double w0, float sigma_r, float delta, float T, int *N_out) {
   const double t = T, d = delta;
   const double eps = w0 * d / (2.0 * t + d);  // eq. eps
   if (!(eps > 0.0) || eps >= 1.0) return BF_ERR_INVALID_ARG;
@@ -240,6 +246,34 @@ bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r
   if (N > BF_MAX_ORDER) return BF_ERR_UNSUPPORTED;
   *N_out = (int)N;
   return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_order_from_delta(int kind, int radius, float sigma_s, float sigma_r, float delta,
+                              float T, int *N_out) {
+  if (!N_out || !(delta > 0.0f) || !(T > 0.0f) || !(sigma_r > 0.0f)) return BF_ERR_INVALID_ARG;
+  double w0 = 0.0;
+  const bf_status st = planar_centre_weight(kind, radius, sigma_s, &w0);
+  if (st != BF_OK) return st;
+  return order_from_centre_weight(w0, sigma_r, delta, T, N_out);
+}
+
+// Volume / video data (the Sec. I and Sec. V extension): the spatial kernel
+// is w1(j_z) w1(j_y) w1(j_x) with the planar filter's normalised 1-D kernel
+// w1, so its centre weight is w1(0)^3 = (planar w(0))^(3/2); eq. eps and the
+// root of nu then follow unchanged (Prop. accuracy holds for any normalised
+// non-negative kernel).
+bf_status bf_volume_order_from_delta(int kind, int radius, float sigma_s, float sigma_r,
+                                     float delta, float T, int *N_out) {
+  if (!N_out || !(delta > 0.0f) || !(T > 0.0f) || !(sigma_r > 0.0f)) return BF_ERR_INVALID_ARG;
+  if (kind != BF_SPATIAL_BOX && kind != BF_SPATIAL_GAUSS) return BF_ERR_INVALID_ARG;
+  double w0 = 0.0;
+  const bf_status st = planar_centre_weight(kind, radius, sigma_s, &w0);
+  if (st != BF_OK) return st;
+  return order_from_centre_weight(w0 * sqrt(w0), sigma_r, delta, T, N_out);
 }
 
 int bf_tuning_radius_bucket(int radius) {

@@ -73,6 +73,28 @@ def test_library_order_vs_delta_table():
         assert abs(api.order_from_delta(L.GAUSS, 0, 5.0, 30.0, delta, 128.0) - int(n_lw)) <= 1
 
 
+def test_library_volume_order_matches_checker():
+    """bf_volume_order_from_delta (C++) against the checker: eq. eps with the
+    volume kernel's w(0) = w1(0)^3 (w1 from the checker's planar kernel), then
+    its Lambert-W order (eq. LambW)."""
+    L = _lib()
+    from oracle import order, volume
+    from paper_1603_08109_gb300 import api
+    for kind, r, ss in ((L.BOX, 3, 0.0), (L.GAUSS, 6, 2.0), (L.GAUSS, 15, 5.0), (L.BOX, 1, 0.0)):
+        w0 = volume.centre_weight_volume(kind, r, ss)
+        for sr in (12.0, 30.0, 70.0):
+            for delta in (0.1, 1.0):
+                eps = order.eps_from_delta(w0, delta, 128.0)
+                ref = order.chernoff_order_lambertw((128.0 / sr) ** 2, eps)[0]
+                assert api.volume_order_from_delta(kind, r, ss, sr, delta) == ref, (kind, r, sr)
+    # the Gaussian radius defaults to ceil(3 sigma_s); invalid arguments
+    assert api.volume_order_from_delta(L.GAUSS, 0, 2.0, 30.0, 1.0) == \
+        api.volume_order_from_delta(L.GAUSS, 6, 2.0, 30.0, 1.0)
+    n = ctypes.c_int()
+    assert L.lib().bf_volume_order_from_delta(2, 0, 3.0, 30.0, 1.0, 128.0, ctypes.byref(n)) == 1
+    assert L.lib().bf_volume_order_from_delta(0, 3, 0.0, 30.0, -1.0, 128.0, ctypes.byref(n)) == 1
+
+
 def test_library_centre_weight():
     from paper_1603_08109_gb300 import api
     assert api.centre_weight(0, 4) == pytest.approx(1.0 / 81.0, rel=1e-15)
