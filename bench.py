@@ -1,19 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the fused Gaussian-polynomial bilateral filter on one GB300.
 
-Workload (one step): a 2048 x 2048 float32 image of 64-pixel blocks with
-uniform levels in [0,255] plus N(0, 10^2) noise (seeded, synthetic), Gaussian
-spatial kernel sigma_s = 3 (W = 9), sigma_r = 30, N = 40 (the order from the
-accuracy bound for delta = 1, eq. eps + eq. LambW).  One step is the whole
-hot path: order selection (host), the fused forward (out and Q'), and the
-fused backward (image gradient and sigma_r gradient).  The headline value is
-forward+backward Mpixel/s; forward-only Mpixel/s, the direct eq. BF filter
-(forward and forward+backward) on the same image, the achieved HBM GB/s and
-the FP32-pipe roofline of the dominant kernel are reported beside it.
+Headline workload (one step): 96 distinct 2048 x 2048 float32 images of
+64-pixel blocks with uniform levels in [0,255] plus N(0, 10^2) noise (seeded,
+synthetic: 8 seeded images in 12 row rotations each, 7.7 GB of images,
+cotangents and outputs, far larger than L2), Gaussian spatial kernel
+sigma_s = 3 (W = 9), sigma_r = 30, N = 40 (the order from the accuracy bound
+for delta = 1, eq. eps + eq. LambW, chosen once on the host before the timed
+region).  Each image of a step goes through the fused forward (out and Q') and
+the fused backward (image gradient and sigma_r gradient).  The headline value
+is forward+backward Mpixel/s over the whole step; forward-only Mpixel/s, the
+direct eq. BF filter (forward and forward+backward) on the same image, the
+end-to-end rate through the Python API with host buffers, the achieved HBM
+GB/s and the FP32-pipe roofline of the dominant kernel are reported beside it.
+
+The other workloads are timed after the headline region, each on its own:
+the fast path at equal stated max error against the direct filter, the
+8192^2 Gaussian W = 60 forward, 32 x 512^2 forward + backward (power images
+recomputed or stored), the uneven 256-image batch as one CUDA graph (built-in
+and autotuned variants), and the small-N box forward at 4096^2 against the
+HBM roofline.  The CPU-baseline leg times the FP64 checker on the host cores
+and measures every kept GPU output against it at sampled pixels.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank filters its own image (weak scaling, no
+Under torchrun (N > 1) every rank filters its own images (weak scaling, no
 data-path collective); the barrier and the max over ranks of the timed
 region are the only collectives.
 """
@@ -35,28 +46,32 @@ if ROOT not in sys.path:
 
 METRIC = "Mpixel/s fwd & fwd+bwd vs direct GPU BF at stated max error; HBM GB/s"
 UNIT = "Mpixel/s"
-WORKLOAD = ("2048x2048 blocks(64)+N(0,10^2) image; Gaussian spatial sigma_s=3 (W=9), "
-            "sigma_r=30, N=40 (bound for delta=1); step = fused forward + fused backward "
-            "(image and sigma_r gradients)")
+WORKLOAD = ("96 x 2048x2048 blocks(64)+N(0,10^2) images per step; Gaussian spatial sigma_s=3 "
+            "(W=9), sigma_r=30, N=40 (bound for delta=1); per image fused forward + fused "
+            "backward (image and sigma_r gradients)")
 
 
-def workload(S, kind, R, ss, sr, N, only):
+def workload(S, kind, R, ss, sr, N, only, B=96):
     """The workload text of a run (the default run's is WORKLOAD)."""
     spatial = ("Gaussian spatial sigma_s=%g (W=%d)" % (ss, R) if kind == 1
                else "box spatial W=%d" % R)
     step = {"all": "fused forward + fused backward (image and sigma_r gradients)",
             "fwd": "fused forward", "bwd": "fused backward (image and sigma_r gradients)"}[only]
-    return "%dx%d blocks(64)+N(0,10^2) image; %s, sigma_r=%g, N=%d; step = %s" % (
-        S, S, spatial, sr, N, step)
-L2_NOTE = "L2 flushed between timed steps (512 MB write, outside the per-step events)"
+    return "%d x %dx%d blocks(64)+N(0,10^2) images per step; %s, sigma_r=%g, N=%d; per image %s" % (
+        B, S, S, spatial, sr, N, step)
+
+
+L2_NOTE = ("inputs larger than L2 (each step filters 96 distinct 2048^2 images); L2 also "
+           "flushed between steps (512 MB write, outside the step's events)")
 FIXED_RADII = (3, 5, 9, 15)  # radii with compile-time-specialised kernels
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=96, help="distinct images per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048, help="image side (profiling runs only)")
     ap.add_argument("--kind", default="gauss", choices=["gauss", "box"])
@@ -69,7 +84,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--no-hbm-study", action="store_true",
-                    help="skip the small-N 4096^2 batch HBM measurement of the JSON line")
+                    help="skip the small-N 4096^2 HBM measurements of the JSON line")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the other workloads (equal error, 8192^2, 32 x 512^2, batch)")
     ap.add_argument("--sweep", default="",
                     help="comma list of extra studies, one JSON line per point: "
                          "grid2048, roofline4096, large8192, recursive, batch256, grad512, "
@@ -312,8 +329,334 @@ def run_reference(args):
     return 0
 
 
-# ----------------------------------------------------------------- our arm
-# ----------------------------------------------------------------- studies
+# ----------------------------------------------------------------- workload studies
+# Each study times one workload on the GPU (CUDA events on the launching
+# stream, L2 flushed between repetitions) and returns its JSON fields; the
+# host copies of sampled outputs go to `keep`, from which the CPU-baseline leg
+# computes the errors against the checker.
+def _samples(rng, H, W, n):
+    ys = rng.integers(0, H, n)
+    xs = rng.integers(0, W, n)
+    return ys, xs
+
+
+def study_equal_error(bf, x_np, x, g, kind, R, ss, sr, N, dev, stream, flush, keep):
+    """Fast forward + backward at equal stated max error against the direct
+    filter: the order N_eq from the accuracy bound for delta = 1e-3 (Prop.
+    accuracy: |f_GPA - f_BF| <= delta), the parity tolerance of the float32
+    outputs, so both filters are stated accurate to 1e-3 of eq. BF; the
+    CPU-baseline leg measures both errors against FP64 eq. BF at the same
+    sampled pixels."""
+    import numpy as np
+    import torch
+    N_eq = bf.order_from_delta(kind, R, ss, sr, 1e-3)
+    o, q = bf.gpa_forward(x, kind, sr, N_eq, radius=R, sigma_s=ss, return_q=True)
+
+    def fb():
+        oo, qq = bf.gpa_forward(x, kind, sr, N_eq, radius=R, sigma_s=ss, return_q=True, out=o)
+        bf.gpa_backward(x, oo, qq, g, kind, sr, N_eq, radius=R, sigma_s=ss)
+    fbms = _time_ms(fb, 5, stream, flush)
+    fms = _time_ms(lambda: bf.gpa_forward(x, kind, sr, N_eq, radius=R, sigma_s=ss, out=o), 5,
+                   stream, flush)
+    S = x.shape[0]
+    ys, xs = _samples(np.random.default_rng(21), S, x.shape[1], 3000)
+    keep["equal_error"] = {"img": x_np, "ys": ys, "xs": xs, "kind": kind, "R": R, "ss": ss,
+                           "sr": sr, "N_eq": N_eq, "fast_eq": _at(o, ys, xs)}
+    px = float(x.numel())
+    return {"workload": "the headline image and filter; fast path at N_eq from the bound for "
+                        "delta = 1e-3 (the float32 parity tolerance) against the direct filter",
+            "delta": 1e-3, "N_eq": N_eq, "fast_fwd_ms": fms, "fast_fwd_bwd_ms": fbms,
+            "fast_fwd_bwd_mpx_s": px / fbms / 1e3}
+
+
+def study_large8192(bf, synth, dev, stream, flush, fp32, keep, with_direct=True):
+    """8192^2 gradient + 64 polygons + N(0, 15^2); Gaussian sigma_s = 20
+    (W = 60), sigma_r = 40, N from the bound for delta = 0.5: the two-pass
+    banded forward, its FP32-pipe fraction, and the direct filter."""
+    import numpy as np
+    import torch
+    S, R, ss, sr = 8192, 60, 20.0, 40.0
+    img = synth.gradient_polygons_image(S, S, 64, 15.0, seed=2001)
+    x = torch.from_numpy(img).to(dev)
+    o = torch.empty_like(x)
+    N = bf.order_from_delta(bf.GAUSS, R, ss, sr, 0.5)
+    fms = _time_ms(lambda: bf.gpa_forward(x, bf.GAUSS, sr, N, radius=R, sigma_s=ss, out=o), 3,
+                   stream, flush)
+    px = float(S * S)
+    ops = fwd_ops_per_pixel(1, R, N) * px
+    ys, xs = _samples(np.random.default_rng(22), S, S, 200)
+    res = {"workload": "8192x8192 gradient+64 polygons+N(0,15^2); Gaussian sigma_s=20 (W=60), "
+                       "sigma_r=40, N=%d (bound for delta=0.5); two-pass banded forward" % N,
+           "N": N, "fwd_ms": fms, "fwd_mpx_s": px / fms / 1e3,
+           "fwd_alu": {"bound": "alu", "kernel": "band_vpass+band_hpass",
+                       "achieved": ops / (fms * 1e-3) / 1e12, "peak": fp32 / 1e12,
+                       "unit": "TFLOP/s", "frac": ops / (fms * 1e-3) / fp32}}
+    keep["large_8192"] = {"img": img, "ys": ys, "xs": xs, "N": N, "R": R, "ss": ss, "sr": sr,
+                          "fast": _at(o, ys, xs)}
+    if with_direct:
+        d = torch.empty_like(x)
+        dms = _time_ms(lambda: bf.direct(x, bf.GAUSS, sr, radius=R, sigma_s=ss, out=d), 1, stream,
+                       flush)
+        res.update({"direct_fwd_ms": dms, "direct_fwd_mpx_s": px / dms / 1e3,
+                    "speedup_vs_direct": dms / fms,
+                    "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max())})
+        keep["large_8192"]["direct"] = _at(d, ys, xs)
+        del d
+    del x, o
+    torch.cuda.empty_cache()
+    return res
+
+
+def _at(t, ys, xs):
+    """Values of a device image at sampled pixels, on the host."""
+    import torch
+    iy = torch.as_tensor(ys, device=t.device, dtype=torch.long)
+    ix = torch.as_tensor(xs, device=t.device, dtype=torch.long)
+    return t[iy, ix].double().cpu().numpy()
+
+
+def _tune_buckets(bf, specs, dev, reps=3):
+    """Autotune every (kind, radius bucket, order bucket) the specs occupy:
+    each bucket is timed on a synthetic image of the size and parameters of
+    its costliest member (the image that dominates the bucket's time); returns
+    the number of buckets and the seconds spent."""
+    import torch
+
+    from paper_1603_08109_gb300 import synth
+    rep = {}
+    for sp in specs:
+        key = (sp["kind"], bf.radius_bucket(sp["radius"]), bf.order_bucket(sp["N"]))
+        cost = (sp["N"] + 1) * (2 * sp["radius"] + 1) * sp["height"] * sp["width"]
+        if key not in rep or cost > rep[key][0]:
+            rep[key] = (cost, sp)
+    t0 = time.perf_counter()
+    for _, sp in rep.values():
+        img = torch.from_numpy(synth.blocks_image(sp["height"], sp["width"], 16, 20.0,
+                                                  seed=sp["seed"] + 7919)).to(dev)
+        bf.autotune(img, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
+                    sigma_s=sp["sigma_s"], reps=reps)
+    torch.cuda.synchronize(dev)
+    return len(rep), time.perf_counter() - t0
+
+
+def study_batch256(bf, synth, dev, stream, flush, keep, tune=True):
+    """256 images, sizes U{64..768} x U{64..1024}, blocks(16)+N(0,20^2), per
+    image kind, sigma_s in [2, 15] (W = ceil(3 sigma_s)), sigma_r in [10, 80],
+    N from the bound for delta = 1: one captured graph of the batch plan, with
+    the built-in variant choice and after autotuning the buckets present."""
+    import collections
+
+    import numpy as np
+    import torch
+    specs = synth.batch_specs(256, seed=3000)
+    for sp in specs:
+        sp["N"] = bf.order_from_delta(sp["kind"], sp["radius"], sp["sigma_s"], sp["sigma_r"], 1.0)
+    host = [synth.blocks_image(sp["height"], sp["width"], 16, 20.0, seed=sp["seed"]) for sp in specs]
+    imgs = [torch.from_numpy(a).to(dev) for a in host]
+    outs = [torch.empty_like(t) for t in imgs]
+    px = float(sum(sp["height"] * sp["width"] for sp in specs))
+    saved = {(k, rb, ob): bf.tuning_get(k, rb, ob)
+             for k in (bf.BOX, bf.GAUSS) for rb in range(8) for ob in range(6)}
+
+    def measure():
+        plan = bf.BatchPlan(imgs, outs, specs)
+        items, ctas = plan.info()
+        var = plan.variants()
+        ms = _time_ms(plan.replay, 5, stream, flush)
+        plan.close()
+        return ms, items, var
+
+    try:
+        for key in saved:
+            bf.tuning_set(*key, -1)
+        ums, items, uvar = measure()
+        res = {"workload": "256 images 64..768 x 64..1024 blocks(16)+N(0,20^2); per image box or "
+                           "Gaussian, sigma_s in [2,15], sigma_r in [10,80], N from delta=1; one "
+                           "CUDA graph of the batch plan",
+               "images": 256, "megapixels": px / 1e6,
+               "N_range": [min(s["N"] for s in specs), max(s["N"] for s in specs)],
+               "untuned": {"graph_ms": ums, "mpx_s": px / ums / 1e3, "work_items": items,
+                           "variants": dict(collections.Counter(str(v) for v in uvar))}}
+        if tune:
+            nb, tsec = _tune_buckets(bf, specs, dev)
+            tms, titems, tvar = measure()
+            res["tuned"] = {"graph_ms": tms, "mpx_s": px / tms / 1e3, "work_items": titems,
+                            "buckets_tuned": nb, "tuning_s": tsec,
+                            "variants": dict(collections.Counter(str(v) for v in tvar)),
+                            "images_changed": int(sum(a != b for a, b in zip(uvar, tvar)))}
+        k = int(np.argmax([sp["N"] for sp in specs]))
+        sp = specs[k]
+        ys, xs = _samples(np.random.default_rng(23), sp["height"], sp["width"], 200)
+        keep["batch_256"] = {"img": host[k], "ys": ys, "xs": xs, "spec": sp,
+                             "fast": _at(outs[k], ys, xs)}
+    finally:
+        for key, v in saved.items():
+            bf.tuning_set(*key, v)
+    del imgs, outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def study_grad512(bf, synth, dev, stream, flush, keep):
+    """32 images of 512^2 blocks(16)+N(0,20^2); Gaussian sigma_s = 5 (W = 15),
+    sigma_r = 25, N from the bound for delta = 1: forward + backward (image and
+    sigma_r gradients), power images recomputed or stored, against the direct
+    filter's forward + backward; the 32 images on 8 streams in one captured
+    graph (a 512^2 image alone fills only part of the GPU)."""
+    import numpy as np
+    import torch
+    R, ss, sr = 15, 5.0, 25.0
+    N = bf.order_from_delta(bf.GAUSS, R, ss, sr, 1.0)
+    host = [synth.blocks_image(512, 512, 16, 20.0, seed=4000 + k) for k in range(32)]
+    ghost = [synth.random_like((512, 512), seed=5000 + k) for k in range(32)]
+    xs_ = [torch.from_numpy(a).to(dev) for a in host]
+    gs_ = [torch.from_numpy(a).to(dev) for a in ghost]
+    side = [torch.cuda.Stream(dev) for _ in range(8)]
+
+    def fanout(body):
+        def run():
+            cur = torch.cuda.current_stream(dev)
+            for k, (x, g) in enumerate(zip(xs_, gs_)):
+                s = side[k % len(side)]
+                s.wait_stream(cur)
+                with torch.cuda.stream(s):
+                    body(x, g)
+            for s in side:
+                cur.wait_stream(s)
+        return run
+
+    def fb(store):
+        def body(x, g):
+            if store:
+                o, q, ab = bf.gpa_forward_stored(x, bf.GAUSS, sr, N, radius=R, sigma_s=ss)
+            else:
+                o, q = bf.gpa_forward(x, bf.GAUSS, sr, N, radius=R, sigma_s=ss, return_q=True)
+                ab = None
+            bf.gpa_backward(x, o, q, g, bf.GAUSS, sr, N, radius=R, sigma_s=ss, abar=ab)
+        return fanout(body)
+
+    def dbody(x, g):
+        bf.direct(x, bf.GAUSS, sr, radius=R, sigma_s=ss)
+        bf.direct_backward(x, g, bf.GAUSS, sr, radius=R, sigma_s=ss)
+
+    def graphed(fn):
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            fn()
+            fn()
+        torch.cuda.synchronize(dev)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            fn()
+        torch.cuda.synchronize(dev)
+        return gr
+
+    px = 32 * 512.0 * 512.0
+    g_r, g_s, g_d = graphed(fb(False)), graphed(fb(True)), graphed(fanout(dbody))
+    rms = _time_ms(g_r.replay, 3, stream, flush)
+    sms = _time_ms(g_s.replay, 3, stream, flush)
+    dms = _time_ms(g_d.replay, 2, stream, flush)
+    del g_r, g_s, g_d
+    # image 0's outputs and gradients (both routes) for the checker
+    x0, g0 = xs_[0], gs_[0]
+    o, q = bf.gpa_forward(x0, bf.GAUSS, sr, N, radius=R, sigma_s=ss, return_q=True)
+    gin, gsig = bf.gpa_backward(x0, o, q, g0, bf.GAUSS, sr, N, radius=R, sigma_s=ss)
+    so, sq, ab = bf.gpa_forward_stored(x0, bf.GAUSS, sr, N, radius=R, sigma_s=ss)
+    sgin, sgsig = bf.gpa_backward(x0, so, sq, g0, bf.GAUSS, sr, N, radius=R, sigma_s=ss, abar=ab)
+    ys, xs = _samples(np.random.default_rng(24), 512, 512, 48)
+    keep["grad_512x32"] = {"img": host[0], "g": ghost[0], "ys": ys, "xs": xs, "N": N, "R": R,
+                           "ss": ss, "sr": sr, "fast": _at(o, ys, xs), "gin": _at(gin, ys, xs),
+                           "gin_scale": float(gin.abs().max()), "gsig": float(gsig.item()),
+                           "stored_gin": _at(sgin, ys, xs), "stored_gsig": float(sgsig.item())}
+    del xs_, gs_
+    torch.cuda.empty_cache()
+    return {"workload": "32 x 512x512 blocks(16)+N(0,20^2); Gaussian sigma_s=5 (W=15), "
+                        "sigma_r=25, N=%d (bound for delta=1); forward + backward (image and "
+                        "sigma_r gradients); 8 streams in one CUDA graph" % N,
+            "N": N, "recompute_fwd_bwd_ms": rms, "recompute_mpx_s": px / rms / 1e3,
+            "stored_fwd_bwd_ms": sms, "stored_mpx_s": px / sms / 1e3,
+            "stored_plane_bytes_per_image": 4 * (N + 1) * 512 * 512,
+            "direct_fwd_bwd_ms": dms, "direct_mpx_s": px / dms / 1e3,
+            "speedup_vs_direct": dms / rms,
+            "max_abs_stored_vs_recompute_gin": float((sgin - gin).abs().max()) /
+            max(float(gin.abs().max()), 1e-30)}
+
+
+# ----------------------------------------------------------------- CPU leg: parity
+def cpu_parity(keep):
+    """Errors of the GPU outputs that the studies kept at sampled pixels,
+    against the FP64 checker: Algorithm 2 at the same N (the parity bar), and
+    eq. BF itself (the filter being approximated), for the fast path and for
+    the direct filter, so that "equal max error" is measured, not assumed."""
+    import numpy as np
+
+    import oracle
+
+    def mx(a, b):
+        return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max())
+
+    out = {}
+    t0 = time.perf_counter()
+    h = keep.get("headline")
+    if h:
+        w = oracle.spatial_kernel(h["kind"], h["R"], h["ss"])
+        pix = (h["ys"], h["xs"])
+        alg2 = oracle.gpa_alg2_at(h["img"], w, h["sr"], h["N"], pix)
+        exact = oracle.bf_direct(h["img"], w, h["sr"], samples=pix)
+        d = {"samples": int(len(h["ys"])), "N": h["N"],
+             "fast_vs_alg2_max_abs": mx(h["fast"], alg2),
+             "fast_vs_eq_bf_max_abs": mx(h["fast"], exact)}
+        if "direct" in h:
+            d["direct_vs_eq_bf_max_abs"] = mx(h["direct"], exact)
+        e = keep.get("equal_error")
+        if e:
+            d["N_eq"] = e["N_eq"]
+            d["fast_N_eq_vs_alg2_max_abs"] = mx(e["fast_eq"], oracle.gpa_alg2_at(
+                e["img"], w, e["sr"], e["N_eq"], (e["ys"], e["xs"])))
+            d["fast_N_eq_vs_eq_bf_max_abs"] = mx(e["fast_eq"], oracle.bf_direct(
+                e["img"], w, e["sr"], samples=(e["ys"], e["xs"])))
+        out["headline"] = d
+    big = keep.get("large_8192")
+    if big:
+        w = oracle.spatial_kernel(1, big["R"], big["ss"])
+        pix = (big["ys"], big["xs"])
+        exact = oracle.bf_direct(big["img"], w, big["sr"], samples=pix)
+        d = {"samples": int(len(big["ys"])),
+             "fast_vs_alg2_max_abs": mx(big["fast"], oracle.gpa_alg2_at(big["img"], w, big["sr"],
+                                                                       big["N"], pix)),
+             "fast_vs_eq_bf_max_abs": mx(big["fast"], exact)}
+        if "direct" in big:
+            d["direct_vs_eq_bf_max_abs"] = mx(big["direct"], exact)
+        out["large_8192"] = d
+    b = keep.get("batch_256")
+    if b:
+        sp = b["spec"]
+        w = oracle.spatial_kernel(sp["kind"], sp["radius"], sp["sigma_s"])
+        out["batch_256"] = {"image": "the largest-N image (N=%d)" % sp["N"],
+                            "samples": int(len(b["ys"])),
+                            "fast_vs_alg2_max_abs": mx(b["fast"], oracle.gpa_alg2_at(
+                                b["img"], w, sp["sigma_r"], sp["N"], (b["ys"], b["xs"])))}
+    gr = keep.get("grad_512x32")
+    if gr:
+        w = oracle.spatial_kernel(1, gr["R"], gr["ss"])
+        pix = (gr["ys"], gr["xs"])
+        gref, gsref = oracle.gpa_grad(gr["img"], w, gr["sr"], gr["N"],
+                                      gr["g"].astype(np.float64), samples=pix)
+        scale = max(float(np.abs(gref).max()), gr["gin_scale"], 1e-30)
+        out["grad_512x32"] = {
+            "image": "the first of the 32", "samples": int(len(gr["ys"])),
+            "fast_vs_alg2_max_abs": mx(gr["fast"], oracle.gpa_alg2_at(gr["img"], w, gr["sr"],
+                                                                      gr["N"], pix)),
+            "gin_rel_err": mx(gr["gin"], gref) / scale,
+            "stored_gin_rel_err": mx(gr["stored_gin"], gref) / scale,
+            "gsigma_rel_err": abs(gr["gsig"] - gsref) / max(abs(gsref), 1e-30),
+            "stored_gsigma_rel_err": abs(gr["stored_gsig"] - gsref) / max(abs(gsref), 1e-30)}
+    out["checker_s"] = time.perf_counter() - t0
+    return out
+
+
+# ----------------------------------------------------------------- sweeps
 def _time_ms(fn, reps, stream, flush=None):
     """Mean CUDA-event time of fn() over reps calls (L2 flushed between)."""
     import torch
@@ -470,23 +813,9 @@ def run_sweeps(args):
                   "frac_of_measured_hbm": gbs / hbm_peak, "hbm_peak_src": pk_src})
         del x, o
     if "large8192" in names:
-        # 8192^2 gradient + polygons; Gaussian sigma_s=20 (W=60), sigma_r=40, N from delta=0.5
-        x = torch.from_numpy(synth.gradient_polygons_image(8192, 8192, 64, 15.0, seed=2001)).to(dev)
-        o = torch.empty_like(x)
-        d = torch.empty_like(x)
-        N = bf.order_from_delta(bf.GAUSS, 60, 20.0, 40.0, 0.5)
-        fms = _time_ms(lambda: bf.gpa_forward(x, bf.GAUSS, 40.0, N, radius=60, sigma_s=20.0,
-                                              out=o), 3, stream, flush)
-        dms = _time_ms(lambda: bf.direct(x, bf.GAUSS, 40.0, radius=60, sigma_s=20.0, out=d),
-                       1, stream, flush)
-        px = 8192.0 * 8192.0
-        emit({"sweep": "large8192", "kind": "gaussian", "radius": 60, "sigma_s": 20.0,
-              "sigma_r": 40.0, "N": N, "fast_fwd_ms": fms, "fast_fwd_mpx_s": px / fms / 1e3,
-              "direct_fwd_ms": dms, "direct_fwd_mpx_s": px / dms / 1e3,
-              "speedup_vs_direct": dms / fms,
-              "max_abs_fast_vs_direct": float((o.double() - d.double()).abs().max()),
-              "fwd_alu_ops_frac": fwd_ops_per_pixel(1, 60, N) * px / (fms * 1e-3) /
-              fp32_peak_ops(152, float(pk.get("sm_max_mhz", 2070.0)))})
+        keep = {}
+        emit(dict(sweep="large8192", **study_large8192(bf, synth, dev, stream, flush, fp32_peak_ops(
+            152, float(pk.get("sm_max_mhz", 2070.0))), keep)))
     if "recursive" in names:
         # Algorithm 2 with the recursive (Deriche) Gaussian: cost independent of
         # sigma_s, against the truncated-Gaussian FIR forward (fused tile or banded
@@ -585,27 +914,7 @@ def run_sweeps(args):
                   "centre_weight_recursive": bf.centre_weight(bf.GAUSS_RECURSIVE, 0, ss),
                   "centre_weight_truncated": bf.centre_weight(bf.GAUSS, int(math.ceil(3 * ss)), ss)})
     if "batch256" in names:
-        specs = synth.batch_specs(256, seed=3000)
-        for sp in specs:
-            sp["N"] = bf.order_from_delta(sp["kind"], sp["radius"], sp["sigma_s"], sp["sigma_r"], 1.0)
-        imgs = [torch.from_numpy(synth.blocks_image(sp["height"], sp["width"], 16, 20.0,
-                                                    seed=sp["seed"])).to(dev) for sp in specs]
-        outs = [torch.empty_like(t) for t in imgs]
-        plan = bf.BatchPlan(imgs, outs, specs)
-        items, ctas = plan.info()
-        gms = _time_ms(plan.replay, 5, stream, flush)
-
-        def loop():
-            for x, o, sp in zip(imgs, outs, specs):
-                bf.gpa_forward(x, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
-                               sigma_s=sp["sigma_s"], out=o)
-        lms = _time_ms(loop, 3, stream, flush)
-        px = float(sum(sp["height"] * sp["width"] for sp in specs))
-        emit({"sweep": "batch256", "images": 256, "megapixels": px / 1e6, "work_items": items,
-              "ctas": ctas, "graph_ms": gms, "graph_mpx_s": px / gms / 1e3,
-              "per_image_launches_ms": lms, "per_image_mpx_s": px / lms / 1e3,
-              "N_range": [min(s["N"] for s in specs), max(s["N"] for s in specs)]})
-        plan.close()
+        emit(dict(sweep="batch256", **study_batch256(bf, synth, dev, stream, flush, {})))
     if "tightness" in names:
         # Fig. tightness: orders from Chebyshev / Chernoff / exact Poisson / exhaustive grid
         # search, and the grid sup-norm error each order achieves (1025^2 grid of [-T, T]^2)
@@ -679,68 +988,7 @@ def run_sweeps(args):
                   "max_abs_rec_vs_fir": float((o.double() - d.double()).abs().max())})
             del ws
     if "grad512" in names:
-        # 32 x 512^2, Gaussian sigma_s=5 (W=15), sigma_r=25, N from delta=1: fwd+bwd
-        N = bf.order_from_delta(bf.GAUSS, 15, 5.0, 25.0, 1.0)
-        xs = [torch.from_numpy(synth.blocks_image(512, 512, 16, 20.0, seed=4000 + k)).to(dev)
-              for k in range(32)]
-        gs = [torch.from_numpy(synth.random_like((512, 512), seed=5000 + k)).to(dev)
-              for k in range(32)]
-
-        # a 512^2 image alone fills only part of the GPU: the 32 images run on 8
-        # streams (parallel branches of the captured graph)
-        side = [torch.cuda.Stream(dev) for _ in range(8)]
-
-        def fanout(body):
-            def run():
-                cur = torch.cuda.current_stream(dev)
-                for k, (x, g) in enumerate(zip(xs, gs)):
-                    s = side[k % len(side)]
-                    s.wait_stream(cur)
-                    with torch.cuda.stream(s):
-                        body(x, g)
-                for s in side:
-                    cur.wait_stream(s)
-            return run
-
-        def fb(store):
-            def body(x, g):
-                if store:
-                    o, q, ab = bf.gpa_forward_stored(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0)
-                else:
-                    o, q = bf.gpa_forward(x, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0,
-                                          return_q=True)
-                    ab = None
-                bf.gpa_backward(x, o, q, g, bf.GAUSS, 25.0, N, radius=15, sigma_s=5.0, abar=ab)
-            return fanout(body)
-
-        def dbody(x, g):
-            bf.direct(x, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
-            bf.direct_backward(x, g, bf.GAUSS, 25.0, radius=15, sigma_s=5.0)
-        dfb = fanout(dbody)
-        def graphed(fn):
-            # capture the 32-image loop once (the library never allocates or
-            # synchronises), then time replays: no Python launch gaps
-            s = torch.cuda.Stream(dev)
-            s.wait_stream(stream)
-            with torch.cuda.stream(s):
-                fn()
-                fn()
-            torch.cuda.synchronize()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                fn()
-            torch.cuda.synchronize()
-            return g
-
-        px = 32 * 512.0 * 512.0
-        g_r, g_s, g_d = graphed(fb(False)), graphed(fb(True)), graphed(dfb)
-        rms = _time_ms(g_r.replay, 3, stream, flush)
-        sms = _time_ms(g_s.replay, 3, stream, flush)
-        dms = _time_ms(g_d.replay, 2, stream, flush)
-        emit({"sweep": "grad512", "images": 32, "N": N, "recompute_fwd_bwd_ms": rms,
-              "recompute_mpx_s": px / rms / 1e3, "stored_fwd_bwd_ms": sms,
-              "stored_mpx_s": px / sms / 1e3, "stored_plane_bytes_per_image": 4 * (N + 1) * 512 * 512,
-              "direct_fwd_bwd_ms": dms, "direct_mpx_s": px / dms / 1e3})
+        emit(dict(sweep="grad512", **study_grad512(bf, synth, dev, stream, flush, {})))
     return 0
 
 
@@ -750,6 +998,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweeps(args)
+
+    import ctypes
 
     import numpy as np
     import torch
@@ -770,21 +1020,26 @@ def main():
 
     kind = bf.GAUSS if args.kind == "gauss" else bf.BOX
     R, ss, sr = args.radius, args.sigma_s, args.sigma_r
-    S = args.size
+    S, B = args.size, args.batch
     t0 = time.perf_counter()
-    N = args.order or bf.order_from_delta(kind, R, ss, sr, 1.0)  # A0, host
+    N = args.order or bf.order_from_delta(kind, R, ss, sr, 1.0)  # A0, host, once per workload
     order_ms = 1e3 * (time.perf_counter() - t0)
-    img_np = synth.blocks_image(S, S, 64, 10.0, seed=1000 + rank)
-    g_np = synth.random_like((S, S), seed=77 + rank)
-    x = torch.from_numpy(img_np).to(dev)
-    gout = torch.from_numpy(g_np).to(dev)
-    out = torch.empty_like(x)
-    q = torch.empty_like(x)
-    gin = torch.empty_like(x)
+    # B distinct device images per step: NB seeded host images, each in B / NB
+    # row rotations (a rotated blocks image is a blocks image of the same recipe)
+    NB = min(B, 8)
+    base_np = [synth.blocks_image(S, S, 64, 10.0, seed=1000 + rank * NB + k) for k in range(NB)]
+    gbase_np = [synth.random_like((S, S), seed=77 + rank * NB + k) for k in range(NB)]
+    base = [torch.from_numpy(a).to(dev) for a in base_np]
+    gbase = [torch.from_numpy(a).to(dev) for a in gbase_np]
+    xs = [torch.roll(base[k % NB], shifts=37 * (k // NB), dims=0).contiguous() for k in range(B)]
+    gs_ = [torch.roll(gbase[k % NB], shifts=37 * (k // NB), dims=0).contiguous() for k in range(B)]
+    del base, gbase
+    outs = [torch.empty_like(xs[0]) for _ in range(B)]
+    qs = [torch.empty_like(xs[0]) for _ in range(B)]
+    gins = [torch.empty_like(xs[0]) for _ in range(B)]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     p = bf._lib.make_params(kind, R, ss, sr, N)
-    import ctypes
     lib = bf._lib.lib()
     sp = ctypes.c_void_p(stream.cuda_stream)
     nws = ctypes.c_size_t(0)
@@ -792,42 +1047,44 @@ def main():
         bf._lib.check(lib.bf_fast_backward_workspace(S, S, ctypes.byref(p), ctypes.byref(nws)),
                       "ws")
     ws = torch.empty(max(nws.value, 1), dtype=torch.uint8, device=dev)
-    gs = torch.zeros(1, dtype=torch.float64, device=dev)
+    gsig = torch.zeros(B, dtype=torch.float64, device=dev)
     P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
-    # radii above 15 run the banded two-pass forward, which needs a workspace
+    # the banded two-pass forward (radii above 15 by default) needs a workspace
     nfws = ctypes.c_size_t(0)
     bf._lib.check(lib.bf_fast_forward_workspace(S, S, ctypes.byref(p), ctypes.byref(nfws)), "fws")
     fws = torch.empty(max(nfws.value, 16), dtype=torch.uint8, device=dev)
 
-    def fwd():
-        bf._lib.check(lib.bf_fast_forward_ws(P(x), P(out), P(q), S, S, S, ctypes.byref(p), P(fws),
-                                             nfws, sp), "fwd")
+    def fwd(k):
+        bf._lib.check(lib.bf_fast_forward_ws(P(xs[k]), P(outs[k]), P(qs[k]), S, S, S,
+                                             ctypes.byref(p), P(fws), nfws, sp), "fwd")
 
-    def bwd():
-        bf._lib.check(lib.bf_fast_backward(P(x), P(out), P(q), P(gout), P(gin), P(gs), S, S, S,
+    def bwd(k):
+        bf._lib.check(lib.bf_fast_backward(P(xs[k]), P(outs[k]), P(qs[k]), P(gs_[k]), P(gins[k]),
+                                           ctypes.c_void_p(gsig.data_ptr() + 8 * k), S, S, S,
                                            ctypes.byref(p), P(ws), nws, sp), "bwd")
 
     fwd_launches = 1
     if nfws.value > 0:  # banded forward: a column pass and a row pass per band
         band_rows = nfws.value // ((N + 1) * ((S + 3) // 4 * 4) * 4)
         fwd_launches = 2 * ((S + band_rows - 1) // band_rows)
-    launches_per = {"all": fwd_launches + 2, "fwd": fwd_launches, "bwd": 2}[args.only]
+    launches_per = B * {"all": fwd_launches + 2, "fwd": fwd_launches, "bwd": 2}[args.only]
+    if args.only == "bwd":
+        for k in range(B):
+            fwd(k)
 
     def step(ev):
-        if args.only in ("all", "fwd"):
-            ev[0].record(stream)
-            fwd()
-            ev[1].record(stream)
-        if args.only in ("all", "bwd"):
-            if args.only == "bwd" and not hasattr(step, "primed"):
-                fwd()
-                step.primed = True
-            ev[2].record(stream)
-            bwd()
-            ev[3].record(stream)
+        for k in range(B):
+            if args.only in ("all", "fwd"):
+                ev[k][0].record(stream)
+                fwd(k)
+                ev[k][1].record(stream)
+            if args.only in ("all", "bwd"):
+                ev[k][2].record(stream)
+                bwd(k)
+                ev[k][3].record(stream)
 
     def new_events():
-        return [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        return [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(B)]
 
     for _ in range(args.warmup):
         step(new_events())
@@ -842,7 +1099,7 @@ def main():
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(float(k))  # evict L2 between steps (not inside the step's events)
+        flush.fill_(float(k))  # evict L2 between steps (outside the step's events)
         step(evs[k])
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -850,26 +1107,32 @@ def main():
         dist.barrier()
     clocks = sampler.stop() if rank == 0 else None
 
-    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs] if args.only in ("all", "fwd") else [0.0]
-    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs] if args.only in ("all", "bwd") else [0.0]
-    step_ms = statistics.mean(fwd_ms) + statistics.mean(bwd_ms)
-    t_total = step_ms * args.steps
+    first = 0 if args.only in ("all", "fwd") else 2
+    last = 3 if args.only in ("all", "bwd") else 1
+    step_spans = [e[0][first].elapsed_time(e[B - 1][last]) for e in evs]
+    fwd_ms = ([e[k][0].elapsed_time(e[k][1]) for e in evs for k in range(B)]
+              if args.only in ("all", "fwd") else [0.0])
+    bwd_ms = ([e[k][2].elapsed_time(e[k][3]) for e in evs for k in range(B)]
+              if args.only in ("all", "bwd") else [0.0])
+    t_total = sum(step_spans)
     if dist:
         tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
     px = float(S) * S
-    value = px * world * args.steps / (t_total * 1e-3) / 1e6
-    fwd_mpx = px / (statistics.mean(fwd_ms) * 1e-3) / 1e6 if args.only != "bwd" else None
+    value = px * B * world * args.steps / (t_total * 1e-3) / 1e6
+    mf = statistics.mean(fwd_ms) if args.only != "bwd" else None
+    mb = statistics.mean(bwd_ms) if args.only != "fwd" else None
+    fwd_mpx = px / (mf * 1e-3) / 1e6 if mf else None
 
     # ---- e2e through the public API with host buffers (pinned), copies inside the region.
-    # Every step copies its own inputs host->device and its gradients device->host;
-    # the copies run on their own streams, double-buffered, so step k+1's upload
-    # and step k's download overlap step k's filter.
+    # Every image copies its own input and cotangent host->device and its gradients
+    # device->host; the copies run on their own streams, double-buffered, so image
+    # k+1's upload and image k's download overlap image k's filter.
     e2e = None
     if args.only == "all":
-        hx = torch.from_numpy(img_np).pin_memory()
-        hg = torch.from_numpy(g_np).pin_memory()
+        hx = torch.from_numpy(base_np[0]).pin_memory()
+        hg = torch.from_numpy(gbase_np[0]).pin_memory()
         hgin = torch.empty((S, S), dtype=torch.float32).pin_memory()
         hgs = torch.empty(1, dtype=torch.float64).pin_memory()
         sig = torch.tensor(sr, device=dev, requires_grad=True)
@@ -883,7 +1146,7 @@ def main():
 
         def upload(k):
             b = k % 2
-            up.wait_event(ev_free[b])  # the step that last used buffer b is done with it
+            up.wait_event(ev_free[b])  # the image that last used buffer b is done with it
             with torch.cuda.stream(up):
                 dx[b].copy_(hx, non_blocking=True)
                 dg[b].copy_(hg, non_blocking=True)
@@ -915,7 +1178,7 @@ def main():
 
         run(2)
         torch.cuda.synchronize(dev)
-        ne = max(10, min(args.steps, 100))
+        ne = max(10, min(args.steps * B, 200))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -925,15 +1188,26 @@ def main():
         torch.cuda.synchronize(dev)
         ems = e0.elapsed_time(e1) / ne
         e2e = {"value": px / (ems * 1e-3) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(hx.numel() * 4 + hg.numel() * 4),
-               "d2h_bytes_per_step": int(hgin.numel() * 4 + 8),
-               "ms_per_step": ems, "api": "paper_1603_08109_gb300.gpa_bilateral + backward",
-               "copies": "separate upload/download streams, double-buffered inputs"}
+               "h2d_bytes_per_step": int(hx.numel() * 4 + hg.numel() * 4) * B,
+               "d2h_bytes_per_step": int(hgin.numel() * 4 + 8) * B,
+               "ms_per_image": ems, "images_timed": ne,
+               "api": "paper_1603_08109_gb300.gpa_bilateral + backward",
+               "copies": "per image: input and cotangent up, image and sigma_r gradients down; "
+                         "separate upload/download streams, double-buffered inputs"}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
+
+    keep = {}
+    x0, out0, g0 = xs[0], outs[0], gs_[0]
+    rng = np.random.default_rng(20)
+    hys, hxs = _samples(rng, S, S, 3000)
+    if args.only != "bwd":
+        fwd(0)
+        keep["headline"] = {"img": base_np[0], "ys": hys, "xs": hxs, "kind": kind, "R": R,
+                            "ss": ss, "sr": sr, "N": N, "fast": _at(out0, hys, hxs)}
 
     # ---- direct filter on the same image (same-GPU comparison)
     direct = None
@@ -943,19 +1217,19 @@ def main():
         bf._lib.check(lib.bf_direct_backward_workspace(S, S, ctypes.byref(pd), ctypes.byref(dws_n)),
                       "dws")
         dws = torch.empty(dws_n.value, dtype=torch.uint8, device=dev)
-        dout = torch.empty_like(x)
-        dgin = torch.empty_like(x)
+        dout = torch.empty_like(x0)
+        dgin = torch.empty_like(x0)
         dgs = torch.zeros(1, dtype=torch.float64, device=dev)
 
         def dfwd():
-            bf._lib.check(lib.bf_direct(P(x), P(dout), S, S, S, ctypes.byref(pd), sp), "direct")
+            bf._lib.check(lib.bf_direct(P(x0), P(dout), S, S, S, ctypes.byref(pd), sp), "direct")
 
         dbwd_ok = [True]
 
         def dbwd():
             if not dbwd_ok[0]:
                 return
-            st = lib.bf_direct_backward(P(x), P(gout), P(dgin), P(dgs), S, S, S,
+            st = lib.bf_direct_backward(P(x0), P(gs_[0]), P(dgin), P(dgs), S, S, S,
                                         ctypes.byref(pd), P(dws), dws_n, sp)
             if st == 3:  # the direct gradient's tile does not fit shared memory at this radius
                 dbwd_ok[0] = False
@@ -976,14 +1250,15 @@ def main():
         torch.cuda.synchronize(dev)
         dfm = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
         dbm = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-        fwd()
-        torch.cuda.synchronize(dev)
-        diff = (out.double() - dout.double())
+        diff = (out0.double() - dout.double())
         direct = {"fwd_mpx_s": px / (dfm * 1e-3) / 1e6,
                   "fwd_bwd_mpx_s": px / ((dfm + dbm) * 1e-3) / 1e6 if dbwd_ok[0] else None,
                   "fwd_ms": dfm, "bwd_ms": dbm if dbwd_ok[0] else None,
                   "fast_vs_direct_max_abs": float(diff.abs().max()),
-                  "fast_vs_direct_mse_db": float(10 * math.log10(max(float((diff ** 2).mean()), 1e-300)))}
+                  "fast_vs_direct_mse_db": float(10 * math.log10(max(float((diff ** 2).mean()),
+                                                                     1e-300)))}
+        keep["headline"]["direct"] = _at(dout, hys, hxs)
+        del dws, dout, dgin
 
     # ---- roofline of the dominant kernel (FP32 pipe), live CUDA-event timing
     pk, pk_src = peaks()
@@ -992,12 +1267,10 @@ def main():
     fpeak = fp32_peak_ops(props.multi_processor_count, sm_max)
     fo = fwd_ops_per_pixel(kind, R, N) * px
     bo = bwd_ops_per_pixel(kind, R, N) * px
-    mf = statistics.mean(fwd_ms) if args.only != "bwd" else None
-    mb = statistics.mean(bwd_ms) if args.only != "fwd" else None
     cand = []
     if mf:
         cand.append(("gpa_fwd_fixed_kernel" if R in FIXED_RADII else
-                     ("band_vpass+band_hpass" if R > 15 else "gpa_fwd_kernel"), mf, fo))
+                     ("band_vpass+band_hpass" if nfws.value > 0 else "gpa_fwd_kernel"), mf, fo))
     if mb:
         cand.append(("gpa_bwd_fixed_kernel" if R in FIXED_RADII else "gpa_bwd_kernel", mb, bo))
     name, ms, ops = max(cand, key=lambda c: c[1])
@@ -1014,18 +1287,21 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved * 1e12 / fpeak, "traffic": traffic,
                 "peak_src": "FP32 pipe: %d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz); one FMA = "
                             "one op" % (props.multi_processor_count, sm_max, pk_src),
-                "ops_per_launch": ops}
+                "ops_per_launch": ops, "launch_ms": ms}
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
-    fwd_bytes = px * 12.0  # read f, write out and Q'
     hbm = None
     if mf:
-        gbs = fwd_bytes / (mf * 1e-3) / 1e9
+        gbs = px * 12.0 / (mf * 1e-3) / 1e9  # read f, write out and Q'
         hbm = {"fwd_algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / hbm_peak,
                "peak_gbs": hbm_peak, "peak_src": pk_src}
+    del xs, gs_, outs, qs, gins, ws, fws
+    torch.cuda.empty_cache()
 
-    # the small-N HBM study at 4096^2 (a batch of 8 same-sized images in one call:
-    # one launch of the warp-strip box kernel), live CUDA events, inputs > L2
-    hbm_4096 = None
+    # ---- the small-N HBM study at 4096^2 (box W = 3, sigma_r = 40, N = 1; inputs
+    # larger than L2): a batch of 8 same-sized images in one call (one launch of
+    # the warp-strip box kernel), and one image alone: single launches after an L2
+    # flush, and back to back over the 8 images
+    hbm_4096 = hbm_4096_single = None
     if world == 1 and not args.no_hbm_study:
         K4, S4 = 8, 4096
         xb = torch.from_numpy(np.stack([synth.blocks_image(S4, S4, 64, 10.0, seed=3000 + k)
@@ -1039,30 +1315,68 @@ def main():
                     "ms_per_image": ms4, "algorithmic_bytes_per_px": 8,
                     "algorithmic_gbs": gbs4, "frac_of_measured_hbm": gbs4 / hbm_peak,
                     "peak_gbs": hbm_peak, "peak_src": pk_src}
+        one = _time_ms(lambda: bf.gpa_forward(xb[0], bf.BOX, 40.0, 1, radius=3, out=ob[0]), 10,
+                       stream, flush)
+        for k in range(K4):
+            bf.gpa_forward(xb[k], bf.BOX, 40.0, 1, radius=3, out=ob[k])
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(3):
+            for k in range(K4):
+                bf.gpa_forward(xb[k], bf.BOX, 40.0, 1, radius=3, out=ob[k])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        b2b = e0.elapsed_time(e1) / (3 * K4)
+        hbm_4096_single = {
+            "workload": "one 4096x4096 blocks(64)+N(0,10^2) image; box W=3, sigma_r=40, N=1; "
+                        "bf_fast_forward (one warp-strip launch)",
+            "single_launch_ms": one,
+            "single_launch_frac_of_measured_hbm": 8.0 * S4 * S4 / (one * 1e-3) / 1e9 / hbm_peak,
+            "back_to_back_ms": b2b,
+            "back_to_back_frac_of_measured_hbm": 8.0 * S4 * S4 / (b2b * 1e-3) / 1e9 / hbm_peak,
+            "peak_gbs": hbm_peak, "peak_src": pk_src}
         del xb, ob
+        torch.cuda.empty_cache()
+
+    # ---- the other workloads (each timed on its own; errors from the CPU leg)
+    studies = {}
+    if world == 1 and not args.no_studies and args.only == "all" and (S, kind, R) == (2048, 1, 9):
+        studies["equal_error"] = study_equal_error(bf, base_np[0], x0, g0, kind, R, ss, sr, N, dev,
+                                                   stream, flush, keep)
+        if direct:
+            ee = studies["equal_error"]
+            ee["direct_fwd_bwd_ms"] = direct["fwd_ms"] + (direct["bwd_ms"] or float("nan"))
+            ee["speedup_vs_direct_fwd_bwd"] = ee["direct_fwd_bwd_ms"] / ee["fast_fwd_bwd_ms"]
+        del x0, out0, g0
+        torch.cuda.empty_cache()
+        studies["large_8192"] = study_large8192(bf, synth, dev, stream, flush, fpeak, keep)
+        studies["grad_512x32"] = study_grad512(bf, synth, dev, stream, flush, keep)
+        studies["batch_256"] = study_batch256(bf, synth, dev, stream, flush, keep)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1 and args.only == "all":
-        fwd()
-        torch.cuda.synchronize(dev)
-        cpu, err = cpu_baseline(img_np, kind, R, ss, sr, N, gpu_out=out.cpu().numpy())
-        cpu["gpu_max_abs_err_at_samples"] = err
+        cpu, _ = cpu_baseline(base_np[0], kind, R, ss, sr, N)
+        cpu["parity"] = cpu_parity(keep)
 
+    default = (S, kind, R, ss, sr, N, args.only, B) == (2048, 1, 9, 3.0, 30.0, 40, "all", 96)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": (WORKLOAD if (S, kind, R, ss, sr, N, args.only) ==
-                                    (2048, 1, 9, 3.0, 30.0, 40, "all")
-                                    else workload(S, kind, R, ss, sr, N, args.only)),
-                       "image": "%dx%d" % (S, S),
+            "config": {"workload": WORKLOAD if default else
+                       workload(S, kind, R, ss, sr, N, args.only, B),
+                       "image": "%dx%d" % (S, S), "images_per_step": B,
                        "kind": "gaussian" if kind == 1 else "box", "radius": R, "sigma_s": ss,
                        "sigma_r": sr, "N": N, "only": args.only, "l2": L2_NOTE,
-                       "parallelism": "dp%d (one image per rank)" % world},
+                       "parallelism": "dp%d (each rank its own images)" % world},
             "fwd_mpx_s": fwd_mpx, "fwd_ms": mf, "bwd_ms": mb, "order_selection_ms": order_ms,
-            "direct": direct, "hbm": hbm, "hbm_4096_batch": hbm_4096, "clocks": clocks, "e2e": e2e,
+            "direct": direct, "hbm": hbm, "hbm_4096_batch": hbm_4096,
+            "hbm_4096_single": hbm_4096_single, "clocks": clocks, "e2e": e2e,
             "gpu_launches": launches_per * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "wall_s_timed_region": wall}
+    line.update(studies)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -32,7 +32,9 @@ def test_reference_arm_json_line():
 def test_workload_text():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.workload(4096, 1, 9, 3.0, 30.0, 40, "all").startswith("4096x4096 ")
+    assert bench.workload(4096, 1, 9, 3.0, 30.0, 40, "all", 8).startswith("8 x 4096x4096 ")
     assert "box spatial W=5" in bench.workload(2048, 0, 5, 0.0, 40.0, 1, "fwd")
-    assert bench.workload(2048, 0, 5, 0.0, 40.0, 1, "fwd").endswith("step = fused forward")
-    assert bench.WORKLOAD.startswith("2048x2048 ")
+    assert bench.workload(2048, 0, 5, 0.0, 40.0, 1, "fwd").endswith("per image fused forward")
+    assert bench.WORKLOAD == bench.workload(2048, 1, 9, 3.0, 30.0, 40, "all", 96).replace(
+        "Gaussian spatial sigma_s=3 (W=9), sigma_r=30, N=40;",
+        "Gaussian spatial sigma_s=3 (W=9), sigma_r=30, N=40 (bound for delta=1);")
