@@ -401,8 +401,10 @@ void bf_graph_destroy(void *graph_exec);
  *         bf_fast_forward_ws; the calls without one skip it).
  * The library keeps a table variant[kind][radius bucket][order bucket]
  * (-1 = the built-in choice); bf_autotune times every variant that fits on
- * caller-provided device buffers (it synchronises `stream`) and records the
- * fastest.  The single-image forwards and the batch plan read the table.
+ * caller-provided device buffers (it synchronises `stream`; each variant's
+ * fastest of `reps` launches counts) and records the fastest, keeping the
+ * built-in choice unless another variant beats it by more than 3%.  The
+ * single-image forwards and the batch plan read the table.
  *  bf_variant_count        number of variants for a kind (>= 1).
  *  bf_fast_forward_variant forward with an explicit variant (-1 = table);
  *                          variant 8 returns BF_ERR_WORKSPACE here.

@@ -69,3 +69,86 @@ def load(path: str) -> int:
                        int(e["variant"]))
         n += 1
     return n
+
+
+def _bucket(spec):
+    return (int(spec["kind"]), api.radius_bucket(spec["radius"]), api.order_bucket(spec["N"]))
+
+
+def autotune_batch(images, outs, specs, reps: int = 3, margin: float = 0.01,
+                   coverage: float = 0.95):
+    """Tune the table for a batch plan on the batch's own time.
+
+    Isolated single-image timings miss what a batch does to a variant (the
+    persistent launches share the GPU with the per-image and banded launches
+    on the plan's side streams), so each (kind, radius bucket, order bucket)
+    that the batch occupies is tuned on the graph time of the whole batch:
+    greedily, buckets in decreasing order of estimated work until `coverage`
+    of it is covered, each bucket trying every variant that its images can
+    run while the other entries stay fixed.  A variant replaces the bucket's
+    current entry only if the batch gets faster by more than `margin` (timing
+    noise must not move the table).  Returns (entries, ms before, ms after)."""
+    import torch
+
+    dev = images[0].device
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(plan):
+        plan.replay()
+        torch.cuda.synchronize(dev)
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.replay()
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None or t < best else best
+        return best
+
+    def measure():
+        plan = api.BatchPlan(images, outs, specs)
+        try:
+            return timed(plan), plan.variants()
+        finally:
+            plan.close()
+
+    work = {}
+    members = {}
+    for k, sp in enumerate(specs):
+        key = _bucket(sp)
+        work[key] = work.get(key, 0.0) + (sp["N"] + 1.0) * (2 * sp["radius"] + 1) * \
+            sp["height"] * sp["width"]
+        members.setdefault(key, []).append(k)
+    order = sorted(work, key=lambda k: -work[k])
+    total = sum(work.values())
+    t0, _ = measure()
+    best = t0
+    entries = []
+    done = 0.0
+    for key in order:
+        if done >= coverage * total:
+            break
+        done += work[key]
+        cur = api.tuning_get(*key)
+        choice = cur
+        for v in range(-1, api.variant_count(key[0])):
+            if v == cur:
+                continue
+            api.tuning_set(*key, v)
+            plan = api.BatchPlan(images, outs, specs)
+            try:
+                got = plan.variants()
+                if v >= 0 and not any(got[k] == v for k in members[key]):
+                    continue  # no image of the bucket can run v
+                t = timed(plan)
+            finally:
+                plan.close()
+            if t < best * (1.0 - margin):
+                best, choice = t, v
+        api.tuning_set(*key, choice)
+        entries.append({"kind": key[0], "radius_bucket": key[1], "order_bucket": key[2],
+                        "variant": choice, "ms": best, "batch": True})
+    return entries, t0, best
