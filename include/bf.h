@@ -526,12 +526,16 @@ bf_status bf_recursive_backward_stored(const float *d_in, const float *d_out,
  * BF_SPATIAL_BOX) or truncated Gaussian (BF_SPATIAL_GAUSS, radius = ceil(3
  * sigma_s) if p->radius <= 0) of the planar filter, the same along every
  * axis; neighbours outside the volume do not contribute.  Outputs f_GPA and
- * optionally Q' (normalised), as bf_fast_forward per voxel.  Choose N from
- * eq. eps with w(0) = w1(0)^3 (bf_order_estimates' Chernoff order for
- * eps = w(0) delta / (2T + delta)).  Two passes: the z-filtering of the N + 1
- * power images into the workspace, then per z-plane the y- and x-filterings
- * and the ratio.  Workspace: bf_volume_workspace bytes = (N + 1) depth height
- * width floats, device memory owned by the caller, 16-byte aligned.
+ * optionally Q' (normalised), as bf_fast_forward per voxel.  Choose N with
+ * bf_volume_order_from_delta (eq. eps with w(0) = w1(0)^3).  Two passes: the
+ * z-filtering of the N + 1 power images into the workspace, then per z-plane
+ * the y- and x-filterings and the ratio (for W <= 8 each channel's plane
+ * region reaches shared memory by one tiled tensor copy).  Workspace:
+ * bf_volume_workspace bytes = 256 + 4 (N + 1) depth height Wp, Wp = width
+ * rounded up to a multiple of 4; device memory owned by the caller, 16-byte
+ * aligned.  Its first 4 bytes are a status word that each call sets to
+ * BF_OK; a copy wait that gives up after about a second (which a healthy GPU
+ * never reaches) leaves BF_ERR_TIMEOUT there and the outputs undefined.
  * BF_ERR_UNSUPPORTED for radius > 31 or depth or height > 65535;
  * BF_ERR_WORKSPACE for a missing or small workspace; BF_ERR_INVALID_ARG for
  * other kinds, aliasing outputs or sizes < 1.  Asynchronous on `stream`. */

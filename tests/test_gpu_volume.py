@@ -24,6 +24,9 @@ CASES = [  # (kind, radius, sigma_s, sigma_r, (D, H, W))
     (bf.GAUSS, 9, 3.0, 50.0, (3, 70, 33)),
     (bf.BOX, 1, 0.0, 25.0, (1, 1, 1)),
     (bf.GAUSS, 4, 4.0 / 3.0, 60.0, (35, 9, 8)),
+    (bf.GAUSS, 7, 7 / 3.0, 40.0, (3, 150, 131)),   # odd radius, several 64 x 48 y/x tiles
+    (bf.BOX, 8, 0.0, 45.0, (4, 129, 97)),          # the largest tensor-copy radius
+    (bf.BOX, 0, 0.0, 30.0, (2, 65, 49)),           # W = 0: the range kernel alone
 ]
 
 
@@ -57,6 +60,7 @@ def test_volume_z_constant_matches_planar_filter():
     out2 = bf.gpa_volume(x, bf.GAUSS, sr, N, radius=r, sigma_s=ss, ws=ws)
     ref = bf.gpa_forward(torch.from_numpy(img).cuda(), bf.GAUSS, sr, N, radius=r, sigma_s=ss)
     torch.cuda.synchronize()
+    assert int(ws[:1].view(torch.int32).item()) == 0  # the workspace's status word: no timeout
     assert torch.equal(out, out2)
     for z in range(D):
         assert float((out[z] - ref).abs().max()) <= 1e-3, z
@@ -72,7 +76,10 @@ def test_volume_errors():
     assert lib.bf_volume_workspace(4, 8, 8, ctypes.byref(p), ctypes.byref(n)) == 3
     p = bf._lib.make_params(bf.BOX, 2, 0.0, 30.0, 10)
     assert lib.bf_volume_workspace(4, 8, 8, ctypes.byref(p), ctypes.byref(n)) == 0
-    assert n.value == 11 * 4 * 8 * 8 * 4
+    assert n.value == 256 + 11 * 4 * 8 * 8 * 4  # status header + N + 1 planes
+    assert lib.bf_volume_workspace(4, 8, 6, ctypes.byref(p), ctypes.byref(n)) == 0
+    assert n.value == 256 + 11 * 4 * 8 * 8 * 4  # rows padded to a multiple of 4 floats
+    assert lib.bf_volume_workspace(4, 8, 8, ctypes.byref(p), ctypes.byref(n)) == 0
     ws = torch.empty(n.value // 4, device="cuda")
     assert lib.bf_volume_forward(ptr(x), ptr(o), None, 4, 8, 8, ctypes.byref(p), ptr(ws),
                                  n.value - 4, None) == 5

@@ -54,3 +54,34 @@ def test_autotune_then_forward_meets_parity(tmp_path, restored_table):
     again = bf.gpa_forward(torch.from_numpy(img).cuda(), bf.GAUSS, 30.0, 24, radius=12,
                            sigma_s=4.0, variant=entries[0]["variant"])
     assert torch.equal(again, out)
+
+
+@pytest.mark.gpu
+@needs_gpu
+def test_batch_autotuner_sets_entries_the_plan_follows(restored_table):
+    """tuning.autotune_batch tunes the batch's buckets on its graph time; the
+    plan built afterwards runs the table's variants, bitwise equal to the
+    single-image calls with those variants."""
+    from paper_1603_08109_gb300 import synth
+    specs = synth.batch_specs(6, seed=31, max_hw=(200, 260))
+    for sp in specs:
+        sp["N"] = bf.order_from_delta(sp["kind"], sp["radius"], sp["sigma_s"], sp["sigma_r"], 1.0)
+    imgs = [torch.from_numpy(image(sp["height"], sp["width"], seed=sp["seed"])).cuda()
+            for sp in specs]
+    outs = [torch.empty_like(x) for x in imgs]
+    entries, before, after = tuning.autotune_batch(imgs, outs, specs, reps=2, coverage=1.0)
+    assert entries and after <= before
+    keys = {(e["kind"], e["radius_bucket"], e["order_bucket"]) for e in entries}
+    assert keys == {(sp["kind"], bf.radius_bucket(sp["radius"]), bf.order_bucket(sp["N"]))
+                    for sp in specs}
+    for e in entries:
+        assert bf.tuning_get(e["kind"], e["radius_bucket"], e["order_bucket"]) == e["variant"]
+    plan = bf.BatchPlan(imgs, outs, specs)
+    variants = plan.variants()
+    plan.run()
+    torch.cuda.synchronize()
+    for x, o, sp, v in zip(imgs, outs, specs, variants):
+        ref = bf.gpa_forward(x, sp["kind"], sp["sigma_r"], sp["N"], radius=sp["radius"],
+                             sigma_s=sp["sigma_s"], variant=v)
+        assert torch.equal(o, ref)
+    plan.close()
