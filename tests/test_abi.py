@@ -234,7 +234,7 @@ def test_volume_host_side():
     n = ctypes.c_size_t()
     p = L.make_params(L.BOX, 3, 0.0, 40.0, 7)
     assert lib.bf_volume_workspace(5, 6, 7, ctypes.byref(p), ctypes.byref(n)) == 0
-    assert n.value == 8 * 5 * 6 * 7 * 4
+    assert n.value == 256 + 8 * 5 * 6 * 8 * 4  # status word header; rows padded to 8 floats
     assert lib.bf_volume_workspace(0, 6, 7, ctypes.byref(p), ctypes.byref(n)) == 1
     big = L.make_params(L.BOX, 32, 0.0, 40.0, 7)
     assert lib.bf_volume_workspace(5, 6, 7, ctypes.byref(big), ctypes.byref(n)) == 3
