@@ -11,7 +11,8 @@
 // exactly as for images; only the N + 1 filterings are 3-D.
 //
 // Two kernels:
-//   vol_zpass   one thread per (y, x) column and 16 output planes z0..z0+15:
+//   vol_zpass   one thread per (y, x) column (two adjacent columns as packed
+//               pairs for W <= 8) and 16 output planes z0..z0+15:
 //               the column's f over the tile plus the W-plane halos is turned
 //               into a_0 and H in shared memory (each thread its own column,
 //               so no barriers), then channel by channel a_n is advanced in
@@ -171,45 +172,6 @@ __global__ void __launch_bounds__(kYNT) vol_yxpass(const __grid_constant__ VolAr
 // x filter per (output row, 4 consecutive voxels), which are also the
 // thread's voxels for the recursion and the sums.
 constexpr int kVolFixedMaxR = 8;
-
-template <int R>
-__global__ void __launch_bounds__(kZNT) vol_zpass_r(const __grid_constant__ VolArgs A) {
-  constexpr int L = 2 * R + 1, RZ = kZT + 2 * R;
-  const int t = threadIdx.x;
-  const int x = blockIdx.x * kZNT + t, y = blockIdx.y, z0 = blockIdx.z * kZT;
-  if (x >= A.W) return;
-  const long long col = (long long)y * A.W + x, zs = (long long)A.H * A.W;
-  const long long wcol = (long long)y * A.Wp + x, wzs = (long long)A.H * A.Wp;
-  float a[RZ], h[RZ];
-#pragma unroll
-  for (int r = 0; r < RZ; ++r) {
-    const int z = z0 - R + r;
-    float av = 0.f, hv = 0.f;
-    if (z >= 0 && z < A.D) {
-      const float d = __ldg(A.in + z * zs + col) - A.tc;
-      hv = d * A.inv_sr;
-      av = exp2f(d * d * A.e2c);  // exp(-H^2/2)
-    }
-    a[r] = av;
-    h[r] = hv;
-  }
-  const int zn = min(kZT, A.D - z0);
-  for (int n = 0; n <= A.N; ++n) {
-    if (n > 0) {
-      const float rs = __frsqrt_rn((float)n);
-#pragma unroll
-      for (int r = 0; r < RZ; ++r) a[r] *= h[r] * rs;
-    }
-    float *dst = A.ws + (long long)n * A.plane + z0 * wzs + wcol;
-#pragma unroll
-    for (int zo = 0; zo < kZT; ++zo) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k < L; ++k) acc = fmaf(A.taps[k], a[zo + k], acc);
-      if (zo < zn) dst[zo * wzs] = acc;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // y/x pass for W <= 8 with TMA staging.  One CTA of 256 threads per 64 x 48
@@ -409,6 +371,58 @@ __global__ void __launch_bounds__(kTNT, 3) vol_yxpass_tma(const __grid_constant_
   }
 }
 
+// z-pass for W <= 8: each thread owns two adjacent (y, x) columns and 16
+// output planes; the two columns' a_n over the planes and their W-plane halos
+// are packed pairs in registers (both columns take the same taps, so each tap
+// is one two-lane FMA), H of the pairs in shared memory (each thread reads only
+// its own), and Z_n = w1 *_z a_n is stored as pairs (the workspace rows hold a
+// multiple of 4 floats, so a pair starting at an even column never leaves them).
+template <int R>
+__global__ void __launch_bounds__(kZNT) vol_zpass_pairs(const __grid_constant__ VolArgs A,
+                                                        const __grid_constant__ VolTapPairs T) {
+  constexpr int L = 2 * R + 1, RZ = kZT + 2 * R;
+  extern __shared__ __align__(16) float2 sH2[];  // [r][thread]
+  const int t = threadIdx.x;
+  const int x = 2 * (blockIdx.x * kZNT + t), y = blockIdx.y, z0 = blockIdx.z * kZT;
+  if (x >= A.W) return;  // no barriers: every thread owns its columns
+  const bool x1in = x + 1 < A.W;
+  const long long col = (long long)y * A.W + x, zs = (long long)A.H * A.W;
+  const long long wcol = (long long)y * A.Wp + x, wzs = (long long)A.H * A.Wp;
+  float2 a[RZ];
+#pragma unroll
+  for (int r = 0; r < RZ; ++r) {
+    const int z = z0 - R + r;
+    float av[2] = {0.f, 0.f}, hv[2] = {0.f, 0.f};
+    if (z >= 0 && z < A.D) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (e == 1 && !x1in) break;
+        const float d = __ldg(A.in + z * zs + col + e) - A.tc;
+        hv[e] = d * A.inv_sr;
+        av[e] = exp2f(d * d * A.e2c);  // exp(-H^2/2)
+      }
+    }
+    a[r] = make_float2(av[0], av[1]);
+    sH2[r * kZNT + t] = make_float2(hv[0], hv[1]);
+  }
+  const int zn = min(kZT, A.D - z0);
+  for (int n = 0; n <= A.N; ++n) {
+    if (n > 0) {
+      const float rs = __frsqrt_rn((float)n);
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) a[r] = __fmul2_rn(a[r], __fmul2_rn(sH2[r * kZNT + t], make_float2(rs, rs)));
+    }
+    float *dst = A.ws + (long long)n * A.plane + z0 * wzs + wcol;
+#pragma unroll
+    for (int zo = 0; zo < kZT; ++zo) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < L; ++k) acc = __ffma2_rn(T.dup[k], a[zo + k], acc);
+      if (zo < zn) *reinterpret_cast<float2 *>(dst + zo * wzs) = acc;
+    }
+  }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library); looked up once.
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -469,8 +483,9 @@ bf_status launch_volume_r(const VolArgs &A, cudaStream_t s) {
   for (int k = 0; k < 2 * kVolFixedMaxR + 1; ++k) T.dup[k] = k < L ? make_float2(A.taps[k], A.taps[k]) : make_float2(0.f, 0.f);
   for (int k = 0; k < 2 * kVolFixedMaxR + 2; ++k)
     T.pair[k] = make_float2(k < L ? A.taps[k] : 0.f, k >= 1 && k <= L ? A.taps[k - 1] : 0.f);
-  dim3 gz((A.W + kZNT - 1) / kZNT, A.H, (A.D + kZT - 1) / kZT);
-  vol_zpass_r<R><<<gz, kZNT, 0, s>>>(A);
+  constexpr size_t zsm = (size_t)(kZT + 2 * R) * kZNT * sizeof(float2);
+  dim3 gz((A.W + 2 * kZNT - 1) / (2 * kZNT), A.H, (A.D + kZT - 1) / kZT);
+  vol_zpass_pairs<R><<<gz, kZNT, zsm, s>>>(A, T);
   st = bfi::check_launch();
   if (st != BF_OK) return st;
   dim3 gy((A.W + kTX - 1) / kTX, (A.H + kTY - 1) / kTY, A.D);
