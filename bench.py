@@ -1347,13 +1347,31 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
         b2b = e0.elapsed_time(e1) / (3 * K4)
+        # the same single launch after a write flush followed by a 256 MB read: L2 then
+        # holds clean lines, so the launch does not also write back the flush's dirty data
+        rbuf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+        class CleanFlush:
+            def fill_(self, v):
+                flush.fill_(v)
+                rbuf.sum()
+        clean = _time_ms(lambda: bf.gpa_forward(xb[0], bf.BOX, 40.0, 1, radius=3, out=ob[0]), 10,
+                         stream, CleanFlush())
+        cp_dirty = _time_ms(lambda: ob[0].copy_(xb[0]), 10, stream, flush)
+        cp_clean = _time_ms(lambda: ob[0].copy_(xb[0]), 10, stream, CleanFlush())
+        del rbuf
+        frac = lambda ms: 8.0 * S4 * S4 / (ms * 1e-3) / 1e9 / hbm_peak  # noqa: E731
         hbm_4096_single = {
             "workload": "one 4096x4096 blocks(64)+N(0,10^2) image; box W=3, sigma_r=40, N=1; "
                         "bf_fast_forward (one warp-strip launch)",
-            "single_launch_ms": one,
-            "single_launch_frac_of_measured_hbm": 8.0 * S4 * S4 / (one * 1e-3) / 1e9 / hbm_peak,
-            "back_to_back_ms": b2b,
-            "back_to_back_frac_of_measured_hbm": 8.0 * S4 * S4 / (b2b * 1e-3) / 1e9 / hbm_peak,
+            "single_launch_ms": one, "single_launch_frac_of_measured_hbm": frac(one),
+            "single_launch_clean_l2_ms": clean,
+            "single_launch_clean_l2_frac_of_measured_hbm": frac(clean),
+            "back_to_back_ms": b2b, "back_to_back_frac_of_measured_hbm": frac(b2b),
+            "copy_reference": {"single_launch_frac": frac(cp_dirty),
+                               "single_launch_clean_l2_frac": frac(cp_clean)},
+            "flush": "single_launch: after a 512 MB write (L2 left full of dirty lines, which the "
+                     "launch writes back); clean_l2: the same write then a 256 MB read",
             "peak_gbs": hbm_peak, "peak_src": pk_src}
         del xb, ob
         torch.cuda.empty_cache()

@@ -13,6 +13,8 @@
 // Out-of-image pixels carry a_n = 0 (zero extension), as in the fused kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "bf_internal.h"
 #include "gpa_fixed.cuh"
 
@@ -103,6 +105,9 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
       }
       __syncthreads();
     }
+    // a warp whose 16 output rows all lie past the band has nothing to filter
+    // (warp-uniform; it still takes part in the advance and the barriers)
+    if (tyb + 16 * yb >= A.rows) continue;
     float2 acc[16];
     if (KIND == BF_SPATIAL_GAUSS) {
       float2 win[16];
@@ -111,16 +116,24 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
         acc[i] = make_float2(0.f, 0.f);
         win[i] = col[i * CS];
       }
-      for (int k = 0; k < fc.ntaps_pad; k += 16) {
+      // blocks of 16 taps; when at most 8 taps remain for the last block it
+      // takes 8 (the taps past 2W are zeros in fc.taps), which halves the
+      // zero-tap work of padding 2W + 1 to a multiple of 16
+      const int L = 2 * R + 1, kl = (L - 1) & ~15;  // first tap of the last block
+      auto block = [&](int k, auto taps_tag) {
+        constexpr int NTB = decltype(taps_tag)::value;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < NTB; ++j) {
           const float w = fc.taps[k + j];
           const float2 w2 = make_float2(w, w);
 #pragma unroll
           for (int i = 0; i < 16; ++i) acc[i] = __ffma2_rn(w2, win[(j + i) & 15], acc[i]);
           win[j] = col[(k + j + 16) * CS];
         }
-      }
+      };
+      for (int k = 0; k < kl; k += 16) block(k, std::integral_constant<int, 16>{});
+      if (L - kl > 8) block(kl, std::integral_constant<int, 16>{});
+      else block(kl, std::integral_constant<int, 8>{});
     } else {
       float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
       int r = 0;
@@ -212,6 +225,10 @@ __device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int b
     }
     __syncthreads();  // plane n is in buffer n & 1 for every thread
     vrow0 = ((n & 1) ? buf1 : buf0) + lane * P + 16 * seg;
+    if (tx + 16 * seg >= A.W) {  // the warp's 16 columns lie past the image (warp-uniform)
+      __syncthreads();           // the barrier that frees buffer n & 1
+      continue;
+    }
     float Ab[16];
     if (KIND == BF_SPATIAL_GAUSS) {
       float win[16];
@@ -220,15 +237,20 @@ __device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int b
         Ab[i] = 0.f;
         win[i] = vrow0[i];
       }
-      for (int k = 0; k < fc.ntaps_pad; k += 16) {
+      const int L = 2 * R + 1, kl = (L - 1) & ~15;  // as in pass V: a last block of 8 or 16
+      auto block = [&](int k, auto taps_tag) {
+        constexpr int NTB = decltype(taps_tag)::value;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < NTB; ++j) {
           const float w = fc.taps[k + j];
 #pragma unroll
           for (int i = 0; i < 16; ++i) Ab[i] = fmaf(w, win[(j + i) & 15], Ab[i]);
           win[j] = vrow0[k + j + 16];
         }
-      }
+      };
+      for (int k = 0; k < kl; k += 16) block(k, std::integral_constant<int, 16>{});
+      if (L - kl > 8) block(kl, std::integral_constant<int, 16>{});
+      else block(kl, std::integral_constant<int, 8>{});
     } else {
       float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
       int j = 0;
