@@ -111,15 +111,25 @@ void launch_tile_kernel(int v, int ctas, size_t smem, cudaStream_t s, const Batc
 }
 
 // ---- banded items
+// slot: the item's image in its launch's tap table, or -1 when its taps do not
+// fit the table (radius above 63): then they are read from the descriptor copy
 struct BandItem {
-  int desc, bx, by, pad;
+  int desc, bx, by, slot;
 };
+
+// A launch carries the taps of (at most) kBandLaunchImages images in its
+// parameter block, so that the filters read them as constant-bank operands,
+// as the single-image kernels do (from a per-CTA shared copy they cost a
+// shared-memory load per tap and left the batch's passes waiting on them).
+constexpr int kBandLaunchImages = 48, kBandTapsMax = 128;
 
 struct BandBatchArgs {
   const bfk::BandArgs *descs;  // .ws holds the byte offset of the image's planes
   const BandItem *items;       // this launch's items, one per CTA
   char *planes;                // the workspace's plane region
+  float taps[kBandLaunchImages][kBandTapsMax];
 };
+static_assert(sizeof(BandBatchArgs) <= 32764, "kernel parameter block");
 
 template <bool VPASS>
 __global__ void __launch_bounds__(VPASS ? bfk::kVNT : bfk::kBandNT) gpa_batched_band_kernel(
@@ -135,22 +145,22 @@ __global__ void __launch_bounds__(VPASS ? bfk::kVNT : bfk::kBandNT) gpa_batched_
   if (threadIdx.x == 0)
     sA.ws = reinterpret_cast<float *>(A.planes + reinterpret_cast<uintptr_t>(sA.ws));
   __syncthreads();
-  if (VPASS) {
-    if (sA.fc.kind == BF_SPATIAL_GAUSS)
-      bfk::band_vpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem);
-    else
-      bfk::band_vpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem);
+  if (sA.fc.kind != BF_SPATIAL_GAUSS) {  // the box filter has no taps
+    if (VPASS) bfk::band_vpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem, sA.fc.taps);
+    else bfk::band_hpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem, sA.fc.taps);
+  } else if (it.slot >= 0) {
+    if (VPASS) bfk::band_vpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem, A.taps[it.slot]);
+    else bfk::band_hpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem, A.taps[it.slot]);
   } else {
-    if (sA.fc.kind == BF_SPATIAL_GAUSS)
-      bfk::band_hpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem);
-    else
-      bfk::band_hpass_tile<BF_SPATIAL_BOX>(sA, it.bx, it.by, smem);
+    if (VPASS) bfk::band_vpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem, sA.fc.taps);
+    else bfk::band_hpass_tile<BF_SPATIAL_GAUSS>(sA, it.bx, it.by, smem, sA.fc.taps);
   }
 }
 
 struct BandGroup {
   int v0, nv, h0, nh;
   size_t vsmem, hsmem;
+  std::vector<float> taps;  // kBandLaunchImages x kBandTapsMax: the launches' tap table
 };
 
 struct TileGroup {
@@ -271,7 +281,9 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
       BandItem it;
     };
     size_t cur = 0;
+    int slots = 0;  // images in the open group
     std::vector<BCost> vq, hq;
+    std::vector<float> gtaps((size_t)kBandLaunchImages * kBandTapsMax, 0.f);
     auto close_group = [&]() {
       if (vq.empty()) return;
       auto by_cost = [](const BCost &a, const BCost &b) { return a.c > b.c; };
@@ -289,17 +301,20 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
         g.vsmem = std::max(g.vsmem, bfk::vpass_smem(fc.kind, fc.R, fc.ntaps_pad));
         g.hsmem = std::max(g.hsmem, bfk::hpass_smem(fc.kind, fc.R, fc.ntaps_pad));
       }
-      plan->groups.push_back(g);
+      g.taps = gtaps;
+      plan->groups.push_back(std::move(g));
       planes_max = std::max(planes_max, cur);
       vq.clear();
       hq.clear();
       cur = 0;
+      slots = 0;
+      std::fill(gtaps.begin(), gtaps.end(), 0.f);
     };
     for (int i : large) {
       const BatchDesc &bd = plan->descs[i];
       const int H = bd.io.H, W = bd.io.W, Wp = (W + 3) / 4 * 4, N = bd.fc.N;
       const size_t pbytes = align256((size_t)(N + 1) * (size_t)H * (size_t)Wp * sizeof(float));
-      if (cur > 0 && cur + pbytes > kBatchPlaneCap) close_group();
+      if (cur > 0 && (cur + pbytes > kBatchPlaneCap || slots == kBandLaunchImages)) close_group();
       bfk::BandArgs a{};
       a.in = bd.io.in;
       a.out = bd.io.out;
@@ -316,11 +331,17 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
       const int di = (int)plan->bdescs.size();
       plan->bdescs.push_back(a);
       cur += pbytes;
+      int slot = -1;
+      if (bd.fc.ntaps_pad <= kBandTapsMax) {
+        slot = slots;
+        for (int k = 0; k < bd.fc.ntaps_pad; ++k) gtaps[(size_t)slot * kBandTapsMax + k] = bd.fc.taps[k];
+      }
+      ++slots;
       const double c = (N + 1.0) * (bd.fc.kind == BF_SPATIAL_GAUSS ? bd.fc.ntaps_pad : 8.0);
       for (int by = 0; by < (H + bfk::kVB - 1) / bfk::kVB; ++by)
-        for (int bx = 0; bx < (Wp + bfk::kVC - 1) / bfk::kVC; ++bx) vq.push_back({c, {di, bx, by, 0}});
+        for (int bx = 0; bx < (Wp + bfk::kVC - 1) / bfk::kVC; ++bx) vq.push_back({c, {di, bx, by, slot}});
       for (int by = 0; by < (H + bfk::kHT - 1) / bfk::kHT; ++by)
-        for (int bx = 0; bx < (W + bfk::kHW - 1) / bfk::kHW; ++bx) hq.push_back({c, {di, bx, by, 0}});
+        for (int bx = 0; bx < (W + bfk::kHW - 1) / bfk::kHW; ++bx) hq.push_back({c, {di, bx, by, slot}});
     }
     close_group();
   }
@@ -423,6 +444,7 @@ bf_status bf_batch_forward(const bf_batch_plan *plan, void *d_ws, size_t ws_byte
   // banded groups (side stream 1)
   for (const BandGroup &g : plan->groups) {
     BandBatchArgs B;
+    memcpy(B.taps, g.taps.data(), sizeof(B.taps));
     B.descs = reinterpret_cast<const bfk::BandArgs *>(base + plan->off_bdescs);
     B.planes = base + plan->off_planes;
     B.items = reinterpret_cast<const BandItem *>(base + plan->off_bitems) + g.v0;

@@ -27,13 +27,13 @@ constexpr long long kBandCTAs = 8 * 152;   // pass-V CTAs per band wanted
 template <int KIND>
 __global__ void __launch_bounds__(kVNT) band_vpass(const __grid_constant__ BandArgs A) {
   extern __shared__ __align__(16) float sm[];
-  band_vpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm);
+  band_vpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm, A.fc.taps);
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(kBandNT) band_hpass(const __grid_constant__ BandArgs A) {
   extern __shared__ __align__(16) float sm[];
-  band_hpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm);
+  band_hpass_tile<KIND>(A, blockIdx.x, blockIdx.y, sm, A.fc.taps);
 }
 
 // Whether a forward with a workspace takes the banded path: the tuning

@@ -61,8 +61,12 @@ inline size_t hpass_smem(int kind, int R, int ntp) {
 }
 
 // Pass V of tile (bx, by): columns 64 bx.., band rows 64 by.. .
+// `taps` holds fc.taps (2W + 1 normalised taps, zero-padded to fc.ntaps_pad):
+// the single-image kernels pass their parameter block's copy, the batch its
+// launch's table, both constant-bank reads.
 template <int KIND>
-__device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int by, float *sm) {
+__device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int by, float *sm,
+                                                const float *taps) {
   const bfi::FilterConsts &fc = A.fc;
   const int R = fc.R, N = fc.N;
   const int RR = vpass_rows(KIND, R, fc.ntaps_pad);
@@ -117,14 +121,14 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
         win[i] = col[i * CS];
       }
       // blocks of 16 taps; when at most 8 taps remain for the last block it
-      // takes 8 (the taps past 2W are zeros in fc.taps), which halves the
+      // takes 8 (the taps past 2W are zeros), which halves the
       // zero-tap work of padding 2W + 1 to a multiple of 16
       const int L = 2 * R + 1, kl = (L - 1) & ~15;  // first tap of the last block
       auto block = [&](int k, auto taps_tag) {
         constexpr int NTB = decltype(taps_tag)::value;
 #pragma unroll
         for (int j = 0; j < NTB; ++j) {
-          const float w = fc.taps[k + j];
+          const float w = taps[k + j];
           const float2 w2 = make_float2(w, w);
 #pragma unroll
           for (int i = 0; i < 16; ++i) acc[i] = __ffma2_rn(w2, win[(j + i) & 15], acc[i]);
@@ -167,7 +171,8 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
 
 // Pass H of tile (bx, by): output columns 128 bx.., band rows 32 by.. .
 template <int KIND>
-__device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int by, float *sm) {
+__device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int by, float *sm,
+                                                const float *taps) {
   const bfi::FilterConsts &fc = A.fc;
   const int R = fc.R, N = fc.N;
   const int RC = hpass_cols(KIND, R, fc.ntaps_pad), P = hpass_pitch(RC);
@@ -242,7 +247,7 @@ __device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int b
         constexpr int NTB = decltype(taps_tag)::value;
 #pragma unroll
         for (int j = 0; j < NTB; ++j) {
-          const float w = fc.taps[k + j];
+          const float w = taps[k + j];
 #pragma unroll
           for (int i = 0; i < 16; ++i) Ab[i] = fmaf(w, win[(j + i) & 15], Ab[i]);
           win[j] = vrow0[k + j + 16];
