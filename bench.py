@@ -1333,8 +1333,24 @@ def main():
                     "ms_per_image": ms4, "algorithmic_bytes_per_px": 8,
                     "algorithmic_gbs": gbs4, "frac_of_measured_hbm": gbs4 / hbm_peak,
                     "peak_gbs": hbm_peak, "peak_src": pk_src}
-        one = _time_ms(lambda: bf.gpa_forward(xb[0], bf.BOX, 40.0, 1, radius=3, out=ob[0]), 10,
-                       stream, flush)
+        # single launches of ~30 us: the median of 20 timed launches (a mean would
+        # carry the occasional launch that waits on the host)
+        def med_ms(fn, fl, reps=20):
+            fn()
+            torch.cuda.synchronize(dev)
+            ts = []
+            for k in range(reps):
+                fl.fill_(float(k))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+        box1 = lambda: bf.gpa_forward(xb[0], bf.BOX, 40.0, 1, radius=3, out=ob[0])  # noqa: E731
+        one = med_ms(box1, flush)
         for k in range(K4):
             bf.gpa_forward(xb[k], bf.BOX, 40.0, 1, radius=3, out=ob[k])
         torch.cuda.synchronize(dev)
@@ -1355,10 +1371,9 @@ def main():
             def fill_(self, v):
                 flush.fill_(v)
                 rbuf.sum()
-        clean = _time_ms(lambda: bf.gpa_forward(xb[0], bf.BOX, 40.0, 1, radius=3, out=ob[0]), 10,
-                         stream, CleanFlush())
-        cp_dirty = _time_ms(lambda: ob[0].copy_(xb[0]), 10, stream, flush)
-        cp_clean = _time_ms(lambda: ob[0].copy_(xb[0]), 10, stream, CleanFlush())
+        clean = med_ms(box1, CleanFlush())
+        cp_dirty = med_ms(lambda: ob[0].copy_(xb[0]), flush)
+        cp_clean = med_ms(lambda: ob[0].copy_(xb[0]), CleanFlush())
         del rbuf
         frac = lambda ms: 8.0 * S4 * S4 / (ms * 1e-3) / 1e9 / hbm_peak  # noqa: E731
         hbm_4096_single = {
@@ -1371,7 +1386,8 @@ def main():
             "copy_reference": {"single_launch_frac": frac(cp_dirty),
                                "single_launch_clean_l2_frac": frac(cp_clean)},
             "flush": "single_launch: after a 512 MB write (L2 left full of dirty lines, which the "
-                     "launch writes back); clean_l2: the same write then a 256 MB read",
+                     "launch writes back); clean_l2: the same write then a 256 MB read; "
+                     "single launches: median of 20",
             "peak_gbs": hbm_peak, "peak_src": pk_src}
         del xb, ob
         torch.cuda.empty_cache()

@@ -330,17 +330,22 @@ template <int R, int NT, int TH>
 struct BwdFixedGeom {
   static constexpr int RH = TH + 2 * R;
   static constexpr int TW = NT - 2 * R;
-  static constexpr int KH = TH >= 16 ? 16 : 8;
-  static constexpr int IPT = TH / KH;
+  // Phase-H segments of KH output columns: for 8-row tiles the fewest columns
+  // that let the TW output columns of 8 rows fit the NT threads (W = 9: 16
+  // segments of 7 for 110 columns, every thread busy, where segments of 8 left
+  // 16 threads idle).
+  static constexpr int KH = TH >= 16 ? 16 : (TW + 15) / 16;
+  static constexpr int NSEG = (TW + KH - 1) / KH;
+  static constexpr int IPT = (TH * NSEG + NT - 1) / NT;
   static constexpr int L = 2 * R + 1;
   // Phase-H lanes: (row = lane % TH, segment = lane / TH), segments KH
-  // columns apart, reading 8-byte (a, c) pairs.  Row pitch 1 (mod 16) pairs
-  // for 8-row tiles (four segments of 8 rows), 9 (mod 16) for 16-row tiles
-  // (two segments of 16 rows): the 16 lanes of each half-warp access
-  // distinct bank pairs.  Reads run up to column NT + KH - 2.
-  static constexpr int VP = TH >= 16 ? NT + 25 : NT + 33;
-  static_assert(VP % 16 == (TH >= 16 ? 9 : 1), "phase-H row pitch");
-  static_assert(VP >= NT + KH - 1, "phase-H window reads stay inside the row");
+  // columns apart, reading 8-byte (a, c) pairs.  Row pitch (in pairs) 1 (mod 16)
+  // for 8-row tiles with 8-column segments, 2 (mod 16) with odd segments, 9
+  // (mod 16) for 16-row tiles (two segments of 16 rows): the 16 lanes of each
+  // half-warp access distinct bank pairs.
+  static constexpr int VP = TH >= 16 ? NT + 25 : (KH % 2 ? NT + 18 : NT + 33);
+  static_assert(VP % 16 == (TH >= 16 ? 9 : (KH % 2 ? 2 : 1)), "phase-H row pitch");
+  static_assert(VP >= (NSEG - 1) * KH + KH + 2 * R + 1, "phase-H window reads stay inside the row");
   // Floats of the vertical-pass rows: (a_n, c_n) pairs, or c_n alone when
   // w*a_n comes from stored planes (kept even so that sQP stays 8-byte aligned).
   __host__ __device__ static constexpr size_t sv_floats(bool stored) {
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   using G = BwdFixedGeom<R, NT, TH>;
   constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L, VP = G::VP;
   constexpr int PP = G::PP;
-  static_assert(TH % KH == 0 && NT % TH == 0 && TW >= KH, "tile geometry");
+  static_assert(NT % TH == 0 && TW >= KH, "tile geometry");
   extern __shared__ __align__(16) float smem[];
   const bfi::FilterConsts &fc = A.fc;
   const int N = fc.N;
