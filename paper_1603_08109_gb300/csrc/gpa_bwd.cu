@@ -346,6 +346,11 @@ struct BwdFixedGeom {
   static constexpr int VP = TH >= 16 ? NT + 25 : (KH % 2 ? NT + 18 : NT + 33);
   static_assert(VP % 16 == (TH >= 16 ? 9 : (KH % 2 ? 2 : 1)), "phase-H row pitch");
   static_assert(VP >= (NSEG - 1) * KH + KH + 2 * R + 1, "phase-H window reads stay inside the row");
+  // Row pitch (floats) of the D_n rows, which phase H reads one float per
+  // lane: with odd segments 4 (mod 32), so that the 8 rows (multiples of 4)
+  // and the 4 segments of a warp (7 s = 0, 3, 2, 1 mod 4) meet 32 banks.
+  static constexpr int DP = KH % 2 ? NT + 4 : VP;
+  static_assert(DP >= NT, "D_n rows hold the region columns");
   // Floats of the vertical-pass rows: (a_n, c_n) pairs, or c_n alone when
   // w*a_n comes from stored planes (kept even so that sQP stays 8-byte aligned).
   __host__ __device__ static constexpr size_t sv_floats(bool stored) {
@@ -356,7 +361,7 @@ struct BwdFixedGeom {
   static constexpr int PP = TW + KH <= 129 ? 129 : 161;
   static_assert(PP >= TW + KH, "plane tile pitch");
   static constexpr size_t smem_bytes(bool stored) {
-    return (sv_floats(stored) + (size_t)RH * NT * 2 + (size_t)TH * VP + (size_t)RH * NT +
+    return (sv_floats(stored) + (size_t)RH * NT * 2 + (size_t)TH * DP + (size_t)RH * NT +
             (stored ? (size_t)TH * PP : 0)) *
            sizeof(float);
   }
@@ -380,8 +385,8 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
   float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (a_n, c_n)
   float *sVc = smem;                              // TH x VP: vertical pass of c_n (STORED)
   float2 *sQP = reinterpret_cast<float2 *>(smem + G::sv_floats(STORED));  // RH x NT: (qbar, pbar)
-  float *sD = reinterpret_cast<float *>(sQP + RH * NT);  // TH x VP: D_n of the centre rows
-  float *sH = sD + TH * VP;                       // RH x NT: H
+  float *sD = reinterpret_cast<float *>(sQP + RH * NT);  // TH x DP: D_n of the centre rows
+  float *sH = sD + TH * G::DP;                    // RH x NT: H
   float *sP = sH + RH * NT;                       // TH x PP: plane tile (STORED)
   const int c = threadIdx.x;
 
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
       // c_n = qbar a_n [n < N] + pbar sqrt(n) a_{n-1}, in place of the second lane
       if (!LAST) ac.y = fmaf(qp.x, ac.x, ac.y);
       a[r] = ac.x;
-      if (r >= R && r < R + TH) sD[(r - R) * VP + c] = fmaf(sq, aold, -h * ac.x);
+      if (r >= R && r < R + TH) sD[(r - R) * G::DP + c] = fmaf(sq, aold, -h * ac.x);
       if (KIND == BF_SPATIAL_GAUSS) {
 #pragma unroll
         for (int y = 0; y < TH; ++y) {
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant
           AC[j] = s2;
         }
       }
-      const float *drow = sD + hy * VP + R + hx0;
+      const float *drow = sD + hy * G::DP + R + hx0;
 #pragma unroll
       for (int k = 0; k < KH; ++k) {
         const float D = drow[k];
