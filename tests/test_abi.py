@@ -273,3 +273,39 @@ def test_library_order_estimates_match_checker():
             assert cn == order.chernoff_order_lambertw(lam, eps)[0]
             assert po == order.poisson_order(lam, eps)
             assert po <= cn <= ch or eps > 0.05
+
+
+def test_variant_routing_host_side():
+    """The banded forward is variant 8: the calls without a workspace refuse it
+    when asked for it explicitly, the workspace query follows the tuning table
+    (a table entry of 8 makes a radius-9 forward take the banded path, so it
+    asks for a workspace), and the new entry points check their arguments
+    before any GPU work."""
+    L = _lib()
+    lib = L.lib()
+    from paper_1603_08109_gb300 import api
+    fake = ctypes.c_void_p(256)
+    out = ctypes.c_void_p(512)
+    p = ctypes.byref(L.make_params(L.GAUSS, 9, 3.0, 30.0, 40))
+    assert api.variant_count() == 9 and api.BANDED_VARIANT == 8
+    assert lib.bf_fast_forward_variant(fake, out, None, 64, 64, 64, p, 8, None) == 5
+    assert lib.bf_fast_forward_ws_variant(fake, out, None, 64, 64, 64, p, 9, None, 0, None) == 1
+    assert lib.bf_fast_forward_ws_variant(fake, out, None, 64, 64, 64, p, 8, None, 0, None) == 5
+    best, ms = ctypes.c_int(), ctypes.c_float()
+    assert lib.bf_autotune_ws(fake, out, 64, 64, 64, p, None, 0, 0, None, ctypes.byref(best),
+                              ctypes.byref(ms)) == 1
+    assert lib.bf_batch_variants(None, ctypes.byref(best), 1) == 1
+    sz = ctypes.c_size_t()
+    rb, ob = api.radius_bucket(9), api.order_bucket(40)
+    old = api.tuning_get(L.GAUSS, rb, ob)
+    try:
+        api.tuning_set(L.GAUSS, rb, ob, -1)
+        assert lib.bf_fast_forward_workspace(512, 512, p, ctypes.byref(sz)) == 0 and sz.value == 0
+        api.tuning_set(L.GAUSS, rb, ob, 8)
+        assert lib.bf_fast_forward_workspace(512, 512, p, ctypes.byref(sz)) == 0
+        assert sz.value >= 64 * 41 * 512 * 4
+        # without a workspace the table's banded entry is passed over (variant 5 runs)
+        assert lib.bf_fast_forward_ws_variant(fake, out, None, 64, 64, 64, p, 8, fake,
+                                              63 * 41 * 64 * 4, None) == 5
+    finally:
+        api.tuning_set(L.GAUSS, rb, ob, old)
