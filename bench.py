@@ -1211,7 +1211,9 @@ def main():
                "ms_per_image": ems, "images_timed": ne,
                "api": "paper_1603_08109_gb300.gpa_bilateral + backward",
                "copies": "per image: input and cotangent up, image and sigma_r gradients down; "
-                         "separate upload/download streams, double-buffered inputs"}
+                         "separate upload/download streams, double-buffered inputs",
+               "sigma_r": "a CUDA tensor with requires_grad, unchanged between images: the "
+                          "binding reads its host value once per tensor version"}
 
     if rank != 0:
         if dist:

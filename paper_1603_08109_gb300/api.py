@@ -552,7 +552,24 @@ def direct_backward(img, gout, kind: int, sigma_r: float, radius: int = 0, sigma
 
 # ------------------------------------------------------------------ autograd
 def _sigma_value(sigma_r) -> float:
-    return float(sigma_r.detach().item()) if isinstance(sigma_r, torch.Tensor) else float(sigma_r)
+    """sigma_r as the host float the library takes.  A tensor's value is read
+    (a device-to-host copy that waits for the stream) once per version: its
+    version counter changes with every in-place update through torch (an
+    optimizer step), so calls with an unchanged sigma_r tensor do not stall
+    the host on the device.  A tensor written behind torch's back (e.g. by a
+    raw kernel) needs a new tensor or a torch in-place op to be re-read."""
+    if not isinstance(sigma_r, torch.Tensor):
+        return float(sigma_r)
+    key = (sigma_r._version, sigma_r.data_ptr(), sigma_r.device)
+    cached = getattr(sigma_r, "_bf_sigma_host", None)
+    if cached is not None and cached[0] == key:
+        return cached[1]
+    v = float(sigma_r.detach().item())
+    try:
+        sigma_r._bf_sigma_host = (key, v)
+    except (AttributeError, RuntimeError):  # pragma: no cover - tensor subclasses without a dict
+        pass
+    return v
 
 
 class GPABilateral(torch.autograd.Function):
@@ -668,8 +685,11 @@ class BatchPlan:
     """Persistent batched forward over images of uneven sizes and parameters.
 
     specs: list of dicts with kind, radius, sigma_s, sigma_r, N (t_c optional).
-    The plan owns its workspace; run() enqueues one memset + one kernel,
-    graph() captures that pair into a CUDA graph for replay."""
+    Each image runs the variant the tuning table names for it when the plan is
+    created (variants()).  The plan owns its workspace; run() enqueues the
+    counters' memset, the persistent launches, the per-image launches and the
+    banded groups (the last two on side streams forked from the current one);
+    graph() captures that into a CUDA graph, replay() launches it."""
 
     def __init__(self, images, outs, specs, qaux=None):
         if not (len(images) == len(outs) == len(specs)) or not images:
