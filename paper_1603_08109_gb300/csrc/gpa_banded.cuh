@@ -182,20 +182,23 @@ __device__ __forceinline__ void band_hpass_tile(const BandArgs &A, int bx, int b
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;  // row lane, 16 columns seg
 
   // plane n of rows tyb.., columns tx - W.., into b; each warp copies four
-  // rows, its lanes consecutive columns (zeros outside the image / band)
+  // rows, its lanes consecutive columns.  The region's in-image columns are
+  // j in [j0, j1) of every row, the same for every channel; the cells outside
+  // the image or the band are zeroed once in both buffers here (no copy ever
+  // writes them), so each channel copies the in-image cells and nothing else.
+  const int j0 = max(0, R - tx), j1 = min(RC, A.W - tx + R);
+  for (int r = seg; r < kHT; r += kBandNT / 32) {
+    const bool rin = tyb + r < A.rows;
+    for (int j = lane; j < RC; j += 32)
+      if (!rin || j < j0 || j >= j1) buf0[r * P + j] = buf1[r * P + j] = 0.f;
+  }
   auto load = [&](int n, float *b) {
-    const float *src = A.ws + (long long)n * A.plane;
-    for (int r = seg; r < kHT; r += kBandNT / 32) {
-      const int orow = tyb + r;
-      const float *srow = src + (long long)orow * A.Wp;
+    // column j of the region is image column tx - W + j (>= 0 for j >= j0)
+    const float *src = A.ws + (long long)n * A.plane + (long long)tyb * A.Wp + (tx - R);
+    for (int r = seg; r < kHT && tyb + r < A.rows; r += kBandNT / 32) {
+      const float *srow = src + (long long)r * A.Wp;
       float *drow = b + r * P;
-      for (int j = lane; j < RC; j += 32) {
-        const int gx = tx - R + j;
-        if (orow < A.rows && gx >= 0 && gx < A.W)
-          bfk::cp_async4(drow + j, srow + gx);
-        else
-          drow[j] = 0.f;
-      }
+      for (int j = j0 + lane; j < j1; j += 32) bfk::cp_async4(drow + j, srow + j);
     }
   };
 
