@@ -310,6 +310,11 @@ bf_status bf_batch_plan_create(const bf_image_desc *descs, int count, bf_batch_p
       slots = 0;
       std::fill(gtaps.begin(), gtaps.end(), 0.f);
     };
+    // images of similar radii share a group: a launch's shared memory is sized
+    // for its largest radius, so small-radius groups keep more CTAs resident
+    std::stable_sort(large.begin(), large.end(), [&](int a, int b) {
+      return plan->descs[a].fc.ntaps_pad < plan->descs[b].fc.ntaps_pad;
+    });
     for (int i : large) {
       const BatchDesc &bd = plan->descs[i];
       const int H = bd.io.H, W = bd.io.W, Wp = (W + 3) / 4 * 4, N = bd.fc.N;
