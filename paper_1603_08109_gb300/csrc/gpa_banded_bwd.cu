@@ -261,22 +261,25 @@ __global__ void __launch_bounds__(kBHNT) band_bwd_hpass(const __grid_constant__ 
     X[i] = Y[i] = Z[i] = Dp[i] = RPp[i] = 0.f;
   }
 
+  // the region's in-image columns are j in [j0, j1) of every row; the cells
+  // outside the image or the band are zeroed once here (no copy writes them)
+  const int j0 = max(0, R - tx), j1 = min(RC, A.W - tx + R);
+  for (int pl = 0; pl < 3; ++pl)
+    for (int r = seg; r < kBHT; r += kBHNT / 32) {
+      const bool rin = tyb + r < A.rows;
+      for (int j = lane; j < RC; j += 32)
+        if (!rin || j < j0 || j >= j1) sm[pl * kBHT * P + r * P + j] = 0.f;
+    }
   for (int n = 0; n <= N; ++n) {
     // the channel's three column-filtered planes, rows tyb.., columns tx - W..
+    // (column j of the region is image column tx - W + j)
     for (int pl = 0; pl < 3; ++pl) {
-      const float *src = A.ws + (3LL * n + pl) * A.plane;
+      const float *src = A.ws + (3LL * n + pl) * A.plane + (long long)tyb * A.Wp + (tx - R);
       float *b = sm + pl * kBHT * P;
-      for (int r = seg; r < kBHT; r += kBHNT / 32) {
-        const int orow = tyb + r;
-        const float *srow = src + (long long)orow * A.Wp;
+      for (int r = seg; r < kBHT && tyb + r < A.rows; r += kBHNT / 32) {
+        const float *srow = src + (long long)r * A.Wp;
         float *drow = b + r * P;
-        for (int j = lane; j < RC; j += 32) {
-          const int gx = tx - R + j;
-          if (orow < A.rows && gx >= 0 && gx < A.W)
-            cp_async4(drow + j, srow + gx);
-          else
-            drow[j] = 0.f;
-        }
+        for (int j = j0 + lane; j < j1; j += 32) cp_async4(drow + j, srow + j);
       }
     }
     cp_async_commit();

@@ -214,21 +214,24 @@ __global__ void __launch_bounds__(kJHNT) joint_band_hpass(const __grid_constant_
     Q[i] = U[i] = 0.f;
   }
 
+  // the region's in-image columns are j in [j0, j1) of every row; the cells
+  // outside the image or the band are zeroed once here (no copy writes them)
+  const int j0 = max(0, R - tx), j1 = min(RC, A.W - tx + R);
+  for (int pl = 0; pl < 2; ++pl)
+    for (int r = seg; r < kJHT; r += kJHNT / 32) {
+      const bool rin = tyb + r < A.rows;
+      for (int j = lane; j < RC; j += 32)
+        if (!rin || j < j0 || j >= j1) sm[pl * kJHT * P + r * P + j] = 0.f;
+    }
   for (int n = 0; n < N; ++n) {
     for (int pl = 0; pl < 2; ++pl) {
-      const float *src = A.ws + (2LL * n + pl) * A.plane;
+      // column j of the region is image column tx - W + j
+      const float *src = A.ws + (2LL * n + pl) * A.plane + (long long)tyb * A.Wp + (tx - R);
       float *buf = sm + pl * kJHT * P;
-      for (int r = seg; r < kJHT; r += kJHNT / 32) {
-        const int orow = tyb + r;
-        const float *srow = src + (long long)orow * A.Wp;
+      for (int r = seg; r < kJHT && tyb + r < A.rows; r += kJHNT / 32) {
+        const float *srow = src + (long long)r * A.Wp;
         float *drow = buf + r * P;
-        for (int j = lane; j < RC; j += 32) {
-          const int gx = tx - R + j;
-          if (orow < A.rows && gx >= 0 && gx < A.W)
-            cp_async4(drow + j, srow + gx);
-          else
-            drow[j] = 0.f;
-        }
+        for (int j = j0 + lane; j < j1; j += 32) cp_async4(drow + j, srow + j);
       }
     }
     cp_async_commit();
