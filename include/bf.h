@@ -162,9 +162,9 @@ bf_status bf_fast_forward(const float *d_in, float *d_out, float *d_qaux,
  * W-row halos) into the workspace, the second filters those planes along the
  * rows (with the W-column halos) and forms P', Q' and f_GPA (Algorithm 2).
  * Results equal bf_fast_forward's up to float rounding.
- * bf_fast_forward_workspace: the workspace in bytes for bands tall enough
- *   to give each launch several waves of CTAs (at most 2 GiB unless 64 rows
- *   need more); 0 when the banded path is not chosen (bf_fast_forward_ws
+ * bf_fast_forward_workspace: the workspace in bytes for bands as tall as
+ *   the image, or as fit 8 GiB (64 rows at least; fewer, taller bands lose
+ *   fewer launch tails); 0 when the banded path is not chosen (bf_fast_forward_ws
  *   then runs the fused kernels, as bf_fast_forward).
  * bf_fast_forward_ws: d_workspace device memory, 16-byte aligned, owned by
  *   the caller, of ws_bytes >= 64 rows of N + 1 planes, i.e. 64 (N+1) Wp
