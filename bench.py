@@ -1292,7 +1292,7 @@ def main():
         cand.append(("gpa_fwd_fixed_kernel" if R in FIXED_RADII else
                      ("band_vpass+band_hpass" if nfws.value > 0 else "gpa_fwd_kernel"), mf, fo))
     if mb:
-        cand.append(("gpa_bwd_fixed_kernel" if R in FIXED_RADII else "gpa_bwd_kernel", mb, bo))
+        cand.append(("gpa_bwd_tmem_kernel" if R in FIXED_RADII else "gpa_bwd_kernel", mb, bo))
     name, ms, ops = max(cand, key=lambda c: c[1])
     achieved = ops / (ms * 1e-3) / 1e12
     traffic = None

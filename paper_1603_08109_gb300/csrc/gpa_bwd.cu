@@ -24,6 +24,7 @@
 #include "bf_internal.h"
 #include "gpa_fixed.cuh"  // cp.async helpers
 #include "gpa_tile.cuh"
+#include "tmem.cuh"
 
 namespace {
 
@@ -680,6 +681,342 @@ bf_status launch_bwd_fixed(const BwdArgs &A, cudaStream_t s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Backward for a compile-time radius with the region's per-pixel inputs in
+// tensor memory.  The kernel above re-reads H, qbar and pbar of every region
+// row from shared memory in each channel's vertical phase, about half of its
+// shared-memory traffic.  Here each column thread keeps them in its own TMEM
+// lane (three columns per region row: H, qbar H, pbar) and reads them with
+// tcgen05.ld.  The shared rows of the two passes alternate between two
+// buffers, so one block barrier per channel suffices: phase V of channel
+// n + 1 writes the buffer that phase H of channel n - 1 read, and every
+// thread has passed channel n's barrier after finishing that phase H.  The
+// seeds are formed as
+//   v = a_{n-1} / sqrt(n),  (a_n, c_n) = v (H, qbar H + n pbar),  D_n = n v - H a_n,
+// which is c_n = qbar a_n + pbar sqrt(n) a_{n-1} and D_n = sqrt(n) a_{n-1} - H a_n
+// with a_n = a_{n-1} H / sqrt(n) substituted (one multiply fewer per region
+// pixel and channel).  Channel 0, the one seed that needs qbar itself, is
+// formed while the region is loaded; H, qbar and pbar of the tile's own
+// pixels are kept in shared memory for the epilogue.
+template <int R, int NT, int TH>
+struct BwdTmemGeom {
+  using G = BwdFixedGeom<R, NT, TH>;
+  static constexpr int RH = G::RH;
+  static constexpr int CPR = 3;            // TMEM columns per region row
+  static constexpr int NG = (RH + 3) / 4;  // groups of four rows
+  static_assert(RH % 4 == 2, "the last group holds two rows");
+  static_assert(CPR * RH <= bft::kCols, "a thread's region rows fit its TMEM lane");
+  // one buffer: TH x VP (a_n, c_n) pairs of the vertical pass, TH x DP floats D_n
+  static constexpr size_t buf_floats = ((size_t)2 * TH * G::VP + (size_t)TH * G::DP + 3) / 4 * 4;
+  static constexpr int EP = NT + 4;  // epilogue rows: lanes (row, segment) meet 32 banks
+  static constexpr size_t smem_used = (2 * buf_floats + (size_t)3 * TH * EP) * sizeof(float);
+  // more than a fifth of an SM's shared memory: at most four CTAs, 4 x 128
+  // TMEM columns, reside on an SM, so an allocation never waits
+  static constexpr size_t kMinSmem = 47 * 1024;
+  static constexpr size_t smem_bytes = smem_used > kMinSmem ? smem_used : kMinSmem;
+};
+
+template <int KIND, int R, int NT, int TH>
+__global__ void __launch_bounds__(NT) gpa_bwd_tmem_kernel(const __grid_constant__ BwdArgs A) {
+  using G = BwdFixedGeom<R, NT, TH>;
+  using T = BwdTmemGeom<R, NT, TH>;
+  constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L, VP = G::VP;
+  constexpr int DP = G::DP, EP = T::EP, NG = T::NG;
+  static_assert(NT == 128, "one TMEM lane per thread: four warps on the four lane quadrants");
+  static_assert(NT % TH == 0 && TW >= KH, "tile geometry");
+  extern __shared__ __align__(16) float smem[];
+  __shared__ uint32_t s_tmem;
+  const bfi::FilterConsts &fc = A.fc;
+  const int N = fc.N;
+  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+  const int c = threadIdx.x;
+  float *sE = smem + 2 * T::buf_floats;  // 3 x TH x EP: H, qbar, pbar of the tile's pixels
+  auto sVb = [&](int b) { return reinterpret_cast<float2 *>(smem + b * T::buf_floats); };
+  auto sDb = [&](int b) { return smem + b * T::buf_floats + 2 * TH * VP; };
+
+  if (c < 32) bft::alloc(&s_tmem);
+  bft::fence_before_sync();
+  __syncthreads();
+  bft::fence_after_sync();
+  const uint32_t tl = s_tmem + ((uint32_t)(c & ~31) << 16);  // this warp's lane quadrant
+
+  // Vertical pass: row r's pair into the TH accumulators (Gaussian) or the
+  // running-sum inputs (box); vfinish forms the box sums and stores the rows.
+  float2 acc[TH];
+  float2 cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
+  auto vrow = [&](int r, float2 ac) {
+    if (KIND == BF_SPATIAL_GAUSS) {
+#pragma unroll
+      for (int y = 0; y < TH; ++y) {
+        if (r - y >= 0 && r - y < L) {
+          const float w = fc.taps[r - y];
+          acc[y] = __ffma2_rn(make_float2(w, w), ac, acc[y]);
+        }
+      }
+    } else {
+      cbox[KIND == BF_SPATIAL_BOX ? r : 0] = ac;
+    }
+  };
+  auto vfinish = [&](int b) {
+    if (KIND == BF_SPATIAL_BOX) {
+      float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < L; ++r) s2 = __fadd2_rn(s2, cbox[KIND == BF_SPATIAL_BOX ? r : 0]);
+      acc[0] = s2;
+#pragma unroll
+      for (int y = 1; y < TH; ++y) {
+        const float2 in = cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0];
+        const float2 out = cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
+        s2 = __fadd2_rn(s2, __fadd2_rn(in, make_float2(-out.x, -out.y)));
+        acc[y] = s2;
+      }
+    }
+    float2 *sV = sVb(b);
+#pragma unroll
+    for (int y = 0; y < TH; ++y) sV[y * VP + c] = acc[y];
+  };
+
+  float X[IPT][KH], Y[IPT][KH], Z[IPT][KH], Dp[IPT][KH];
+#pragma unroll
+  for (int m = 0; m < IPT; ++m)
+#pragma unroll
+    for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
+
+  // Phase H of channel n from buffer b: horizontal pass of (a_n, c_n) and the
+  // running sums.  FIRST (n = 0): no pbar term; LAST (n = N): no qbar term.
+  auto phase_h = [&](int n, int b, auto first_tag, auto last_tag) {
+    constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
+    const float sq = __fsqrt_rn((float)n);
+    const float2 *sV = sVb(b);
+    const float *sD = sDb(b);
+#pragma unroll
+    for (int m = 0; m < IPT; ++m) {
+      const int it = c + m * NT;
+      const int hy = it % TH, hx0 = (it / TH) * KH;
+      if (hx0 >= TW) continue;
+      const float2 *rv = sV + hy * VP + hx0;
+      float2 AC[KH];
+      if (KIND == BF_SPATIAL_GAUSS) {
+        float2 win[KH];
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+          AC[i] = make_float2(0.f, 0.f);
+          win[i] = rv[i];
+        }
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          const float w = fc.taps[t];
+#pragma unroll
+          for (int i = 0; i < KH; ++i) AC[i] = __ffma2_rn(make_float2(w, w), win[(t + i) % KH], AC[i]);
+          win[t % KH] = rv[t + KH];
+        }
+      } else {
+        float2 v[KH + 2 * R];
+#pragma unroll
+        for (int i = 0; i < KH + 2 * R; ++i) v[i] = rv[i];
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < L; ++i) s2 = __fadd2_rn(s2, v[i]);
+        AC[0] = s2;
+#pragma unroll
+        for (int j = 1; j < KH; ++j) {
+          s2 = __fadd2_rn(s2, __fadd2_rn(v[j + 2 * R], make_float2(-v[j - 1].x, -v[j - 1].y)));
+          AC[j] = s2;
+        }
+      }
+      const float *drow = sD + hy * DP + R + hx0;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const float D = drow[k];
+        if (!LAST) X[m][k] = fmaf(AC[k].x, D, X[m][k]);
+        Y[m][k] = fmaf(AC[k].y, D, Y[m][k]);
+        if (!FIRST) Z[m][k] = fmaf(AC[k].x * sq, Dp[m][k], Z[m][k]);
+        Dp[m][k] = D;
+      }
+    }
+  };
+
+  // Region inputs, four rows per group (all loads of a group issued before
+  // any is used; out-of-image pixels load the image origin and are masked):
+  // (H, qbar H, pbar) to TMEM, a_0 to registers, channel 0's vertical pass,
+  // and the first term of the sigma_r partial, sum g (out - t_c) over the
+  // tile's own pixels.
+  float a[RH];
+  float pf_go = 0.f;
+#pragma unroll
+  for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
+  {
+    const int gx = tx0 - R + c;
+    const bool colin = gx >= 0 && gx < A.W;
+    const bool colown = c >= R && c < R + TW && gx < A.W;
+    float *sD0 = sDb(0);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      float fv[4], gv[4], ov[4], qv[4];
+      bool in[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j, gy = ty0 - R + r;
+        in[j] = r < RH && colin && gy >= 0 && gy < A.H;
+        const long long o = in[j] ? (long long)gy * A.pitch + gx : 0;
+        fv[j] = __ldg(A.in + o);
+        gv[j] = __ldg(A.gout + o);
+        ov[j] = __ldg(A.out + o);
+        qv[j] = __ldg(A.qaux + o);
+      }
+      float t[12];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j;
+        if (r >= RH) {
+          t[3 * j] = t[3 * j + 1] = t[3 * j + 2] = 0.f;
+          continue;
+        }
+        float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
+        if (in[j]) {
+          const float d = fv[j] - fc.tc;
+          h = d * fc.inv_sr;
+          a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
+          const float go = gv[j] * (ov[j] - fc.tc);
+          // kernel-sum units: Q_u = Q' / qscale; approximate division (2 ulp)
+          const float iq = __fdividef(fc.qscale, qv[j]);
+          qb = -go * iq;
+          pb = gv[j] * fc.sr * iq;
+          if (r >= R && r < R + TH && colown) pf_go += go;
+        }
+        t[3 * j] = h;
+        t[3 * j + 1] = qb * h;
+        t[3 * j + 2] = pb;
+        a[r] = a0;
+        // channel 0: (a_0, qbar a_0) (no qbar term when N = 0), D_0 = -H a_0
+        const float2 ac = make_float2(a0, N > 0 ? qb * a0 : 0.f);
+        if (r >= R && r < R + TH) {
+          const int y = r - R;
+          sD0[y * DP + c] = -h * a0;
+          sE[y * EP + c] = h;
+          sE[(TH + y) * EP + c] = qb;
+          sE[(2 * TH + y) * EP + c] = pb;
+        }
+        vrow(r, ac);
+      }
+      if (4 * g + 4 <= RH) {
+        bft::st12(tl + 12 * g, t);
+      } else {
+        const float t6[6] = {t[0], t[1], t[2], t[3], t[4], t[5]};
+        bft::st6(tl + 12 * g, t6);
+      }
+    }
+  }
+  bft::wait_st();
+  vfinish(0);
+  __syncthreads();
+  using F = std::false_type;
+  using Tt = std::true_type;
+  if (N == 0) phase_h(0, 0, Tt{}, Tt{});
+  else phase_h(0, 0, Tt{}, F{});
+
+  // Channels 1 .. N: phase V from TMEM into buffer n & 1, one barrier, phase H.
+  auto channel = [&](int n, auto last_tag) {
+    constexpr bool LAST = decltype(last_tag)::value;
+    const int b = n & 1;
+    const float rs = __frsqrt_rn((float)n), nf = (float)n;
+    float *sD = sDb(b);
+#pragma unroll
+    for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      float t[12];
+      if (4 * g + 4 <= RH) {
+        bft::ld12(tl + 12 * g, t);
+      } else {
+        float t6[6];
+        bft::ld6(tl + 12 * g, t6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = t6[i];
+#pragma unroll
+        for (int i = 6; i < 12; ++i) t[i] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j;
+        if (r >= RH) break;
+        const float h = t[3 * j], qh = t[3 * j + 1], pb = t[3 * j + 2];
+        const float v = a[r] * rs;
+        const float k = LAST ? nf * pb : fmaf(nf, pb, qh);
+        const float2 ac = __fmul2_rn(make_float2(v, v), make_float2(h, k));
+        a[r] = ac.x;
+        if (r >= R && r < R + TH) sD[(r - R) * DP + c] = fmaf(nf, v, -h * ac.x);
+        vrow(r, ac);
+      }
+    }
+    vfinish(b);
+    __syncthreads();
+    phase_h(n, b, F{}, last_tag);
+  };
+  for (int n = 1; n < N; ++n) channel(n, F{});
+  if (N >= 1) channel(N, Tt{});
+
+  // every warp's TMEM reads are complete: free the columns
+  bft::fence_before_sync();
+  __syncthreads();
+  if (c < 32) {
+    bft::fence_after_sync();
+    bft::dealloc(s_tmem);
+  }
+
+  // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
+  double part = (double)pf_go * (double)fc.inv_sr;
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    const int it = c + m * NT;
+    const int hy = it % TH, hx0 = (it / TH) * KH;
+    const int gy = ty0 + hy;
+    if (hx0 >= TW || gy >= A.H) continue;
+    const long long ro = (long long)gy * A.pitch;
+    float pf = 0.f;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      const int gx = tx0 + hx0 + k;
+      if (hx0 + k < TW && gx < A.W) {
+        const int e = hy * EP + R + hx0 + k;
+        const float h = sE[e], qb = sE[TH * EP + e], pb = sE[2 * TH * EP + e];
+        const float hbar = fmaf(qb, X[m][k], fmaf(pb, Z[m][k], Y[m][k]));
+        A.gin[ro + gx] = hbar * fc.inv_sr;
+        pf = fmaf(-hbar, h, pf);
+      }
+    }
+    part += (double)pf * (double)fc.inv_sr;
+  }
+  if (A.partials) {
+    __shared__ double red[32];
+    const double t = block_sum(part, red);
+    if (threadIdx.x == 0) A.partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <int KIND, int R>
+bf_status launch_bwd_tmem_r(const BwdArgs &A, cudaStream_t s) {
+  using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
+  constexpr size_t smem = BwdTmemGeom<R, kBwdFixedNT, kBwdFixedTH>::smem_bytes;
+  auto kern = gpa_bwd_tmem_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH>;
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
+  if (st != BF_OK) return st;
+  dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
+  kern<<<grid, kBwdFixedNT, smem, s>>>(A);
+  return bfi::check_launch();
+}
+
+template <int KIND>
+bf_status launch_bwd_tmem(const BwdArgs &A, cudaStream_t s) {
+  switch (A.fc.R) {
+    case 3: return launch_bwd_tmem_r<KIND, 3>(A, s);
+    case 5: return launch_bwd_tmem_r<KIND, 5>(A, s);
+    case 9: return launch_bwd_tmem_r<KIND, 9>(A, s);
+    case 15: return launch_bwd_tmem_r<KIND, 15>(A, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
+}
+
 struct BwdVariant {
   int NT, TH;
 };
@@ -799,7 +1136,7 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   if (bwd_fixed_radius(A.fc.R)) {
     const bool g = A.fc.kind == BF_SPATIAL_GAUSS;
     if (abar) st = g ? launch_bwd_fixed<1, true>(A, s) : launch_bwd_fixed<0, true>(A, s);
-    else st = g ? launch_bwd_fixed<1, false>(A, s) : launch_bwd_fixed<0, false>(A, s);
+    else st = g ? launch_bwd_tmem<1>(A, s) : launch_bwd_tmem<0>(A, s);
     const int TWf = kBwdFixedNT - 2 * A.fc.R;
     ctas = ((width + TWf - 1) / TWf) * ((height + kBwdFixedTH - 1) / kBwdFixedTH);
   } else {
