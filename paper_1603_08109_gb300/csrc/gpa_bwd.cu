@@ -782,11 +782,14 @@ __global__ void __launch_bounds__(NT) gpa_bwd_tmem_kernel(const __grid_constant_
 #pragma unroll
     for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
 
-  // Phase H of channel n from buffer b: horizontal pass of (a_n, c_n) and the
-  // running sums.  FIRST (n = 0): no pbar term; LAST (n = N): no qbar term.
-  auto phase_h = [&](int n, int b, auto first_tag, auto last_tag) {
+  // Phase H of channel n from buffer b: horizontal pass of the carried pair
+  // and the running sums X += (w*ã_n) E_n, Y += (w*c̃_n) E_n,
+  // Z += (w*ã_n) E_{n-1} (times zf = sqrt(n) s_n / s_{n-1} on a channel that
+  // resets the scale; 1 otherwise).  FIRST (n = 0): no pbar term; LAST
+  // (n = N): no qbar term.
+  auto phase_h = [&](int b, auto first_tag, auto last_tag, auto zf_tag, float zf) {
     constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
-    const float sq = __fsqrt_rn((float)n);
+    constexpr bool ZF = decltype(zf_tag)::value;
     const float2 *sV = sVb(b);
     const float *sD = sDb(b);
 #pragma unroll
@@ -830,7 +833,7 @@ __global__ void __launch_bounds__(NT) gpa_bwd_tmem_kernel(const __grid_constant_
         const float D = drow[k];
         if (!LAST) X[m][k] = fmaf(AC[k].x, D, X[m][k]);
         Y[m][k] = fmaf(AC[k].y, D, Y[m][k]);
-        if (!FIRST) Z[m][k] = fmaf(AC[k].x * sq, Dp[m][k], Z[m][k]);
+        if (!FIRST) Z[m][k] = fmaf(ZF ? AC[k].x * zf : AC[k].x, Dp[m][k], Z[m][k]);
         Dp[m][k] = D;
       }
     }
@@ -912,14 +915,31 @@ __global__ void __launch_bounds__(NT) gpa_bwd_tmem_kernel(const __grid_constant_
   __syncthreads();
   using F = std::false_type;
   using Tt = std::true_type;
-  if (N == 0) phase_h(0, 0, Tt{}, Tt{});
-  else phase_h(0, 0, Tt{}, F{});
+  if (N == 0) phase_h(0, Tt{}, Tt{}, F{}, 1.f);
+  else phase_h(0, Tt{}, F{}, F{}, 1.f);
 
   // Channels 1 .. N: phase V from TMEM into buffer n & 1, one barrier, phase H.
-  auto channel = [&](int n, auto last_tag) {
-    constexpr bool LAST = decltype(last_tag)::value;
+  // The powers are carried unnormalised, a_n = s_n ã_n: within a run of
+  // channels s_n = s_{n-1} / sqrt(n), so that
+  //   ã_n = ã_{n-1} H,  c̃_n = c_n / s_n = ã_{n-1} (qbar H + n pbar),
+  //   E_n = s_n D_n = s_n^2 (n ã_{n-1} - H ã_n)
+  // (one packed multiply and one fma per region pixel); every kRenorm-th
+  // channel resets s_n = 1 (v = ã_{n-1} s_{n-1} / sqrt(n), (ã_n, c̃_n) =
+  // v (H, qbar H + n pbar), E_n = sqrt(n) s_{n-1} ã_{n-1} - H ã_n), so that
+  // ã_n <= n^{kRenorm/2} a_n stays far inside the float range.  The filtered
+  // pair enters the running sums with E_n in place of D_n, which also drops
+  // the sqrt(n) multiply of the Z sum.
+  constexpr int kRenorm = 8;
+  float s = 1.f;  // s_0 = 1: a[] holds a_0
+  auto channel = [&](int n, auto last_tag, auto renorm_tag) {
+    constexpr bool LAST = decltype(last_tag)::value, RENORM = decltype(renorm_tag)::value;
     const int b = n & 1;
     const float rs = __frsqrt_rn((float)n), nf = (float)n;
+    const float sp = s, rho = sp * rs;
+    s = RENORM ? 1.f : rho;
+    const float s2 = s * s;
+    const float ea = RENORM ? __fsqrt_rn(nf) * sp : 0.f;
+    const float zf = RENORM ? __fsqrt_rn(nf) / sp : 1.f;
     float *sD = sDb(b);
 #pragma unroll
     for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
@@ -941,20 +961,28 @@ __global__ void __launch_bounds__(NT) gpa_bwd_tmem_kernel(const __grid_constant_
         const int r = 4 * g + j;
         if (r >= RH) break;
         const float h = t[3 * j], qh = t[3 * j + 1], pb = t[3 * j + 2];
-        const float v = a[r] * rs;
+        const float ao = a[r];
+        const float v = RENORM ? ao * rho : ao;
         const float k = LAST ? nf * pb : fmaf(nf, pb, qh);
         const float2 ac = __fmul2_rn(make_float2(v, v), make_float2(h, k));
         a[r] = ac.x;
-        if (r >= R && r < R + TH) sD[(r - R) * DP + c] = fmaf(nf, v, -h * ac.x);
+        if (r >= R && r < R + TH)
+          sD[(r - R) * DP + c] = RENORM ? fmaf(ea, ao, -h * ac.x) : s2 * fmaf(nf, ao, -h * ac.x);
         vrow(r, ac);
       }
     }
     vfinish(b);
     __syncthreads();
-    phase_h(n, b, F{}, last_tag);
+    phase_h(b, F{}, last_tag, renorm_tag, zf);
   };
-  for (int n = 1; n < N; ++n) channel(n, F{});
-  if (N >= 1) channel(N, Tt{});
+  for (int n = 1; n < N; ++n) {
+    if (n % kRenorm) channel(n, F{}, F{});
+    else channel(n, F{}, Tt{});
+  }
+  if (N >= 1) {
+    if (N % kRenorm) channel(N, Tt{}, F{});
+    else channel(N, Tt{}, Tt{});
+  }
 
   // every warp's TMEM reads are complete: free the columns
   bft::fence_before_sync();

@@ -71,16 +71,19 @@ def test_stored_fixed_radius_backward(case):
     plane through shared memory and writes whole rows, the backward copies
     each channel's plane block into shared memory and filters only the
     adjoint seeds.  Images several tiles wide (238 and 110 output columns per
-    tile) and tall with ragged edges; gradients against recompute (the same
-    arithmetic: bitwise for the Gaussian, within the plane normalisation's
-    rounding for the box) and against the checker's exact derivatives."""
+    tile) and tall with ragged edges; gradients against recompute and against
+    the checker's exact derivatives.  The recompute kernel carries the powers
+    unnormalised (a_n = s_n ã_n) where the stored planes hold the normalised
+    a_n, so the two are different float32 roundings of the same sums: each
+    sigma_r gradient lies within about 2e-5 (relative) of the exact one, and
+    the two agree to 1e-4."""
     kind, r, ss, sr, N, (H, W) = case
     img = image(H, W, seed=H * 13 + W)
     g = synth.random_like((H, W), seed=H * W)
     gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
     gin2, gs2 = _fast_grads(img, g, kind, r, ss, sr, N, store=True)
     assert _rel(gin2, gin) <= 1e-5
-    assert abs(gs2 - gs) <= 1e-5 * abs(gs)
+    assert abs(gs2 - gs) <= 1e-4 * abs(gs)
     rgin, rgs = oracle.gpa_grad(img, spatial(kind, r, ss), sr, N, g.astype(np.float64))
     assert _rel(gin2, rgin) <= GIN_RTOL
     assert abs(gs2 - rgs) <= GSIG_RTOL * abs(rgs)
