@@ -245,3 +245,47 @@ def test_backward_full_size_512_sampled():
                               samples=(ys, xs))
     scale = np.abs(gin).max()
     assert np.abs(gin[ys, xs] - rgin).max() <= GIN_RTOL * scale
+
+
+@pytest.mark.parametrize("kind,r,ss,sr", [(bf.GAUSS, 3, 1.0, 35.0), (bf.GAUSS, 9, 3.0, 30.0),
+                                          (bf.GAUSS, 15, 5.0, 45.0), (bf.BOX, 9, 0.0, 40.0)],
+                         ids=lambda v: str(v))
+def test_compile_time_radius_backward_orders(kind, r, ss, sr):
+    """The compile-time-radius backward carries the powers unnormalised and
+    resets their scale every 8 channels: orders that end before, on and just
+    after a reset (and N = 1, 2, a long run at N = 200) against the checker's
+    exact derivatives, on a ragged image several tiles wide."""
+    H, W = 23, 251
+    img = image(H, W, seed=400 + r)
+    g = synth.random_like((H, W), seed=401 + r)
+    w = spatial(kind, r, ss)
+    for N in (1, 2, 7, 8, 9, 16, 17, 33, 200):
+        gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
+        rgin, rgs = oracle.gpa_grad(img, w, sr, N, g.astype(np.float64))
+        assert _rel(gin, rgin) <= GIN_RTOL, (N, _rel(gin, rgin))
+        assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs) + 1e-9, (N, gs, rgs)
+
+
+def test_backward_concurrent_streams_match_sequential():
+    """Backward launches on four streams at once (their CTAs share the SMs'
+    tensor memory) give bitwise the results of the same calls one after
+    another."""
+    S, N = 700, 40
+    imgs = [torch.from_numpy(image(S, S + 37 * k, seed=500 + k)).cuda() for k in range(4)]
+    gs = [torch.from_numpy(synth.random_like(tuple(x.shape), seed=510 + k)).cuda()
+          for k, x in enumerate(imgs)]
+    fw = [bf.gpa_forward(x, bf.GAUSS, 30.0, N, radius=9, sigma_s=3.0, return_q=True) for x in imgs]
+    seq = [bf.gpa_backward(x, o, q, g, bf.GAUSS, 30.0, N, radius=9, sigma_s=3.0)
+           for x, (o, q), g in zip(imgs, fw, gs)]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in imgs]
+    for _ in range(3):
+        par = [None] * len(imgs)
+        for k, (s, x, (o, q), g) in enumerate(zip(streams, imgs, fw, gs)):
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                par[k] = bf.gpa_backward(x, o, q, g, bf.GAUSS, 30.0, N, radius=9, sigma_s=3.0)
+        torch.cuda.synchronize()
+        for (a_gin, a_gs), (b_gin, b_gs) in zip(seq, par):
+            assert torch.equal(a_gin, b_gin)
+            assert float(a_gs.item()) == float(b_gs.item())
