@@ -254,7 +254,14 @@ def test_compile_time_radius_backward_orders(kind, r, ss, sr):
     """The compile-time-radius backward carries the powers unnormalised and
     resets their scale every 8 channels: orders that end before, on and just
     after a reset (and N = 1, 2, a long run at N = 200) against the checker's
-    exact derivatives, on a ragged image several tiles wide."""
+    exact derivatives, on a ragged image several tiles wide.
+
+    The sigma_r gradient is a sum over pixels of g (out - t_c) / sigma_r -
+    Hbar H / sigma_r whose terms can nearly cancel (at W = 9, N = 33 it is
+    1.6e-6 of the sum of their magnitudes S); float32 terms then fix it only
+    to a few units of 2^-24 S, so its bar is 1e-3 of the exact value plus
+    2^-24 S (the conditioning allowance of the forward's bar, from the terms'
+    magnitudes)."""
     H, W = 23, 251
     img = image(H, W, seed=400 + r)
     g = synth.random_like((H, W), seed=401 + r)
@@ -263,7 +270,9 @@ def test_compile_time_radius_backward_orders(kind, r, ss, sr):
         gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
         rgin, rgs = oracle.gpa_grad(img, w, sr, N, g.astype(np.float64))
         assert _rel(gin, rgin) <= GIN_RTOL, (N, _rel(gin, rgin))
-        assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs) + 1e-9, (N, gs, rgs)
+        ro = oracle.gpa_alg2(img, w, sr, N)
+        S = (np.abs(g * (ro - 128.0)).sum() + np.abs(rgin * (img - 128.0)).sum()) / sr
+        assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs) + 2.0 ** -24 * S, (N, gs, rgs, S)
 
 
 def test_backward_concurrent_streams_match_sequential():
