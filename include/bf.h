@@ -230,6 +230,13 @@ bf_status bf_fast_forward_stored(const float *d_in, float *d_out, float *d_qaux,
  * workspace (the query's value) also holds the qbar and pbar planes.  With a
  * workspace too small for 64 band rows, or none, the fused runtime-W kernel
  * runs instead where its tile fits (W up to about 52).
+ * For W in {3, 5, 9, 15} (without stored planes) the fused kernel keeps each
+ * thread's region inputs in tensor memory: every CTA of 128 threads
+ * allocates 128 TMEM columns for its lifetime and frees them before it
+ * exits, and at most four of its CTAs share an SM (4 x 128 = the SM's 512
+ * columns).  A kernel of another library that holds TMEM columns on the same
+ * SMs at the same time (another stream) makes an allocation wait until
+ * columns are free; it never fails.
  * BF_ERR_WORKSPACE if the workspace is missing or too small. */
 bf_status bf_fast_backward_workspace(int height, int width, const bf_params *p,
                                      size_t *bytes);
