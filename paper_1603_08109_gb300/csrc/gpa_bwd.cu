@@ -316,17 +316,17 @@ __global__ void __launch_bounds__(256) reduce_partials(const double *p, int n, d
 
 // ---------------------------------------------------------------------------
 // Backward specialised for a compile-time radius R (same math, same result
-// up to rounding).  Each column thread keeps its RH = TH + 2R power-image
-// values in registers; H and (qbar, pbar) of the region stay in shared
-// memory; taps are constant-bank FMA operands.  The adjoint gather is
-// re-associated: with D_n = d a_n / dH = sqrt(n) a_{n-1} - H a_n,
+// up to rounding): tiles of TH output rows and NT region columns, one column
+// thread per region column in the vertical phase (its RH = TH + 2R power-image
+// values in registers), taps as constant-bank FMA operands.  The adjoint
+// gather is re-associated: with D_n = d a_n / dH = sqrt(n) a_{n-1} - H a_n,
 //   Hbar = qbar * sum_{n<N} (w*a_n) D_n + sum_n (w*c_n) D_n
 //          + pbar * sum_{m>=1} sqrt(m) (w*a_m) D_{m-1},
 // so phase H keeps three running sums per output and reads only D_n, which
-// phase V computes for the centre rows.  The two filterings of a channel
-// (w*a_n and w*c_n) share every tap, so they run as one filtering of the pair
-// (a_n, c_n) with the packed two-lane FP32 instructions (each lane rounded
-// exactly as the scalar operation).
+// phase V computes for the centre rows.  Recomputing, the two filterings of a
+// channel (w*a_n and w*c_n) share every tap, so they run as one filtering of
+// the pair (a_n, c_n) with the packed two-lane FP32 instructions (each lane
+// rounded exactly as the scalar operation).
 template <int R, int NT, int TH>
 struct BwdFixedGeom {
   static constexpr int RH = TH + 2 * R;
@@ -352,342 +352,18 @@ struct BwdFixedGeom {
   // and the 4 segments of a warp (7 s = 0, 3, 2, 1 mod 4) meet 32 banks.
   static constexpr int DP = KH % 2 ? NT + 4 : VP;
   static_assert(DP >= NT, "D_n rows hold the region columns");
-  // Floats of the vertical-pass rows: (a_n, c_n) pairs, or c_n alone when
-  // w*a_n comes from stored planes (kept even so that sQP stays 8-byte aligned).
-  __host__ __device__ static constexpr size_t sv_floats(bool stored) {
-    return stored ? ((size_t)TH * VP + 1) / 2 * 2 : (size_t)2 * TH * VP;
-  }
-  // STORED: one TH x PP tile of the current channel's plane; PP = 1 (mod 32)
-  // keeps the phase-H reads conflict-free, PP >= TW + KH covers their columns.
-  static constexpr int PP = TW + KH <= 129 ? 129 : 161;
-  static_assert(PP >= TW + KH, "plane tile pitch");
-  static constexpr size_t smem_bytes(bool stored) {
-    return (sv_floats(stored) + (size_t)RH * NT * 2 + (size_t)TH * DP + (size_t)RH * NT +
-            (stored ? (size_t)TH * PP : 0)) *
-           sizeof(float);
-  }
 };
-
-// STORED: w*a_n is read from the planes of the stored-plane forward
-// (normalised, plane n at abar + n * plane_stride) instead of filtered here;
-// only c_n goes through the two passes.  The tile's TH x TW block of plane n
-// is copied (cp.async, consecutive threads on consecutive columns) into a
-// shared tile at the start of channel n, while phase V computes.
-template <int KIND, int R, int NT, int TH, bool STORED>
-__global__ void __launch_bounds__(NT) gpa_bwd_fixed_kernel(const __grid_constant__ BwdArgs A) {
-  using G = BwdFixedGeom<R, NT, TH>;
-  constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L, VP = G::VP;
-  constexpr int PP = G::PP;
-  static_assert(NT % TH == 0 && TW >= KH, "tile geometry");
-  extern __shared__ __align__(16) float smem[];
-  const bfi::FilterConsts &fc = A.fc;
-  const int N = fc.N;
-  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-  float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (a_n, c_n)
-  float *sVc = smem;                              // TH x VP: vertical pass of c_n (STORED)
-  float2 *sQP = reinterpret_cast<float2 *>(smem + G::sv_floats(STORED));  // RH x NT: (qbar, pbar)
-  float *sD = reinterpret_cast<float *>(sQP + RH * NT);  // TH x DP: D_n of the centre rows
-  float *sH = sD + TH * G::DP;                    // RH x NT: H
-  float *sP = sH + RH * NT;                       // TH x PP: plane tile (STORED)
-  const int c = threadIdx.x;
-
-  // Region inputs, in groups of rows whose loads are all issued before any
-  // is used (out-of-image pixels load the image origin and are masked).  The
-  // sigma_r partial's first term, sum g (out - t_c) over the tile's own
-  // pixels, is taken here while g and out are in registers.
-  float a[RH];
-  float pf_go = 0.f;
-  {
-    const int gx = tx0 - R + c;
-    const bool colin = gx >= 0 && gx < A.W;
-    const bool colown = c >= R && c < R + TW && gx < A.W;
-    constexpr int GR = 7;  // rows per load group
-#pragma unroll
-    for (int r0 = 0; r0 < RH; r0 += GR) {
-      float fv[GR], gv[GR], ov[GR], qv[GR];
-      bool in[GR];
-#pragma unroll
-      for (int j = 0; j < GR; ++j) {
-        const int r = r0 + j, gy = ty0 - R + r;
-        in[j] = r < RH && colin && gy >= 0 && gy < A.H;
-        const long long o = in[j] ? (long long)gy * A.pitch + gx : 0;
-        fv[j] = __ldg(A.in + o);
-        gv[j] = __ldg(A.gout + o);
-        ov[j] = __ldg(A.out + o);
-        qv[j] = __ldg(A.qaux + o);
-      }
-#pragma unroll
-      for (int j = 0; j < GR; ++j) {
-        const int r = r0 + j;
-        if (r >= RH) break;
-        float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
-        if (in[j]) {
-          const float d = fv[j] - fc.tc;
-          h = d * fc.inv_sr;
-          a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
-          const float go = gv[j] * (ov[j] - fc.tc);
-          // kernel-sum units: Q_u = Q' / qscale; approximate division (2 ulp)
-          const float iq = __fdividef(fc.qscale, qv[j]);
-          qb = -go * iq;
-          pb = gv[j] * fc.sr * iq;
-          if (r >= R && r < R + TH && colown) pf_go += go;
-        }
-        a[r] = a0;
-        sH[r * NT + c] = h;
-        sQP[r * NT + c] = make_float2(qb, pb);
-      }
-    }
-  }
-
-  float X[IPT][KH], Y[IPT][KH], Z[IPT][KH], Dp[IPT][KH];
-#pragma unroll
-  for (int m = 0; m < IPT; ++m)
-#pragma unroll
-    for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
-
-  // One channel n.  FIRST (n = 0): a_0 as loaded, no p-bar term; LAST (n = N):
-  // no q-bar term (the sums of Q' stop at N - 1).
-  const float inv_qscale = 1.0f / fc.qscale;  // plane units -> kernel-sum units
-  auto channel = [&](int n, auto first_tag, auto last_tag) {
-    constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
-    const float rs = FIRST ? 0.f : __frsqrt_rn((float)n);
-    const float sq = __fsqrt_rn((float)n);
-    __syncthreads();
-    if (STORED) {  // plane n's block (clamped at the image edges); the tile's
-                   // last reader was phase H of channel n - 1
-      const float *src = A.abar + (long long)n * A.plane_stride;
-      for (int e = c; e < TH * TW; e += NT) {
-        const int y = e / TW, j = e - y * TW;
-        bfk::cp_async4(sP + y * PP + j, src + (long long)min(ty0 + y, A.H - 1) * A.pitch +
-                                            min(tx0 + j, A.W - 1));
-      }
-      bfk::cp_async_commit();
-    }
-
-    // ---------------- phase V: advance, seeds c_n, D_n of centre rows, vertical pass of (a_n, c_n)
-    float2 acc[TH];
-#pragma unroll
-    for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
-    float2 cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
-#pragma unroll
-    for (int r = 0; r < RH; ++r) {
-      const float h = sH[r * NT + c];
-      const float aold = a[r];
-      const float2 qp = sQP[r * NT + c];
-      // (a_n, pbar sqrt(n) a_{n-1}) = a_{n-1} (H / sqrt(n), pbar sqrt(n))
-      float2 ac;
-      if (FIRST) {
-        ac = make_float2(aold, 0.f);
-      } else {
-        ac = __fmul2_rn(make_float2(aold, aold), __fmul2_rn(make_float2(h, qp.y), make_float2(rs, sq)));
-      }
-      // c_n = qbar a_n [n < N] + pbar sqrt(n) a_{n-1}, in place of the second lane
-      if (!LAST) ac.y = fmaf(qp.x, ac.x, ac.y);
-      a[r] = ac.x;
-      if (r >= R && r < R + TH) sD[(r - R) * G::DP + c] = fmaf(sq, aold, -h * ac.x);
-      if (KIND == BF_SPATIAL_GAUSS) {
-#pragma unroll
-        for (int y = 0; y < TH; ++y) {
-          if (r - y >= 0 && r - y < L) {
-            const float w = fc.taps[r - y];
-            if (STORED) acc[y].y = fmaf(w, ac.y, acc[y].y);  // the c_n lane alone
-            else acc[y] = __ffma2_rn(make_float2(w, w), ac, acc[y]);
-          }
-        }
-      } else {
-        cbox[KIND == BF_SPATIAL_BOX ? r : 0] = ac;
-      }
-    }
-    if (KIND == BF_SPATIAL_BOX && STORED) {
-      float s1 = 0.f;
-#pragma unroll
-      for (int r = 0; r < L; ++r) s1 += cbox[KIND == BF_SPATIAL_BOX ? r : 0].y;
-      acc[0].y = s1;
-#pragma unroll
-      for (int y = 1; y < TH; ++y) {
-        const float in = cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0].y;
-        const float out = cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0].y;
-        s1 += in + -out;
-        acc[y].y = s1;
-      }
-    } else if (KIND == BF_SPATIAL_BOX) {
-      float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int r = 0; r < L; ++r) s2 = __fadd2_rn(s2, cbox[KIND == BF_SPATIAL_BOX ? r : 0]);
-      acc[0] = s2;
-#pragma unroll
-      for (int y = 1; y < TH; ++y) {
-        const float2 in = cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0];
-        const float2 out = cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
-        s2 = __fadd2_rn(s2, __fadd2_rn(in, make_float2(-out.x, -out.y)));
-        acc[y] = s2;
-      }
-    }
-#pragma unroll
-    for (int y = 0; y < TH; ++y) {
-      if (STORED) sVc[y * VP + c] = acc[y].y;
-      else sV[y * VP + c] = acc[y];
-    }
-    if (STORED) bfk::cp_async_wait<0>();  // this thread's copies of plane n have landed
-    __syncthreads();
-
-    // ---------------- phase H: horizontal pass of (a_n, c_n) + running sums
-#pragma unroll
-    for (int m = 0; m < IPT; ++m) {
-      const int it = c + m * NT;
-      const int hy = it % TH, hx0 = (it / TH) * KH;
-      if (hx0 >= TW) continue;
-      const float2 *rv = sV + hy * VP + hx0;
-      float2 AC[KH];
-      if (STORED) {
-        const float *rc = sVc + hy * VP + hx0;
-        float Cc[KH];
-        if (KIND == BF_SPATIAL_GAUSS) {
-          float win[KH];
-#pragma unroll
-          for (int i = 0; i < KH; ++i) {
-            Cc[i] = 0.f;
-            win[i] = rc[i];
-          }
-#pragma unroll
-          for (int t = 0; t < L; ++t) {
-            const float w = fc.taps[t];
-#pragma unroll
-            for (int i = 0; i < KH; ++i) Cc[i] = fmaf(w, win[(t + i) % KH], Cc[i]);
-            win[t % KH] = rc[t + KH];
-          }
-        } else {
-          float v[KH + 2 * R];
-#pragma unroll
-          for (int i = 0; i < KH + 2 * R; ++i) v[i] = rc[i];
-          float s1 = 0.f;
-#pragma unroll
-          for (int i = 0; i < L; ++i) s1 += v[i];
-          Cc[0] = s1;
-#pragma unroll
-          for (int j = 1; j < KH; ++j) {
-            s1 += v[j + 2 * R] + -v[j - 1];
-            Cc[j] = s1;
-          }
-        }
-#pragma unroll
-        const float *pr = sP + hy * PP + hx0;
-#pragma unroll
-        for (int k = 0; k < KH; ++k) AC[k] = make_float2(pr[k] * inv_qscale, Cc[k]);
-      } else if (KIND == BF_SPATIAL_GAUSS) {
-        float2 win[KH];
-#pragma unroll
-        for (int i = 0; i < KH; ++i) {
-          AC[i] = make_float2(0.f, 0.f);
-          win[i] = rv[i];
-        }
-#pragma unroll
-        for (int t = 0; t < L; ++t) {
-          const float w = fc.taps[t];
-#pragma unroll
-          for (int i = 0; i < KH; ++i) AC[i] = __ffma2_rn(make_float2(w, w), win[(t + i) % KH], AC[i]);
-          win[t % KH] = rv[t + KH];
-        }
-      } else {
-        float2 v[KH + 2 * R];
-#pragma unroll
-        for (int i = 0; i < KH + 2 * R; ++i) v[i] = rv[i];
-        float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < L; ++i) s2 = __fadd2_rn(s2, v[i]);
-        AC[0] = s2;
-#pragma unroll
-        for (int j = 1; j < KH; ++j) {
-          s2 = __fadd2_rn(s2, __fadd2_rn(v[j + 2 * R], make_float2(-v[j - 1].x, -v[j - 1].y)));
-          AC[j] = s2;
-        }
-      }
-      const float *drow = sD + hy * G::DP + R + hx0;
-#pragma unroll
-      for (int k = 0; k < KH; ++k) {
-        const float D = drow[k];
-        if (!LAST) X[m][k] = fmaf(AC[k].x, D, X[m][k]);
-        Y[m][k] = fmaf(AC[k].y, D, Y[m][k]);
-        if (!FIRST) Z[m][k] = fmaf(AC[k].x * sq, Dp[m][k], Z[m][k]);
-        Dp[m][k] = D;
-      }
-    }
-  };
-  using F = std::false_type;
-  using T = std::true_type;
-  if (N == 0) {
-    channel(0, T{}, T{});
-  } else {
-    channel(0, T{}, F{});
-    for (int n = 1; n < N; ++n) channel(n, F{}, F{});
-    channel(N, F{}, T{});
-  }
-
-  // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
-  // sigma_r partial: sum over the tile's pixels of (g (out - t_c) - Hbar H) / sigma_r;
-  // each thread's terms summed in float, the CTA's in double
-  double part = (double)pf_go * (double)fc.inv_sr;
-#pragma unroll
-  for (int m = 0; m < IPT; ++m) {
-    const int it = c + m * NT;
-    const int hy = it % TH, hx0 = (it / TH) * KH;
-    const int gy = ty0 + hy;
-    if (hx0 >= TW || gy >= A.H) continue;
-    const long long ro = (long long)gy * A.pitch;
-    float pf = 0.f;
-#pragma unroll
-    for (int k = 0; k < KH; ++k) {
-      const int gx = tx0 + hx0 + k;
-      if (hx0 + k < TW && gx < A.W) {
-        const int ci = (hy + R) * NT + R + hx0 + k;
-        const float2 qp = sQP[ci];
-        const float hbar = fmaf(qp.x, X[m][k], fmaf(qp.y, Z[m][k], Y[m][k]));
-        A.gin[ro + gx] = hbar * fc.inv_sr;
-        pf = fmaf(-hbar, sH[ci], pf);
-      }
-    }
-    part += (double)pf * (double)fc.inv_sr;
-  }
-  if (A.partials) {
-    __shared__ double red[32];
-    const double t = block_sum(part, red);
-    if (threadIdx.x == 0) A.partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
-  }
-}
 
 constexpr int kBwdFixedNT = 128, kBwdFixedTH = 8;
 bool bwd_fixed_radius(int R) { return R == 3 || R == 5 || R == 9 || R == 15; }
 
-template <int KIND, int R, bool STORED>
-bf_status launch_bwd_fixed_r(const BwdArgs &A, cudaStream_t s) {
-  using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
-  constexpr size_t smem = G::smem_bytes(STORED);
-  auto kern = gpa_bwd_fixed_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH, STORED>;
-  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
-  if (st != BF_OK) return st;
-  dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
-  kern<<<grid, kBwdFixedNT, smem, s>>>(A);
-  return bfi::check_launch();
-}
-
-template <int KIND, bool STORED>
-bf_status launch_bwd_fixed(const BwdArgs &A, cudaStream_t s) {
-  switch (A.fc.R) {
-    case 3: return launch_bwd_fixed_r<KIND, 3, STORED>(A, s);
-    case 5: return launch_bwd_fixed_r<KIND, 5, STORED>(A, s);
-    case 9: return launch_bwd_fixed_r<KIND, 9, STORED>(A, s);
-    case 15: return launch_bwd_fixed_r<KIND, 15, STORED>(A, s);
-    default: return BF_ERR_UNSUPPORTED;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Backward for a compile-time radius with the region's per-pixel inputs in
-// tensor memory.  The kernel above re-reads H, qbar and pbar of every region
-// row from shared memory in each channel's vertical phase, about half of its
-// shared-memory traffic.  Here each column thread keeps them in its own TMEM
-// lane (three columns per region row: H, qbar H, pbar) and reads them with
-// tcgen05.ld.  The shared rows of the two passes alternate between two
+// tensor memory.  Every channel's vertical phase needs H, qbar and pbar of
+// all region rows; re-read from shared memory they were about half of the
+// kernel's shared-memory traffic.  Instead each column thread keeps them in
+// its own TMEM lane (three columns per region row: H, qbar H, pbar) and reads
+// them with tcgen05.ld.  The shared rows of the two passes alternate between two
 // buffers, so one block barrier per channel suffices: phase V of channel
 // n + 1 writes the buffer that phase H of channel n - 1 read, and every
 // thread has passed channel n's barrier after finishing that phase H.  The
@@ -1045,6 +721,346 @@ bf_status launch_bwd_tmem(const BwdArgs &A, cudaStream_t s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stored-plane backward for a compile-time radius, region inputs in tensor
+// memory.  w*a_n comes from plane n of the stored-plane forward (normalised),
+// so only the adjoint seeds c_n are filtered: half the recompute kernel's
+// filter work.  Layout as gpa_bwd_tmem_kernel (H, qbar H, pbar of each region
+// row in the thread's TMEM lane, two alternating shared buffers, one barrier
+// per channel); each buffer adds the tile's TH x TW block of plane n, copied
+// with cp.async (consecutive threads on consecutive columns, clamped at the
+// image edges) while phase V runs.  The powers stay normalised here
+// (v = a_{n-1} / sqrt(n), (a_n, c_n) = v (H, qbar H + n pbar),
+// D_n = n v - H a_n), so the plane values enter the sums unscaled.
+template <int R, int NT, int TH>
+struct BwdTmemStoredGeom {
+  using G = BwdFixedGeom<R, NT, TH>;
+  static constexpr int RH = G::RH;
+  static constexpr int NG = (RH + 3) / 4;  // groups of four rows
+  static_assert(RH % 4 == 2 && 3 * RH <= bft::kCols, "region rows in the TMEM lane");
+  // c_n rows, D_n rows and the plane block: pitch 4 (mod 32) floats, so that
+  // with 7-column segments the 8 rows (multiples of 4) and the 4 segments of
+  // a warp (7 s = 0, 3, 2, 1 mod 4) meet 32 banks
+  static constexpr int CP = G::KH % 2 ? NT + 4 : NT + 12;  // 8-column segments: wider rows
+  static_assert(CP >= (G::NSEG - 1) * G::KH + G::KH + 2 * R + 1, "phase-H windows stay in the row");
+  static constexpr size_t buf_floats = (size_t)3 * TH * CP;  // sVc, sD, sP
+  static constexpr int EP = NT + 4;
+  static constexpr size_t smem_used = (2 * buf_floats + (size_t)3 * TH * EP) * sizeof(float);
+  static constexpr size_t kMinSmem = 47 * 1024;  // at most four CTAs per SM
+  static constexpr size_t smem_bytes = smem_used > kMinSmem ? smem_used : kMinSmem;
+};
+
+template <int KIND, int R, int NT, int TH>
+__global__ void __launch_bounds__(NT) gpa_bwd_tmem_stored_kernel(const __grid_constant__ BwdArgs A) {
+  using G = BwdFixedGeom<R, NT, TH>;
+  using T = BwdTmemStoredGeom<R, NT, TH>;
+  constexpr int RH = G::RH, TW = G::TW, KH = G::KH, IPT = G::IPT, L = G::L;
+  constexpr int CP = T::CP, EP = T::EP, NG = T::NG;
+  static_assert(NT == 128, "one TMEM lane per thread: four warps on the four lane quadrants");
+  static_assert(NT % TH == 0 && TW >= KH, "tile geometry");
+  extern __shared__ __align__(16) float smem[];
+  __shared__ uint32_t s_tmem;
+  const bfi::FilterConsts &fc = A.fc;
+  const int N = fc.N;
+  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+  const int c = threadIdx.x;
+  float *sE = smem + 2 * T::buf_floats;  // 3 x TH x EP: H, qbar, pbar of the tile's pixels
+  auto sVb = [&](int b) { return smem + b * T::buf_floats; };
+  auto sDb = [&](int b) { return smem + b * T::buf_floats + TH * CP; };
+  auto sPb = [&](int b) { return smem + b * T::buf_floats + 2 * TH * CP; };
+  const float inv_qscale = 1.0f / fc.qscale;  // plane units -> kernel-sum units
+
+  // plane n's TH x TW block into buffer b (clamped at the image edges)
+  auto copy_plane = [&](int n, int b) {
+    const float *src = A.abar + (long long)n * A.plane_stride;
+    float *dst = sPb(b);
+    for (int e = c; e < TH * TW; e += NT) {
+      const int y = e / TW, j = e - y * TW;
+      bfk::cp_async4(dst + y * CP + j, src + (long long)min(ty0 + y, A.H - 1) * A.pitch +
+                                           min(tx0 + j, A.W - 1));
+    }
+    bfk::cp_async_commit();
+  };
+  copy_plane(0, 0);
+
+  if (c < 32) bft::alloc(&s_tmem);
+  bft::fence_before_sync();
+  __syncthreads();
+  bft::fence_after_sync();
+  const uint32_t tl = s_tmem + ((uint32_t)(c & ~31) << 16);  // this warp's lane quadrant
+
+  // vertical pass of c_n: row r's seed into the TH accumulators (Gaussian)
+  // or the running-sum inputs (box)
+  float acc[TH];
+  float cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
+  auto vrow = [&](int r, float cv) {
+    if (KIND == BF_SPATIAL_GAUSS) {
+#pragma unroll
+      for (int y = 0; y < TH; ++y)
+        if (r - y >= 0 && r - y < L) acc[y] = fmaf(fc.taps[r - y], cv, acc[y]);
+    } else {
+      cbox[KIND == BF_SPATIAL_BOX ? r : 0] = cv;
+    }
+  };
+  auto vfinish = [&](int b) {
+    if (KIND == BF_SPATIAL_BOX) {
+      float s1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < L; ++r) s1 += cbox[KIND == BF_SPATIAL_BOX ? r : 0];
+      acc[0] = s1;
+#pragma unroll
+      for (int y = 1; y < TH; ++y) {
+        s1 += cbox[KIND == BF_SPATIAL_BOX ? y + 2 * R : 0] + -cbox[KIND == BF_SPATIAL_BOX ? y - 1 : 0];
+        acc[y] = s1;
+      }
+    }
+    float *sV = sVb(b);
+#pragma unroll
+    for (int y = 0; y < TH; ++y) sV[y * CP + c] = acc[y];
+  };
+
+  float X[IPT][KH], Y[IPT][KH], Z[IPT][KH], Dp[IPT][KH];
+#pragma unroll
+  for (int m = 0; m < IPT; ++m)
+#pragma unroll
+    for (int k = 0; k < KH; ++k) X[m][k] = Y[m][k] = Z[m][k] = Dp[m][k] = 0.f;
+
+  // Phase H of channel n from buffer b: horizontal pass of c_n, the plane's
+  // w*a_n, and the running sums X += (w*a_n) D_n [n<N], Y += (w*c_n) D_n,
+  // Z += sqrt(n) (w*a_n) D_{n-1} [n>=1].
+  auto phase_h = [&](int n, int b, auto first_tag, auto last_tag) {
+    constexpr bool FIRST = decltype(first_tag)::value, LAST = decltype(last_tag)::value;
+    const float sq = __fsqrt_rn((float)n);
+    const float *sV = sVb(b), *sD = sDb(b), *sP = sPb(b);
+#pragma unroll
+    for (int m = 0; m < IPT; ++m) {
+      const int it = c + m * NT;
+      const int hy = it % TH, hx0 = (it / TH) * KH;
+      if (hx0 >= TW) continue;
+      const float *rc = sV + hy * CP + hx0;
+      float Cc[KH];
+      if (KIND == BF_SPATIAL_GAUSS) {
+        float win[KH];
+#pragma unroll
+        for (int i = 0; i < KH; ++i) {
+          Cc[i] = 0.f;
+          win[i] = rc[i];
+        }
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          const float w = fc.taps[t];
+#pragma unroll
+          for (int i = 0; i < KH; ++i) Cc[i] = fmaf(w, win[(t + i) % KH], Cc[i]);
+          win[t % KH] = rc[t + KH];
+        }
+      } else {
+        float v[KH + 2 * R];
+#pragma unroll
+        for (int i = 0; i < KH + 2 * R; ++i) v[i] = rc[i];
+        float s1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) s1 += v[i];
+        Cc[0] = s1;
+#pragma unroll
+        for (int j = 1; j < KH; ++j) {
+          s1 += v[j + 2 * R] + -v[j - 1];
+          Cc[j] = s1;
+        }
+      }
+      const float *drow = sD + hy * CP + R + hx0;
+      const float *prow = sP + hy * CP + hx0;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const float D = drow[k];
+        const float P = prow[k] * inv_qscale;
+        if (!LAST) X[m][k] = fmaf(P, D, X[m][k]);
+        Y[m][k] = fmaf(Cc[k], D, Y[m][k]);
+        if (!FIRST) Z[m][k] = fmaf(P * sq, Dp[m][k], Z[m][k]);
+        Dp[m][k] = D;
+      }
+    }
+  };
+
+  // Region inputs, four rows per group: (H, qbar H, pbar) to TMEM, a_0 to
+  // registers, channel 0's seeds (c_0 = qbar a_0; none when N = 0) through the
+  // vertical pass, D_0 = -H a_0, and the first term of the sigma_r partial.
+  float a[RH];
+  float pf_go = 0.f;
+#pragma unroll
+  for (int y = 0; y < TH; ++y) acc[y] = 0.f;
+  {
+    const int gx = tx0 - R + c;
+    const bool colin = gx >= 0 && gx < A.W;
+    const bool colown = c >= R && c < R + TW && gx < A.W;
+    float *sD0 = sDb(0);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      float fv[4], gv[4], ov[4], qv[4];
+      bool in[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j, gy = ty0 - R + r;
+        in[j] = r < RH && colin && gy >= 0 && gy < A.H;
+        const long long o = in[j] ? (long long)gy * A.pitch + gx : 0;
+        fv[j] = __ldg(A.in + o);
+        gv[j] = __ldg(A.gout + o);
+        ov[j] = __ldg(A.out + o);
+        qv[j] = __ldg(A.qaux + o);
+      }
+      float t[12];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j;
+        if (r >= RH) {
+          t[3 * j] = t[3 * j + 1] = t[3 * j + 2] = 0.f;
+          continue;
+        }
+        float h = 0.f, a0 = 0.f, qb = 0.f, pb = 0.f;
+        if (in[j]) {
+          const float d = fv[j] - fc.tc;
+          h = d * fc.inv_sr;
+          a0 = exp2f(d * d * fc.e2c);  // exp(-H^2/2), as in the forward
+          const float go = gv[j] * (ov[j] - fc.tc);
+          const float iq = __fdividef(fc.qscale, qv[j]);  // kernel-sum units (2 ulp)
+          qb = -go * iq;
+          pb = gv[j] * fc.sr * iq;
+          if (r >= R && r < R + TH && colown) pf_go += go;
+        }
+        t[3 * j] = h;
+        t[3 * j + 1] = qb * h;
+        t[3 * j + 2] = pb;
+        a[r] = a0;
+        if (r >= R && r < R + TH) {
+          const int y = r - R;
+          sD0[y * CP + c] = -h * a0;
+          sE[y * EP + c] = h;
+          sE[(TH + y) * EP + c] = qb;
+          sE[(2 * TH + y) * EP + c] = pb;
+        }
+        vrow(r, N > 0 ? qb * a0 : 0.f);
+      }
+      if (4 * g + 4 <= RH) {
+        bft::st12(tl + 12 * g, t);
+      } else {
+        const float t6[6] = {t[0], t[1], t[2], t[3], t[4], t[5]};
+        bft::st6(tl + 12 * g, t6);
+      }
+    }
+  }
+  bft::wait_st();
+  vfinish(0);
+  bfk::cp_async_wait<0>();  // this thread's copies of plane 0 have landed
+  __syncthreads();
+  using F = std::false_type;
+  using Tt = std::true_type;
+  if (N == 0) phase_h(0, 0, Tt{}, Tt{});
+  else phase_h(0, 0, Tt{}, F{});
+
+  // Channels 1 .. N: plane n's copy, phase V from TMEM into buffer n & 1, one
+  // barrier, phase H.
+  auto channel = [&](int n, auto last_tag) {
+    constexpr bool LAST = decltype(last_tag)::value;
+    const int b = n & 1;
+    copy_plane(n, b);
+    const float rs = __frsqrt_rn((float)n), nf = (float)n;
+    float *sD = sDb(b);
+#pragma unroll
+    for (int y = 0; y < TH; ++y) acc[y] = 0.f;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      float t[12];
+      if (4 * g + 4 <= RH) {
+        bft::ld12(tl + 12 * g, t);
+      } else {
+        float t6[6];
+        bft::ld6(tl + 12 * g, t6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = t6[i];
+#pragma unroll
+        for (int i = 6; i < 12; ++i) t[i] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j;
+        if (r >= RH) break;
+        const float h = t[3 * j], qh = t[3 * j + 1], pb = t[3 * j + 2];
+        const float v = a[r] * rs;
+        const float k = LAST ? nf * pb : fmaf(nf, pb, qh);
+        const float2 ac = __fmul2_rn(make_float2(v, v), make_float2(h, k));
+        a[r] = ac.x;
+        if (r >= R && r < R + TH) sD[(r - R) * CP + c] = fmaf(nf, v, -h * ac.x);
+        vrow(r, ac.y);
+      }
+    }
+    vfinish(b);
+    bfk::cp_async_wait<0>();  // this thread's copies of plane n have landed
+    __syncthreads();
+    phase_h(n, b, F{}, last_tag);
+  };
+  for (int n = 1; n < N; ++n) channel(n, F{});
+  if (N >= 1) channel(N, Tt{});
+
+  // every warp's TMEM reads are complete: free the columns
+  bft::fence_before_sync();
+  __syncthreads();
+  if (c < 32) {
+    bft::fence_after_sync();
+    bft::dealloc(s_tmem);
+  }
+
+  // ---- epilogue: Hbar = qbar X + Y + pbar Z; d in = Hbar / sigma_r; sigma_r partials
+  double part = (double)pf_go * (double)fc.inv_sr;
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    const int it = c + m * NT;
+    const int hy = it % TH, hx0 = (it / TH) * KH;
+    const int gy = ty0 + hy;
+    if (hx0 >= TW || gy >= A.H) continue;
+    const long long ro = (long long)gy * A.pitch;
+    float pf = 0.f;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      const int gx = tx0 + hx0 + k;
+      if (hx0 + k < TW && gx < A.W) {
+        const int e = hy * EP + R + hx0 + k;
+        const float h = sE[e], qb = sE[TH * EP + e], pb = sE[2 * TH * EP + e];
+        const float hbar = fmaf(qb, X[m][k], fmaf(pb, Z[m][k], Y[m][k]));
+        A.gin[ro + gx] = hbar * fc.inv_sr;
+        pf = fmaf(-hbar, h, pf);
+      }
+    }
+    part += (double)pf * (double)fc.inv_sr;
+  }
+  if (A.partials) {
+    __shared__ double red[32];
+    const double t = block_sum(part, red);
+    if (threadIdx.x == 0) A.partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <int KIND, int R>
+bf_status launch_bwd_tmem_stored_r(const BwdArgs &A, cudaStream_t s) {
+  using G = BwdFixedGeom<R, kBwdFixedNT, kBwdFixedTH>;
+  constexpr size_t smem = BwdTmemStoredGeom<R, kBwdFixedNT, kBwdFixedTH>::smem_bytes;
+  auto kern = gpa_bwd_tmem_stored_kernel<KIND, R, kBwdFixedNT, kBwdFixedTH>;
+  const bf_status st = bfi::ensure_smem(reinterpret_cast<const void *>(kern), smem);
+  if (st != BF_OK) return st;
+  dim3 grid((A.W + G::TW - 1) / G::TW, (A.H + kBwdFixedTH - 1) / kBwdFixedTH);
+  kern<<<grid, kBwdFixedNT, smem, s>>>(A);
+  return bfi::check_launch();
+}
+
+template <int KIND>
+bf_status launch_bwd_tmem_stored(const BwdArgs &A, cudaStream_t s) {
+  switch (A.fc.R) {
+    case 3: return launch_bwd_tmem_stored_r<KIND, 3>(A, s);
+    case 5: return launch_bwd_tmem_stored_r<KIND, 5>(A, s);
+    case 9: return launch_bwd_tmem_stored_r<KIND, 9>(A, s);
+    case 15: return launch_bwd_tmem_stored_r<KIND, 15>(A, s);
+    default: return BF_ERR_UNSUPPORTED;
+  }
+}
+
 struct BwdVariant {
   int NT, TH;
 };
@@ -1163,7 +1179,7 @@ bf_status backward_impl(const float *in, const float *out, const float *qaux, co
   int ctas = 0;
   if (bwd_fixed_radius(A.fc.R)) {
     const bool g = A.fc.kind == BF_SPATIAL_GAUSS;
-    if (abar) st = g ? launch_bwd_fixed<1, true>(A, s) : launch_bwd_fixed<0, true>(A, s);
+    if (abar) st = g ? launch_bwd_tmem_stored<1>(A, s) : launch_bwd_tmem_stored<0>(A, s);
     else st = g ? launch_bwd_tmem<1>(A, s) : launch_bwd_tmem<0>(A, s);
     const int TWf = kBwdFixedNT - 2 * A.fc.R;
     ctas = ((width + TWf - 1) / TWf) * ((height + kBwdFixedTH - 1) / kBwdFixedTH);
