@@ -253,8 +253,9 @@ def test_backward_full_size_512_sampled():
 def test_compile_time_radius_backward_orders(kind, r, ss, sr):
     """The compile-time-radius backward carries the powers unnormalised and
     resets their scale every 8 channels: orders that end before, on and just
-    after a reset (and N = 1, 2, a long run at N = 200) against the checker's
-    exact derivatives, on a ragged image several tiles wide.
+    after a reset (and N = 1, 2, a long run at N = 200, the largest order at
+    W = 3, where the scale s_n is smallest) against the checker's exact
+    derivatives, on a ragged image several tiles wide.
 
     The sigma_r gradient is a sum over pixels of g (out - t_c) / sigma_r -
     Hbar H / sigma_r whose terms can nearly cancel (at W = 9, N = 33 it is
@@ -266,11 +267,12 @@ def test_compile_time_radius_backward_orders(kind, r, ss, sr):
     img = image(H, W, seed=400 + r)
     g = synth.random_like((H, W), seed=401 + r)
     w = spatial(kind, r, ss)
-    for N in (1, 2, 7, 8, 9, 16, 17, 33, 200):
+    orders = (1, 2, 7, 8, 9, 16, 17, 33, 200) + ((1024,) if r == 3 else ())  # BF_MAX_ORDER
+    for N in orders:
         gin, gs = _fast_grads(img, g, kind, r, ss, sr, N)
         rgin, rgs = oracle.gpa_grad(img, w, sr, N, g.astype(np.float64))
         assert _rel(gin, rgin) <= GIN_RTOL, (N, _rel(gin, rgin))
-        ro = oracle.gpa_alg2(img, w, sr, N)
+        ro = oracle.gpa_definition(img, w, sr, N)  # eq. GPA: Algorithm 2's output, any N
         S = (np.abs(g * (ro - 128.0)).sum() + np.abs(rgin * (img - 128.0)).sum()) / sr
         assert abs(gs - rgs) <= GSIG_RTOL * abs(rgs) + 2.0 ** -24 * S, (N, gs, rgs, S)
 
