@@ -78,10 +78,16 @@ __device__ __forceinline__ void prefetch_region(const TileIO &io, int ty0, int t
   }
 }
 
-template <int KIND, int R, int NT, int TH, bool STORE>
+// DB: sV / sC are pairs of buffers (sV1 / sC1 the second) that alternate
+// between channels, so one block barrier per channel suffices (phase V of
+// channel n + 1 writes the pair that phase H of channel n - 1 read, and every
+// thread has passed channel n's barrier after finishing that phase H).
+template <int KIND, int R, int NT, int TH, bool STORE, bool DB = false>
 __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::FilterConsts &fc,
                                                    const float2 *tap2, int ty0, int tx0, float *sH,
-                                                   float *sV, float *sC, const float2 *sRS) {
+                                                   float *sV0, float *sC0, const float2 *sRS,
+                                                   float *sV1 = nullptr, float *sC1 = nullptr) {
+  static_assert(!(DB && STORE), "the stored planes are staged in the single pair");
   using G = FixedGeom<R, NT, TH>;
   constexpr int RH = G::RH, TW = G::TW, KH = G::KH, L = G::L, VP = G::VP;
   static_assert(TW >= KH, "tile too narrow for this radius");
@@ -112,13 +118,15 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
   float Q[KH], P[KH], ap[KH];
 #pragma unroll
   for (int k = 0; k < KH; ++k) Q[k] = P[k] = ap[k] = 0.f;
-  const float *vrow = sV + hy * VP + hx0;
-  const float *crow = sC + hy * VP + R + hx0;
 
   for (int n = 0; n <= N; ++n) {
     const float2 rsq = sRS[n];  // (1/sqrt(n), sqrt(n)), correctly rounded
     const float rs = rsq.x, sq = rsq.y;
-    __syncthreads();  // phase H of the previous channel (or tile) is done with sV / sC
+    float *sV = DB && (n & 1) ? sV1 : sV0;
+    float *sC = DB && (n & 1) ? sC1 : sC0;
+    const float *vrow = sV + hy * VP + hx0;
+    const float *crow = sC + hy * VP + R + hx0;
+    if (!DB) __syncthreads();  // phase H of the previous channel (or tile) is done with sV / sC
 
     // ---------------- phase V (registers): advance, centre copy, vertical pass
     if (n > 0) {
@@ -227,8 +235,11 @@ __device__ __forceinline__ void gpa_fwd_tile_fixed(const TileIO &io, const bfi::
     }
   }
 
-  // ---- epilogue: f_GPA = t_c + sigma_r P'/Q', staged in sV / sC, stored row-wise
-  __syncthreads();  // every thread is done reading sV / sC
+  // ---- epilogue: f_GPA = t_c + sigma_r P'/Q', staged in sV / sC (DB: the
+  // pair channel N's phase H does not read), stored row-wise
+  float *sV = DB && ((N + 1) & 1) ? sV1 : sV0;
+  float *sC = DB && ((N + 1) & 1) ? sC1 : sC0;
+  if (!DB) __syncthreads();  // every thread is done reading sV / sC
   if (hact) {
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
@@ -286,6 +297,49 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
     gpa_fwd_tile_fixed<KIND, R, NT, TH, STORE>(io, fc, tap2, (t / ntx) * TH, (t % ntx) * G::TW, cur,
                                                sV, sC, sRS);
     buf ^= 1;
+  }
+}
+
+// Without stored planes: two alternating pairs of phase rows (one block
+// barrier per channel, see gpa_fwd_tile_fixed) and a single region buffer,
+// filled at the start of each tile (the second pair takes the shared memory
+// of the region copy that would otherwise be in flight).
+template <int R, int NT, int TH>
+struct FixedDbGeom {
+  using G = FixedGeom<R, NT, TH>;
+  static constexpr size_t smem_bytes(int N) {
+    return ((size_t)4 * TH * G::VP + (size_t)G::RH * NT) * sizeof(float) +
+           (size_t)(N + 1) * sizeof(float2);
+  }
+};
+
+template <int KIND, int R, int NT, int TH>
+__device__ __forceinline__ void gpa_fwd_fixed_persistent_db(const TileIO &io,
+                                                            const bfi::FilterConsts &fc,
+                                                            const float2 *tap2, float *smem) {
+  using G = FixedGeom<R, NT, TH>;
+  float *sV0 = smem;
+  float *sC0 = sV0 + TH * G::VP;
+  float *sV1 = sC0 + TH * G::VP;
+  float *sC1 = sV1 + TH * G::VP;
+  float *sF = sC1 + TH * G::VP;
+  float2 *sRS = reinterpret_cast<float2 *>(sF + G::RH * NT);
+  const int ntx = (io.W + G::TW - 1) / G::TW;
+  const int nty = (io.H + TH - 1) / TH;
+  const int ntiles = ntx * nty;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  // channel constants 1/sqrt(n), sqrt(n), correctly rounded, once per CTA
+  for (int n = threadIdx.x; n <= fc.N; n += NT)
+    sRS[n] = make_float2(n > 0 ? __frsqrt_rn((float)n) : 0.f, __fsqrt_rn((float)n));
+  for (; t < ntiles; t += gridDim.x) {
+    const int ty0 = (t / ntx) * TH, tx0 = (t % ntx) * G::TW;
+    prefetch_region<R, NT, TH>(io, ty0, tx0, sF);  // each thread its own column
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();  // sRS written; the previous tile's epilogue is done with the pairs
+    gpa_fwd_tile_fixed<KIND, R, NT, TH, false, true>(io, fc, tap2, ty0, tx0, sF, sV0, sC0, sRS,
+                                                     sV1, sC1);
   }
 }
 
