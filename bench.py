@@ -1289,7 +1289,7 @@ def main():
     bo = bwd_ops_per_pixel(kind, R, N) * px
     cand = []
     if mf:
-        cand.append(("gpa_fwd_fixed_kernel" if R in FIXED_RADII else
+        cand.append(("gpa_fwd_fixed_db_kernel" if R in FIXED_RADII else
                      ("band_vpass+band_hpass" if nfws.value > 0 else "gpa_fwd_kernel"), mf, fo))
     if mb:
         cand.append(("gpa_bwd_tmem_kernel" if R in FIXED_RADII else "gpa_bwd_kernel", mb, bo))
