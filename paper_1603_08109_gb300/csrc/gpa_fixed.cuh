@@ -300,17 +300,23 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent(const TileIO &io,
   }
 }
 
-// Without stored planes: two alternating pairs of phase rows (one block
-// barrier per channel, see gpa_fwd_tile_fixed) and a single region buffer,
-// filled at the start of each tile (the second pair takes the shared memory
-// of the region copy that would otherwise be in flight).
+// Without stored planes: a single region buffer, filled at the start of
+// each tile, and two alternating pairs of phase rows (one block barrier per
+// channel, see gpa_fwd_tile_fixed), the second pair taking the shared memory
+// of the region copy that would otherwise be in flight.  Where two such
+// pairs keep the CTA from sharing an SM with a second one (W = 15: 46 region
+// rows), a single pair and two barriers per channel: 2 CTAs per SM instead
+// of 1.
 template <int R, int NT, int TH>
 struct FixedDbGeom {
   using G = FixedGeom<R, NT, TH>;
-  static constexpr size_t smem_bytes(int N) {
-    return ((size_t)4 * TH * G::VP + (size_t)G::RH * NT) * sizeof(float) +
+  static constexpr size_t bytes(int pairs, int N) {
+    return ((size_t)2 * pairs * TH * G::VP + (size_t)G::RH * NT) * sizeof(float) +
            (size_t)(N + 1) * sizeof(float2);
   }
+  // two CTAs (and their 1 KB reserves) in an SM's 228 KB at every order
+  static constexpr bool DB = 2 * (bytes(2, BF_MAX_ORDER) + 1024) <= 228 * 1024;
+  static constexpr size_t smem_bytes(int N) { return bytes(DB ? 2 : 1, N); }
 };
 
 template <int KIND, int R, int NT, int TH>
@@ -318,11 +324,12 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent_db(const TileIO &io,
                                                             const bfi::FilterConsts &fc,
                                                             const float2 *tap2, float *smem) {
   using G = FixedGeom<R, NT, TH>;
+  constexpr bool DB = FixedDbGeom<R, NT, TH>::DB;
   float *sV0 = smem;
   float *sC0 = sV0 + TH * G::VP;
-  float *sV1 = sC0 + TH * G::VP;
-  float *sC1 = sV1 + TH * G::VP;
-  float *sF = sC1 + TH * G::VP;
+  float *sV1 = DB ? sC0 + TH * G::VP : nullptr;
+  float *sC1 = DB ? sV1 + TH * G::VP : nullptr;
+  float *sF = sC0 + (DB ? 3 : 1) * TH * G::VP;
   float2 *sRS = reinterpret_cast<float2 *>(sF + G::RH * NT);
   const int ntx = (io.W + G::TW - 1) / G::TW;
   const int nty = (io.H + TH - 1) / TH;
@@ -338,8 +345,8 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent_db(const TileIO &io,
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();  // sRS written; the previous tile's epilogue is done with the pairs
-    gpa_fwd_tile_fixed<KIND, R, NT, TH, false, true>(io, fc, tap2, ty0, tx0, sF, sV0, sC0, sRS,
-                                                     sV1, sC1);
+    gpa_fwd_tile_fixed<KIND, R, NT, TH, false, DB>(io, fc, tap2, ty0, tx0, sF, sV0, sC0, sRS,
+                                                   sV1, sC1);
   }
 }
 
