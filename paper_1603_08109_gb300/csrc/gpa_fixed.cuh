@@ -316,15 +316,23 @@ struct FixedDbGeom {
   }
   // two CTAs (and their 1 KB reserves) in an SM's 228 KB at every order
   static constexpr bool DB = 2 * (bytes(2, BF_MAX_ORDER) + 1024) <= 228 * 1024;
-  static constexpr size_t smem_bytes(int N) { return bytes(DB ? 2 : 1, N); }
+  static constexpr size_t smem_bytes(int N, bool store = false) {
+    return bytes(DB && !store ? 2 : 1, N);
+  }
+  // with stored planes: the layout with the next tile's region in flight
+  // (G::smem_bytes) where it fits two CTAs per SM, else this one
+  static constexpr bool STORE_PREFETCH = 2 * (G::smem_bytes(BF_MAX_ORDER) + 1024) <= 228 * 1024;
 };
 
-template <int KIND, int R, int NT, int TH>
+// STORE: the stored planes are staged in the single pair (DB off); this
+// layout serves them where the one with the next tile's region in flight
+// does not fit two CTAs per SM.
+template <int KIND, int R, int NT, int TH, bool STORE = false>
 __device__ __forceinline__ void gpa_fwd_fixed_persistent_db(const TileIO &io,
                                                             const bfi::FilterConsts &fc,
                                                             const float2 *tap2, float *smem) {
   using G = FixedGeom<R, NT, TH>;
-  constexpr bool DB = FixedDbGeom<R, NT, TH>::DB;
+  constexpr bool DB = FixedDbGeom<R, NT, TH>::DB && !STORE;
   float *sV0 = smem;
   float *sC0 = sV0 + TH * G::VP;
   float *sV1 = DB ? sC0 + TH * G::VP : nullptr;
@@ -345,7 +353,7 @@ __device__ __forceinline__ void gpa_fwd_fixed_persistent_db(const TileIO &io,
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();  // sRS written; the previous tile's epilogue is done with the pairs
-    gpa_fwd_tile_fixed<KIND, R, NT, TH, false, DB>(io, fc, tap2, ty0, tx0, sF, sV0, sC0, sRS,
+    gpa_fwd_tile_fixed<KIND, R, NT, TH, STORE, DB>(io, fc, tap2, ty0, tx0, sF, sV0, sC0, sRS,
                                                    sV1, sC1);
   }
 }

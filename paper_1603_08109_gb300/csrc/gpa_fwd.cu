@@ -39,10 +39,10 @@ __global__ void __launch_bounds__(256, 2) gpa_fwd_fixed_kernel(const __grid_cons
 
 // The same without stored planes: alternating pairs of phase rows, one
 // barrier per channel.
-template <int KIND, int R>
+template <int KIND, int R, bool STORE = false>
 __global__ void __launch_bounds__(256, 2) gpa_fwd_fixed_db_kernel(const __grid_constant__ FwdArgs args) {
   extern __shared__ __align__(16) float smem[];
-  bfk::gpa_fwd_fixed_persistent_db<KIND, R, 256, 16>(args.io, args.fc, args.tap2, smem);
+  bfk::gpa_fwd_fixed_persistent_db<KIND, R, 256, 16, STORE>(args.io, args.fc, args.tap2, smem);
 }
 
 // Warp-strip box kernel for small N (box_warp.cuh): one warp per strip of
@@ -128,12 +128,16 @@ template <int KIND, int R, bool STORE>
 bf_status launch_fixed_r(const FwdArgs &args, cudaStream_t s) {
   using G = bfk::FixedGeom<R, 256, 16>;
   using D = bfk::FixedDbGeom<R, 256, 16>;
-  const size_t smem = STORE ? G::smem_bytes(args.fc.N) : D::smem_bytes(args.fc.N);
+  // stored planes: the next tile's region in flight where two CTAs fit, else
+  // (W = 15) the single-buffer layout
+  constexpr bool PF = STORE && D::STORE_PREFETCH;
+  const size_t smem = PF ? G::smem_bytes(args.fc.N) : D::smem_bytes(args.fc.N, STORE);
   void (*kern)(const FwdArgs);
-  if constexpr (STORE) kern = gpa_fwd_fixed_kernel<KIND, R, true>;
-  else kern = gpa_fwd_fixed_db_kernel<KIND, R>;
+  if constexpr (PF) kern = gpa_fwd_fixed_kernel<KIND, R, true>;
+  else kern = gpa_fwd_fixed_db_kernel<KIND, R, STORE>;
   const void *fn = reinterpret_cast<const void *>(kern);
-  bf_status st = bfi::ensure_smem(fn, STORE ? G::smem_bytes(BF_MAX_ORDER) : D::smem_bytes(BF_MAX_ORDER));
+  bf_status st = bfi::ensure_smem(fn, PF ? G::smem_bytes(BF_MAX_ORDER)
+                                        : D::smem_bytes(BF_MAX_ORDER, STORE));
   int resident = 0;  // resident CTAs (SMs x CTAs per SM) at this shared-memory size
   if (st == BF_OK) st = bfi::resident_ctas(fn, 256, smem, &resident);
   if (st != BF_OK) return st;
