@@ -317,6 +317,9 @@ bf_status bf_direct_backward(const float *d_in, const float *d_gout, float *d_gi
  * spatial filterings in one fused pass.  For e = f it equals bf_fast_forward.
  * d_qaux (optional) receives Q' as in bf_fast_forward.  The guide follows the
  * image's layout (same height, width, pitch).  Radius limit: W <= 56.
+ * For W in {3, 5, 9, 15} the kernel keeps each thread's region inputs in
+ * tensor memory (128 TMEM columns per CTA of 128 threads, at most four CTAs
+ * per SM; see bf_fast_backward).
  * bf_joint_forward_workspace / bf_joint_forward_ws: the same filter for
  * Gaussian W > 15 and box W > 24 (where the fused box tile stops being the
  * faster form) by the two-pass banded split (see bf_fast_forward_ws): a column pass

@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "bf_internal.h"
+#include "tmem.cuh"
 
 namespace {
 
@@ -222,9 +223,14 @@ __global__ void __launch_bounds__(NT) joint_kernel(const __grid_constant__ Joint
 
 // Compile-time-radius joint tile (W in {3, 5, 9, 15}): 128 threads, 8-row
 // tiles; each column thread keeps its RH = 8 + 2W guide power images b_n in
-// registers, (E, f~) of the region stay in shared memory, Gaussian taps are
-// constant-bank FMA operands; phase V writes the centre rows of b_n for the
-// recombination.  The two filterings of a channel (b_n and b_n f~ share
+// registers, (E, f~) of the thread's region column in its own tensor-memory
+// lane (three TMEM columns per region row, read with tcgen05.ld in every
+// channel instead of from shared memory), Gaussian taps are constant-bank FMA
+// operands; phase V writes the centre rows of b_n for the recombination.  The
+// rows of the two phases alternate between two shared buffers, so one block
+// barrier per channel suffices (phase V of channel n + 1 writes the buffer
+// that phase H of channel n - 1 read, and every thread has passed channel n's
+// barrier after finishing that phase H).  The two filterings of a channel (b_n and b_n f~ share
 // every tap) run as one filtering of the pair with the packed two-lane FP32
 // instructions (each lane rounded exactly as the scalar operation), and the
 // recombination updates (Q', U') as a pair.
@@ -235,9 +241,13 @@ struct JointFixedGeom {
   // 1 (mod 32): the 4 x 8 phase-H lanes read distinct bank pairs of the
   // (b, c) rows (per half-warp) and distinct banks of the b_n centre rows
   static constexpr int VP = NT + 33;
-  static constexpr size_t smem_bytes() {
-    return (size_t)3 * TH * VP * sizeof(float) + (size_t)RH * NT * sizeof(float2);
-  }
+  static constexpr int NG = (RH + 3) / 4;  // groups of four region rows in TMEM
+  static_assert(RH % 4 == 2 && 3 * RH <= bft::kCols, "region rows in the TMEM lane");
+  static constexpr size_t buf_floats = (size_t)3 * TH * VP;  // (b, c) pairs + b_n centre rows
+  static constexpr size_t smem_used = 2 * buf_floats * sizeof(float);
+  // more than a fifth of an SM's shared memory: at most four CTAs (4 x 128
+  // TMEM columns) per SM, so an allocation never waits
+  static constexpr size_t smem_bytes() { return smem_used > 47 * 1024 ? smem_used : 47 * 1024; }
 };
 
 template <int KIND, int R>
@@ -246,49 +256,77 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
   constexpr int NT = G::NT, TH = G::TH, KH = G::KH, RH = G::RH, TW = G::TW, L = G::L, VP = G::VP;
   static_assert(G::VP % 32 == 1 && TW >= KH, "geometry");
   extern __shared__ __align__(16) float smem[];
+  __shared__ uint32_t s_tmem;
   const bfi::FilterConsts &fc = A.fc;
   const int N = fc.N;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-  float2 *sV = reinterpret_cast<float2 *>(smem);  // TH x VP: vertical pass of (b_n, b_n f~)
-  float *sCb = smem + 2 * TH * VP;                // TH x VP: b_n of the centre rows
-  float2 *sEF = reinterpret_cast<float2 *>(sCb + TH * VP);  // (E, f - t_c)
   const int c = threadIdx.x;
+  if (c < 32) bft::alloc(&s_tmem);
+  bft::fence_before_sync();
+  __syncthreads();
+  bft::fence_after_sync();
+  const uint32_t tl = s_tmem + ((uint32_t)(c & ~31) << 16);  // this warp's lane quadrant
   float b[RH];
-  {
+  {  // (E, f - t_c) of the region column to TMEM, b_0 to registers
     const int gx = tx0 - R + c;
     const bool colin = gx >= 0 && gx < A.W;
 #pragma unroll
-    for (int r = 0; r < RH; ++r) {
-      const int gy = ty0 - R + r;
-      float E = 0.f, ft = 0.f, b0 = 0.f;
-      if (colin && gy >= 0 && gy < A.H) {
-        const long long o = (long long)gy * A.pitch + gx;
-        E = (__ldg(A.guide + o) - fc.tc) * fc.inv_sr;
-        ft = __ldg(A.in + o) - fc.tc;
-        b0 = expf(-0.5f * E * E);
+    for (int g = 0; g < G::NG; ++g) {
+      float t[12];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = 4 * g + j, gy = ty0 - R + r;
+        float E = 0.f, ft = 0.f, b0 = 0.f;
+        if (r < RH && colin && gy >= 0 && gy < A.H) {
+          const long long o = (long long)gy * A.pitch + gx;
+          E = (__ldg(A.guide + o) - fc.tc) * fc.inv_sr;
+          ft = __ldg(A.in + o) - fc.tc;
+          b0 = expf(-0.5f * E * E);
+        }
+        if (r < RH) b[r] = b0;
+        t[3 * j] = E;
+        t[3 * j + 1] = ft;
+        t[3 * j + 2] = 0.f;
       }
-      b[r] = b0;
-      sEF[r * NT + c] = make_float2(E, ft);
+      if (4 * g + 4 <= RH) {
+        bft::st12(tl + 12 * g, t);
+      } else {
+        const float t6[6] = {t[0], t[1], t[2], t[3], t[4], t[5]};
+        bft::st6(tl + 12 * g, t6);
+      }
     }
   }
+  bft::wait_st();
   const int hy = c % TH, hx0 = (c / TH) * KH;
   const bool hact = hx0 < TW;
   float2 QU[KH];  // (Q', U')
 #pragma unroll
   for (int k = 0; k < KH; ++k) QU[k] = make_float2(0.f, 0.f);
-  const float2 *rv = sV + hy * VP + hx0;
-  const float *cb = sCb + hy * VP + R + hx0;
 
   for (int n = 0; n < N; ++n) {
     const float rs = n > 0 ? __frsqrt_rn((float)n) : 0.f;
-    __syncthreads();
+    float2 *sV = reinterpret_cast<float2 *>(smem + (n & 1) * G::buf_floats);  // (b_n, b_n f~)
+    float *sCb = smem + (n & 1) * G::buf_floats + 2 * TH * VP;               // b_n centre rows
+    const float2 *rv = sV + hy * VP + hx0;
+    const float *cb = sCb + hy * VP + R + hx0;
     float2 acc[TH];  // (b_n, b_n f~) of the TH output rows
 #pragma unroll
     for (int y = 0; y < TH; ++y) acc[y] = make_float2(0.f, 0.f);
     float cbox[KIND == BF_SPATIAL_BOX ? RH : 1];
+    float t[12];  // (E, f~, -) of the current group of four rows
 #pragma unroll
     for (int r = 0; r < RH; ++r) {
-      const float2 ef = sEF[r * NT + c];
+      if (r % 4 == 0) {  // (E, f~) of rows r .. r + 3 from TMEM
+        if (r + 4 <= RH) {
+          bft::ld12(tl + 3 * r, t);
+        } else {
+          float t6[6];
+          bft::ld6(tl + 3 * r, t6);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) t[i] = t6[i];
+        }
+      }
+      const float2 ef = make_float2(t[3 * (r % 4)], t[3 * (r % 4) + 1]);
       if (n > 0) b[r] *= ef.x * rs;
       const float cn = b[r] * ef.y;
       if (r >= R && r < R + TH) sCb[(r - R) * VP + c] = b[r];
@@ -366,6 +404,13 @@ __global__ void __launch_bounds__(128) joint_fixed_kernel(const __grid_constant_
         QU[k] = __ffma2_rn(make_float2(bk, bk), BC[k], QU[k]);
       }
     }
+  }
+  // every warp's TMEM reads are complete: free the columns
+  bft::fence_before_sync();
+  __syncthreads();
+  if (c < 32) {
+    bft::fence_after_sync();
+    bft::dealloc(s_tmem);
   }
   if (hact) {
     const int gy = ty0 + hy;
