@@ -28,6 +28,9 @@ def _pair(H, W, seed):
     (bf.GAUSS, 3, 1.0, 20.0, 70, (1, 9)),
     (bf.GAUSS, 15, 5.0, 25.0, 54, (33, 250)),
     (bf.BOX, 15, 0.0, 40.0, 30, (9, 131)),
+    (bf.GAUSS, 3, 1.0, 35.0, 30, (45, 290)),
+    (bf.GAUSS, 5, 5 / 3.0, 40.0, 26, (26, 240)),
+    (bf.BOX, 9, 0.0, 40.0, 30, (30, 280)),
 ], ids=lambda c: "k%d_r%d_sr%g_N%d" % (c[0], c[1], c[3], c[4]))
 def test_joint_forward_matches_definition(case):
     kind, r, ss, sr, N, (H, W) = case
