@@ -21,7 +21,7 @@
 namespace bfk {
 
 constexpr int kBandNT = 256;        // pass H threads per CTA
-constexpr int kVNT = 128;           // pass V threads per CTA (two columns each)
+constexpr int kVNT = 256;           // pass V threads per CTA (two columns, 8 output rows each)
 constexpr int kVC = 64, kVB = 64;   // pass V tile: columns, output rows
 constexpr int kHT = 32, kHW = 128;  // pass H tile: rows, output columns
 
@@ -87,11 +87,14 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
     sH[i] = h;
     sA[i] = a0;
   }
-  // each thread: two adjacent columns (a packed pair) x 16 output rows
-  constexpr int CS = kVC / 2;  // row stride in column pairs
-  const int cp = threadIdx.x % CS, yb = threadIdx.x / CS;  // 4 blocks of 16 output rows
+  // each thread: two adjacent columns (a packed pair) x RPT output rows; a
+  // warp holds one block of RPT rows (the 32 column pairs of the tile)
+  constexpr int CS = kVC / 2;                // row stride in column pairs
+  constexpr int RPT = kVB * CS / kVNT;       // output rows per thread
+  static_assert(CS == 32 && RPT == 8, "a warp per block of 8 output rows");
+  const int cp = threadIdx.x % CS, yb = threadIdx.x / CS;  // kVB / RPT blocks of RPT rows
   const int gx = tx + 2 * cp;
-  const float2 *col = reinterpret_cast<const float2 *>(sA + 16 * yb * kVC) + cp;
+  const float2 *col = reinterpret_cast<const float2 *>(sA + RPT * yb * kVC) + cp;
   for (int n = 0; n <= N; ++n) {
     __syncthreads();  // region loaded / previous channel's filtering done
     if (n > 0) {
@@ -109,35 +112,31 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
       }
       __syncthreads();
     }
-    // a warp whose 16 output rows all lie past the band has nothing to filter
+    // a warp whose output rows all lie past the band has nothing to filter
     // (warp-uniform; it still takes part in the advance and the barriers)
-    if (tyb + 16 * yb >= A.rows) continue;
-    float2 acc[16];
+    if (tyb + RPT * yb >= A.rows) continue;
+    float2 acc[RPT];
     if (KIND == BF_SPATIAL_GAUSS) {
-      float2 win[16];
+      // window of the RPT rows tap t reads, rotated one row per tap; taps
+      // in blocks of RPT (those past 2W are zeros: the table is padded to a
+      // multiple of 16, and the region's rows to the padded count)
+      float2 win[RPT];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < RPT; ++i) {
         acc[i] = make_float2(0.f, 0.f);
         win[i] = col[i * CS];
       }
-      // blocks of 16 taps; when at most 8 taps remain for the last block it
-      // takes 8 (the taps past 2W are zeros), which halves the
-      // zero-tap work of padding 2W + 1 to a multiple of 16
-      const int L = 2 * R + 1, kl = (L - 1) & ~15;  // first tap of the last block
-      auto block = [&](int k, auto taps_tag) {
-        constexpr int NTB = decltype(taps_tag)::value;
+      const int L = 2 * R + 1;
+      for (int k = 0; k < L; k += RPT) {
 #pragma unroll
-        for (int j = 0; j < NTB; ++j) {
+        for (int j = 0; j < RPT; ++j) {
           const float w = taps[k + j];
           const float2 w2 = make_float2(w, w);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[i] = __ffma2_rn(w2, win[(j + i) & 15], acc[i]);
-          win[j] = col[(k + j + 16) * CS];
+          for (int i = 0; i < RPT; ++i) acc[i] = __ffma2_rn(w2, win[(j + i) % RPT], acc[i]);
+          win[j] = col[(k + j + RPT) * CS];
         }
-      };
-      for (int k = 0; k < kl; k += 16) block(k, std::integral_constant<int, 16>{});
-      if (L - kl > 8) block(kl, std::integral_constant<int, 16>{});
-      else block(kl, std::integral_constant<int, 8>{});
+      }
     } else {
       float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
       int r = 0;
@@ -151,7 +150,7 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
       float2 s = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
       acc[0] = s;
 #pragma unroll
-      for (int i = 1; i < 16; ++i) {
+      for (int i = 1; i < RPT; ++i) {
         const float2 in = col[(i + 2 * R) * CS], out = col[(i - 1) * CS];
         s = __fadd2_rn(s, __fadd2_rn(in, make_float2(-out.x, -out.y)));
         acc[i] = s;
@@ -161,8 +160,8 @@ __device__ __forceinline__ void band_vpass_tile(const BandArgs &A, int bx, int b
     if (gx < A.Wp) {
       float *dst = A.ws + (long long)n * A.plane + gx;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int orow = tyb + 16 * yb + i;
+      for (int i = 0; i < RPT; ++i) {
+        const int orow = tyb + RPT * yb + i;
         if (orow < A.rows) *reinterpret_cast<float2 *>(dst + (long long)orow * A.Wp) = acc[i];
       }
     }
