@@ -390,6 +390,8 @@ struct BwdTmemGeom {
   // TMEM columns, reside on an SM, so an allocation never waits
   static constexpr size_t kMinSmem = 47 * 1024;
   static constexpr size_t smem_bytes = smem_used > kMinSmem ? smem_used : kMinSmem;
+  // a fifth CTA (with its 1 KB reserve) does not fit an SM's 228 KB
+  static_assert(5 * (smem_bytes + 1024) > 228 * 1024, "at most four CTAs per SM");
 };
 
 template <int KIND, int R, int NT, int TH>
@@ -748,6 +750,7 @@ struct BwdTmemStoredGeom {
   static constexpr size_t smem_used = (2 * buf_floats + (size_t)3 * TH * EP) * sizeof(float);
   static constexpr size_t kMinSmem = 47 * 1024;  // at most four CTAs per SM
   static constexpr size_t smem_bytes = smem_used > kMinSmem ? smem_used : kMinSmem;
+  static_assert(5 * (smem_bytes + 1024) > 228 * 1024, "at most four CTAs per SM");
 };
 
 template <int KIND, int R, int NT, int TH>

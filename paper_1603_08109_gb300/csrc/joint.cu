@@ -248,6 +248,8 @@ struct JointFixedGeom {
   // more than a fifth of an SM's shared memory: at most four CTAs (4 x 128
   // TMEM columns) per SM, so an allocation never waits
   static constexpr size_t smem_bytes() { return smem_used > 47 * 1024 ? smem_used : 47 * 1024; }
+  // a fifth CTA (with its 1 KB reserve) does not fit an SM's 228 KB
+  static_assert(5 * (smem_bytes() + 1024) > 228 * 1024, "at most four CTAs per SM");
 };
 
 template <int KIND, int R>
